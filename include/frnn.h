@@ -1,0 +1,191 @@
+/*
+ * frnn.h — C ABI of the GB300 (sm_103a) exact fixed-radius nearest-neighbour
+ * library.
+ *
+ * The operation is the paper's Eq. 1 (Sec. 1): for query points x_i and
+ * reference points x_j in R^D,
+ *
+ *     N_r(i) = { j : ||x_i - x_j||_2 <= r },
+ *
+ * keeping at most K neighbours in distance order.  Membership and distances
+ * follow one fixed float32 contract, identical to a brute-force scan:
+ *
+ *     s = +0;  for k = 0..D-1:  d = fl(q_k - p_k);  s = fl(s + fl(d*d));
+ *     j in N_r(i)  <=>  s <= fl(r*r)
+ *
+ * (round to nearest, dimensions in index order, no fused multiply-add; the
+ * paper's Sec. 4.2 reports that reordered accumulation changed membership near
+ * the radius and was rejected as inexact).  Each result row holds
+ * min(degree, K) neighbours sorted by (s, original index) ascending; the rest
+ * of the row is padded with index -1 and distance +inf.  Returned distances
+ * are the squared distances s, bit for bit.
+ *
+ * Conventions for every call:
+ *   - Pointers marked "device" are CUDA device (or managed) pointers; the
+ *     caller owns them and keeps them alive until the work is complete.
+ *   - Work is enqueued asynchronously on the context's stream.  Host-side
+ *     argument errors are returned at once; device-side errors (non-finite
+ *     coordinates, an exceeded internal capacity, a bounded wait that ran out)
+ *     are recorded in a device status word and returned by frnn_sync().
+ *   - The library owns its contexts, workspaces and grids.
+ *   - A context is not thread-safe: use one per host thread.
+ *   - Limits: 1 <= D <= 16, 1 <= K <= 1024, 0 <= N, M < 2^31 - 1 (per call,
+ *     summed over events for batched calls); r finite with
+ *     2^-60 <= r <= 2^60.
+ */
+#ifndef FRNN_H
+#define FRNN_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum frnn_status {
+    FRNN_OK = 0,
+    FRNN_ERR_INVALID_ARG = -1,   /* bad pointer, size, D, K, r or flag */
+    FRNN_ERR_UNSUPPORTED = -2,   /* valid request this build does not serve */
+    FRNN_ERR_OUT_OF_MEMORY = -3, /* a device allocation failed */
+    FRNN_ERR_BUDGET = -4,        /* the request does not fit the memory budget */
+    FRNN_ERR_NONFINITE = -5,     /* an input coordinate is NaN or +-inf */
+    FRNN_ERR_CUDA = -6,          /* a CUDA runtime call failed */
+    FRNN_ERR_TIMEOUT = -7,       /* a bounded device-side wait ran out */
+    FRNN_ERR_CAPACITY = -8       /* an internal device-side capacity overflowed */
+} frnn_status;
+
+/* frnn_query / frnn_query_batched flags */
+#define FRNN_SELF_QUERY 0x1u  /* queries are the grid's own points, same order;
+                                 reference j == i is excluded by index */
+#define FRNN_PATH_AUTO 0x0u   /* library (autotuner) chooses the path */
+#define FRNN_PATH_GRID 0x2u   /* uniform-grid scan with the exact screen */
+#define FRNN_PATH_TC 0x4u     /* tensor-core BF16 pre-filter + exact recheck
+                                 (D >= 8 only) */
+
+typedef struct frnn_ctx frnn_ctx;
+typedef struct frnn_grid frnn_grid;
+
+/* Library version as "major.minor.patch"; static storage. */
+const char* frnn_version(void);
+
+/*
+ * Create a context on the current CUDA device.
+ *   cuda_stream       cudaStream_t to enqueue on (NULL = the legacy default
+ *                     stream).  Not owned.
+ *   mem_budget_bytes  cap on device memory the context may hold for grids and
+ *                     workspace (0 = no cap).  Requests beyond it fail with
+ *                     FRNN_ERR_BUDGET.
+ * On success *out receives the context.  Errors: INVALID_ARG (out NULL),
+ * CUDA (no usable device), OUT_OF_MEMORY.
+ */
+frnn_status frnn_create(frnn_ctx** out, void* cuda_stream, size_t mem_budget_bytes);
+
+/* Synchronise the context's stream and free everything it owns (grids built
+ * through it stay valid until frnn_grid_destroy).  NULL is accepted. */
+frnn_status frnn_destroy(frnn_ctx* ctx);
+
+/*
+ * Build the uniform grid over reference points (Sec. 2: the uniform-grid /
+ * cell-list method of the original FRNN, whose spacing divides r; Table 1
+ * "roundoff-safe grid").
+ *   refs  device, [N, D] row-major float32.  Read during the call's device
+ *         work only; the grid keeps its own cell-sorted copy.
+ *   N     number of points (>= 0)
+ *   D     dimensions, 1..16
+ *   r     the largest radius this grid will be queried with
+ *   grid  in/out.  If *grid is NULL a new grid is allocated.  If *grid is a
+ *         grid from this context with D equal and capacity >= N, it is rebuilt
+ *         in place without allocating (the previous contents are replaced).
+ * The grid bins at most 3 coordinates with cells of edge (r/m)(1+2^-10),
+ * m = the cell-multiple option, enlarged when needed so that the cell count
+ * stays bounded; the choice never changes results (the cell assignment is
+ * proven conservative).  A non-finite coordinate makes frnn_sync return
+ * FRNN_ERR_NONFINITE and later queries on the grid return no neighbours.
+ */
+frnn_status frnn_build_grid(frnn_ctx* ctx, const float* refs, int64_t N, int D, float r,
+                            frnn_grid** grid);
+
+/* Free a grid (after its pending work completes).  NULL is accepted. */
+frnn_status frnn_grid_destroy(frnn_grid* grid);
+
+/*
+ * Fixed-radius query (Eq. 1) of M points against a grid.
+ *   queries  device, [M, D] row-major float32.  With FRNN_SELF_QUERY it must
+ *            be the pointer the grid was built from, and M its N.
+ *   r        radius, 0 < r <= the grid's r
+ *   K        neighbours kept per query, 1..1024
+ *   flags    FRNN_SELF_QUERY | one FRNN_PATH_*
+ *   counts   device, [M] int32 out: min(degree, K)
+ *   idx      device, [M, K] int32 out: original reference indices
+ *   dist2    device, [M, K] float32 out: squared distances (the contract's s)
+ * Rows follow the original query order.  Errors: INVALID_ARG, UNSUPPORTED
+ * (FRNN_PATH_TC with D < 8), BUDGET, OUT_OF_MEMORY, CUDA.
+ */
+frnn_status frnn_query(frnn_ctx* ctx, const frnn_grid* grid, const float* queries, int64_t M,
+                       float r, int K, unsigned flags, int32_t* counts, int32_t* idx,
+                       float* dist2);
+
+/* One independent event of a batched call: a self-query of pts. */
+typedef struct frnn_event {
+    const float* pts; /* device, [n, D] row-major float32 */
+    int64_t n;        /* points in this event (>= 0) */
+    int32_t* counts;  /* device, [n] out */
+    int32_t* idx;     /* device, [n, K] out */
+    float* dist2;     /* device, [n, K] out */
+} frnn_event;
+
+/*
+ * Self-query of many independent events of uneven size (each event is its own
+ * point set; no pair crosses events).  All events' grids are built by one set
+ * of segmented launches and all queries run in one persistent launch, the
+ * whole sequence captured once in a CUDA graph and replayed while the event
+ * list (pointers and sizes) stays the same.  Results per event are bit-identical
+ * to frnn_build_grid + frnn_query(FRNN_SELF_QUERY) on that event alone.
+ *   ev        host array of n_events descriptors (copied; device buffers are
+ *             the caller's)
+ *   flags     FRNN_SELF_QUERY is implied; FRNN_PATH_* as for frnn_query
+ * Errors: INVALID_ARG, BUDGET, OUT_OF_MEMORY, CUDA.
+ */
+frnn_status frnn_query_batched(frnn_ctx* ctx, const frnn_event* ev, int n_events, int D,
+                               float r, int K, unsigned flags);
+
+/*
+ * The whole path with HOST buffers: copies refs to the device, builds the
+ * grid, self-queries it and copies the results back, synchronising before it
+ * returns (the host-side interface of Sec. 4.2's NumPy binding comparison).
+ * Host buffers may be pageable; page-locked buffers copy faster.
+ *   refs_host [N, D] float32 in; counts_host [N], idx_host [N, K],
+ *   dist2_host [N, K] out.  Device memory is taken from the context's
+ *   workspace and reused across calls.
+ */
+frnn_status frnn_self_query_host(frnn_ctx* ctx, const float* refs_host, int64_t N, int D,
+                                 float r, int K, unsigned flags, int32_t* counts_host,
+                                 int32_t* idx_host, float* dist2_host);
+
+/* Wait for the context's stream and report (then clear) the device status
+ * word: FRNN_OK or the first device-side error since the last sync. */
+frnn_status frnn_sync(frnn_ctx* ctx);
+
+/* Text of the last error on this context (static storage of the context;
+ * "" when none).  ctx NULL gives the last frnn_create failure. */
+const char* frnn_last_error(const frnn_ctx* ctx);
+
+/* Tunable options (none changes results, only speed). */
+typedef enum frnn_option {
+    FRNN_OPT_CELL_MULT = 1,   /* m in {1, 2}: cell edge ~ r/m, search +-m cells */
+    FRNN_OPT_GRID_AXES = 2,   /* 0: the last min(D,3) axes; 1: the 3 widest axes */
+    FRNN_OPT_EXIT_DIMS = 3,   /* dims summed before the warp-uniform early exit
+                                 (0 = library default) */
+    FRNN_OPT_USE_GRAPH = 4,   /* 1 (default): batched calls replay a CUDA graph */
+    FRNN_OPT_AUTOTUNE = 5     /* 1 (default): FRNN_PATH_AUTO consults the tuner */
+} frnn_option;
+
+frnn_status frnn_set_option(frnn_ctx* ctx, frnn_option opt, int64_t value);
+frnn_status frnn_get_option(const frnn_ctx* ctx, frnn_option opt, int64_t* value);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FRNN_H */

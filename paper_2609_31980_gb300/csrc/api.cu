@@ -1,0 +1,514 @@
+// api.cu — the C ABI (include/frnn.h): contexts, grids, argument validation,
+// the single-event, cross-set, batched (CUDA-graph) and host-buffer paths.
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "frnn_host.h"
+
+using namespace frnn;
+
+struct frnn_grid {
+    frnn_ctx* ctx = nullptr;
+    GridBufs g;
+    const float* refs = nullptr;
+    int64_t N = 0;
+    int D = 0;
+    float r = 0.f;
+};
+
+struct frnn_ctx {
+    int device = 0;
+    int num_sms = 0;
+    cudaStream_t stream = nullptr;
+    size_t budget = 0;        // 0 = no cap
+    size_t held = 0;          // bytes of grids + workspaces currently held
+    int32_t* d_status = nullptr;
+    int32_t* h_status = nullptr;
+    std::string err;
+    // options
+    int cell_mult = 1;
+    int axes_mode = 0;
+    int exit_dims = 0;
+    int use_graph = 1;
+    int autotune = 1;
+    // workspaces
+    GridBufs qset;            // cross-set query binning
+    GridBufs batch;           // batched multi-event grid
+    frnn_grid* host_grid = nullptr;   // grid of the host-buffer path
+    void* hp_buf = nullptr;   // device buffers of the host-buffer path
+    size_t hp_bytes = 0;
+    // batched graph cache
+    cudaGraphExec_t graph = nullptr;
+    std::vector<frnn_event> g_ev;
+    int g_D = 0, g_K = 0;
+    float g_r = 0.f;
+    unsigned g_flags = 0;
+    int g_opts[4] = {0, 0, 0, 0};
+};
+
+static thread_local std::string g_create_err;
+
+static frnn_status fail(frnn_ctx* c, frnn_status s, const std::string& msg) {
+    if (c) c->err = msg;
+    return s;
+}
+
+static frnn_status cuda_fail(frnn_ctx* c, cudaError_t e, const char* what) {
+    cudaGetLastError();
+    return fail(c, FRNN_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+static bool radius_ok(float r) {
+    return std::isfinite(r) && r >= 0x1p-60f && r <= 0x1p60f;
+}
+
+static bool budget_allows(frnn_ctx* c, size_t old_bytes, size_t new_bytes) {
+    if (c->budget == 0) return true;
+    return c->held - old_bytes + new_bytes <= c->budget;
+}
+
+// Predicted device bytes of a GridBufs layout (mirrors grid_alloc's layout).
+static size_t predict_grid_bytes(int E, const int64_t* n, int D, const int64_t* caps) {
+    const int DP = padded_dim(D);
+    int64_t nt = 0, L = 0, tc = 0;
+    for (int e = 0; e < E; ++e) {
+        const int64_t cap = caps ? caps[e] : cell_cap_for(n[e]);
+        nt += n[e];
+        L += cap + 1;
+        tc += n[e] / kTaskQueries + cap + 2;
+    }
+    nt = std::max<int64_t>(nt, 1);
+    size_t b = 0;
+    b += sizeof(EventHdr) * E + 16 * (E + 1) + sizeof(int32_t) * kBBoxStride * E;
+    b += (size_t)nt * (sizeof(float) * DP + 4 * sizeof(int32_t) + sizeof(Overflow));
+    b += (size_t)L * 2 * sizeof(int32_t) + (size_t)tc * sizeof(Task);
+    b += 64 * 1024 + 16 * 256;
+    return b;
+}
+
+static frnn_status alloc_accounted(frnn_ctx* c, GridBufs& g, int E, const int64_t* n, int D,
+                                   const int64_t* caps) {
+    const size_t old_bytes = g.bytes;
+    const size_t need = predict_grid_bytes(E, n, D, caps);
+    const bool reuse = g.base && need <= g.bytes;
+    if (!reuse && !budget_allows(c, old_bytes, need))
+        return fail(c, FRNN_ERR_BUDGET, "request exceeds the context's memory budget");
+    std::string err;
+    frnn_status s = grid_alloc(g, E, n, D, err, caps);
+    c->held = c->held - old_bytes + g.bytes;
+    if (s != FRNN_OK) return fail(c, s, err);
+    return FRNN_OK;
+}
+
+extern "C" {
+
+const char* frnn_version(void) { return "0.1.0"; }
+
+frnn_status frnn_create(frnn_ctx** out, void* cuda_stream, size_t mem_budget_bytes) {
+    if (!out) {
+        g_create_err = "out is NULL";
+        return FRNN_ERR_INVALID_ARG;
+    }
+    *out = nullptr;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        g_create_err = std::string("no CUDA device: ") + cudaGetErrorString(e);
+        return FRNN_ERR_CUDA;
+    }
+    cudaDeviceProp prop;
+    e = cudaGetDeviceProperties(&prop, dev);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        g_create_err = std::string("cudaGetDeviceProperties: ") + cudaGetErrorString(e);
+        return FRNN_ERR_CUDA;
+    }
+    if (prop.major < 10) {
+        g_create_err = "this library is built for sm_103a (GB300); device is sm_" +
+                       std::to_string(prop.major) + std::to_string(prop.minor);
+        return FRNN_ERR_UNSUPPORTED;
+    }
+    frnn_ctx* c = new frnn_ctx();
+    c->device = dev;
+    c->num_sms = prop.multiProcessorCount;
+    c->stream = static_cast<cudaStream_t>(cuda_stream);
+    c->budget = mem_budget_bytes;
+    if (cudaMalloc(&c->d_status, 64) != cudaSuccess ||
+        cudaMallocHost(&c->h_status, 64) != cudaSuccess) {
+        cudaGetLastError();
+        g_create_err = "allocation of the status word failed";
+        if (c->d_status) cudaFree(c->d_status);
+        delete c;
+        return FRNN_ERR_OUT_OF_MEMORY;
+    }
+    cudaMemsetAsync(c->d_status, 0, 64, c->stream);
+    e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        g_create_err = std::string("stream unusable: ") + cudaGetErrorString(e);
+        cudaFree(c->d_status);
+        cudaFreeHost(c->h_status);
+        delete c;
+        return FRNN_ERR_CUDA;
+    }
+    *out = c;
+    return FRNN_OK;
+}
+
+frnn_status frnn_grid_destroy(frnn_grid* grid) {
+    if (!grid) return FRNN_OK;
+    if (grid->ctx) {
+        cudaStreamSynchronize(grid->ctx->stream);
+        grid->ctx->held -= std::min(grid->ctx->held, grid->g.bytes);
+    }
+    grid_free(grid->g);
+    delete grid;
+    return FRNN_OK;
+}
+
+frnn_status frnn_destroy(frnn_ctx* ctx) {
+    if (!ctx) return FRNN_OK;
+    cudaStreamSynchronize(ctx->stream);
+    if (ctx->graph) cudaGraphExecDestroy(ctx->graph);
+    if (ctx->host_grid) {
+        frnn_grid* g = ctx->host_grid;
+        ctx->host_grid = nullptr;
+        g->ctx = nullptr;
+        grid_free(g->g);
+        delete g;
+    }
+    grid_free(ctx->qset);
+    grid_free(ctx->batch);
+    if (ctx->hp_buf) cudaFree(ctx->hp_buf);
+    cudaFree(ctx->d_status);
+    cudaFreeHost(ctx->h_status);
+    delete ctx;
+    return FRNN_OK;
+}
+
+frnn_status frnn_build_grid(frnn_ctx* ctx, const float* refs, int64_t N, int D, float r,
+                            frnn_grid** grid) {
+    if (!ctx) return FRNN_ERR_INVALID_ARG;
+    if (!grid) return fail(ctx, FRNN_ERR_INVALID_ARG, "grid is NULL");
+    if (D < 1 || D > kMaxD) return fail(ctx, FRNN_ERR_INVALID_ARG, "D must be in 1..16");
+    if (N < 0 || N >= INT32_MAX) return fail(ctx, FRNN_ERR_INVALID_ARG, "N out of range");
+    if (N > 0 && !refs) return fail(ctx, FRNN_ERR_INVALID_ARG, "refs is NULL");
+    if (!radius_ok(r)) return fail(ctx, FRNN_ERR_INVALID_ARG, "r must be finite, 2^-60..2^60");
+    frnn_grid* g = *grid;
+    if (g && (g->ctx != ctx || g->D != D)) g = nullptr;   // not reusable: make a new one
+    const bool fresh = (g == nullptr);
+    if (fresh) {
+        g = new frnn_grid();
+        g->ctx = ctx;
+        g->D = D;
+    }
+    frnn_status s = alloc_accounted(ctx, g->g, 1, &N, D, nullptr);
+    if (s != FRNN_OK) {
+        if (fresh) {
+            ctx->held -= std::min(ctx->held, g->g.bytes);
+            grid_free(g->g);
+            delete g;
+        }
+        return s;
+    }
+    g->refs = refs;
+    g->N = N;
+    g->r = r;
+    BuildOpts o;
+    o.r = r;
+    o.m = ctx->cell_mult;
+    o.axes_mode = ctx->axes_mode;
+    std::string err;
+    const float* ev_refs[1] = {refs};
+    s = enqueue_build(g->g, ev_refs, o, nullptr, ctx->d_status, ctx->stream, false, err);
+    if (s != FRNN_OK) {
+        if (fresh) frnn_grid_destroy(g);
+        return fail(ctx, s, err);
+    }
+    *grid = g;
+    return FRNN_OK;
+}
+
+static frnn_status check_query_args(frnn_ctx* ctx, int64_t M, float r, int K, unsigned flags,
+                                    const int32_t* counts, const int32_t* idx,
+                                    const float* dist2) {
+    if (M < 0 || M >= INT32_MAX) return fail(ctx, FRNN_ERR_INVALID_ARG, "M out of range");
+    if (K < 1 || K > kMaxK) return fail(ctx, FRNN_ERR_INVALID_ARG, "K must be in 1..1024");
+    if (!radius_ok(r)) return fail(ctx, FRNN_ERR_INVALID_ARG, "r must be finite, 2^-60..2^60");
+    if (flags & ~(FRNN_SELF_QUERY | FRNN_PATH_GRID | FRNN_PATH_TC))
+        return fail(ctx, FRNN_ERR_INVALID_ARG, "unknown flag bits");
+    if ((flags & FRNN_PATH_GRID) && (flags & FRNN_PATH_TC))
+        return fail(ctx, FRNN_ERR_INVALID_ARG, "choose one path");
+    if (M > 0 && (!counts || !idx || !dist2))
+        return fail(ctx, FRNN_ERR_INVALID_ARG, "output pointer is NULL");
+    return FRNN_OK;
+}
+
+frnn_status frnn_query(frnn_ctx* ctx, const frnn_grid* grid, const float* queries, int64_t M,
+                       float r, int K, unsigned flags, int32_t* counts, int32_t* idx,
+                       float* dist2) {
+    if (!ctx) return FRNN_ERR_INVALID_ARG;
+    if (!grid || grid->ctx != ctx) return fail(ctx, FRNN_ERR_INVALID_ARG, "grid is not of ctx");
+    frnn_status s = check_query_args(ctx, M, r, K, flags, counts, idx, dist2);
+    if (s != FRNN_OK) return s;
+    if (r > grid->r) return fail(ctx, FRNN_ERR_INVALID_ARG, "r exceeds the grid's radius");
+    if (M > 0 && !queries) return fail(ctx, FRNN_ERR_INVALID_ARG, "queries is NULL");
+    const bool self = (flags & FRNN_SELF_QUERY) != 0;
+    if (self && (queries != grid->refs || M != grid->N))
+        return fail(ctx, FRNN_ERR_INVALID_ARG,
+                    "FRNN_SELF_QUERY needs the grid's own points (same pointer and count)");
+    if ((flags & FRNN_PATH_TC) && grid->D < 8)
+        return fail(ctx, FRNN_ERR_UNSUPPORTED, "the tensor-core path needs D >= 8");
+    if (M == 0) return FRNN_OK;
+    QueryLaunch q{};
+    q.rset = &grid->g;
+    q.r2 = r * r;
+    q.K = K;
+    q.self = self ? 1 : 0;
+    q.exit_dims = ctx->exit_dims;
+    q.counts = counts;
+    q.idx = idx;
+    q.dist2 = dist2;
+    q.d_status = ctx->d_status;
+    q.num_sms = ctx->num_sms;
+    std::string err;
+    if (self) {
+        q.qset = &grid->g;
+    } else {
+        const int64_t cap = grid->g.h_hdr[0].cell_cap;
+        s = alloc_accounted(ctx, ctx->qset, 1, &M, grid->D, &cap);
+        if (s != FRNN_OK) return s;
+        BuildOpts o;
+        const float* ev_q[1] = {queries};
+        s = enqueue_build(ctx->qset, ev_q, o, &grid->g, ctx->d_status, ctx->stream, false, err);
+        if (s != FRNN_OK) return fail(ctx, s, err);
+        q.qset = &ctx->qset;
+    }
+    s = enqueue_grid_query(q, ctx->stream, err);
+    if (s != FRNN_OK) return fail(ctx, s, err);
+    return FRNN_OK;
+}
+
+static bool same_events(const frnn_ctx* c, const frnn_event* ev, int n) {
+    if ((int)c->g_ev.size() != n) return false;
+    for (int e = 0; e < n; ++e) {
+        const frnn_event& a = c->g_ev[e];
+        const frnn_event& b = ev[e];
+        if (a.pts != b.pts || a.n != b.n || a.counts != b.counts || a.idx != b.idx ||
+            a.dist2 != b.dist2)
+            return false;
+    }
+    return true;
+}
+
+static frnn_status enqueue_batched(frnn_ctx* ctx, const frnn_event* ev, int n_events, int D,
+                                   float r, int K, bool capturing) {
+    std::vector<const float*> refs(n_events);
+    for (int e = 0; e < n_events; ++e) {
+        refs[e] = ev[e].pts;
+        ctx->batch.h_hdr[e].counts = ev[e].counts;
+        ctx->batch.h_hdr[e].idx = ev[e].idx;
+        ctx->batch.h_hdr[e].dist2 = ev[e].dist2;
+    }
+    BuildOpts o;
+    o.r = r;
+    o.m = ctx->cell_mult;
+    o.axes_mode = ctx->axes_mode;
+    std::string err;
+    frnn_status s = enqueue_build(ctx->batch, refs.data(), o, nullptr, ctx->d_status,
+                                  ctx->stream, capturing, err);
+    if (s != FRNN_OK) return fail(ctx, s, err);
+    QueryLaunch q{};
+    q.qset = &ctx->batch;
+    q.rset = &ctx->batch;
+    q.r2 = r * r;
+    q.K = K;
+    q.self = 1;
+    q.exit_dims = ctx->exit_dims;
+    q.d_status = ctx->d_status;
+    q.num_sms = ctx->num_sms;
+    s = enqueue_grid_query(q, ctx->stream, err);
+    if (s != FRNN_OK) return fail(ctx, s, err);
+    return FRNN_OK;
+}
+
+frnn_status frnn_query_batched(frnn_ctx* ctx, const frnn_event* ev, int n_events, int D,
+                               float r, int K, unsigned flags) {
+    if (!ctx) return FRNN_ERR_INVALID_ARG;
+    if (n_events < 0 || (n_events > 0 && !ev))
+        return fail(ctx, FRNN_ERR_INVALID_ARG, "bad event list");
+    if (D < 1 || D > kMaxD) return fail(ctx, FRNN_ERR_INVALID_ARG, "D must be in 1..16");
+    if (K < 1 || K > kMaxK) return fail(ctx, FRNN_ERR_INVALID_ARG, "K must be in 1..1024");
+    if (!radius_ok(r)) return fail(ctx, FRNN_ERR_INVALID_ARG, "r must be finite, 2^-60..2^60");
+    if (flags & ~(FRNN_SELF_QUERY | FRNN_PATH_GRID | FRNN_PATH_TC))
+        return fail(ctx, FRNN_ERR_INVALID_ARG, "unknown flag bits");
+    if ((flags & FRNN_PATH_TC) && D < 8)
+        return fail(ctx, FRNN_ERR_UNSUPPORTED, "the tensor-core path needs D >= 8");
+    if (n_events == 0) return FRNN_OK;
+    std::vector<int64_t> n(n_events);
+    for (int e = 0; e < n_events; ++e) {
+        const frnn_event& x = ev[e];
+        if (x.n < 0 || x.n >= INT32_MAX) return fail(ctx, FRNN_ERR_INVALID_ARG, "event n");
+        if (x.n > 0 && (!x.pts || !x.counts || !x.idx || !x.dist2))
+            return fail(ctx, FRNN_ERR_INVALID_ARG, "event pointer is NULL");
+        n[e] = x.n;
+    }
+    const int opts[4] = {ctx->cell_mult, ctx->axes_mode, ctx->exit_dims, 0};
+    const bool hit = ctx->use_graph && ctx->graph && same_events(ctx, ev, n_events) &&
+                     ctx->g_D == D && ctx->g_K == K && ctx->g_r == r && ctx->g_flags == flags &&
+                     std::memcmp(opts, ctx->g_opts, sizeof(opts)) == 0;
+    if (hit) {
+        cudaError_t e = cudaGraphLaunch(ctx->graph, ctx->stream);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaGraphLaunch");
+        return FRNN_OK;
+    }
+    if (ctx->graph) {
+        cudaGraphExecDestroy(ctx->graph);
+        ctx->graph = nullptr;
+        ctx->g_ev.clear();
+    }
+    frnn_status s = alloc_accounted(ctx, ctx->batch, n_events, n.data(), D, nullptr);
+    if (s != FRNN_OK) return s;
+    if (!ctx->use_graph) return enqueue_batched(ctx, ev, n_events, D, r, K, false);
+    // make sure the pinned table mirror is free before capturing its upload
+    if (ctx->batch.h_pinned_free) cudaEventSynchronize(ctx->batch.h_pinned_free);
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaStreamBeginCapture");
+    s = enqueue_batched(ctx, ev, n_events, D, r, K, true);
+    e = cudaStreamEndCapture(ctx->stream, &graph);
+    if (s != FRNN_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return s;
+    }
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaStreamEndCapture");
+    cudaGraphExec_t exec = nullptr;
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaGraphInstantiate");
+    ctx->graph = exec;
+    ctx->g_ev.assign(ev, ev + n_events);
+    ctx->g_D = D;
+    ctx->g_K = K;
+    ctx->g_r = r;
+    ctx->g_flags = flags;
+    std::memcpy(ctx->g_opts, opts, sizeof(opts));
+    e = cudaGraphLaunch(exec, ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaGraphLaunch");
+    return FRNN_OK;
+}
+
+frnn_status frnn_self_query_host(frnn_ctx* ctx, const float* refs_host, int64_t N, int D,
+                                 float r, int K, unsigned flags, int32_t* counts_host,
+                                 int32_t* idx_host, float* dist2_host) {
+    if (!ctx) return FRNN_ERR_INVALID_ARG;
+    if (D < 1 || D > kMaxD) return fail(ctx, FRNN_ERR_INVALID_ARG, "D must be in 1..16");
+    frnn_status s = check_query_args(ctx, N, r, K, flags | FRNN_SELF_QUERY, counts_host,
+                                     idx_host, dist2_host);
+    if (s != FRNN_OK) return s;
+    if (N > 0 && !refs_host) return fail(ctx, FRNN_ERR_INVALID_ARG, "refs_host is NULL");
+    if (N == 0) return FRNN_OK;
+    const size_t b_in = sizeof(float) * (size_t)N * D;
+    const size_t b_cnt = sizeof(int32_t) * (size_t)N;
+    const size_t b_row = sizeof(int32_t) * (size_t)N * K;
+    auto al = [](size_t x) { return (x + 255) / 256 * 256; };
+    const size_t need = al(b_in) + al(b_cnt) + 2 * al(b_row);
+    if (need > ctx->hp_bytes) {
+        if (!budget_allows(ctx, ctx->hp_bytes, need))
+            return fail(ctx, FRNN_ERR_BUDGET, "request exceeds the context's memory budget");
+        cudaStreamSynchronize(ctx->stream);
+        if (ctx->hp_buf) cudaFree(ctx->hp_buf);
+        ctx->held -= std::min(ctx->held, ctx->hp_bytes);
+        ctx->hp_buf = nullptr;
+        ctx->hp_bytes = 0;
+        if (cudaMalloc(&ctx->hp_buf, need) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(ctx, FRNN_ERR_OUT_OF_MEMORY, "cudaMalloc of host-path buffers failed");
+        }
+        ctx->hp_bytes = need;
+        ctx->held += need;
+    }
+    char* b = static_cast<char*>(ctx->hp_buf);
+    float* d_in = reinterpret_cast<float*>(b);
+    int32_t* d_cnt = reinterpret_cast<int32_t*>(b + al(b_in));
+    int32_t* d_idx = reinterpret_cast<int32_t*>(b + al(b_in) + al(b_cnt));
+    float* d_d2 = reinterpret_cast<float*>(b + al(b_in) + al(b_cnt) + al(b_row));
+    cudaError_t e = cudaMemcpyAsync(d_in, refs_host, b_in, cudaMemcpyHostToDevice, ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "H2D copy");
+    s = frnn_build_grid(ctx, d_in, N, D, r, &ctx->host_grid);
+    if (s != FRNN_OK) return s;
+    s = frnn_query(ctx, ctx->host_grid, d_in, N, r, K, flags | FRNN_SELF_QUERY, d_cnt, d_idx,
+                   d_d2);
+    if (s != FRNN_OK) return s;
+    cudaMemcpyAsync(counts_host, d_cnt, b_cnt, cudaMemcpyDeviceToHost, ctx->stream);
+    cudaMemcpyAsync(idx_host, d_idx, b_row, cudaMemcpyDeviceToHost, ctx->stream);
+    e = cudaMemcpyAsync(dist2_host, d_d2, b_row, cudaMemcpyDeviceToHost, ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "D2H copy");
+    return frnn_sync(ctx);
+}
+
+frnn_status frnn_sync(frnn_ctx* ctx) {
+    if (!ctx) return FRNN_ERR_INVALID_ARG;
+    cudaError_t e = cudaMemcpyAsync(ctx->h_status, ctx->d_status, sizeof(int32_t),
+                                    cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "synchronise");
+    const int32_t st = *ctx->h_status;
+    if (st == 0) return FRNN_OK;
+    cudaMemsetAsync(ctx->d_status, 0, sizeof(int32_t), ctx->stream);
+    cudaStreamSynchronize(ctx->stream);
+    if (st & kStatusNonFinite)
+        return fail(ctx, FRNN_ERR_NONFINITE, "an input coordinate is NaN or infinite");
+    if (st & kStatusCapacity)
+        return fail(ctx, FRNN_ERR_CAPACITY, "an internal device-side capacity overflowed");
+    if (st & kStatusTimeout)
+        return fail(ctx, FRNN_ERR_TIMEOUT, "a bounded device-side wait ran out");
+    return fail(ctx, FRNN_ERR_CUDA, "unknown device status");
+}
+
+const char* frnn_last_error(const frnn_ctx* ctx) {
+    if (!ctx) return g_create_err.c_str();
+    return ctx->err.c_str();
+}
+
+frnn_status frnn_set_option(frnn_ctx* ctx, frnn_option opt, int64_t value) {
+    if (!ctx) return FRNN_ERR_INVALID_ARG;
+    switch (opt) {
+        case FRNN_OPT_CELL_MULT:
+            if (value < 1 || value > 2) return fail(ctx, FRNN_ERR_INVALID_ARG, "m must be 1 or 2");
+            ctx->cell_mult = (int)value;
+            return FRNN_OK;
+        case FRNN_OPT_GRID_AXES:
+            if (value < 0 || value > 1) return fail(ctx, FRNN_ERR_INVALID_ARG, "axes mode 0 or 1");
+            ctx->axes_mode = (int)value;
+            return FRNN_OK;
+        case FRNN_OPT_EXIT_DIMS:
+            if (value < 0 || value > kMaxD) return fail(ctx, FRNN_ERR_INVALID_ARG, "exit dims");
+            ctx->exit_dims = (int)value;
+            return FRNN_OK;
+        case FRNN_OPT_USE_GRAPH:
+            ctx->use_graph = value ? 1 : 0;
+            return FRNN_OK;
+        case FRNN_OPT_AUTOTUNE:
+            ctx->autotune = value ? 1 : 0;
+            return FRNN_OK;
+    }
+    return fail(ctx, FRNN_ERR_INVALID_ARG, "unknown option");
+}
+
+frnn_status frnn_get_option(const frnn_ctx* ctx, frnn_option opt, int64_t* value) {
+    if (!ctx || !value) return FRNN_ERR_INVALID_ARG;
+    switch (opt) {
+        case FRNN_OPT_CELL_MULT: *value = ctx->cell_mult; return FRNN_OK;
+        case FRNN_OPT_GRID_AXES: *value = ctx->axes_mode; return FRNN_OK;
+        case FRNN_OPT_EXIT_DIMS: *value = ctx->exit_dims; return FRNN_OK;
+        case FRNN_OPT_USE_GRAPH: *value = ctx->use_graph; return FRNN_OK;
+        case FRNN_OPT_AUTOTUNE: *value = ctx->autotune; return FRNN_OK;
+    }
+    return FRNN_ERR_INVALID_ARG;
+}
+
+}  // extern "C"

@@ -1,0 +1,696 @@
+// build.cu — uniform-grid build: bounding boxes, cell parameters, cell ids,
+// counting sort into cell-sorted padded rows, and the warp-task list.
+//
+// The uniform grid / cell list is the method of the original FRNN the paper
+// starts from (Sec. 2: uniform-grid kernel, spacing chosen so that r is an
+// integer multiple of it).  Here at most 3 coordinates are gridded; the cell
+// assignment is "roundoff-safe" (Table 1): it provably never separates two
+// points the float32 contract accepts by more than m cells per axis (proof at
+// choose_params below).
+//
+// Steps, all on the device, no host synchronisation:
+//   k_init      zero the cell counts, reset bounding boxes
+//   k_bbox      per-event per-axis min / max (+ non-finite flag), float4 staged
+//   k_params    per event: gridded axes, cell edge, cells per axis
+//   k_cellid    cell id of every point and its rank inside the cell (atomics)
+//   scan        exclusive warp-shuffle prefix scan of the counts -> cell starts
+//   k_scatter   write cell-sorted padded rows, slot -> original index, slot -> cell
+//   k_rowtasks  per row of cells: number of 32-query warp tasks
+//   scan        -> task starts
+//   k_emit      write the tasks
+#include <algorithm>
+#include <cmath>
+
+#include "frnn_host.h"
+
+namespace frnn {
+
+// ------------------------------------------------------------------ helpers
+
+__device__ __forceinline__ int find_event(const int32_t* starts, int E, int b) {
+    // largest e with starts[e] <= b
+    int lo = 0, hi = E - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (starts[mid] <= b) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ int find_event64(const int64_t* starts, int E, int64_t i) {
+    int lo = 0, hi = E - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (starts[mid] <= i) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Stage nf consecutive floats of a row-major point array into shared memory,
+// using 16-byte vector loads for the aligned body.
+__device__ __forceinline__ void stage_floats(float* sm, const float* src, int nf) {
+    const uintptr_t a = reinterpret_cast<uintptr_t>(src);
+    int head = (int)(((16u - (uint32_t)(a & 15u)) & 15u) >> 2);
+    if (a & 3u) head = nf;   // not even 4-byte aligned: scalar path (cannot happen for float*)
+    head = min(head, nf);
+    for (int i = threadIdx.x; i < head; i += blockDim.x) sm[i] = __ldg(src + i);
+    const int n4 = (nf - head) >> 2;
+    const float4* s4 = reinterpret_cast<const float4*>(src + head);
+    for (int i = threadIdx.x; i < n4; i += blockDim.x) {
+        float4 v = __ldg(s4 + i);
+        float* d = sm + head + 4 * i;
+        d[0] = v.x; d[1] = v.y; d[2] = v.z; d[3] = v.w;
+    }
+    for (int i = head + 4 * n4 + threadIdx.x; i < nf; i += blockDim.x) sm[i] = __ldg(src + i);
+}
+
+// Cell coordinate along one gridded axis: floor(fl(fl(x' - lo) * inv_h))
+// clamped to [0, dim - 1], with x' = x clamped to [lo, hi].  Every kernel that
+// bins points (references and queries) uses exactly this function.
+__device__ __forceinline__ int cell_coord(float x, float lo, float hi, float inv_h, int dim) {
+    float xc = fminf(fmaxf(x, lo), hi);
+    float g = __fmul_rn(__fsub_rn(xc, lo), inv_h);
+    int c = __float2int_rd(g);
+    return min(max(c, 0), dim - 1);
+}
+
+__device__ __forceinline__ int point_cell(const float* p, const EventHdr& h) {
+    int c = 0, stride = 1;
+#pragma unroll
+    for (int a = 0; a < kMaxAxes; ++a) {
+        if (a < h.naxes) {
+            c += cell_coord(p[h.axes[a]], h.lo[a], h.hi[a], h.inv_h, h.dims[a]) * stride;
+            stride *= h.dims[a];
+        }
+    }
+    return c;
+}
+
+// ------------------------------------------------------------------ kernels
+
+__global__ void k_init(int32_t* counts, int64_t L, int32_t* bbox, int E, int32_t* scalars,
+                       int32_t bb_min_init, int32_t bb_max_init) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t j = i; j < L; j += stride) counts[j] = 0;
+    for (int64_t j = i; j < (int64_t)E * kBBoxStride; j += stride) {
+        int k = (int)(j % kBBoxStride);
+        bbox[j] = k < 16 ? bb_min_init : (k < 32 ? bb_max_init : 0);
+    }
+    if (i < kScalars) scalars[i] = 0;
+}
+
+__global__ void __launch_bounds__(kBuildPtsPerBlock) k_bbox(const EventHdr* hdr,
+                                                            const int32_t* blk_start, int E,
+                                                            int D, int32_t* bbox,
+                                                            int32_t* status) {
+    extern __shared__ float sm[];
+    __shared__ float red_mn[kMaxD][kBuildPtsPerBlock / 32];
+    __shared__ float red_mx[kMaxD][kBuildPtsPerBlock / 32];
+    __shared__ int red_bad;
+    const int e = find_event(blk_start, E, blockIdx.x);
+    const EventHdr& h = hdr[e];
+    const int64_t p0 = (int64_t)(blockIdx.x - blk_start[e]) * kBuildPtsPerBlock;
+    const int np = (int)min((int64_t)kBuildPtsPerBlock, h.n - p0);
+    if (threadIdx.x == 0) red_bad = 0;
+    if (np > 0) stage_floats(sm, h.refs + p0 * D, np * D);
+    __syncthreads();
+    float mn[kMaxD], mx[kMaxD];
+    bool bad = false;
+#pragma unroll
+    for (int k = 0; k < kMaxD; ++k) { mn[k] = INFINITY; mx[k] = -INFINITY; }
+    if ((int)threadIdx.x < np) {
+        const float* p = sm + threadIdx.x * D;
+#pragma unroll
+        for (int k = 0; k < kMaxD; ++k) {
+            if (k < D) {
+                float v = p[k];
+                bad |= !isfinite(v);
+                mn[k] = fminf(mn[k], v);
+                mx[k] = fmaxf(mx[k], v);
+            }
+        }
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < kMaxD; ++k) {
+        if (k < D) {
+            float a = mn[k], b = mx[k];
+            for (int o = 16; o > 0; o >>= 1) {
+                a = fminf(a, __shfl_xor_sync(0xffffffffu, a, o));
+                b = fmaxf(b, __shfl_xor_sync(0xffffffffu, b, o));
+            }
+            if (lane == 0) { red_mn[k][warp] = a; red_mx[k][warp] = b; }
+        }
+    }
+    if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(&red_bad, 1);
+    __syncthreads();
+    if (threadIdx.x < (unsigned)D) {
+        const int k = threadIdx.x;
+        float a = INFINITY, b = -INFINITY;
+        for (int w = 0; w < kBuildPtsPerBlock / 32; ++w) {
+            a = fminf(a, red_mn[k][w]);
+            b = fmaxf(b, red_mx[k][w]);
+        }
+        int32_t* bb = bbox + (int64_t)e * kBBoxStride;
+        atomicMin(bb + k, float_to_ordered(a));
+        atomicMax(bb + 16 + k, float_to_ordered(b));
+    }
+    if (threadIdx.x == 0 && red_bad) {
+        atomicOr(bbox + (int64_t)e * kBBoxStride + 32, 1);
+        atomicOr(status, kStatusNonFinite);
+    }
+}
+
+// Grid parameters of one event (one thread per event).
+//
+// Roundoff-safe cell assignment (proof).  Let u = 2^-24.  If the contract
+// accepts (x, y), every rounded square t_a = fl(fl(x_a - y_a)^2) is <= the
+// final sum s (partial sums of non-negative terms never decrease under
+// round-to-nearest) and s <= r2 = fl(r*r) <= r^2 (1 + u); with r2 normal this
+// gives |fl(x_a - y_a)| <= r (1 + 2u) and |x_a - y_a| <= rho := r (1 + 2^-20).
+// For lo <= x <= y <= hi the cell coordinate g(.) = fl(fl(. - lo) * inv_h) is
+// monotone and g(y) - g(x) <= inv_h (rho + 2^-21 E) + 2^-148, E = hi - lo.  If
+// that bound is < m, floor(g(y)) - floor(g(x)) <= m, and clamping to
+// [0, dim-1] keeps it so; queries are clamped to [lo, hi] first, which only
+// shrinks their distance to any reference.  So searching +-m cells per gridded
+// axis finds every accepted pair.  inv_h starts at fl_down(m / (r (1+2^-10)))
+// and is lowered until the bound holds with 2^-20 to spare, every axis has at
+// most 1024 cells, and the event's cell count fits its capacity.
+__global__ void k_params(EventHdr* hdr, int E, int D, const int32_t* bbox, float r, int m,
+                         int axes_mode) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= E) return;
+    EventHdr& h = hdr[e];
+    const int32_t* bb = bbox + (int64_t)e * kBBoxStride;
+    const int naxes = D < 3 ? D : 3;
+    h.naxes = naxes;
+    h.m = m;
+    int axes[3] = {0, 0, 0};
+    if (axes_mode == 1 && D > naxes) {
+        // the naxes widest coordinates (ties by lower index), in index order
+        bool used[kMaxD];
+        for (int k = 0; k < kMaxD; ++k) used[k] = false;
+        for (int a = 0; a < naxes; ++a) {
+            int best = -1;
+            float bw = -1.f;
+            for (int k = 0; k < D; ++k) {
+                if (used[k]) continue;
+                float w = ordered_to_float(bb[16 + k]) - ordered_to_float(bb[k]);
+                if (!(w <= bw)) { best = k; bw = w; }   // NaN-safe: first wins on NaN
+            }
+            used[best] = true;
+        }
+        int a = 0;
+        for (int k = 0; k < D; ++k) if (used[k]) axes[a++] = k;
+    } else {
+        for (int a = 0; a < naxes; ++a) axes[a] = D - naxes + a;
+    }
+    bool valid = bb[32] == 0 && h.n > 0;
+    double ext[3] = {0.0, 0.0, 0.0};
+    for (int a = 0; a < 3; ++a) {
+        h.axes[a] = a < naxes ? axes[a] : 0;
+        h.dims[a] = 1;
+        h.lo[a] = 0.f;
+        h.hi[a] = 0.f;
+        if (a < naxes && valid) {
+            float lo = ordered_to_float(bb[axes[a]]);
+            float hi = ordered_to_float(bb[16 + axes[a]]);
+            if (!isfinite(lo) || !isfinite(hi)) valid = false;
+            h.lo[a] = lo;
+            h.hi[a] = hi;
+            ext[a] = (double)hi - (double)lo;
+        }
+    }
+    h.valid = valid ? 1 : 0;
+    if (!valid) {
+        h.inv_h = 0.f;
+        h.ncells = 1;
+        return;
+    }
+    const double rd = (double)r;
+    const double rho = rd * (1.0 + 0x1p-20);
+    float ih = __double2float_rd((double)m / (rd * (1.0 + 0x1p-10)));
+    int dims[3] = {1, 1, 1};
+    for (int it = 0; it < 4096; ++it) {
+        bool ok = true;
+        int64_t cells = 1;
+        for (int a = 0; a < naxes; ++a) {
+            double c = floor(ext[a] * (double)ih) + 1.0;
+            if (c > kMaxDimsPerAxis) { ok = false; break; }
+            dims[a] = (int)c;
+            cells *= dims[a];
+            if ((double)ih * (rho + 0x1p-21 * ext[a]) + 0x1p-148 >= (double)m - 0x1p-20) ok = false;
+        }
+        if (ok && cells <= h.cell_cap) break;
+        ih = __double2float_rd((double)ih * 0.9);
+        if (!(ih > 0.f)) { ih = 0.f; dims[0] = dims[1] = dims[2] = 1; break; }
+    }
+    h.inv_h = ih;
+    int64_t cells = 1;
+    for (int a = 0; a < 3; ++a) {
+        h.dims[a] = a < naxes ? dims[a] : 1;
+        cells *= h.dims[a];
+    }
+    h.ncells = (int32_t)cells;
+}
+
+// Cross-set binning: take the reference grid's parameters for each event.
+__global__ void k_copy_params(EventHdr* dst, const EventHdr* src, int E) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= E) return;
+    EventHdr& d = dst[e];
+    const EventHdr& s = src[e];
+    d.naxes = s.naxes;
+    d.m = s.m;
+    d.valid = s.valid;
+    d.inv_h = s.inv_h;
+    d.ncells = s.ncells;
+    for (int a = 0; a < 3; ++a) {
+        d.axes[a] = s.axes[a];
+        d.dims[a] = s.dims[a];
+        d.lo[a] = s.lo[a];
+        d.hi[a] = s.hi[a];
+    }
+}
+
+// Non-finite check of a query set binned with foreign parameters (the bbox
+// kernel does it for reference sets).
+__global__ void __launch_bounds__(kBuildPtsPerBlock) k_cellid(const EventHdr* hdr,
+                                                              const int32_t* blk_start, int E,
+                                                              int D, int32_t* counts,
+                                                              int32_t* cid, int32_t* rnk,
+                                                              int check_finite, int32_t* status) {
+    extern __shared__ float sm[];
+    const int e = find_event(blk_start, E, blockIdx.x);
+    const EventHdr& h = hdr[e];
+    const int64_t p0 = (int64_t)(blockIdx.x - blk_start[e]) * kBuildPtsPerBlock;
+    const int np = (int)min((int64_t)kBuildPtsPerBlock, h.n - p0);
+    if (np > 0) stage_floats(sm, h.refs + p0 * D, np * D);
+    __syncthreads();
+    const int i = threadIdx.x;
+    if (i >= np) return;
+    const float* p = sm + i * D;
+    int c = 0;
+    if (check_finite) {
+        bool bad = false;
+        for (int k = 0; k < D; ++k) bad |= !isfinite(p[k]);
+        if (bad) atomicOr(status, kStatusNonFinite);
+    }
+    if (h.valid) c = point_cell(p, h);
+    const int64_t gi = h.pt_off + p0 + i;
+    cid[gi] = c;
+    rnk[gi] = atomicAdd(counts + h.cell_off + c, 1);
+}
+
+__global__ void __launch_bounds__(kBuildPtsPerBlock) k_scatter(const EventHdr* hdr,
+                                                               const int32_t* blk_start, int E,
+                                                               int D, int DP,
+                                                               const int32_t* cstart,
+                                                               const int32_t* cid,
+                                                               const int32_t* rnk, float* pts,
+                                                               int32_t* perm, int32_t* cell) {
+    extern __shared__ float sm[];
+    const int e = find_event(blk_start, E, blockIdx.x);
+    const EventHdr& h = hdr[e];
+    const int64_t p0 = (int64_t)(blockIdx.x - blk_start[e]) * kBuildPtsPerBlock;
+    const int np = (int)min((int64_t)kBuildPtsPerBlock, h.n - p0);
+    if (np > 0) stage_floats(sm, h.refs + p0 * D, np * D);
+    __syncthreads();
+    const int i = threadIdx.x;
+    if (i >= np) return;
+    const int64_t gi = h.pt_off + p0 + i;
+    const int c = cid[gi];
+    const int64_t slot = (int64_t)cstart[h.cell_off + c] + rnk[gi];
+    const float* p = sm + i * D;
+    float4* dst = reinterpret_cast<float4*>(pts + slot * DP);
+    for (int k4 = 0; k4 < DP / 4; ++k4) {
+        float v[4];
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            int k = 4 * k4 + t;
+            v[t] = k < D ? p[k] : 0.f;
+        }
+        dst[k4] = make_float4(v[0], v[1], v[2], v[3]);
+    }
+    perm[slot] = (int32_t)(p0 + i);
+    cell[slot] = c;
+}
+
+// Per row of cells (all gridded coordinates but the fastest fixed): number of
+// 32-query warp tasks.  Entry i of the cell arrays doubles as row slot i.
+__global__ void k_rowtasks(const EventHdr* hdr, const int64_t* cell_off, int E, int64_t L,
+                           const int32_t* cstart, int32_t* rtask) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= L) return;
+    const int e = find_event64(cell_off, E, i);
+    const EventHdr& h = hdr[e];
+    const int64_t row = i - cell_off[e];
+    const int64_t nrows = (int64_t)h.dims[1] * h.dims[2];
+    int32_t nt = 0;
+    if (h.valid && row < nrows) {
+        const int64_t c0 = h.cell_off + row * h.dims[0];
+        const int32_t cnt = cstart[c0 + h.dims[0]] - cstart[c0];
+        nt = (cnt + kTaskQueries - 1) / kTaskQueries;
+    } else if (!h.valid && row == 0) {
+        // invalid event: its queries still get (empty) rows written
+        nt = (int32_t)((h.n + kTaskQueries - 1) / kTaskQueries);
+    }
+    rtask[i] = nt;
+}
+
+__global__ void k_emit(const EventHdr* hdr, const int64_t* cell_off, int E, int64_t L,
+                       const int32_t* cstart, const int32_t* rtask_start,
+                       const int32_t* rtask_count_src, Task* tasks) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= L) return;
+    const int e = find_event64(cell_off, E, i);
+    const EventHdr& h = hdr[e];
+    const int64_t row = i - cell_off[e];
+    const int32_t t0 = rtask_start[i];
+    const int32_t t1 = (i + 1 < L) ? rtask_start[i + 1] : rtask_count_src[0];
+    if (t1 <= t0) return;
+    int32_t base, cnt;
+    if (h.valid) {
+        const int64_t c0 = h.cell_off + row * h.dims[0];
+        base = cstart[c0];
+        cnt = cstart[c0 + h.dims[0]] - base;
+    } else {
+        base = (int32_t)h.pt_off;
+        cnt = (int32_t)h.n;
+    }
+    for (int32_t t = t0; t < t1; ++t) {
+        const int32_t k = t - t0;
+        Task tk;
+        tk.qslot = base + k * kTaskQueries;
+        tk.nq = min(kTaskQueries, cnt - k * kTaskQueries);
+        tk.ev = e;
+        tk.row = (int32_t)row;
+        tasks[t] = tk;
+    }
+}
+
+// ------------------------------------------------------------------ scan
+// Exclusive prefix scan of int32 in place (three phases: per-block totals,
+// scan of the totals, per-block scan with offset).  Inside a block each thread
+// scans kScanItems consecutive values, then warp shuffles scan the thread
+// totals and a second warp pass scans the warp totals.
+
+constexpr int kScanThreads = 1024;
+constexpr int kScanItems = 8;
+constexpr int kScanChunk = kScanThreads * kScanItems;
+
+__device__ __forceinline__ int32_t block_exclusive_scan(int32_t v, int32_t* warp_tot,
+                                                        int32_t* block_total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_tot[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        int32_t w = lane < (kScanThreads / 32) ? warp_tot[lane] : 0;
+        int32_t z = w;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int32_t y = __shfl_up_sync(0xffffffffu, z, o);
+            if (lane >= o) z += y;
+        }
+        if (lane < kScanThreads / 32) warp_tot[lane] = z - w;
+        if (lane == 31) *block_total = z;
+    }
+    __syncthreads();
+    return x - v + warp_tot[warp];
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const int32_t* data, int64_t n,
+                                                              int32_t* parts) {
+    __shared__ int32_t red[kScanThreads / 32];
+    const int64_t base = (int64_t)blockIdx.x * kScanChunk;
+    int32_t s = 0;
+    for (int k = 0; k < kScanItems; ++k) {
+        int64_t i = base + (int64_t)k * kScanThreads + threadIdx.x;
+        if (i < n) s += data[i];
+    }
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        int32_t t = red[threadIdx.x];
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+        if (threadIdx.x == 0) parts[blockIdx.x] = t;
+    }
+}
+
+// Scan one chunk of kScanChunk values in place with an added offset.
+__device__ void scan_chunk(int32_t* data, int64_t n, int64_t base, int32_t offset,
+                           int32_t* total_out) {
+    __shared__ int32_t buf[kScanChunk];
+    __shared__ int32_t warp_tot[kScanThreads / 32];
+    __shared__ int32_t btot;
+    for (int k = 0; k < kScanItems; ++k) {
+        int64_t i = base + (int64_t)k * kScanThreads + threadIdx.x;
+        buf[k * kScanThreads + threadIdx.x] = i < n ? data[i] : 0;
+    }
+    __syncthreads();
+    int32_t v[kScanItems];
+    int32_t t = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        v[k] = buf[threadIdx.x * kScanItems + k];
+        t += v[k];
+    }
+    int32_t ex = block_exclusive_scan(t, warp_tot, &btot) + offset;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        buf[threadIdx.x * kScanItems + k] = ex;
+        ex += v[k];
+    }
+    __syncthreads();
+    for (int k = 0; k < kScanItems; ++k) {
+        int64_t i = base + (int64_t)k * kScanThreads + threadIdx.x;
+        if (i < n) data[i] = buf[k * kScanThreads + threadIdx.x];
+    }
+    if (total_out && threadIdx.x == 0) *total_out = btot + offset;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_single(int32_t* data, int64_t n,
+                                                              int32_t* total) {
+    scan_chunk(data, n, 0, 0, total);
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_down(int32_t* data, int64_t n,
+                                                            const int32_t* parts) {
+    scan_chunk(data, n, (int64_t)blockIdx.x * kScanChunk, parts[blockIdx.x], nullptr);
+}
+
+int64_t scan_parts_needed(int64_t n) { return std::max<int64_t>(1, ceil_div(n, kScanChunk)); }
+
+void enqueue_scan(int32_t* data, int64_t n, int32_t* parts, int32_t* total, cudaStream_t st) {
+    const int64_t nb = scan_parts_needed(n);
+    if (nb == 1) {
+        k_scan_single<<<1, kScanThreads, 0, st>>>(data, n, total);
+        return;
+    }
+    k_scan_reduce<<<(unsigned)nb, kScanThreads, 0, st>>>(data, n, parts);
+    // nb <= kScanChunk is guaranteed by the capacity limits (2^26 entries)
+    k_scan_single<<<1, kScanThreads, 0, st>>>(parts, nb, total);
+    k_scan_down<<<(unsigned)nb, kScanThreads, 0, st>>>(data, n, parts);
+}
+
+// ------------------------------------------------------------------ host
+
+int64_t cell_cap_for(int64_t n) {
+    int64_t c = std::max<int64_t>(16384, n / 2 + 1);
+    return std::min<int64_t>(c, (int64_t)1 << 24);
+}
+
+static size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+void grid_free(GridBufs& g) {
+    if (g.base) cudaFree(g.base);
+    if (g.h_pinned) cudaFreeHost(g.h_pinned);
+    if (g.h_pinned_free) cudaEventDestroy(g.h_pinned_free);
+    g = GridBufs();
+}
+
+frnn_status grid_alloc(GridBufs& g, int E, const int64_t* n, int D, std::string& err,
+                       const int64_t* caps) {
+    const int DP = padded_dim(D);
+    int64_t n_total = 0, L = 0, task_cap = 0, nblk = 0;
+    g.h_hdr.assign(E, EventHdr{});
+    g.h_blk_start.assign(E + 1, 0);
+    g.h_cell_off.assign(E + 1, 0);
+    for (int e = 0; e < E; ++e) {
+        const int64_t cap = caps ? caps[e] : cell_cap_for(n[e]);
+        EventHdr& h = g.h_hdr[e];
+        h.n = n[e];
+        h.pt_off = n_total;
+        h.cell_off = L;
+        h.cell_cap = (int32_t)cap;
+        g.h_blk_start[e] = (int32_t)nblk;
+        g.h_cell_off[e] = L;
+        n_total += n[e];
+        L += cap + 1;
+        task_cap += n[e] / kTaskQueries + cap + 2;
+        nblk += std::max<int64_t>(1, ceil_div(n[e], kBuildPtsPerBlock));
+    }
+    g.h_blk_start[E] = (int32_t)nblk;
+    g.h_cell_off[E] = L;
+    if (n_total >= INT32_MAX || L >= ((int64_t)1 << 26) || task_cap >= INT32_MAX ||
+        nblk >= INT32_MAX) {
+        err = "problem too large for one call (points, cells or tasks exceed the limits)";
+        return FRNN_ERR_INVALID_ARG;
+    }
+    g.E = E;
+    g.D = D;
+    g.DP = DP;
+    g.n_total = n_total;
+    g.L = L;
+    g.task_cap = task_cap;
+    g.nblk = nblk;
+    g.nparts = scan_parts_needed(L);
+    const bool fits = g.base && g.cap_n >= n_total && g.cap_L >= L && g.cap_tasks >= task_cap &&
+                      g.cap_E >= E && g.cap_blk >= nblk;
+    const int64_t cn = std::max<int64_t>(n_total, 1);
+    if (!fits) {
+        if (g.base) {
+            cudaFree(g.base);
+            g.base = nullptr;
+        }
+        size_t off = 0;
+        auto take = [&](size_t bytes) {
+            size_t o = off;
+            off = align_up(off + bytes, 256);
+            return o;
+        };
+        const size_t o_hdr = take(sizeof(EventHdr) * E);
+        const size_t o_blk = take(sizeof(int32_t) * (E + 1));
+        const size_t o_coff = take(sizeof(int64_t) * (E + 1));
+        const size_t o_bbox = take(sizeof(int32_t) * kBBoxStride * E);
+        const size_t o_pts = take(sizeof(float) * DP * cn);
+        const size_t o_perm = take(sizeof(int32_t) * cn);
+        const size_t o_cell = take(sizeof(int32_t) * cn);
+        const size_t o_cid = take(sizeof(int32_t) * cn);
+        const size_t o_rnk = take(sizeof(int32_t) * cn);
+        const size_t o_cst = take(sizeof(int32_t) * L);
+        const size_t o_rt = take(sizeof(int32_t) * L);
+        const size_t o_tasks = take(sizeof(Task) * task_cap);
+        const size_t o_ovf = take(sizeof(Overflow) * cn);
+        const size_t o_sc = take(sizeof(int32_t) * kScalars);
+        const size_t o_parts = take(sizeof(int32_t) * g.nparts);
+        void* base = nullptr;
+        cudaError_t ce = cudaMalloc(&base, off);
+        if (ce != cudaSuccess) {
+            cudaGetLastError();
+            err = std::string("cudaMalloc of grid buffers failed: ") + cudaGetErrorString(ce);
+            g.cap_n = g.cap_L = g.cap_tasks = g.cap_E = g.cap_blk = 0;
+            return FRNN_ERR_OUT_OF_MEMORY;
+        }
+        char* b = static_cast<char*>(base);
+        g.base = base;
+        g.bytes = off;
+        g.hdr = reinterpret_cast<EventHdr*>(b + o_hdr);
+        g.blk_start = reinterpret_cast<int32_t*>(b + o_blk);
+        g.cell_off = reinterpret_cast<int64_t*>(b + o_coff);
+        g.bbox = reinterpret_cast<int32_t*>(b + o_bbox);
+        g.pts = reinterpret_cast<float*>(b + o_pts);
+        g.perm = reinterpret_cast<int32_t*>(b + o_perm);
+        g.cell = reinterpret_cast<int32_t*>(b + o_cell);
+        g.cid = reinterpret_cast<int32_t*>(b + o_cid);
+        g.rnk = reinterpret_cast<int32_t*>(b + o_rnk);
+        g.cstart = reinterpret_cast<int32_t*>(b + o_cst);
+        g.rtask = reinterpret_cast<int32_t*>(b + o_rt);
+        g.tasks = reinterpret_cast<Task*>(b + o_tasks);
+        g.ovf = reinterpret_cast<Overflow*>(b + o_ovf);
+        g.scalars = reinterpret_cast<int32_t*>(b + o_sc);
+        g.parts = reinterpret_cast<int32_t*>(b + o_parts);
+        g.cap_n = n_total;
+        g.cap_L = L;
+        g.cap_tasks = task_cap;
+        g.cap_E = E;
+        g.cap_blk = nblk;
+    }
+    // page-locked mirror for the per-event tables
+    const size_t hbytes = sizeof(EventHdr) * E + sizeof(int32_t) * (E + 1) +
+                          sizeof(int64_t) * (E + 1) + 64;
+    if (g.h_pinned_bytes < hbytes) {
+        if (g.h_pinned) {
+            if (g.h_pinned_free) cudaEventSynchronize(g.h_pinned_free);
+            cudaFreeHost(g.h_pinned);
+            g.h_pinned = nullptr;
+        }
+        if (cudaMallocHost(&g.h_pinned, hbytes) != cudaSuccess) {
+            cudaGetLastError();
+            g.h_pinned_bytes = 0;
+            err = "cudaMallocHost of grid tables failed";
+            return FRNN_ERR_OUT_OF_MEMORY;
+        }
+        g.h_pinned_bytes = hbytes;
+    }
+    if (!g.h_pinned_free) cudaEventCreateWithFlags(&g.h_pinned_free, cudaEventDisableTiming);
+    return FRNN_OK;
+}
+
+static inline unsigned blocks_for(int64_t n, int t) {
+    return (unsigned)std::max<int64_t>(1, ceil_div(n, t));
+}
+
+frnn_status enqueue_build(GridBufs& g, const float* const* refs, const BuildOpts& o,
+                          const GridBufs* params_from, int32_t* d_status, cudaStream_t st,
+                          bool capturing, std::string& err) {
+    const int E = g.E, D = g.D;
+    for (int e = 0; e < E; ++e) {
+        g.h_hdr[e].refs = refs[e];
+        g.h_hdr[e].valid = 1;
+    }
+    // upload the per-event tables through the pinned mirror (wait until the
+    // previous upload from it has been consumed)
+    if (!capturing) cudaEventSynchronize(g.h_pinned_free);
+    char* hp = static_cast<char*>(g.h_pinned);
+    const size_t s_hdr = sizeof(EventHdr) * E;
+    const size_t s_blk = sizeof(int32_t) * (E + 1);
+    const size_t s_coff = sizeof(int64_t) * (E + 1);
+    memcpy(hp, g.h_hdr.data(), s_hdr);
+    memcpy(hp + s_hdr, g.h_blk_start.data(), s_blk);
+    memcpy(hp + s_hdr + s_blk, g.h_cell_off.data(), s_coff);
+    cudaMemcpyAsync(g.hdr, hp, s_hdr, cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(g.blk_start, hp + s_hdr, s_blk, cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(g.cell_off, hp + s_hdr + s_blk, s_coff, cudaMemcpyHostToDevice, st);
+    if (!capturing) cudaEventRecord(g.h_pinned_free, st);
+
+    const int32_t bbmin = host_float_to_ordered(INFINITY);
+    const int32_t bbmax = host_float_to_ordered(-INFINITY);
+    const int64_t init_n = std::max<int64_t>(g.L, (int64_t)E * kBBoxStride);
+    k_init<<<std::min<unsigned>(blocks_for(init_n, 256), 4096), 256, 0, st>>>(
+        g.cstart, g.L, g.bbox, E, g.scalars, bbmin, bbmax);
+    const size_t smem_pts = sizeof(float) * kBuildPtsPerBlock * D;
+    if (params_from) {
+        k_copy_params<<<blocks_for(E, 128), 128, 0, st>>>(g.hdr, params_from->hdr, E);
+    } else {
+        k_bbox<<<(unsigned)g.nblk, kBuildPtsPerBlock, smem_pts, st>>>(g.hdr, g.blk_start, E, D,
+                                                                     g.bbox, d_status);
+        k_params<<<blocks_for(E, 128), 128, 0, st>>>(g.hdr, E, D, g.bbox, o.r, o.m, o.axes_mode);
+    }
+    k_cellid<<<(unsigned)g.nblk, kBuildPtsPerBlock, smem_pts, st>>>(
+        g.hdr, g.blk_start, E, D, g.cstart, g.cid, g.rnk, params_from ? 1 : 0, d_status);
+    enqueue_scan(g.cstart, g.L, g.parts, g.scalars + kScCellTotal, st);
+    k_scatter<<<(unsigned)g.nblk, kBuildPtsPerBlock, smem_pts, st>>>(
+        g.hdr, g.blk_start, E, D, g.DP, g.cstart, g.cid, g.rnk, g.pts, g.perm, g.cell);
+    k_rowtasks<<<blocks_for(g.L, 256), 256, 0, st>>>(g.hdr, g.cell_off, E, g.L, g.cstart,
+                                                      g.rtask);
+    enqueue_scan(g.rtask, g.L, g.parts, g.scalars + kScNTasks, st);
+    k_emit<<<blocks_for(g.L, 256), 256, 0, st>>>(g.hdr, g.cell_off, E, g.L, g.cstart, g.rtask,
+                                                  g.scalars + kScNTasks, g.tasks);
+    cudaError_t ce = cudaGetLastError();
+    if (ce != cudaSuccess) {
+        err = std::string("grid build launch failed: ") + cudaGetErrorString(ce);
+        return FRNN_ERR_CUDA;
+    }
+    return FRNN_OK;
+}
+
+}  // namespace frnn

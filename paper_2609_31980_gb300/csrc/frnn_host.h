@@ -1,0 +1,110 @@
+// frnn_host.h — host-side structures shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "frnn_internal.cuh"
+
+namespace frnn {
+
+// Device buffers of one (possibly multi-event) cell-sorted point set: the
+// reference grid of frnn_build_grid / frnn_query_batched, or the binned query
+// set of a cross-set frnn_query.  One cudaMalloc block, carved into arrays.
+struct GridBufs {
+    int E = 0;              // events
+    int D = 0, DP = 0;      // dimensions, padded row length (floats)
+    int64_t n_total = 0;    // points over all events
+    int64_t L = 0;          // cell-array entries: sum over events of (cell_cap + 1)
+    int64_t task_cap = 0;   // warp-task capacity
+    int64_t nblk = 0;       // blocks of the per-point build kernels
+    int64_t nparts = 0;     // scan partial sums needed
+
+    // allocation (reused when large enough)
+    void* base = nullptr;
+    size_t bytes = 0;
+    int64_t cap_n = 0, cap_L = 0, cap_tasks = 0, cap_E = 0, cap_blk = 0;
+    void* h_pinned = nullptr;      // page-locked host mirror of the small tables
+    size_t h_pinned_bytes = 0;
+    cudaEvent_t h_pinned_free = nullptr;   // last upload from the mirror has run
+
+    // device arrays
+    EventHdr* hdr = nullptr;       // [E]
+    int32_t* blk_start = nullptr;  // [E + 1] first build block of each event
+    int64_t* cell_off = nullptr;   // [E + 1] first cell-array entry of each event
+    int32_t* bbox = nullptr;       // [E * kBBoxStride] ordered-int min / max / flag
+    float* pts = nullptr;          // [n_total * DP] cell-sorted coordinates
+    int32_t* perm = nullptr;       // [n_total] slot -> original index in its event
+    int32_t* cell = nullptr;       // [n_total] slot -> local cell id
+    int32_t* cid = nullptr;        // [n_total] input order -> local cell id
+    int32_t* rnk = nullptr;        // [n_total] input order -> rank inside its cell
+    int32_t* cstart = nullptr;     // [L] cell counts, then (scanned) global start slots
+    int32_t* rtask = nullptr;      // [L] per-row task counts, then task starts
+    Task* tasks = nullptr;         // [task_cap]
+    Overflow* ovf = nullptr;       // [n_total]
+    int32_t* scalars = nullptr;    // [kScalars] counters (below)
+    int32_t* parts = nullptr;      // [nparts] scan partial sums
+
+    // host copies
+    std::vector<EventHdr> h_hdr;
+    std::vector<int32_t> h_blk_start;
+    std::vector<int64_t> h_cell_off;
+};
+
+constexpr int kBBoxStride = 34;      // 16 minima, 16 maxima, non-finite flag, pad
+constexpr int kBuildPtsPerBlock = 256;
+// indices into GridBufs::scalars
+constexpr int kScNTasks = 0;        // number of warp tasks
+constexpr int kScCellTotal = 1;     // total of the cell-count scan (= n_total)
+constexpr int kScTaskCounter = 2;   // dynamic task counter of the query kernel
+constexpr int kScOvfCount = 3;      // overflowed queries
+constexpr int kScTcCounter = 4;     // task counter of the tensor-core kernel
+constexpr int kScalars = 16;
+
+int64_t cell_cap_for(int64_t n);
+
+// Compute the layout for E events of sizes n[e] and allocate (or reuse).
+// caps (optional): per-event cell capacities (a query set binned with a
+// reference grid's parameters must use that grid's capacities).
+frnn_status grid_alloc(GridBufs& g, int E, const int64_t* n, int D, std::string& err,
+                       const int64_t* caps = nullptr);
+void grid_free(GridBufs& g);
+
+struct BuildOpts {
+    float r = 0.f;          // grid radius
+    int m = 1;              // cell multiple
+    int axes_mode = 0;      // 0: last axes, 1: widest axes
+};
+
+// Enqueue a full build (bounding boxes, parameters, binning, counting sort,
+// tasks).  refs[e] = event e's [n_e, D] device input.  If params_from is not
+// NULL the grid parameters are copied from it (cross-set query binning) instead
+// of being derived from this set's bounding box.  capturing: the stream is
+// being captured into a CUDA graph (no host-side event waits or records).
+frnn_status enqueue_build(GridBufs& g, const float* const* refs, const BuildOpts& o,
+                          const GridBufs* params_from, int32_t* d_status, cudaStream_t st,
+                          bool capturing, std::string& err);
+
+// Exclusive scan of n int32 values in place; the total goes to *total.
+void enqueue_scan(int32_t* data, int64_t n, int32_t* parts, int32_t* total, cudaStream_t st);
+int64_t scan_parts_needed(int64_t n);
+
+// Query launch (grid path).
+struct QueryLaunch {
+    const GridBufs* qset;   // query slots and tasks
+    const GridBufs* rset;   // reference grid
+    float r2;
+    int K;
+    int self;
+    int exit_dims;          // 0 = default
+    int32_t* counts;        // single event outputs, or NULL to use the event headers'
+    int32_t* idx;
+    float* dist2;
+    int32_t* d_status;
+    int num_sms;
+};
+frnn_status enqueue_grid_query(const QueryLaunch& q, cudaStream_t st, std::string& err);
+
+}  // namespace frnn

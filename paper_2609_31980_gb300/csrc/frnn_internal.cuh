@@ -1,0 +1,168 @@
+// frnn_internal.cuh — device data layout, launch helpers and PTX wrappers
+// shared by the library's translation units (not part of the public ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
+
+#include "../../include/frnn.h"
+
+namespace frnn {
+
+constexpr int kMaxD = 16;
+constexpr int kMaxK = 1024;
+constexpr int kMaxAxes = 3;
+constexpr int kMaxDimsPerAxis = 1024;   // the grid roundoff proof assumes <= 2^10 cells per axis
+constexpr int kTaskQueries = 32;        // queries per warp task (one per lane)
+
+// Device status word bits (frnn_sync maps them to frnn_status).
+constexpr int kStatusNonFinite = 1;
+constexpr int kStatusTimeout = 2;
+constexpr int kStatusCapacity = 4;
+
+// Bounded spin limit for mbarrier waits (iterations of try_wait, each of which
+// itself blocks for a hardware-defined interval): far above any legitimate wait.
+constexpr uint32_t kSpinLimit = 1u << 24;
+
+// Padded point row: D floats rounded up to a multiple of 4 (16 bytes), so every
+// sorted point starts on a 16-byte boundary (bulk-copy and float4 alignment).
+__host__ __device__ constexpr int padded_dim(int D) { return (D + 3) & ~3; }
+
+// Per-event grid header (device-resident, one per event of a build).
+struct EventHdr {
+    const float* refs;     // caller's [n, D] input (build only)
+    int64_t n;             // points in this event
+    int64_t pt_off;        // first sorted slot of this event (global slot numbering)
+    int64_t cell_off;      // first entry of this event in the cell arrays (cap + 1 entries)
+    int32_t cell_cap;      // cells allowed for this event
+    int32_t ncells;        // dims[0] * dims[1] * dims[2] (written by the params kernel)
+    int32_t naxes;         // gridded axes (1..3)
+    int32_t m;             // cell multiple: neighbours are within +-m cells per gridded axis
+    int32_t valid;         // 0 if a coordinate was non-finite
+    int32_t axes[3];       // gridded coordinate indices; axes[0] varies fastest
+    int32_t dims[3];       // cells per gridded axis (1 for unused axes)
+    float lo[3];           // per-axis minimum coordinate
+    float hi[3];           // per-axis maximum coordinate
+    float inv_h;           // 1 / cell edge (float; the value the cell ids use)
+    int32_t pad_;
+    // query outputs for batched self-queries (row = original point index)
+    int32_t* counts;
+    int32_t* idx;
+    float* dist2;
+};
+
+// One warp task: up to 32 consecutive cell-sorted query slots lying in one
+// row of cells (all gridded coordinates but the fastest equal).
+struct Task {
+    int32_t qslot;   // first query slot (global)
+    int32_t nq;      // queries in the task (1..32)
+    int32_t ev;      // event index
+    int32_t row;     // row index within the event: y + dims[1] * z
+};
+
+// Overflowed query (degree > K): handled by the exact selection kernel.
+struct Overflow {
+    int32_t qslot;
+    int32_t ev;
+};
+
+// Everything the query kernels need, passed by value.
+struct QueryArgs {
+    const EventHdr* ev;          // per-event headers (reference grids)
+    const Task* tasks;           // warp tasks over the query slots
+    const int32_t* ntasks;       // device scalar: number of tasks
+    const float* qpts;           // cell-sorted query coordinates [*, DP]
+    const int32_t* qperm;        // query slot -> original query index (within its event)
+    const int32_t* qcell;        // query slot -> local cell id
+    const float* rpts;           // cell-sorted reference coordinates [*, DP]
+    const int32_t* rperm;        // reference slot -> original index (within its event)
+    const int32_t* cstart;       // reference cell starts (global slots), per event cap+1
+    int32_t* counts;             // single-event outputs (NULL: use the per-event ones)
+    int32_t* idx;
+    float* dist2;
+    float r2;                    // fl(r * r)
+    int32_t K;
+    int32_t self;                // 1: query slot == reference slot is excluded
+    int32_t D;
+    int32_t* task_counter;       // device scalar, zero at launch
+    int32_t* status;             // device status word
+    Overflow* ovf;               // overflow list
+    int32_t* ovf_count;          // device scalar
+    int32_t ovf_cap;
+    int32_t exit_dims;           // dims summed before the warp early-exit vote
+};
+
+// ---------------------------------------------------------------- PTX helpers
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+                 : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+// 1-D bulk copy global -> shared, completion signalled on an mbarrier.
+// dst, src 16-byte aligned; bytes a positive multiple of 16.
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes,
+                                         uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+            "r"(smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait: returns false (and the caller records a timeout) if the phase
+// did not complete within kSpinLimit polls.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+    for (uint32_t it = 0; it < kSpinLimit; ++it)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+
+// Ordered-int encoding of float for atomic min/max (monotone in float order).
+__device__ __forceinline__ int32_t float_to_ordered(float f) {
+    int32_t i = __float_as_int(f);
+    return i >= 0 ? i : i ^ 0x7fffffff;
+}
+__device__ __forceinline__ float ordered_to_float(int32_t i) {
+    return __int_as_float(i >= 0 ? i : i ^ 0x7fffffff);
+}
+inline int32_t host_float_to_ordered(float f) {
+    int32_t i;
+    memcpy(&i, &f, 4);
+    return i >= 0 ? i : i ^ 0x7fffffff;
+}
+
+__host__ __device__ constexpr int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+}  // namespace frnn

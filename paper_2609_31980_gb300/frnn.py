@@ -1,0 +1,245 @@
+"""Thin ctypes binding of libfrnn (include/frnn.h): argument marshalling only.
+
+Every computation runs in the library's CUDA kernels.  PyTorch supplies device
+memory and streams.  If libfrnn.so is missing the import of this module fails:
+there is no other implementation to fall back on.
+
+Low-level functions carry the C names (``frnn_create``, ``frnn_build_grid``,
+``frnn_query``, ``frnn_query_batched``, ``frnn_sync`` ...); ``Context`` wraps
+them for torch tensors.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libfrnn.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"libfrnn.so not built ({LIB_PATH}); run "
+                      "`python -m paper_2609_31980_gb300.build` (needs nvcc)")
+
+_lib = ctypes.CDLL(LIB_PATH)
+
+FRNN_OK = 0
+STATUS_NAMES = {
+    0: "FRNN_OK", -1: "FRNN_ERR_INVALID_ARG", -2: "FRNN_ERR_UNSUPPORTED",
+    -3: "FRNN_ERR_OUT_OF_MEMORY", -4: "FRNN_ERR_BUDGET", -5: "FRNN_ERR_NONFINITE",
+    -6: "FRNN_ERR_CUDA", -7: "FRNN_ERR_TIMEOUT", -8: "FRNN_ERR_CAPACITY",
+}
+FRNN_SELF_QUERY = 0x1
+FRNN_PATH_AUTO = 0x0
+FRNN_PATH_GRID = 0x2
+FRNN_PATH_TC = 0x4
+PATHS = {"auto": FRNN_PATH_AUTO, "grid": FRNN_PATH_GRID, "tc": FRNN_PATH_TC}
+
+FRNN_OPT_CELL_MULT = 1
+FRNN_OPT_GRID_AXES = 2
+FRNN_OPT_EXIT_DIMS = 3
+FRNN_OPT_USE_GRAPH = 4
+FRNN_OPT_AUTOTUNE = 5
+
+EXPORTED = ["frnn_version", "frnn_create", "frnn_destroy", "frnn_build_grid",
+            "frnn_grid_destroy", "frnn_query", "frnn_query_batched", "frnn_self_query_host",
+            "frnn_sync", "frnn_last_error", "frnn_set_option", "frnn_get_option"]
+
+
+class frnn_event(ctypes.Structure):
+    _fields_ = [("pts", ctypes.c_void_p), ("n", ctypes.c_int64), ("counts", ctypes.c_void_p),
+                ("idx", ctypes.c_void_p), ("dist2", ctypes.c_void_p)]
+
+
+_vp, _i64, _int, _f32, _u32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_float, ctypes.c_uint
+_sigs = {
+    "frnn_version": ([], ctypes.c_char_p),
+    "frnn_create": ([ctypes.POINTER(_vp), _vp, ctypes.c_size_t], _int),
+    "frnn_destroy": ([_vp], _int),
+    "frnn_build_grid": ([_vp, _vp, _i64, _int, _f32, ctypes.POINTER(_vp)], _int),
+    "frnn_grid_destroy": ([_vp], _int),
+    "frnn_query": ([_vp, _vp, _vp, _i64, _f32, _int, _u32, _vp, _vp, _vp], _int),
+    "frnn_query_batched": ([_vp, ctypes.POINTER(frnn_event), _int, _int, _f32, _int, _u32], _int),
+    "frnn_self_query_host": ([_vp, _vp, _i64, _int, _f32, _int, _u32, _vp, _vp, _vp], _int),
+    "frnn_sync": ([_vp], _int),
+    "frnn_last_error": ([_vp], ctypes.c_char_p),
+    "frnn_set_option": ([_vp, _int, _i64], _int),
+    "frnn_get_option": ([_vp, _int, ctypes.POINTER(_i64)], _int),
+}
+for _name, (_args, _res) in _sigs.items():
+    _fn = getattr(_lib, _name)
+    _fn.argtypes = _args
+    _fn.restype = _res
+    globals()[_name] = _fn
+
+
+class FrnnError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+def _check(ctx, status: int):
+    if status != FRNN_OK:
+        msg = frnn_last_error(ctx)
+        raise FrnnError(status, msg.decode() if msg else "")
+
+
+def version() -> str:
+    return frnn_version().decode()
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _dev_f32(t, name):
+    torch = _torch()
+    if not isinstance(t, torch.Tensor) or t.device.type != "cuda":
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != torch.float32 or t.dim() != 2 or not t.is_contiguous():
+        raise TypeError(f"{name} must be a contiguous float32 [N, D] tensor")
+    return t
+
+
+class Grid:
+    """A built grid (owns the library's frnn_grid)."""
+
+    def __init__(self, ctx: "Context", handle, points, r: float):
+        self.ctx = ctx
+        self.handle = handle
+        self.points = points   # keeps the caller's tensor alive for self-queries
+        self.r = r
+
+    def close(self):
+        if self.handle:
+            frnn_grid_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Context:
+    """A library context bound to a CUDA stream (default: torch's current)."""
+
+    def __init__(self, stream=None, budget_bytes: int = 0):
+        torch = _torch()
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        h = _vp()
+        rc = frnn_create(ctypes.byref(h), _vp(stream.cuda_stream), budget_bytes)
+        _check(None, rc)
+        self.handle = h
+
+    def close(self):
+        if getattr(self, "handle", None):
+            frnn_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def set_option(self, opt: int, value: int):
+        _check(self.handle, frnn_set_option(self.handle, opt, int(value)))
+
+    def get_option(self, opt: int) -> int:
+        v = _i64(0)
+        _check(self.handle, frnn_get_option(self.handle, opt, ctypes.byref(v)))
+        return int(v.value)
+
+    def build_grid(self, points, r: float, grid: Grid | None = None) -> Grid:
+        """frnn_build_grid on a [N, D] float32 CUDA tensor (rebuilds ``grid``
+        in place when given and large enough)."""
+        _dev_f32(points, "points")
+        old = grid.handle.value if (grid is not None and grid.handle) else None
+        h = _vp(old)
+        rc = frnn_build_grid(self.handle, _vp(points.data_ptr()), points.shape[0],
+                             points.shape[1], float(r), ctypes.byref(h))
+        _check(self.handle, rc)
+        if old is not None and h.value == old:
+            grid.points, grid.r = points, r
+            return grid
+        return Grid(self, h, points, r)
+
+    def query(self, grid: Grid, queries, r: float, K: int, self_query: bool = True,
+              path: str = "auto", out=None):
+        """frnn_query; returns (counts [M] int32, idx [M,K] int32, dist2 [M,K] f32)."""
+        torch = _torch()
+        _dev_f32(queries, "queries")
+        M = queries.shape[0]
+        if out is None:
+            dev = queries.device
+            out = (torch.empty(M, dtype=torch.int32, device=dev),
+                   torch.empty((M, K), dtype=torch.int32, device=dev),
+                   torch.empty((M, K), dtype=torch.float32, device=dev))
+        counts, idx, dist2 = out
+        flags = PATHS[path] | (FRNN_SELF_QUERY if self_query else 0)
+        rc = frnn_query(self.handle, grid.handle, _vp(queries.data_ptr()), M, float(r), int(K),
+                        flags, _vp(counts.data_ptr()), _vp(idx.data_ptr()),
+                        _vp(dist2.data_ptr()))
+        _check(self.handle, rc)
+        return counts, idx, dist2
+
+    def self_query(self, points, r: float, K: int, path: str = "auto", out=None):
+        """Build a grid on ``points`` and self-query it (one call each)."""
+        g = self.build_grid(points, r)
+        res = self.query(g, points, r, K, True, path, out)
+        self._last_grid = g
+        return res
+
+    def query_batched(self, events, r: float, K: int, path: str = "auto", outs=None):
+        """frnn_query_batched over a list of [n_e, D] tensors (self-queries)."""
+        torch = _torch()
+        n = len(events)
+        if n == 0:
+            return []
+        D = events[0].shape[1]
+        if outs is None:
+            outs = []
+            for p in events:
+                _dev_f32(p, "event points")
+                m = p.shape[0]
+                outs.append((torch.empty(m, dtype=torch.int32, device=p.device),
+                             torch.empty((m, K), dtype=torch.int32, device=p.device),
+                             torch.empty((m, K), dtype=torch.float32, device=p.device)))
+        arr = (frnn_event * n)()
+        for e, (p, (c, i, d)) in enumerate(zip(events, outs)):
+            _dev_f32(p, "event points")
+            arr[e] = frnn_event(p.data_ptr(), p.shape[0], c.data_ptr(), i.data_ptr(), d.data_ptr())
+        self._batch_keep = (events, outs)
+        rc = frnn_query_batched(self.handle, arr, n, D, float(r), int(K), PATHS[path])
+        _check(self.handle, rc)
+        return outs
+
+    def self_query_host(self, points_np, r: float, K: int, path: str = "auto", out=None):
+        """frnn_self_query_host on NumPy arrays (copies in and out, synchronous)."""
+        import numpy as np
+        p = np.ascontiguousarray(points_np, dtype=np.float32)
+        N, D = p.shape
+        if out is None:
+            out = (np.empty(N, np.int32), np.empty((N, K), np.int32),
+                   np.empty((N, K), np.float32))
+        c, i, d = out
+        rc = frnn_self_query_host(self.handle, _vp(p.ctypes.data), N, D, float(r), int(K),
+                                  PATHS[path], _vp(c.ctypes.data), _vp(i.ctypes.data),
+                                  _vp(d.ctypes.data))
+        _check(self.handle, rc)
+        return out
+
+    def sync(self):
+        """frnn_sync: wait and raise the device status (non-finite input, ...)."""
+        _check(self.handle, frnn_sync(self.handle))

@@ -1,0 +1,64 @@
+"""Host-side checks that need no GPU: the C-ABI library builds, loads and
+exports every entry point include/frnn.h declares, and the binding wraps each."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from conftest import ROOT
+
+
+def _declared():
+    with open(os.path.join(ROOT, "include", "frnn.h")) as f:
+        src = f.read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = re.findall(r"\b(frnn_[a-z_0-9]+)\s*\(", src)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def lib_path():
+    from paper_2609_31980_gb300 import build
+    return build.build()
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for required in ("frnn_create", "frnn_destroy", "frnn_build_grid", "frnn_grid_destroy",
+                     "frnn_query", "frnn_query_batched", "frnn_sync", "frnn_last_error"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(lib_path):
+    lib = ctypes.CDLL(lib_path)
+    missing = [n for n in _declared() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_binding_wraps_every_declared_symbol(lib_path):
+    from paper_2609_31980_gb300 import frnn
+    assert sorted(frnn.EXPORTED) == _declared()
+    for n in _declared():
+        assert callable(getattr(frnn, n))
+    assert re.match(r"^\d+\.\d+\.\d+$", frnn.version())
+
+
+def test_create_without_gpu_reports_an_error_code(lib_path):
+    """With no usable CUDA device frnn_create must fail cleanly (no crash)."""
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    from paper_2609_31980_gb300 import frnn
+    h = ctypes.c_void_p()
+    rc = frnn.frnn_create(ctypes.byref(h), None, 0)
+    assert rc != 0 and not h.value
+    assert frnn.frnn_last_error(None)
+
+
+def test_null_context_is_rejected(lib_path):
+    from paper_2609_31980_gb300 import frnn
+    assert frnn.frnn_sync(None) == -1
+    assert frnn.frnn_destroy(None) == 0
+    assert frnn.frnn_grid_destroy(None) == 0
+    assert frnn.frnn_build_grid(None, None, 0, 3, 0.1, None) == -1

@@ -1,0 +1,256 @@
+"""GPU path vs the CPU oracle, element by element (bit-exact).
+
+Counts and indices must be equal; distances must match to 0 ULP (compared as
+bit patterns).  Inputs come from the seeded generators; full-size workloads are
+compared on sampled rows (the oracle computes each sampled row by brute force
+against all N points), smaller ones on every row.
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle
+from paper_2609_31980_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("needs a GPU")
+    from paper_2609_31980_gb300 import frnn
+    c = frnn.Context()
+    yield c
+    c.close()
+
+
+def _gpu_self(ctx, pts, r, K, path="grid"):
+    import torch
+    t = torch.from_numpy(np.ascontiguousarray(pts, np.float32)).cuda()
+    counts, idx, d2 = ctx.self_query(t, r, K, path=path)
+    ctx.sync()
+    return counts.cpu().numpy(), idx.cpu().numpy(), d2.cpu().numpy()
+
+
+def _assert_rows_equal(got, want, rows=None):
+    gc, gi, gd = got
+    wc, wi, wd = want[:3]
+    if rows is not None:
+        gc, gi, gd = gc[rows], gi[rows], gd[rows]
+    bad = np.flatnonzero((gc != wc) | (gi != wi).any(1) |
+                         (gd.view(np.uint32) != wd.view(np.uint32)).any(1))
+    if len(bad):
+        b = bad[0]
+        raise AssertionError(
+            f"{len(bad)} rows differ; first row {b if rows is None else rows[b]}: "
+            f"count {gc[b]} vs {wc[b]}\n gpu idx {gi[b][:12]}\n ora idx {wi[b][:12]}\n"
+            f" gpu d2 {gd[b][:6]}\n ora d2 {wd[b][:6]}")
+
+
+def _sample_rows(n, k, seed):
+    g = np.random.default_rng(seed)
+    return np.sort(g.choice(n, size=min(k, n), replace=False))
+
+
+def test_uniform_4096x3_full(ctx):
+    w = synth.config1()
+    got = _gpu_self(ctx, w.points, w.r, w.K)
+    want = oracle.self_query(w.points, w.r, w.K)
+    _assert_rows_equal(got, want)
+    assert got[0].sum() > 4000
+
+
+def test_event_30k_x8_full(ctx):
+    pts = synth.clustered(800, 30, 6000, 8, 0.02, seed=21)
+    got = _gpu_self(ctx, pts, 0.1, 64)
+    want = oracle.self_query(pts, 0.1, 64)
+    _assert_rows_equal(got, want)
+
+
+def test_event_300k_x8_sampled(ctx):
+    w = synth.config2()
+    got = _gpu_self(ctx, w.points, w.r, w.K)
+    rows = _sample_rows(len(w.points), 3000, 22)
+    want = oracle.self_query(w.points, w.r, w.K, rows=rows)
+    _assert_rows_equal(got, want, rows)
+    # symmetry holds at any size: j in N(i) <=> i in N(j) with identical bits
+    c, i, d = got
+    assert c.max() < w.K
+    sel = rows[:200]
+    for q in sel:
+        for e in range(c[q]):
+            j = i[q, e]
+            pos = np.flatnonzero(i[j, :c[j]] == q)
+            assert len(pos) == 1 and d[j, pos[0]].view(np.uint32) == d[q, e].view(np.uint32)
+
+
+def test_event_40k_x12_full(ctx):
+    pts = synth.clustered(1280, 25, 8000, 12, 0.025, seed=23)
+    got = _gpu_self(ctx, pts, 0.12, 128)
+    want = oracle.self_query(pts, 0.12, 128)
+    _assert_rows_equal(got, want)
+
+
+def test_event_500k_x12_sampled(ctx):
+    w = synth.config3()
+    got = _gpu_self(ctx, w.points, w.r, w.K)
+    rows = _sample_rows(len(w.points), 1500, 24)
+    want = oracle.self_query(w.points, w.r, w.K, rows=rows)
+    _assert_rows_equal(got, want, rows)
+
+
+@pytest.mark.parametrize("D", [1, 2, 3, 4, 5, 8, 12, 16])
+def test_dimensions(ctx, D):
+    pts = synth.clustered(60, 20, 300, D, 0.03, seed=100 + D)
+    r = 0.08 * np.sqrt(D)
+    got = _gpu_self(ctx, pts, r, 48)
+    _assert_rows_equal(got, oracle.self_query(pts, r, 48))
+
+
+@pytest.mark.parametrize("N", [0, 1, 2, 31, 32, 33, 65])
+def test_small_sizes(ctx, N):
+    pts = synth.uniform(N, 3, seed=200 + N) if N else np.zeros((0, 3), np.float32)
+    got = _gpu_self(ctx, pts, 0.4, 8)
+    want = oracle.self_query(pts, 0.4, 8)
+    _assert_rows_equal(got, want)
+
+
+@pytest.mark.parametrize("K", [1, 2, 31, 32, 33, 64, 128, 129, 1024])
+def test_k_values_with_truncation(ctx, K):
+    # dense: degrees well above small K, some above 128
+    pts = synth.clustered(10, 150, 200, 3, 0.02, seed=300)
+    got = _gpu_self(ctx, pts, 0.05, K)
+    want = oracle.self_query(pts, 0.05, K)
+    assert (want[3] > K).any() or K >= 1024
+    _assert_rows_equal(got, want)
+
+
+def test_all_points_in_one_cell(ctx):
+    pts = synth.uniform(3000, 3, seed=301, lo=0.0, hi=0.01)
+    got = _gpu_self(ctx, pts, 0.05, 32)
+    _assert_rows_equal(got, oracle.self_query(pts, 0.05, 32))
+
+
+def test_duplicates(ctx):
+    base = synth.uniform(50, 4, seed=302)
+    pts = np.repeat(base, 7, axis=0)
+    got = _gpu_self(ctx, pts, 0.2, 16)
+    _assert_rows_equal(got, oracle.self_query(pts, 0.2, 16))
+    assert (got[2][:, 0].view(np.uint32) == 0).all()
+
+
+def test_points_exactly_at_r_and_on_cell_boundaries(ctx):
+    """Integer lattice scaled by 2^-3: many pairs at exactly r, and with
+    r = 2 steps the cell edge r(1+2^-10) puts lattice planes near cell edges;
+    plus copies shifted by +-1 ulp."""
+    side = 9
+    g = np.stack(np.meshgrid(*[np.arange(side)] * 3, indexing="ij"), -1).reshape(-1, 3)
+    pts = (g * 0.125).astype(np.float32)
+    up = np.nextafter(pts, np.float32(np.inf))
+    dn = np.nextafter(pts, np.float32(-np.inf))
+    allp = np.concatenate([pts, up[::3], dn[1::3]]).astype(np.float32)
+    perm = np.random.default_rng(303).permutation(len(allp))
+    allp = allp[perm]
+    for r in (0.25, 0.125, float(np.nextafter(np.float32(0.25), np.float32(0)))):
+        got = _gpu_self(ctx, allp, r, 128)
+        _assert_rows_equal(got, oracle.self_query(allp, r, 128))
+
+
+def test_cross_set_queries(ctx):
+    import torch
+    refs = synth.clustered(200, 20, 2000, 8, 0.03, seed=304)
+    qs = np.concatenate([synth.clustered(50, 10, 500, 8, 0.03, seed=305),
+                         synth.uniform(100, 8, seed=306, lo=-1.5, hi=1.5)])
+    tr = torch.from_numpy(refs).cuda()
+    tq = torch.from_numpy(qs).cuda()
+    g = ctx.build_grid(tr, 0.15)
+    c, i, d = ctx.query(g, tq, 0.15, 40, self_query=False, path="grid")
+    ctx.sync()
+    got = (c.cpu().numpy(), i.cpu().numpy(), d.cpu().numpy())
+    _assert_rows_equal(got, oracle.frnn(qs, refs, 0.15, 40))
+    # a smaller radius on the same grid
+    c, i, d = ctx.query(g, tq, 0.07, 40, self_query=False, path="grid")
+    ctx.sync()
+    _assert_rows_equal((c.cpu().numpy(), i.cpu().numpy(), d.cpu().numpy()),
+                       oracle.frnn(qs, refs, 0.07, 40))
+
+
+@pytest.mark.parametrize("m,axes", [(2, 0), (1, 1), (2, 1)])
+def test_grid_options_do_not_change_results(ctx, m, axes):
+    from paper_2609_31980_gb300 import frnn
+    pts = synth.clustered(300, 30, 3000, 8, 0.02, seed=307)
+    want = oracle.self_query(pts, 0.1, 64)
+    ctx.set_option(frnn.FRNN_OPT_CELL_MULT, m)
+    ctx.set_option(frnn.FRNN_OPT_GRID_AXES, axes)
+    try:
+        _assert_rows_equal(_gpu_self(ctx, pts, 0.1, 64), want)
+    finally:
+        ctx.set_option(frnn.FRNN_OPT_CELL_MULT, 1)
+        ctx.set_option(frnn.FRNN_OPT_GRID_AXES, 0)
+
+
+@pytest.mark.parametrize("e", [1, 3, 4, 6])
+def test_exit_dims_do_not_change_results(ctx, e):
+    from paper_2609_31980_gb300 import frnn
+    pts = synth.clustered(300, 30, 3000, 8, 0.02, seed=308)
+    want = oracle.self_query(pts, 0.1, 64)
+    ctx.set_option(frnn.FRNN_OPT_EXIT_DIMS, e)
+    try:
+        _assert_rows_equal(_gpu_self(ctx, pts, 0.1, 64), want)
+    finally:
+        ctx.set_option(frnn.FRNN_OPT_EXIT_DIMS, 0)
+
+
+def test_grid_rebuild_in_place(ctx):
+    import torch
+    a = synth.uniform(5000, 3, seed=309)
+    b = synth.uniform(3000, 3, seed=310)
+    ta, tb = torch.from_numpy(a).cuda(), torch.from_numpy(b).cuda()
+    g = ctx.build_grid(ta, 0.05)
+    g2 = ctx.build_grid(tb, 0.05, grid=g)
+    assert g2 is g
+    c, i, d = ctx.query(g, tb, 0.05, 16, self_query=True, path="grid")
+    ctx.sync()
+    _assert_rows_equal((c.cpu().numpy(), i.cpu().numpy(), d.cpu().numpy()),
+                       oracle.self_query(b, 0.05, 16))
+
+
+def test_nonfinite_input_is_reported(ctx):
+    import torch
+    from paper_2609_31980_gb300 import frnn
+    pts = synth.uniform(1000, 3, seed=311)
+    pts[17, 1] = np.nan
+    t = torch.from_numpy(pts).cuda()
+    c, i, d = ctx.self_query(t, 0.05, 8, path="grid")
+    with pytest.raises(frnn.FrnnError) as ei:
+        ctx.sync()
+    assert ei.value.status == -5
+    assert (c.cpu().numpy() == 0).all()
+    ctx.sync()   # status is cleared
+
+
+def test_host_buffer_path(ctx):
+    w = synth.config1()
+    c, i, d = ctx.self_query_host(w.points, w.r, w.K, path="grid")
+    _assert_rows_equal((c, i, d), oracle.self_query(w.points, w.r, w.K))
+
+
+def test_invalid_arguments(ctx):
+    import torch
+    from paper_2609_31980_gb300 import frnn
+    t = torch.zeros((10, 3), device="cuda")
+    g = ctx.build_grid(t, 0.1)
+    with pytest.raises(frnn.FrnnError):
+        ctx.query(g, t, 0.1, 0)            # K = 0
+    with pytest.raises(frnn.FrnnError):
+        ctx.query(g, t, 0.1, 2000)         # K too large
+    with pytest.raises(frnn.FrnnError):
+        ctx.query(g, t, 0.2, 4)            # r above the grid's radius
+    with pytest.raises(frnn.FrnnError):
+        ctx.query(g, t.clone(), 0.1, 4, self_query=True)   # not the grid's own points
+    with pytest.raises(frnn.FrnnError):
+        ctx.query(g, t, 0.1, 4, path="tc")  # D < 8
+    with pytest.raises(frnn.FrnnError):
+        ctx.build_grid(torch.zeros((4, 17), device="cuda"), 0.1)
+    ctx.sync()
