@@ -81,8 +81,9 @@ const char* frnn_version(void);
  */
 frnn_status frnn_create(frnn_ctx** out, void* cuda_stream, size_t mem_budget_bytes);
 
-/* Synchronise the context's stream and free everything it owns (grids built
- * through it stay valid until frnn_grid_destroy).  NULL is accepted. */
+/* Synchronise the context's stream and free everything it owns.  Grids built
+ * through it are detached: they can no longer be queried, and must still be
+ * released with frnn_grid_destroy.  NULL is accepted. */
 frnn_status frnn_destroy(frnn_ctx* ctx);
 
 /*

@@ -3,6 +3,7 @@
 #include <cmath>
 #include <cstring>
 #include <string>
+#include <unordered_set>
 #include <vector>
 
 #include "frnn_host.h"
@@ -39,6 +40,8 @@ struct frnn_ctx {
     frnn_grid* host_grid = nullptr;   // grid of the host-buffer path
     void* hp_buf = nullptr;   // device buffers of the host-buffer path
     size_t hp_bytes = 0;
+    // live grids built through this context (detached when it is destroyed)
+    std::unordered_set<frnn_grid*> grids;
     // batched graph cache
     cudaGraphExec_t graph = nullptr;
     std::vector<frnn_event> g_ev;
@@ -163,6 +166,9 @@ frnn_status frnn_grid_destroy(frnn_grid* grid) {
     if (grid->ctx) {
         cudaStreamSynchronize(grid->ctx->stream);
         grid->ctx->held -= std::min(grid->ctx->held, grid->g.bytes);
+        grid->ctx->grids.erase(grid);
+    } else {
+        cudaDeviceSynchronize();   // context gone: its stream may still hold work on the buffers
     }
     grid_free(grid->g);
     delete grid;
@@ -176,10 +182,14 @@ frnn_status frnn_destroy(frnn_ctx* ctx) {
     if (ctx->host_grid) {
         frnn_grid* g = ctx->host_grid;
         ctx->host_grid = nullptr;
+        ctx->grids.erase(g);
         g->ctx = nullptr;
         grid_free(g->g);
         delete g;
     }
+    // grids the caller still holds stay valid for frnn_grid_destroy only
+    for (frnn_grid* g : ctx->grids) g->ctx = nullptr;
+    ctx->grids.clear();
     grid_free(ctx->qset);
     grid_free(ctx->batch);
     if (ctx->hp_buf) cudaFree(ctx->hp_buf);
@@ -204,11 +214,13 @@ frnn_status frnn_build_grid(frnn_ctx* ctx, const float* refs, int64_t N, int D, 
         g = new frnn_grid();
         g->ctx = ctx;
         g->D = D;
+        ctx->grids.insert(g);
     }
     frnn_status s = alloc_accounted(ctx, g->g, 1, &N, D, nullptr);
     if (s != FRNN_OK) {
         if (fresh) {
             ctx->held -= std::min(ctx->held, g->g.bytes);
+            ctx->grids.erase(g);
             grid_free(g->g);
             delete g;
         }
