@@ -42,7 +42,11 @@ struct frnn_ctx {
     size_t hp_bytes = 0;
     // live grids built through this context (detached when it is destroyed)
     std::unordered_set<frnn_grid*> grids;
-    // batched graph cache
+    // batched graph cache; captured and replayed on an internal stream fenced
+    // to the context's stream with events (the legacy default stream cannot
+    // be captured)
+    cudaStream_t gstream = nullptr;
+    cudaEvent_t g_in = nullptr, g_out = nullptr;
     cudaGraphExec_t graph = nullptr;
     std::vector<frnn_event> g_ev;
     int g_D = 0, g_K = 0;
@@ -179,6 +183,10 @@ frnn_status frnn_destroy(frnn_ctx* ctx) {
     if (!ctx) return FRNN_OK;
     cudaStreamSynchronize(ctx->stream);
     if (ctx->graph) cudaGraphExecDestroy(ctx->graph);
+    if (ctx->gstream) cudaStreamSynchronize(ctx->gstream);
+    if (ctx->gstream) cudaStreamDestroy(ctx->gstream);
+    if (ctx->g_in) cudaEventDestroy(ctx->g_in);
+    if (ctx->g_out) cudaEventDestroy(ctx->g_out);
     if (ctx->host_grid) {
         frnn_grid* g = ctx->host_grid;
         ctx->host_grid = nullptr;
@@ -317,7 +325,7 @@ static bool same_events(const frnn_ctx* c, const frnn_event* ev, int n) {
 }
 
 static frnn_status enqueue_batched(frnn_ctx* ctx, const frnn_event* ev, int n_events, int D,
-                                   float r, int K, bool capturing) {
+                                   float r, int K, bool capturing, cudaStream_t st) {
     std::vector<const float*> refs(n_events);
     for (int e = 0; e < n_events; ++e) {
         refs[e] = ev[e].pts;
@@ -330,8 +338,8 @@ static frnn_status enqueue_batched(frnn_ctx* ctx, const frnn_event* ev, int n_ev
     o.m = ctx->cell_mult;
     o.axes_mode = ctx->axes_mode;
     std::string err;
-    frnn_status s = enqueue_build(ctx->batch, refs.data(), o, nullptr, ctx->d_status,
-                                  ctx->stream, capturing, err);
+    frnn_status s = enqueue_build(ctx->batch, refs.data(), o, nullptr, ctx->d_status, st,
+                                  capturing, err);
     if (s != FRNN_OK) return fail(ctx, s, err);
     QueryLaunch q{};
     q.qset = &ctx->batch;
@@ -342,8 +350,20 @@ static frnn_status enqueue_batched(frnn_ctx* ctx, const frnn_event* ev, int n_ev
     q.exit_dims = ctx->exit_dims;
     q.d_status = ctx->d_status;
     q.num_sms = ctx->num_sms;
-    s = enqueue_grid_query(q, ctx->stream, err);
+    s = enqueue_grid_query(q, st, err);
     if (s != FRNN_OK) return fail(ctx, s, err);
+    return FRNN_OK;
+}
+
+// Replay the captured graph on the internal stream, ordered after the work
+// already on the context's stream and before anything enqueued there later.
+static frnn_status launch_graph(frnn_ctx* ctx) {
+    cudaError_t e = cudaEventRecord(ctx->g_in, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->gstream, ctx->g_in, 0);
+    if (e == cudaSuccess) e = cudaGraphLaunch(ctx->graph, ctx->gstream);
+    if (e == cudaSuccess) e = cudaEventRecord(ctx->g_out, ctx->gstream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->stream, ctx->g_out, 0);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "graph launch");
     return FRNN_OK;
 }
 
@@ -372,11 +392,7 @@ frnn_status frnn_query_batched(frnn_ctx* ctx, const frnn_event* ev, int n_events
     const bool hit = ctx->use_graph && ctx->graph && same_events(ctx, ev, n_events) &&
                      ctx->g_D == D && ctx->g_K == K && ctx->g_r == r && ctx->g_flags == flags &&
                      std::memcmp(opts, ctx->g_opts, sizeof(opts)) == 0;
-    if (hit) {
-        cudaError_t e = cudaGraphLaunch(ctx->graph, ctx->stream);
-        if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaGraphLaunch");
-        return FRNN_OK;
-    }
+    if (hit) return launch_graph(ctx);
     if (ctx->graph) {
         cudaGraphExecDestroy(ctx->graph);
         ctx->graph = nullptr;
@@ -384,14 +400,22 @@ frnn_status frnn_query_batched(frnn_ctx* ctx, const frnn_event* ev, int n_events
     }
     frnn_status s = alloc_accounted(ctx, ctx->batch, n_events, n.data(), D, nullptr);
     if (s != FRNN_OK) return s;
-    if (!ctx->use_graph) return enqueue_batched(ctx, ev, n_events, D, r, K, false);
-    // make sure the pinned table mirror is free before capturing its upload
+    if (!ctx->use_graph) return enqueue_batched(ctx, ev, n_events, D, r, K, false, ctx->stream);
+    if (!ctx->gstream) {
+        cudaError_t e = cudaStreamCreateWithFlags(&ctx->gstream, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->g_in, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->g_out, cudaEventDisableTiming);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "graph stream setup");
+    }
+    // the pinned table mirror must be free before its upload is captured, and
+    // the previous replay must be done before the tables change
+    cudaStreamSynchronize(ctx->gstream);
     if (ctx->batch.h_pinned_free) cudaEventSynchronize(ctx->batch.h_pinned_free);
     cudaGraph_t graph = nullptr;
-    cudaError_t e = cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal);
+    cudaError_t e = cudaStreamBeginCapture(ctx->gstream, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaStreamBeginCapture");
-    s = enqueue_batched(ctx, ev, n_events, D, r, K, true);
-    e = cudaStreamEndCapture(ctx->stream, &graph);
+    s = enqueue_batched(ctx, ev, n_events, D, r, K, true, ctx->gstream);
+    e = cudaStreamEndCapture(ctx->gstream, &graph);
     if (s != FRNN_OK) {
         if (graph) cudaGraphDestroy(graph);
         return s;
@@ -408,9 +432,7 @@ frnn_status frnn_query_batched(frnn_ctx* ctx, const frnn_event* ev, int n_events
     ctx->g_r = r;
     ctx->g_flags = flags;
     std::memcpy(ctx->g_opts, opts, sizeof(opts));
-    e = cudaGraphLaunch(exec, ctx->stream);
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaGraphLaunch");
-    return FRNN_OK;
+    return launch_graph(ctx);
 }
 
 frnn_status frnn_self_query_host(frnn_ctx* ctx, const float* refs_host, int64_t N, int D,

@@ -178,10 +178,13 @@ __global__ void __launch_bounds__(kBuildPtsPerBlock) k_bbox(const EventHdr* hdr,
 // and is lowered until the bound holds with 2^-20 to spare, every axis has at
 // most 1024 cells, and the event's cell count fits its capacity.
 __global__ void k_params(EventHdr* hdr, int E, int D, const int32_t* bbox, float r, int m,
-                         int axes_mode) {
+                         int axes_mode, int32_t* counts) {
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= E) return;
     EventHdr& h = hdr[e];
+    // the last cell-array entry of the event counts its pair padding slot, so
+    // the next event's slots start on a pair boundary
+    counts[h.cell_off + h.cell_cap] = (int32_t)(h.n & 1);
     const int32_t* bb = bbox + (int64_t)e * kBBoxStride;
     const int naxes = D < 3 ? D : 3;
     h.naxes = naxes;
@@ -246,20 +249,26 @@ __global__ void k_params(EventHdr* hdr, int E, int D, const int32_t* bbox, float
         ih = __double2float_rd((double)ih * 0.9);
         if (!(ih > 0.f)) { ih = 0.f; dims[0] = dims[1] = dims[2] = 1; break; }
     }
-    h.inv_h = ih;
     int64_t cells = 1;
     for (int a = 0; a < 3; ++a) {
         h.dims[a] = a < naxes ? dims[a] : 1;
         cells *= h.dims[a];
     }
+    if (cells > h.cell_cap) {   // unreachable in practice; one cell is always safe
+        ih = 0.f;
+        cells = 1;
+        for (int a = 0; a < 3; ++a) h.dims[a] = 1;
+    }
+    h.inv_h = ih;
     h.ncells = (int32_t)cells;
 }
 
 // Cross-set binning: take the reference grid's parameters for each event.
-__global__ void k_copy_params(EventHdr* dst, const EventHdr* src, int E) {
+__global__ void k_copy_params(EventHdr* dst, const EventHdr* src, int E, int32_t* counts) {
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= E) return;
     EventHdr& d = dst[e];
+    counts[d.cell_off + d.cell_cap] = (int32_t)(d.n & 1);
     const EventHdr& s = src[e];
     d.naxes = s.naxes;
     d.m = s.m;
@@ -315,6 +324,13 @@ __global__ void __launch_bounds__(kBuildPtsPerBlock) k_scatter(const EventHdr* h
     const EventHdr& h = hdr[e];
     const int64_t p0 = (int64_t)(blockIdx.x - blk_start[e]) * kBuildPtsPerBlock;
     const int np = (int)min((int64_t)kBuildPtsPerBlock, h.n - p0);
+    if (p0 == 0 && threadIdx.x == 0 && (h.n & 1)) {
+        // pair padding slot: NaN coordinates are never within any radius
+        const int64_t slot = h.pt_off + h.n;
+        for (int k = 0; k < DP; ++k) pts[pair_index(slot, k, DP)] = __int_as_float(0x7fc00000);
+        perm[slot] = -1;
+        cell[slot] = 0;
+    }
     if (np > 0) stage_floats(sm, h.refs + p0 * D, np * D);
     __syncthreads();
     const int i = threadIdx.x;
@@ -323,16 +339,8 @@ __global__ void __launch_bounds__(kBuildPtsPerBlock) k_scatter(const EventHdr* h
     const int c = cid[gi];
     const int64_t slot = (int64_t)cstart[h.cell_off + c] + rnk[gi];
     const float* p = sm + i * D;
-    float4* dst = reinterpret_cast<float4*>(pts + slot * DP);
-    for (int k4 = 0; k4 < DP / 4; ++k4) {
-        float v[4];
-#pragma unroll
-        for (int t = 0; t < 4; ++t) {
-            int k = 4 * k4 + t;
-            v[t] = k < D ? p[k] : 0.f;
-        }
-        dst[k4] = make_float4(v[0], v[1], v[2], v[3]);
-    }
+    float* dst = pts + pair_index(slot, 0, DP);
+    for (int k = 0; k < DP; ++k) dst[2 * k] = k < D ? p[k] : 0.f;
     perm[slot] = (int32_t)(p0 + i);
     cell[slot] = c;
 }
@@ -533,7 +541,7 @@ frnn_status grid_alloc(GridBufs& g, int E, const int64_t* n, int D, std::string&
         h.cell_cap = (int32_t)cap;
         g.h_blk_start[e] = (int32_t)nblk;
         g.h_cell_off[e] = L;
-        n_total += n[e];
+        n_total += (n[e] + 1) & ~(int64_t)1;   // pair-aligned event regions
         L += cap + 1;
         task_cap += n[e] / kTaskQueries + cap + 2;
         nblk += std::max<int64_t>(1, ceil_div(n[e], kBuildPtsPerBlock));
@@ -669,11 +677,12 @@ frnn_status enqueue_build(GridBufs& g, const float* const* refs, const BuildOpts
         g.cstart, g.L, g.bbox, E, g.scalars, bbmin, bbmax);
     const size_t smem_pts = sizeof(float) * kBuildPtsPerBlock * D;
     if (params_from) {
-        k_copy_params<<<blocks_for(E, 128), 128, 0, st>>>(g.hdr, params_from->hdr, E);
+        k_copy_params<<<blocks_for(E, 128), 128, 0, st>>>(g.hdr, params_from->hdr, E, g.cstart);
     } else {
         k_bbox<<<(unsigned)g.nblk, kBuildPtsPerBlock, smem_pts, st>>>(g.hdr, g.blk_start, E, D,
                                                                      g.bbox, d_status);
-        k_params<<<blocks_for(E, 128), 128, 0, st>>>(g.hdr, E, D, g.bbox, o.r, o.m, o.axes_mode);
+        k_params<<<blocks_for(E, 128), 128, 0, st>>>(g.hdr, E, D, g.bbox, o.r, o.m, o.axes_mode,
+                                                      g.cstart);
     }
     k_cellid<<<(unsigned)g.nblk, kBuildPtsPerBlock, smem_pts, st>>>(
         g.hdr, g.blk_start, E, D, g.cstart, g.cid, g.rnk, params_from ? 1 : 0, d_status);

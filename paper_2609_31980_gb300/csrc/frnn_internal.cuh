@@ -25,9 +25,17 @@ constexpr int kStatusCapacity = 4;
 // itself blocks for a hardware-defined interval): far above any legitimate wait.
 constexpr uint32_t kSpinLimit = 1u << 24;
 
-// Padded point row: D floats rounded up to a multiple of 4 (16 bytes), so every
-// sorted point starts on a 16-byte boundary (bulk-copy and float4 alignment).
+// Padded point row: D floats rounded up to a multiple of 4 (16 bytes).
 __host__ __device__ constexpr int padded_dim(int D) { return (D + 3) & ~3; }
+
+// Cell-sorted points are stored pair-interleaved: slots 2p and 2p+1 share a
+// block of 2*DP floats laid out as [s0.d0, s1.d0, s0.d1, s1.d1, ...], so one
+// 16-byte load yields two dimensions of two candidates, the operand layout of
+// the packed f32x2 arithmetic.  Every event's slot range starts on a pair
+// boundary (odd events get one padding slot with NaN coordinates).
+__host__ __device__ constexpr int64_t pair_index(int64_t slot, int k, int DP) {
+    return (slot >> 1) * 2 * DP + 2 * k + (slot & 1);
+}
 
 // Per-event grid header (device-resident, one per event of a build).
 struct EventHdr {
@@ -82,6 +90,7 @@ struct QueryArgs {
     int32_t* idx;
     float* dist2;
     float r2;                    // fl(r * r)
+    float r2_screen;             // r2 (1 + 2^-16) rounded up: conservative screen bound
     int32_t K;
     int32_t self;                // 1: query slot == reference slot is excluded
     int32_t D;

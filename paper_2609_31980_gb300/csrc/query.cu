@@ -16,164 +16,135 @@
 //     lane 0 copies into the warp's shared-memory ring with cp.async.bulk,
 //     completion tracked by one mbarrier per buffer (prefetch depth kNBuf-1);
 //   * every lane screens every candidate of the tile (broadcast shared loads):
-//     warp-uniform control flow, no per-lane candidate lists;
+//     warp-uniform control flow.  Points are stored pair-interleaved, so each
+//     16-byte shared load gives two dimensions of two candidates and the
+//     packed f32x2 instructions evaluate two candidates per instruction, each
+//     lane rounded exactly as the scalar contract;
 //   * exact early rejection: after the first `EXIT` dimensions the warp votes;
 //     partial sums never decrease (round-to-nearest of non-negative terms), so
 //     if every lane's partial sum is already > r2 the candidate is rejected
 //     for all of them without changing any verdict (the paper's "roundoff-safe
 //     early rejection", Sec. 6).  Gridded axes are the last ones by default,
 //     so the first dimensions are the ungridded, most selective ones;
-//   * survivors are appended (d2, original index) straight into the query's
-//     output row (the original index is looked up only for survivors: the
+//   * survivors are appended (d2, original index) to the lane's list in
+//     shared memory (the original index is looked up only for survivors: the
 //     paper's deferred lookup, Table 3);
-//   * at the end of the task the warp sorts each query's row by
-//     (d2 bits << 32 | index) with a register bitonic network (shuffles) and
-//     rewrites it coalesced with its padding.  Degree > K is rare (never in
-//     the tracking-like workloads) and goes to an exact selection kernel.
+//   * at the end of the task every lane insertion-sorts its own list by
+//     (d2, index) in parallel, keeps the first K (count = min(degree, K)),
+//     and the warp writes the rows coalesced with their padding.  Lists longer
+//     than 32 (never in the tracking-like workloads) go to an exact selection
+//     kernel; so does any degree > K beyond the list, keeping results exact
+//     for dense inputs (the paper's Sec. 5 caveat on heap-free top-K).
 #include <algorithm>
+#include <cmath>
 
 #include "frnn_host.h"
 
 namespace frnn {
 
-constexpr int kQueryWarps = 8;
-constexpr int kNBuf = 3;
+constexpr int kQueryWarps = 4;
+constexpr int kNBuf = 2;
 constexpr uint32_t kFull = 0xffffffffu;
+constexpr int kListCap = 32;      // per-lane neighbour list in shared memory
+constexpr int kListStride = 33;   // entry e of lane l at e*33 + l: conflict-free both ways
 
 template <int D>
 struct QCfg {
     static constexpr int DP = padded_dim(D);
-    // candidates per tile: about 2 KB per buffer
-    static constexpr int TILE = DP == 4 ? 128 : (DP == 8 ? 64 : (DP == 12 ? 48 : 32));
-    static constexpr int EXIT = D <= 4 ? D : 2;                         // default vote point
+    // candidate pairs per tile: about 2 KB per buffer
+    static constexpr int TILEP = DP == 4 ? 64 : (DP == 8 ? 32 : (DP == 12 ? 24 : 16));
+    static constexpr int EXIT = D <= 4 ? D : 2;   // default vote point
 };
 
-__host__ __device__ constexpr size_t query_smem_bytes(int DP, int TILE) {
-    return (size_t)kQueryWarps * kNBuf * TILE * DP * sizeof(float) +
-           (size_t)kQueryWarps * kNBuf * sizeof(uint64_t);
+__host__ __device__ constexpr size_t ring_floats(int DP, int TILEP) {
+    return (size_t)kNBuf * TILEP * 2 * DP;
+}
+__host__ __device__ constexpr size_t query_smem_bytes(int DP, int TILEP) {
+    return (size_t)kQueryWarps *
+           (ring_floats(DP, TILEP) * sizeof(float) + 2 * kListCap * kListStride * 4 +
+            kNBuf * sizeof(uint64_t));
 }
 
-// ------------------------------------------------------------- top-K sorting
+// ------------------------------------------------------------- packed f32x2
+// Two float32 lanes per instruction.  The assembler contracts packed
+// multiply/add pairs into fused multiply-adds whatever the flags (measured), so
+// packed arithmetic is used ONLY for a conservative screen: for any subset of
+// k <= 16 dimensions, fused or unfused rounding keeps the packed partial sum
+// s' within (1 +- 2^-24)^(2k) of the exact sum S of the same rounded squared
+// differences, and the contract's full sum s_D >= S (1 - 2^-24)^(2D).  Hence
+// s' > r2 (1 + 2^-16) implies s_D > r2: rejecting there never drops a pair.
+// Every candidate that survives is recomputed with the scalar contract
+// (__fsub_rn / __fmul_rn / __fadd_rn, never contracted), which decides
+// membership and gives the returned distance (the paper's "conservative
+// screening and canonical-order recomputation", Sec. 4.2).
+
+__device__ __forceinline__ uint64_t f2_sub(uint64_t a, uint64_t b) {
+    uint64_t d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ uint64_t f2_fma(uint64_t a, uint64_t b, uint64_t c) {
+    uint64_t d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ uint64_t f2_pack(float lo, float hi) {
+    uint64_t d;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(d) : "f"(lo), "f"(hi));
+    return d;
+}
+__device__ __forceinline__ void f2_unpack(uint64_t v, float& lo, float& hi) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+// screening step for two candidates: s' += (q - c)^2 (fused)
+__device__ __forceinline__ uint64_t f2_screen(uint64_t s, uint64_t q, uint64_t c) {
+    const uint64_t d = f2_sub(q, c);
+    return f2_fma(d, d, s);
+}
 
 __device__ __forceinline__ uint64_t make_key(float d2, int32_t j) {
     return ((uint64_t)__float_as_uint(d2) << 32) | (uint32_t)j;
-}
-
-// Ascending bitonic sort of 32*R keys held by one warp: element e = i*32+lane
-// lives in register v[i].
-template <int R>
-__device__ __forceinline__ void warp_bitonic(uint64_t (&v)[R]) {
-    const int lane = threadIdx.x & 31;
-    constexpr int N = 32 * R;
-#pragma unroll
-    for (int k = 2; k <= N; k <<= 1) {
-#pragma unroll
-        for (int j = k >> 1; j > 0; j >>= 1) {
-            if (j >= 32) {
-                const int jr = j >> 5;
-#pragma unroll
-                for (int i = 0; i < R; ++i) {
-                    if ((i & jr) == 0) {
-                        const int e = i * 32 + lane;
-                        const bool up = (e & k) == 0;
-                        const uint64_t a = v[i], b = v[i | jr];
-                        const bool sw = up ? (a > b) : (a < b);
-                        v[i] = sw ? b : a;
-                        v[i | jr] = sw ? a : b;
-                    }
-                }
-            } else {
-#pragma unroll
-                for (int i = 0; i < R; ++i) {
-                    const int e = i * 32 + lane;
-                    const uint64_t o = __shfl_xor_sync(kFull, v[i], j);
-                    const bool lower = (lane & j) == 0;
-                    const bool up = (e & k) == 0;
-                    const bool keep_min = (lower == up);
-                    const uint64_t mn = v[i] < o ? v[i] : o;
-                    const uint64_t mx = v[i] < o ? o : v[i];
-                    v[i] = keep_min ? mn : mx;
-                }
-            }
-        }
-    }
-}
-
-template <int R>
-__device__ void sort_row_t(int32_t* irow, float* drow, int c, int K) {
-    const int lane = threadIdx.x & 31;
-    uint64_t v[R];
-#pragma unroll
-    for (int i = 0; i < R; ++i) {
-        const int e = i * 32 + lane;
-        v[i] = e < c ? make_key(drow[e], irow[e]) : ~0ull;
-    }
-    warp_bitonic<R>(v);
-#pragma unroll
-    for (int i = 0; i < R; ++i) {
-        const int e = i * 32 + lane;
-        if (e < K) {
-            const bool real = e < c;
-            irow[e] = real ? (int32_t)(uint32_t)v[i] : -1;
-            drow[e] = real ? __uint_as_float((uint32_t)(v[i] >> 32)) : INFINITY;
-        }
-    }
-    for (int e = 32 * R + lane; e < K; e += 32) {
-        irow[e] = -1;
-        drow[e] = INFINITY;
-    }
-}
-
-// Rows longer than this (or with degree > K) are finished by the selection
-// kernel below, which keeps the register footprint of the scan kernel small.
-constexpr int kFastSortMax = 128;
-
-// Sort the first c (<= min(K, kFastSortMax)) entries of a row in place and pad
-// the rest.
-__device__ __noinline__ void finalize_row(int32_t* irow, float* drow, int c, int K) {
-    const int lane = threadIdx.x & 31;
-    if (c <= 1) {
-        for (int e = c + lane; e < K; e += 32) {
-            irow[e] = -1;
-            drow[e] = INFINITY;
-        }
-        return;
-    }
-    if (c <= 32) sort_row_t<1>(irow, drow, c, K);
-    else if (c <= 64) sort_row_t<2>(irow, drow, c, K);
-    else sort_row_t<4>(irow, drow, c, K);
 }
 
 // ------------------------------------------------------------- grid query
 
 struct TaskGeom {
     int total_tiles;
-    int rs, re, tp;   // this lane's neighbour-row slot range and inclusive tile prefix
+    int rs, re;     // this lane's neighbour-row slot range (original, unrounded)
+    int prs, pre;   // the same range in pairs, widened to pair boundaries
+    int tp;         // inclusive prefix of tiles over lanes
 };
 
-template <int TILE>
-__device__ __forceinline__ void tile_info(const TaskGeom& g, int t, int& base, int& len) {
+template <int TILEP>
+__device__ __forceinline__ void tile_info(const TaskGeom& g, int t, int& basep, int& lenp,
+                                          int& lo, int& hi) {
     const unsigned below = __ballot_sync(kFull, g.tp <= t);
     const int L = __popc(below);
-    const int rs = __shfl_sync(kFull, g.rs, L);
-    const int re = __shfl_sync(kFull, g.re, L);
+    const int prs = __shfl_sync(kFull, g.prs, L);
+    const int pre = __shfl_sync(kFull, g.pre, L);
     const int tp = __shfl_sync(kFull, g.tp, L);
-    const int ntl = (re - rs + TILE - 1) / TILE;
-    const int first = tp - ntl;
-    base = rs + (t - first) * TILE;
-    len = min(TILE, re - base);
+    lo = __shfl_sync(kFull, g.rs, L);
+    hi = __shfl_sync(kFull, g.re, L);
+    const int ntl = (pre - prs + TILEP - 1) / TILEP;
+    basep = prs + (t - (tp - ntl)) * TILEP;
+    lenp = min(TILEP, pre - basep);
 }
 
 template <int D, int EXIT>
-__global__ void __launch_bounds__(kQueryWarps * 32, 3) k_grid_query(QueryArgs a) {
+__global__ void __launch_bounds__(kQueryWarps * 32, 4) k_grid_query(QueryArgs a) {
     using C = QCfg<D>;
     constexpr int DP = C::DP;
-    constexpr int TILE = C::TILE;
+    constexpr int TILEP = C::TILEP;
+    constexpr int PAIRF = 2 * DP;   // floats per candidate pair
     extern __shared__ __align__(128) unsigned char smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    float* ring = reinterpret_cast<float*>(smem) + (size_t)warp * kNBuf * TILE * DP;
-    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + (size_t)kQueryWarps * kNBuf * TILE * DP *
-                                                            sizeof(float)) +
+    float* ring = reinterpret_cast<float*>(smem) + (size_t)warp * ring_floats(DP, TILEP);
+    float* Ld = reinterpret_cast<float*>(smem) + (size_t)kQueryWarps * ring_floats(DP, TILEP) +
+                (size_t)warp * 2 * kListCap * kListStride;
+    int32_t* Li = reinterpret_cast<int32_t*>(Ld + kListCap * kListStride);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(
+                         smem + (size_t)kQueryWarps * (ring_floats(DP, TILEP) * 4 +
+                                                       2 * kListCap * kListStride * 4)) +
                      warp * kNBuf;
     if (lane == 0)
         for (int b = 0; b < kNBuf; ++b) mbar_init(&bars[b], 1);
@@ -183,6 +154,7 @@ __global__ void __launch_bounds__(kQueryWarps * 32, 3) k_grid_query(QueryArgs a)
 
     const int ntasks = *a.ntasks;
     const float r2 = a.r2;
+    const float rs2 = a.r2_screen;
     const int K = a.K;
 
     for (;;) {
@@ -203,22 +175,19 @@ __global__ void __launch_bounds__(kQueryWarps * 32, 3) k_grid_query(QueryArgs a)
             // grid built from non-finite input: empty rows (frnn_sync reports it)
             for (int ql = 0; ql < task.nq; ++ql) {
                 const int qo = __shfl_sync(kFull, qorig, ql);
-                finalize_row(oidx + (int64_t)qo * K, od2 + (int64_t)qo * K, 0, K);
-                if (lane == 0) counts[qo] = 0;
+                for (int e = lane; e < K; e += 32) {
+                    oidx[(int64_t)qo * K + e] = -1;
+                    od2[(int64_t)qo * K + e] = INFINITY;
+                }
             }
+            if (act) counts[qorig] = 0;
             continue;
         }
-        float q[DP];
-        if (act) {
-            const float4* src = reinterpret_cast<const float4*>(a.qpts + (int64_t)qs * DP);
+        uint64_t qq[D];   // each query coordinate duplicated into both f32x2 lanes
 #pragma unroll
-            for (int k4 = 0; k4 < DP / 4; ++k4) {
-                float4 v = src[k4];
-                q[4 * k4 + 0] = v.x; q[4 * k4 + 1] = v.y; q[4 * k4 + 2] = v.z; q[4 * k4 + 3] = v.w;
-            }
-        } else {
-#pragma unroll
-            for (int k = 0; k < DP; ++k) q[k] = __int_as_float(0x7fc00000);   // NaN: never accepted
+        for (int k = 0; k < D; ++k) {
+            const float v = act ? a.qpts[pair_index(qs, k, DP)] : __int_as_float(0x7fc00000);
+            qq[k] = f2_pack(v, v);   // inactive lanes: NaN, never within r
         }
         const int qc = act ? a.qcell[qs] : 0;
         const int dims0 = h.dims[0], dims1 = h.dims[1], dims2 = h.dims[2], m = h.m;
@@ -243,7 +212,9 @@ __global__ void __launch_bounds__(kQueryWarps * 32, 3) k_grid_query(QueryArgs a)
                 g.re = a.cstart[rowbase + x1 + 1];
             }
         }
-        const int ntl = (g.re - g.rs + TILE - 1) / TILE;
+        g.prs = g.rs >> 1;
+        g.pre = g.re > g.rs ? (g.re + 1) >> 1 : g.prs;
+        const int ntl = (g.pre - g.prs + TILEP - 1) / TILEP;
         int tp = ntl;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
@@ -253,65 +224,77 @@ __global__ void __launch_bounds__(kQueryWarps * 32, 3) k_grid_query(QueryArgs a)
         g.tp = tp;
         g.total_tiles = __shfl_sync(kFull, tp, 31);
 
-        int32_t* irow = oidx + (int64_t)qorig * K;
-        float* drow = od2 + (int64_t)qorig * K;
         int cnt = 0;
         const int self_slot = a.self ? qs : -1;
 
         // prologue: fill the ring
         const int pre = min(kNBuf, g.total_tiles);
         for (int tt = 0; tt < pre; ++tt) {
-            int base, len;
-            tile_info<TILE>(g, tt, base, len);
+            int basep, lenp, lo, hi;
+            tile_info<TILEP>(g, tt, basep, lenp, lo, hi);
             if (lane == 0) {
-                const uint32_t bytes = (uint32_t)len * DP * sizeof(float);
+                const uint32_t bytes = (uint32_t)lenp * PAIRF * sizeof(float);
                 mbar_arrive_expect_tx(&bars[tt], bytes);
-                bulk_g2s(ring + (size_t)tt * TILE * DP, a.rpts + (int64_t)base * DP, bytes,
-                         &bars[tt]);
+                bulk_g2s(ring + (size_t)tt * TILEP * PAIRF, a.rpts + (int64_t)basep * PAIRF,
+                         bytes, &bars[tt]);
             }
         }
         int timed_out_at = -1;
         for (int tt = 0; tt < g.total_tiles; ++tt) {
             const int b = tt % kNBuf;
-            int base, len;
-            tile_info<TILE>(g, tt, base, len);
+            int basep, lenp, lo, hi;
+            tile_info<TILEP>(g, tt, basep, lenp, lo, hi);
             if (!mbar_wait_bounded(&bars[b], (phase >> b) & 1u)) {
                 timed_out_at = tt;
                 break;
             }
             phase ^= 1u << b;
-            const float* tile = ring + (size_t)b * TILE * DP;
+            const float* tile = ring + (size_t)b * TILEP * PAIRF;
 #pragma unroll 2
-            for (int c = 0; c < len; ++c) {
-                const float4* cp4 = reinterpret_cast<const float4*>(tile + c * DP);
-                float cv[DP];
-#pragma unroll
-                for (int k4 = 0; k4 < DP / 4; ++k4) {
-                    float4 v = cp4[k4];
-                    cv[4 * k4 + 0] = v.x; cv[4 * k4 + 1] = v.y;
-                    cv[4 * k4 + 2] = v.z; cv[4 * k4 + 3] = v.w;
-                }
-                float s = 0.f;
+            for (int p = 0; p < lenp; ++p) {
+                const ulonglong2* cp = reinterpret_cast<const ulonglong2*>(tile + p * PAIRF);
+                uint64_t s2 = 0;   // two +0.0f
 #pragma unroll
                 for (int k = 0; k < EXIT; ++k) {
-                    const float d = __fsub_rn(q[k], cv[k]);
-                    s = __fadd_rn(s, __fmul_rn(d, d));
+                    const ulonglong2 v = cp[k >> 1];
+                    s2 = f2_screen(s2, qq[k], (k & 1) ? v.y : v.x);
                 }
+                float s0, s1;
                 if (EXIT < D) {
-                    if (!__any_sync(kFull, s <= r2)) continue;
+                    f2_unpack(s2, s0, s1);
+                    if (!__any_sync(kFull, (s0 <= rs2) | (s1 <= rs2))) continue;
 #pragma unroll
                     for (int k = EXIT; k < D; ++k) {
-                        const float d = __fsub_rn(q[k], cv[k]);
-                        s = __fadd_rn(s, __fmul_rn(d, d));
+                        const ulonglong2 v = cp[k >> 1];
+                        s2 = f2_screen(s2, qq[k], (k & 1) ? v.y : v.x);
                     }
                 }
-                if (s <= r2) {
-                    const int cs = base + c;
-                    if (cs != self_slot) {
-                        const int pos = cnt++;
-                        if (pos < K) {
-                            irow[pos] = a.rperm[cs];
-                            drow[pos] = s;
+                f2_unpack(s2, s0, s1);
+                if ((s0 <= rs2) | (s1 <= rs2)) {
+                    const int cs0 = 2 * (basep + p);
+                    const float* cpf = tile + p * PAIRF;
+#pragma unroll
+                    for (int h2 = 0; h2 < 2; ++h2) {
+                        const int cs = cs0 + h2;
+                        // slots outside the row's own range were read only
+                        // because tiles start on pair boundaries: skip them
+                        if ((h2 ? s1 : s0) <= rs2 && cs >= lo && cs < hi && cs != self_slot) {
+                            // exact contract, index order, no contraction
+                            float sv = 0.f;
+#pragma unroll
+                            for (int k = 0; k < D; ++k) {
+                                float qk, qk2;
+                                f2_unpack(qq[k], qk, qk2);
+                                const float d = __fsub_rn(qk, cpf[2 * k + h2]);
+                                sv = __fadd_rn(sv, __fmul_rn(d, d));
+                            }
+                            if (sv <= r2) {
+                                if (cnt < kListCap) {
+                                    Ld[cnt * kListStride + lane] = sv;
+                                    Li[cnt * kListStride + lane] = a.rperm[cs];
+                                }
+                                ++cnt;
+                            }
                         }
                     }
                 }
@@ -319,14 +302,14 @@ __global__ void __launch_bounds__(kQueryWarps * 32, 3) k_grid_query(QueryArgs a)
             __syncwarp();
             const int nt = tt + kNBuf;
             if (nt < g.total_tiles) {
-                int nbase, nlen;
-                tile_info<TILE>(g, nt, nbase, nlen);
+                int nbasep, nlenp, nlo, nhi;
+                tile_info<TILEP>(g, nt, nbasep, nlenp, nlo, nhi);
                 if (lane == 0) {
                     fence_proxy_async_smem();
-                    const uint32_t bytes = (uint32_t)nlen * DP * sizeof(float);
+                    const uint32_t bytes = (uint32_t)nlenp * PAIRF * sizeof(float);
                     mbar_arrive_expect_tx(&bars[b], bytes);
-                    bulk_g2s(ring + (size_t)b * TILE * DP, a.rpts + (int64_t)nbase * DP, bytes,
-                             &bars[b]);
+                    bulk_g2s(ring + (size_t)b * TILEP * PAIRF, a.rpts + (int64_t)nbasep * PAIRF,
+                             bytes, &bars[b]);
                 }
             }
         }
@@ -341,31 +324,60 @@ __global__ void __launch_bounds__(kQueryWarps * 32, 3) k_grid_query(QueryArgs a)
             }
             return;
         }
-        __syncwarp();
-        for (int ql = 0; ql < task.nq; ++ql) {
-            const int c = __shfl_sync(kFull, cnt, ql);
-            const int qo = __shfl_sync(kFull, qorig, ql);
-            if (c > K || c > kFastSortMax) {
-                if (lane == 0) {
-                    const int pos = atomicAdd(a.ovf_count, 1);
-                    if (pos < a.ovf_cap) {
-                        a.ovf[pos].qslot = task.qslot + ql;
-                        a.ovf[pos].ev = task.ev;
-                    } else {
-                        atomicOr(a.status, kStatusCapacity);
-                    }
+        // each lane sorts its own list by (d2, index): insertion sort, all
+        // lanes in parallel (the transposed layout keeps every access in the
+        // lane's own bank)
+        const bool spill = cnt > kListCap;
+        if (act && !spill) {
+            for (int e = 1; e < cnt; ++e) {
+                const float kd = Ld[e * kListStride + lane];
+                const int ki = Li[e * kListStride + lane];
+                int j = e - 1;
+                while (j >= 0) {
+                    const float dj = Ld[j * kListStride + lane];
+                    const int ij = Li[j * kListStride + lane];
+                    if (dj < kd || (dj == kd && ij < ki)) break;
+                    Ld[(j + 1) * kListStride + lane] = dj;
+                    Li[(j + 1) * kListStride + lane] = ij;
+                    --j;
                 }
-                continue;
+                Ld[(j + 1) * kListStride + lane] = kd;
+                Li[(j + 1) * kListStride + lane] = ki;
             }
-            finalize_row(oidx + (int64_t)qo * K, od2 + (int64_t)qo * K, c, K);
-            if (lane == 0) counts[qo] = c;
+            counts[qorig] = min(cnt, K);
         }
+        if (act && spill) {
+            // longer than the list: the exact selection kernel finishes this row
+            const int pos = atomicAdd(a.ovf_count, 1);
+            if (pos < a.ovf_cap) {
+                a.ovf[pos].qslot = qs;
+                a.ovf[pos].ev = task.ev;
+            } else {
+                atomicOr(a.status, kStatusCapacity);
+            }
+        }
+        __syncwarp();
+        // coalesced row writes: one query row at a time across the warp
+        const unsigned spill_mask = __ballot_sync(kFull, spill);
+        for (int ql = 0; ql < task.nq; ++ql) {
+            if (spill_mask & (1u << ql)) continue;
+            const int c = min(__shfl_sync(kFull, cnt, ql), K);
+            const int qo = __shfl_sync(kFull, qorig, ql);
+            int32_t* irow = oidx + (int64_t)qo * K;
+            float* drow = od2 + (int64_t)qo * K;
+            for (int e = lane; e < K; e += 32) {
+                const bool real = e < c;
+                irow[e] = real ? Li[e * kListStride + ql] : -1;
+                drow[e] = real ? Ld[e * kListStride + ql] : INFINITY;
+            }
+        }
+        __syncwarp();
     }
 }
 
 // ------------------------------------------------------------- overflow path
-// Exact selection for queries whose degree exceeds K (or whose row is longer
-// than kFastSortMax, which needs K > 128): one warp per query scans
+// Exact selection for queries with more than kListCap neighbours (whether or
+// not that exceeds K): one warp per query scans
 // the query's own +-m neighbourhood with lanes over candidates, appends keys
 // below the current threshold to a shared buffer, and whenever the buffer is
 // nearly full sorts it and keeps the K smallest (the threshold becomes the
@@ -407,7 +419,9 @@ __global__ void __launch_bounds__(kOvfWarps * 32) k_overflow(QueryArgs a, int ca
         float* od2 = a.counts ? a.dist2 : h.dist2;
         const int qs = o.qslot;
         const int qo = a.qperm[qs];
-        const float* qp = a.qpts + (int64_t)qs * DP;
+        float qv[kMaxD];
+#pragma unroll
+        for (int k = 0; k < kMaxD; ++k) qv[k] = k < D ? a.qpts[pair_index(qs, k, DP)] : 0.f;
         const int qc = a.qcell[qs];
         const int dims0 = h.dims[0], dims1 = h.dims[1], dims2 = h.dims[2], m = h.m;
         const int x = qc % dims0, y = (qc / dims0) % dims1, z = qc / (dims0 * dims1);
@@ -428,11 +442,13 @@ __global__ void __launch_bounds__(kOvfWarps * 32) k_overflow(QueryArgs a, int ca
                     const int cs = c0 + lane;
                     uint64_t key = ~0ull;
                     if (cs < re && cs != self_slot) {
-                        const float* cp = a.rpts + (int64_t)cs * DP;
                         float s = 0.f;
-                        for (int k = 0; k < D; ++k) {
-                            const float d = __fsub_rn(qp[k], cp[k]);
-                            s = __fadd_rn(s, __fmul_rn(d, d));
+#pragma unroll
+                        for (int k = 0; k < kMaxD; ++k) {
+                            if (k < D) {
+                                const float d = __fsub_rn(qv[k], a.rpts[pair_index(cs, k, DP)]);
+                                s = __fadd_rn(s, __fmul_rn(d, d));
+                            }
                         }
                         if (s <= a.r2) {
                             key = make_key(s, a.rperm[cs]);
@@ -474,7 +490,7 @@ template <int D>
 static cudaError_t launch_grid_query_d(const QueryArgs& a, int exit_dims, int num_sms,
                                        cudaStream_t st) {
     using C = QCfg<D>;
-    const size_t smem = query_smem_bytes(C::DP, C::TILE);
+    const size_t smem = query_smem_bytes(C::DP, C::TILEP);
     auto kern = &k_grid_query<D, C::EXIT>;
     // other vote points are compiled for the tracking-like dimensions only
     if constexpr (D == 8 || D == 12) {
@@ -511,6 +527,7 @@ frnn_status enqueue_grid_query(const QueryLaunch& q, cudaStream_t st, std::strin
     a.idx = q.idx;
     a.dist2 = q.dist2;
     a.r2 = q.r2;
+    a.r2_screen = std::nextafter((float)((double)q.r2 * (1.0 + 0x1p-16)), INFINITY);
     a.K = q.K;
     a.self = q.self;
     a.D = rs.D;

@@ -254,3 +254,32 @@ def test_invalid_arguments(ctx):
     with pytest.raises(frnn.FrnnError):
         ctx.build_grid(torch.zeros((4, 17), device="cuda"), 0.1)
     ctx.sync()
+
+
+def test_subnormal_squares_gradual_underflow(ctx):
+    """Coordinates near 2^-60: many squared differences are subnormal; both
+    sides must keep gradual underflow (no flush to zero)."""
+    g = np.random.default_rng(312)
+    pts = (g.integers(0, 64, size=(400, 4)) * 2.0 ** -66).astype(np.float32)
+    r = float(2.0 ** -60)
+    got = _gpu_self(ctx, pts, r, 64)
+    want = oracle.self_query(pts, r, 64)
+    assert (want[2][want[2] < np.inf] < np.finfo(np.float32).tiny).any()
+    _assert_rows_equal(got, want)
+
+
+def test_batched_equals_alone_and_oracle(ctx):
+    import torch
+    sizes = [0, 1, 33, 2000, 4097, 15000, 777]
+    evs = [synth.event_mix(n, 8, (40, e)) if n else np.zeros((0, 8), np.float32)
+           for e, n in enumerate(sizes)]
+    tev = [torch.from_numpy(np.ascontiguousarray(p)).cuda() for p in evs]
+    for rep in range(2):   # second call replays the captured graph
+        outs = ctx.query_batched(tev, 0.1, 64, path="grid")
+        ctx.sync()
+        for e, (p, (c, i, d)) in enumerate(zip(evs, outs)):
+            got = (c.cpu().numpy(), i.cpu().numpy(), d.cpu().numpy())
+            alone = _gpu_self(ctx, p, 0.1, 64)
+            _assert_rows_equal(got, alone)
+            if len(p) and e % 2 == 0:
+                _assert_rows_equal(got, oracle.self_query(p, 0.1, 64))
