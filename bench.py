@@ -149,6 +149,12 @@ def run_ours(args):
     N, D, r, K = pts_np.shape[0], w.D, w.r, w.K
     stream = torch.cuda.Stream()
     ctx = frnn.Context(stream=stream)
+    if args.cell_mult:
+        ctx.set_option(frnn.FRNN_OPT_CELL_MULT, args.cell_mult)
+    if args.exit_dims:
+        ctx.set_option(frnn.FRNN_OPT_EXIT_DIMS, args.exit_dims)
+    if args.grid_axes:
+        ctx.set_option(frnn.FRNN_OPT_GRID_AXES, args.grid_axes)
     with torch.cuda.stream(stream):
         pts = torch.from_numpy(pts_np).to(dev)
         counts = torch.empty(N, dtype=torch.int32, device=dev)
@@ -233,6 +239,8 @@ def run_ours(args):
         "dtype": "f32",
         "data": "synthetic (seeded clusters + background shaped like a tracking event)",
         "config": {"workload": w.name, "N": N, "D": D, "r": r, "K": K, "path": "grid",
+                   "cell_mult": ctx.get_option(frnn.FRNN_OPT_CELL_MULT),
+                   "exit_dims": ctx.get_option(frnn.FRNN_OPT_EXIT_DIMS),
                    "self_query": True, "l2": "flushed between timed steps (256 MB write)",
                    "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
         "pairs_per_s": pairs * ws * args.steps / (total_ms / 1e3),
@@ -319,6 +327,9 @@ def main():
     ap.add_argument("--cpu-rows", type=int, default=4000)
     ap.add_argument("--ref-rows", type=int, default=1000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cell-mult", type=int, default=0, help="grid cell multiple m (0: library default)")
+    ap.add_argument("--exit-dims", type=int, default=0, help="dims before the warp vote (0: default)")
+    ap.add_argument("--grid-axes", type=int, default=0, help="0: last axes, 1: widest axes")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

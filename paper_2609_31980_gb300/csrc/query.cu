@@ -224,7 +224,9 @@ __global__ void __launch_bounds__(kQueryWarps * 32, 4) k_grid_query(QueryArgs a)
         g.tp = tp;
         g.total_tiles = __shfl_sync(kFull, tp, 31);
 
-        int cnt = 0;
+        int cnt = 0;          // confirmed + this tile's tentative entries
+        int kept = 0;         // confirmed (exactly rechecked) entries
+        bool lost = false;    // an entry did not fit the list: the row goes to the selection kernel
         const int self_slot = a.self ? qs : -1;
 
         // prologue: fill the ring
@@ -250,54 +252,79 @@ __global__ void __launch_bounds__(kQueryWarps * 32, 4) k_grid_query(QueryArgs a)
             }
             phase ^= 1u << b;
             const float* tile = ring + (size_t)b * TILEP * PAIRF;
-#pragma unroll 2
-            for (int p = 0; p < lenp; ++p) {
-                const ulonglong2* cp = reinterpret_cast<const ulonglong2*>(tile + p * PAIRF);
-                uint64_t s2 = 0;   // two +0.0f
+            // four candidate pairs per step: their first-stage screens are
+            // independent, which hides the packed pipeline's latency
+            for (int p0 = 0; p0 < lenp; p0 += 4) {
+                uint64_t sg[4];
 #pragma unroll
-                for (int k = 0; k < EXIT; ++k) {
-                    const ulonglong2 v = cp[k >> 1];
-                    s2 = f2_screen(s2, qq[k], (k & 1) ? v.y : v.x);
-                }
-                float s0, s1;
-                if (EXIT < D) {
-                    f2_unpack(s2, s0, s1);
-                    if (!__any_sync(kFull, (s0 <= rs2) | (s1 <= rs2))) continue;
+                for (int j = 0; j < 4; ++j) {
+                    // pairs past the tile's end hold stale data: force them out
+                    const ulonglong2* cp = reinterpret_cast<const ulonglong2*>(tile + (p0 + j) * PAIRF);
+                    uint64_t s2 = 0;
 #pragma unroll
-                    for (int k = EXIT; k < D; ++k) {
+                    for (int k = 0; k < EXIT; ++k) {
                         const ulonglong2 v = cp[k >> 1];
                         s2 = f2_screen(s2, qq[k], (k & 1) ? v.y : v.x);
                     }
+                    sg[j] = (p0 + j < lenp) ? s2 : 0x7f8000007f800000ull;   // +inf, +inf
                 }
-                f2_unpack(s2, s0, s1);
-                if ((s0 <= rs2) | (s1 <= rs2)) {
-                    const int cs0 = 2 * (basep + p);
-                    const float* cpf = tile + p * PAIRF;
 #pragma unroll
-                    for (int h2 = 0; h2 < 2; ++h2) {
-                        const int cs = cs0 + h2;
-                        // slots outside the row's own range were read only
-                        // because tiles start on pair boundaries: skip them
-                        if ((h2 ? s1 : s0) <= rs2 && cs >= lo && cs < hi && cs != self_slot) {
-                            // exact contract, index order, no contraction
-                            float sv = 0.f;
+                for (int j = 0; j < 4; ++j) {
+                    const int p = p0 + j;
+                    const ulonglong2* cp = reinterpret_cast<const ulonglong2*>(tile + p * PAIRF);
+                    uint64_t s2 = sg[j];
+                    float s0, s1;
+                    f2_unpack(s2, s0, s1);
+                    if (!__any_sync(kFull, (s0 <= rs2) | (s1 <= rs2))) continue;
+                    if (EXIT < D) {
 #pragma unroll
-                            for (int k = 0; k < D; ++k) {
-                                float qk, qk2;
-                                f2_unpack(qq[k], qk, qk2);
-                                const float d = __fsub_rn(qk, cpf[2 * k + h2]);
-                                sv = __fadd_rn(sv, __fmul_rn(d, d));
-                            }
-                            if (sv <= r2) {
-                                if (cnt < kListCap) {
-                                    Ld[cnt * kListStride + lane] = sv;
-                                    Li[cnt * kListStride + lane] = a.rperm[cs];
-                                }
+                        for (int k = EXIT; k < D; ++k) {
+                            const ulonglong2 v = cp[k >> 1];
+                            s2 = f2_screen(s2, qq[k], (k & 1) ? v.y : v.x);
+                        }
+                        f2_unpack(s2, s0, s1);
+                    }
+                    if ((s0 <= rs2) | (s1 <= rs2)) {
+                        // tentative: remember the slot, recheck at the tile's end
+                        const int cs0 = 2 * (basep + p);
+#pragma unroll
+                        for (int h2 = 0; h2 < 2; ++h2) {
+                            const int cs = cs0 + h2;
+                            // slots outside the row's own range were read only
+                            // because tiles start on pair boundaries: skip them
+                            if ((h2 ? s1 : s0) <= rs2 && cs >= lo && cs < hi && cs != self_slot) {
+                                if (cnt < kListCap) Li[cnt * kListStride + lane] = cs;
+                                else lost = true;
                                 ++cnt;
                             }
                         }
                     }
                 }
+            }
+            // exact recheck of this tile's tentative entries, every lane its
+            // own in parallel: the scalar contract in index order, no
+            // contraction; keep (d2, original index) of the accepted ones
+            if (!lost) {
+                const int tile_slot0 = 2 * basep;
+                int wpos = kept;
+                for (int e = kept; e < cnt; ++e) {
+                    const int cs = Li[e * kListStride + lane];
+                    const float* cpf = tile + (cs - tile_slot0 - (cs & 1)) * DP + (cs & 1);
+                    float sv = 0.f;
+#pragma unroll
+                    for (int k = 0; k < D; ++k) {
+                        float qk, qk2;
+                        f2_unpack(qq[k], qk, qk2);
+                        const float d = __fsub_rn(qk, cpf[2 * k]);
+                        sv = __fadd_rn(sv, __fmul_rn(d, d));
+                    }
+                    if (sv <= r2) {
+                        Ld[wpos * kListStride + lane] = sv;
+                        Li[wpos * kListStride + lane] = a.rperm[cs];
+                        ++wpos;
+                    }
+                }
+                cnt = kept = wpos;
             }
             __syncwarp();
             const int nt = tt + kNBuf;
@@ -327,7 +354,7 @@ __global__ void __launch_bounds__(kQueryWarps * 32, 4) k_grid_query(QueryArgs a)
         // each lane sorts its own list by (d2, index): insertion sort, all
         // lanes in parallel (the transposed layout keeps every access in the
         // lane's own bank)
-        const bool spill = cnt > kListCap;
+        const bool spill = lost;
         if (act && !spill) {
             for (int e = 1; e < cnt; ++e) {
                 const float kd = Ld[e * kListStride + lane];
