@@ -179,7 +179,13 @@ typedef enum frnn_option {
     FRNN_OPT_EXIT_DIMS = 3,   /* dims summed before the warp-uniform early exit
                                  (0 = library default) */
     FRNN_OPT_USE_GRAPH = 4,   /* 1 (default): batched calls replay a CUDA graph */
-    FRNN_OPT_AUTOTUNE = 5     /* 1 (default): FRNN_PATH_AUTO consults the tuner */
+    FRNN_OPT_AUTOTUNE = 5,    /* 1 (default): FRNN_PATH_AUTO consults the tuner */
+    FRNN_OPT_AUTO_TC = 6,     /* 1 (default): FRNN_PATH_AUTO takes the tensor-core
+                                 path for D >= 8 */
+    FRNN_OPT_TC_SURVIVORS = 7,/* read: candidates that passed the tensor-core
+                                 pre-filter since the last reset (synchronises);
+                                 set (any value): reset both counters */
+    FRNN_OPT_TC_ACCEPTED = 8  /* read: of those, accepted by the exact recheck */
 } frnn_option;
 
 frnn_status frnn_set_option(frnn_ctx* ctx, frnn_option opt, int64_t value);

@@ -27,6 +27,7 @@ struct frnn_ctx {
     size_t held = 0;          // bytes of grids + workspaces currently held
     int32_t* d_status = nullptr;
     int32_t* h_status = nullptr;
+    unsigned long long* d_tcstat = nullptr;   // [2] tensor-core survivors / exact accepts
     std::string err;
     // options
     int cell_mult = 1;
@@ -34,6 +35,7 @@ struct frnn_ctx {
     int exit_dims = 0;
     int use_graph = 1;
     int autotune = 1;
+    int auto_tc = 1;          // FRNN_PATH_AUTO uses the tensor-core path for D >= 8
     // workspaces
     GridBufs qset;            // cross-set query binning
     GridBufs batch;           // batched multi-event grid
@@ -109,6 +111,28 @@ static frnn_status alloc_accounted(frnn_ctx* c, GridBufs& g, int E, const int64_
     return FRNN_OK;
 }
 
+// Path choice: FRNN_PATH_TC forces the tensor-core pre-filter (D >= 8),
+// FRNN_PATH_GRID the scalar grid scan; FRNN_PATH_AUTO takes the tensor-core
+// path for D >= 8 unless the context's option says otherwise.
+static bool use_tc_path(const frnn_ctx* ctx, int D, unsigned flags) {
+    if (flags & FRNN_PATH_TC) return true;
+    if (flags & FRNN_PATH_GRID) return false;
+    return D >= 8 && ctx->auto_tc;
+}
+
+// Build (or reuse) the tensor-core operands of a point set; accounted in the
+// context's memory budget.
+static frnn_status prepare_tc(frnn_ctx* ctx, GridBufs& g, const GridBufs& center_src,
+                              bool capturing = false) {
+    if (g.tc_ready && &g == &center_src) return FRNN_OK;
+    const size_t before = g.tc_bytes;
+    std::string err;
+    frnn_status s = tc_prepare(g, center_src, capturing ? ctx->gstream : ctx->stream, err);
+    ctx->held = ctx->held - std::min(ctx->held, before) + g.tc_bytes;
+    if (s != FRNN_OK) return fail(ctx, s, err);
+    return FRNN_OK;
+}
+
 extern "C" {
 
 const char* frnn_version(void) { return "0.1.0"; }
@@ -152,6 +176,7 @@ frnn_status frnn_create(frnn_ctx** out, void* cuda_stream, size_t mem_budget_byt
         return FRNN_ERR_OUT_OF_MEMORY;
     }
     cudaMemsetAsync(c->d_status, 0, 64, c->stream);
+    c->d_tcstat = reinterpret_cast<unsigned long long*>(c->d_status + 8);   // same block
     e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -295,8 +320,9 @@ frnn_status frnn_query(frnn_ctx* ctx, const frnn_grid* grid, const float* querie
     q.d_status = ctx->d_status;
     q.num_sms = ctx->num_sms;
     std::string err;
+    GridBufs& rg = const_cast<frnn_grid*>(grid)->g;   // tensor-core operands are a lazy cache
     if (self) {
-        q.qset = &grid->g;
+        q.qset = &rg;
     } else {
         const int64_t cap = grid->g.h_hdr[0].cell_cap;
         s = alloc_accounted(ctx, ctx->qset, 1, &M, grid->D, &cap);
@@ -307,7 +333,15 @@ frnn_status frnn_query(frnn_ctx* ctx, const frnn_grid* grid, const float* querie
         if (s != FRNN_OK) return fail(ctx, s, err);
         q.qset = &ctx->qset;
     }
-    s = enqueue_grid_query(q, ctx->stream, err);
+    if (use_tc_path(ctx, grid->D, flags)) {
+        s = prepare_tc(ctx, rg, rg);
+        if (s == FRNN_OK && !self) s = prepare_tc(ctx, ctx->qset, rg);
+        if (s != FRNN_OK) return s;
+        q.tc_stats = ctx->d_tcstat;
+        s = enqueue_tc_query(q, ctx->stream, err);
+    } else {
+        s = enqueue_grid_query(q, ctx->stream, err);
+    }
     if (s != FRNN_OK) return fail(ctx, s, err);
     return FRNN_OK;
 }
@@ -325,7 +359,8 @@ static bool same_events(const frnn_ctx* c, const frnn_event* ev, int n) {
 }
 
 static frnn_status enqueue_batched(frnn_ctx* ctx, const frnn_event* ev, int n_events, int D,
-                                   float r, int K, bool capturing, cudaStream_t st) {
+                                   float r, int K, unsigned flags, bool capturing,
+                                   cudaStream_t st) {
     std::vector<const float*> refs(n_events);
     for (int e = 0; e < n_events; ++e) {
         refs[e] = ev[e].pts;
@@ -350,7 +385,15 @@ static frnn_status enqueue_batched(frnn_ctx* ctx, const frnn_event* ev, int n_ev
     q.exit_dims = ctx->exit_dims;
     q.d_status = ctx->d_status;
     q.num_sms = ctx->num_sms;
-    s = enqueue_grid_query(q, st, err);
+    if (use_tc_path(ctx, D, flags)) {
+        // operands were allocated before any capture; enqueue their build
+        s = tc_prepare(ctx->batch, ctx->batch, st, err);
+        if (s != FRNN_OK) return fail(ctx, s, err);
+        q.tc_stats = ctx->d_tcstat;
+        s = enqueue_tc_query(q, st, err);
+    } else {
+        s = enqueue_grid_query(q, st, err);
+    }
     if (s != FRNN_OK) return fail(ctx, s, err);
     return FRNN_OK;
 }
@@ -400,7 +443,14 @@ frnn_status frnn_query_batched(frnn_ctx* ctx, const frnn_event* ev, int n_events
     }
     frnn_status s = alloc_accounted(ctx, ctx->batch, n_events, n.data(), D, nullptr);
     if (s != FRNN_OK) return s;
-    if (!ctx->use_graph) return enqueue_batched(ctx, ev, n_events, D, r, K, false, ctx->stream);
+    if (use_tc_path(ctx, D, flags)) {
+        // allocate the tensor-core operands outside any capture (no work enqueued)
+        std::string err;
+        s = tc_reserve(ctx->batch, err);
+        if (s != FRNN_OK) return fail(ctx, s, err);
+    }
+    if (!ctx->use_graph)
+        return enqueue_batched(ctx, ev, n_events, D, r, K, flags, false, ctx->stream);
     if (!ctx->gstream) {
         cudaError_t e = cudaStreamCreateWithFlags(&ctx->gstream, cudaStreamNonBlocking);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->g_in, cudaEventDisableTiming);
@@ -414,7 +464,7 @@ frnn_status frnn_query_batched(frnn_ctx* ctx, const frnn_event* ev, int n_events
     cudaGraph_t graph = nullptr;
     cudaError_t e = cudaStreamBeginCapture(ctx->gstream, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaStreamBeginCapture");
-    s = enqueue_batched(ctx, ev, n_events, D, r, K, true, ctx->gstream);
+    s = enqueue_batched(ctx, ev, n_events, D, r, K, flags, true, ctx->gstream);
     e = cudaStreamEndCapture(ctx->gstream, &graph);
     if (s != FRNN_OK) {
         if (graph) cudaGraphDestroy(graph);
@@ -529,6 +579,14 @@ frnn_status frnn_set_option(frnn_ctx* ctx, frnn_option opt, int64_t value) {
         case FRNN_OPT_AUTOTUNE:
             ctx->autotune = value ? 1 : 0;
             return FRNN_OK;
+        case FRNN_OPT_AUTO_TC:
+            ctx->auto_tc = value ? 1 : 0;
+            return FRNN_OK;
+        case FRNN_OPT_TC_SURVIVORS:
+        case FRNN_OPT_TC_ACCEPTED:
+            cudaStreamSynchronize(ctx->stream);
+            cudaMemset(ctx->d_tcstat, 0, 2 * sizeof(unsigned long long));
+            return FRNN_OK;
     }
     return fail(ctx, FRNN_ERR_INVALID_ARG, "unknown option");
 }
@@ -541,6 +599,16 @@ frnn_status frnn_get_option(const frnn_ctx* ctx, frnn_option opt, int64_t* value
         case FRNN_OPT_EXIT_DIMS: *value = ctx->exit_dims; return FRNN_OK;
         case FRNN_OPT_USE_GRAPH: *value = ctx->use_graph; return FRNN_OK;
         case FRNN_OPT_AUTOTUNE: *value = ctx->autotune; return FRNN_OK;
+        case FRNN_OPT_AUTO_TC: *value = ctx->auto_tc; return FRNN_OK;
+        case FRNN_OPT_TC_SURVIVORS:
+        case FRNN_OPT_TC_ACCEPTED: {
+            unsigned long long h[2] = {0, 0};
+            cudaStreamSynchronize(ctx->stream);
+            if (cudaMemcpy(h, ctx->d_tcstat, sizeof(h), cudaMemcpyDeviceToHost) != cudaSuccess)
+                return FRNN_ERR_CUDA;
+            *value = (int64_t)(opt == FRNN_OPT_TC_SURVIVORS ? h[0] : h[1]);
+            return FRNN_OK;
+        }
     }
     return FRNN_ERR_INVALID_ARG;
 }

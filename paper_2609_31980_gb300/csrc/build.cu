@@ -226,6 +226,15 @@ __global__ void k_params(EventHdr* hdr, int E, int D, const int32_t* bbox, float
         }
     }
     h.valid = valid ? 1 : 0;
+    for (int k = 0; k < kMaxD; ++k) {
+        float c = 0.f;
+        if (valid && k < D) {
+            const float lo = ordered_to_float(bb[k]), hi = ordered_to_float(bb[16 + k]);
+            c = __fadd_rn(lo, __fmul_rn(0.5f, __fsub_rn(hi, lo)));
+            if (!isfinite(c)) c = 0.f;
+        }
+        h.ctr[k] = c;
+    }
     if (!valid) {
         h.inv_h = 0.f;
         h.ncells = 1;
@@ -281,6 +290,7 @@ __global__ void k_copy_params(EventHdr* dst, const EventHdr* src, int E, int32_t
         d.lo[a] = s.lo[a];
         d.hi[a] = s.hi[a];
     }
+    for (int k = 0; k < kMaxD; ++k) d.ctr[k] = s.ctr[k];
 }
 
 // Non-finite check of a query set binned with foreign parameters (the bbox
@@ -346,30 +356,47 @@ __global__ void __launch_bounds__(kBuildPtsPerBlock) k_scatter(const EventHdr* h
 }
 
 // Per row of cells (all gridded coordinates but the fastest fixed): number of
-// 32-query warp tasks.  Entry i of the cell arrays doubles as row slot i.
+// query tasks.  A task is the intersection of the row's slot range with a
+// window of W slots; windows start at the row's first slot rounded down to a
+// multiple of A (A = 1 for the 32-query warp tasks of the grid path, A = 8 for
+// the 128-query tensor-core tiles, whose operand rows come in groups of 8).
+// Entry i of the cell arrays doubles as row slot i.
+__device__ __forceinline__ void row_slots(const EventHdr& h, const int32_t* cstart, int64_t row,
+                                          int32_t& base, int32_t& cnt) {
+    if (h.valid) {
+        const int64_t c0 = h.cell_off + row * h.dims[0];
+        base = cstart[c0];
+        cnt = cstart[c0 + h.dims[0]] - base;
+    } else {
+        // invalid event: all its queries in one row (they get empty rows)
+        base = (int32_t)h.pt_off;
+        cnt = row == 0 ? (int32_t)h.n : 0;
+    }
+}
+
 __global__ void k_rowtasks(const EventHdr* hdr, const int64_t* cell_off, int E, int64_t L,
-                           const int32_t* cstart, int32_t* rtask) {
+                           const int32_t* cstart, int32_t* rtask, int W, int A) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= L) return;
     const int e = find_event64(cell_off, E, i);
     const EventHdr& h = hdr[e];
     const int64_t row = i - cell_off[e];
-    const int64_t nrows = (int64_t)h.dims[1] * h.dims[2];
+    const int64_t nrows = h.valid ? (int64_t)h.dims[1] * h.dims[2] : 1;
     int32_t nt = 0;
-    if (h.valid && row < nrows) {
-        const int64_t c0 = h.cell_off + row * h.dims[0];
-        const int32_t cnt = cstart[c0 + h.dims[0]] - cstart[c0];
-        nt = (cnt + kTaskQueries - 1) / kTaskQueries;
-    } else if (!h.valid && row == 0) {
-        // invalid event: its queries still get (empty) rows written
-        nt = (int32_t)((h.n + kTaskQueries - 1) / kTaskQueries);
+    if (row < nrows) {
+        int32_t base, cnt;
+        row_slots(h, cstart, row, base, cnt);
+        if (cnt > 0) {
+            const int32_t w0 = base & ~(A - 1);
+            nt = (base + cnt - w0 + W - 1) / W;
+        }
     }
     rtask[i] = nt;
 }
 
 __global__ void k_emit(const EventHdr* hdr, const int64_t* cell_off, int E, int64_t L,
                        const int32_t* cstart, const int32_t* rtask_start,
-                       const int32_t* rtask_count_src, Task* tasks) {
+                       const int32_t* rtask_count_src, Task* tasks, int W, int A) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= L) return;
     const int e = find_event64(cell_off, E, i);
@@ -379,23 +406,27 @@ __global__ void k_emit(const EventHdr* hdr, const int64_t* cell_off, int E, int6
     const int32_t t1 = (i + 1 < L) ? rtask_start[i + 1] : rtask_count_src[0];
     if (t1 <= t0) return;
     int32_t base, cnt;
-    if (h.valid) {
-        const int64_t c0 = h.cell_off + row * h.dims[0];
-        base = cstart[c0];
-        cnt = cstart[c0 + h.dims[0]] - base;
-    } else {
-        base = (int32_t)h.pt_off;
-        cnt = (int32_t)h.n;
-    }
+    row_slots(h, cstart, row, base, cnt);
+    const int32_t w0 = base & ~(A - 1);
     for (int32_t t = t0; t < t1; ++t) {
-        const int32_t k = t - t0;
+        const int32_t ws = w0 + (t - t0) * W;
+        const int32_t a = max(ws, base);
+        const int32_t b = min(ws + W, base + cnt);
         Task tk;
-        tk.qslot = base + k * kTaskQueries;
-        tk.nq = min(kTaskQueries, cnt - k * kTaskQueries);
+        tk.qslot = a;
+        tk.nq = b - a;
         tk.ev = e;
         tk.row = (int32_t)row;
         tasks[t] = tk;
     }
+}
+
+void enqueue_tasks(GridBufs& g, int W, int A, Task* out, int32_t* count_out, cudaStream_t st) {
+    const unsigned nb = (unsigned)std::max<int64_t>(1, ceil_div(g.L, 256));
+    k_rowtasks<<<nb, 256, 0, st>>>(g.hdr, g.cell_off, g.E, g.L, g.cstart, g.rtask, W, A);
+    enqueue_scan(g.rtask, g.L, g.parts, count_out, st);
+    k_emit<<<nb, 256, 0, st>>>(g.hdr, g.cell_off, g.E, g.L, g.cstart, g.rtask, count_out, out, W,
+                               A);
 }
 
 // ------------------------------------------------------------------ scan
@@ -519,6 +550,7 @@ int64_t cell_cap_for(int64_t n) {
 static size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 void grid_free(GridBufs& g) {
+    tc_free(g);
     if (g.base) cudaFree(g.base);
     if (g.h_pinned) cudaFreeHost(g.h_pinned);
     if (g.h_pinned_free) cudaEventDestroy(g.h_pinned_free);
@@ -579,7 +611,7 @@ frnn_status grid_alloc(GridBufs& g, int E, const int64_t* n, int D, std::string&
         const size_t o_blk = take(sizeof(int32_t) * (E + 1));
         const size_t o_coff = take(sizeof(int64_t) * (E + 1));
         const size_t o_bbox = take(sizeof(int32_t) * kBBoxStride * E);
-        const size_t o_pts = take(sizeof(float) * DP * cn);
+        const size_t o_pts = take(sizeof(float) * DP * (cn + kTcRowPad));
         const size_t o_perm = take(sizeof(int32_t) * cn);
         const size_t o_cell = take(sizeof(int32_t) * cn);
         const size_t o_cid = take(sizeof(int32_t) * cn);
@@ -689,11 +721,8 @@ frnn_status enqueue_build(GridBufs& g, const float* const* refs, const BuildOpts
     enqueue_scan(g.cstart, g.L, g.parts, g.scalars + kScCellTotal, st);
     k_scatter<<<(unsigned)g.nblk, kBuildPtsPerBlock, smem_pts, st>>>(
         g.hdr, g.blk_start, E, D, g.DP, g.cstart, g.cid, g.rnk, g.pts, g.perm, g.cell);
-    k_rowtasks<<<blocks_for(g.L, 256), 256, 0, st>>>(g.hdr, g.cell_off, E, g.L, g.cstart,
-                                                      g.rtask);
-    enqueue_scan(g.rtask, g.L, g.parts, g.scalars + kScNTasks, st);
-    k_emit<<<blocks_for(g.L, 256), 256, 0, st>>>(g.hdr, g.cell_off, E, g.L, g.cstart, g.rtask,
-                                                  g.scalars + kScNTasks, g.tasks);
+    enqueue_tasks(g, kTaskQueries, 1, g.tasks, g.scalars + kScNTasks, st);
+    g.tc_ready = false;   // tensor-core operands describe the previous contents
     cudaError_t ce = cudaGetLastError();
     if (ce != cudaSuccess) {
         err = std::string("grid build launch failed: ") + cudaGetErrorString(ce);

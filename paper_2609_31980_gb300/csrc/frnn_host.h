@@ -47,6 +47,18 @@ struct GridBufs {
     int32_t* scalars = nullptr;    // [kScalars] counters (below)
     int32_t* parts = nullptr;      // [nparts] scan partial sums
 
+    // tensor-core operands (allocated on the first tensor-core query)
+    bool tc_ready = false;
+    void* tc_base = nullptr;
+    size_t tc_bytes = 0;
+    int64_t tc_cap_rows = 0, tc_cap_tasks = 0, tc_cap_E = 0;
+    int tc_K = 0;                  // operand row length (bf16 elements, multiple of 16)
+    uint16_t* tcA = nullptr;       // [rows] query-role rows, core-matrix layout
+    uint16_t* tcB = nullptr;       // [rows] candidate-role rows, core-matrix layout
+    float* tcn = nullptr;          // [rows] squared norm of the centred split coordinates
+    int32_t* tcnu = nullptr;       // [E] ordered-int max norm per event
+    Task* tc_tasks = nullptr;      // 128-query tasks
+
     // host copies
     std::vector<EventHdr> h_hdr;
     std::vector<int32_t> h_blk_start;
@@ -61,7 +73,9 @@ constexpr int kScCellTotal = 1;     // total of the cell-count scan (= n_total)
 constexpr int kScTaskCounter = 2;   // dynamic task counter of the query kernel
 constexpr int kScOvfCount = 3;      // overflowed queries
 constexpr int kScTcCounter = 4;     // task counter of the tensor-core kernel
+constexpr int kScTcTasks = 5;      // number of tensor-core tasks
 constexpr int kScalars = 16;
+constexpr int kTcRowPad = 512;      // rows readable past the last slot (chunk round-up)
 
 int64_t cell_cap_for(int64_t n);
 
@@ -87,6 +101,9 @@ frnn_status enqueue_build(GridBufs& g, const float* const* refs, const BuildOpts
                           const GridBufs* params_from, int32_t* d_status, cudaStream_t st,
                           bool capturing, std::string& err);
 
+// Task list: windows of W slots aligned to A within each row of cells.
+void enqueue_tasks(GridBufs& g, int W, int A, Task* out, int32_t* count_out, cudaStream_t st);
+
 // Exclusive scan of n int32 values in place; the total goes to *total.
 void enqueue_scan(int32_t* data, int64_t n, int32_t* parts, int32_t* total, cudaStream_t st);
 int64_t scan_parts_needed(int64_t n);
@@ -104,7 +121,18 @@ struct QueryLaunch {
     float* dist2;
     int32_t* d_status;
     int num_sms;
+    unsigned long long* tc_stats = nullptr;   // [2]: pre-filter survivors, exact accepts
 };
 frnn_status enqueue_grid_query(const QueryLaunch& q, cudaStream_t st, std::string& err);
+
+// Tensor-core path: prepare operands (and 128-query tasks) of a point set.
+// center_src: the grid whose per-event centres the operands use (the
+// reference grid; the set itself for self-queries).
+frnn_status tc_prepare(GridBufs& g, const GridBufs& center_src, cudaStream_t st,
+                       std::string& err);
+frnn_status enqueue_tc_query(const QueryLaunch& q, cudaStream_t st, std::string& err);
+frnn_status tc_reserve(GridBufs& g, std::string& err);
+void tc_free(GridBufs& g);
+frnn_status enqueue_overflow(const QueryArgs& a, int num_sms, cudaStream_t st, std::string& err);
 
 }  // namespace frnn

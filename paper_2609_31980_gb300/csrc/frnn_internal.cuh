@@ -21,9 +21,11 @@ constexpr int kStatusNonFinite = 1;
 constexpr int kStatusTimeout = 2;
 constexpr int kStatusCapacity = 4;
 
-// Bounded spin limit for mbarrier waits (iterations of try_wait, each of which
-// itself blocks for a hardware-defined interval): far above any legitimate wait.
-constexpr uint32_t kSpinLimit = 1u << 24;
+// Bounded waits: an mbarrier wait gives up after about two seconds of wall
+// time (%globaltimer), far above any legitimate wait, with an iteration cap as
+// a backstop.
+constexpr uint64_t kWaitLimitNs = 2000000000ull;
+constexpr uint32_t kSpinLimit = 1u << 30;
 
 // Padded point row: D floats rounded up to a multiple of 4 (16 bytes).
 __host__ __device__ constexpr int padded_dim(int D) { return (D + 3) & ~3; }
@@ -54,6 +56,7 @@ struct EventHdr {
     float hi[3];           // per-axis maximum coordinate
     float inv_h;           // 1 / cell edge (float; the value the cell ids use)
     int32_t pad_;
+    float ctr[16];         // per-dimension centre of the bounding box (tensor-core operands)
     // query outputs for batched self-queries (row = original point index)
     int32_t* counts;
     int32_t* idx;
@@ -150,11 +153,21 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
     return ok != 0;
 }
 
+__device__ __forceinline__ uint64_t globaltimer_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
 // Bounded wait: returns false (and the caller records a timeout) if the phase
-// did not complete within kSpinLimit polls.
+// did not complete within kWaitLimitNs.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
-    for (uint32_t it = 0; it < kSpinLimit; ++it)
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = globaltimer_ns();
+    for (uint32_t it = 1; it < kSpinLimit; ++it) {
         if (mbar_try_wait(bar, parity)) return true;
+        if ((it & 63u) == 0 && globaltimer_ns() - t0 > kWaitLimitNs) return false;
+    }
     return false;
 }
 

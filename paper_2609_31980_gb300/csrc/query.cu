@@ -580,17 +580,22 @@ frnn_status enqueue_grid_query(const QueryLaunch& q, cudaStream_t st, std::strin
         err = std::string("grid query launch failed: ") + cudaGetErrorString(ce);
         return FRNN_ERR_CUDA;
     }
-    // overflow pass: buffer of a power of two >= 2K keys per warp
+    return enqueue_overflow(a, q.num_sms, st, err);
+}
+
+frnn_status enqueue_overflow(const QueryArgs& a, int num_sms, cudaStream_t st, std::string& err) {
+    // buffer of a power of two >= 2K keys per warp
     int cap = 64;
-    while (cap < 2 * q.K) cap <<= 1;
+    while (cap < 2 * a.K) cap <<= 1;
     const size_t osmem = (size_t)kOvfWarps * cap * sizeof(uint64_t);
-    ce = cudaFuncSetAttribute(k_overflow, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)osmem);
+    cudaError_t ce =
+        cudaFuncSetAttribute(k_overflow, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)osmem);
     if (ce == cudaSuccess) {
-        k_overflow<<<q.num_sms, kOvfWarps * 32, osmem, st>>>(a, cap);
+        k_overflow<<<num_sms, kOvfWarps * 32, osmem, st>>>(a, cap);
         ce = cudaGetLastError();
     }
     if (ce != cudaSuccess) {
-        err = std::string("overflow launch failed: ") + cudaGetErrorString(ce);
+        err = std::string("selection kernel launch failed: ") + cudaGetErrorString(ce);
         return FRNN_ERR_CUDA;
     }
     return FRNN_OK;

@@ -39,6 +39,9 @@ FRNN_OPT_GRID_AXES = 2
 FRNN_OPT_EXIT_DIMS = 3
 FRNN_OPT_USE_GRAPH = 4
 FRNN_OPT_AUTOTUNE = 5
+FRNN_OPT_AUTO_TC = 6
+FRNN_OPT_TC_SURVIVORS = 7
+FRNN_OPT_TC_ACCEPTED = 8
 
 EXPORTED = ["frnn_version", "frnn_create", "frnn_destroy", "frnn_build_grid",
             "frnn_grid_destroy", "frnn_query", "frnn_query_batched", "frnn_self_query_host",

@@ -283,3 +283,72 @@ def test_batched_equals_alone_and_oracle(ctx):
             _assert_rows_equal(got, alone)
             if len(p) and e % 2 == 0:
                 _assert_rows_equal(got, oracle.self_query(p, 0.1, 64))
+
+
+# ------------------------------------------------------------ tensor-core path
+
+@pytest.mark.parametrize("D", [8, 9, 11, 12, 16])
+def test_tc_path_matches_oracle(ctx, D):
+    pts = synth.clustered(400, 25, 3000, D, 0.025, seed=500 + D)
+    r = 0.1 * np.sqrt(D / 8.0)
+    got = _gpu_self(ctx, pts, r, 64, path="tc")
+    _assert_rows_equal(got, oracle.self_query(pts, r, 64))
+
+
+def test_tc_path_event_300k_x8_sampled_and_equal_to_grid(ctx):
+    w = synth.config2()
+    tc = _gpu_self(ctx, w.points, w.r, w.K, path="tc")
+    grid = _gpu_self(ctx, w.points, w.r, w.K, path="grid")
+    _assert_rows_equal(tc, grid)
+    rows = _sample_rows(len(w.points), 1000, 25)
+    _assert_rows_equal(tc, oracle.self_query(w.points, w.r, w.K, rows=rows), rows)
+
+
+def test_tc_path_event_500k_x12_equal_to_grid(ctx):
+    from paper_2609_31980_gb300 import frnn
+    w = synth.config3()
+    ctx.set_option(frnn.FRNN_OPT_TC_SURVIVORS, 0)
+    tc = _gpu_self(ctx, w.points, w.r, w.K, path="tc")
+    surv = ctx.get_option(frnn.FRNN_OPT_TC_SURVIVORS)
+    acc = ctx.get_option(frnn.FRNN_OPT_TC_ACCEPTED)
+    grid = _gpu_self(ctx, w.points, w.r, w.K, path="grid")
+    _assert_rows_equal(tc, grid)
+    assert acc == int(grid[0].sum()) and surv >= acc
+    rows = _sample_rows(len(w.points), 800, 26)
+    _assert_rows_equal(tc, oracle.self_query(w.points, w.r, w.K, rows=rows), rows)
+
+
+def test_tc_path_dense_and_duplicates(ctx):
+    pts = np.repeat(synth.clustered(20, 40, 100, 8, 0.01, seed=502), 3, axis=0)
+    for K in (8, 32, 100):
+        got = _gpu_self(ctx, pts, 0.05, K, path="tc")
+        _assert_rows_equal(got, oracle.self_query(pts, 0.05, K))
+
+
+def test_tc_path_cross_set_and_small_sizes(ctx):
+    import torch
+    refs = synth.clustered(100, 20, 1000, 8, 0.03, seed=503)
+    qs = np.concatenate([synth.clustered(30, 10, 300, 8, 0.03, seed=504),
+                         synth.uniform(50, 8, seed=505, lo=-1.5, hi=1.5)])
+    g = ctx.build_grid(torch.from_numpy(refs).cuda(), 0.15)
+    c, i, d = ctx.query(g, torch.from_numpy(qs).cuda(), 0.15, 40, self_query=False, path="tc")
+    ctx.sync()
+    _assert_rows_equal((c.cpu().numpy(), i.cpu().numpy(), d.cpu().numpy()),
+                       oracle.frnn(qs, refs, 0.15, 40))
+    for n in (1, 2, 7, 9, 129, 300):
+        pts = synth.uniform(n, 8, seed=506 + n) * np.float32(0.3)
+        _assert_rows_equal(_gpu_self(ctx, pts, 0.2, 16, path="tc"), oracle.self_query(pts, 0.2, 16))
+
+
+def test_tc_path_batched_equals_alone(ctx):
+    import torch
+    sizes = [3000, 1, 0, 5001, 129]
+    evs = [synth.event_mix(n, 8, (41, e)) if n else np.zeros((0, 8), np.float32)
+           for e, n in enumerate(sizes)]
+    tev = [torch.from_numpy(np.ascontiguousarray(p)).cuda() for p in evs]
+    for rep in range(2):
+        outs = ctx.query_batched(tev, 0.1, 64, path="tc")
+        ctx.sync()
+        for p, (c, i, d) in zip(evs, outs):
+            got = (c.cpu().numpy(), i.cpu().numpy(), d.cpu().numpy())
+            _assert_rows_equal(got, _gpu_self(ctx, p, 0.1, 64, path="grid"))
