@@ -110,9 +110,9 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def workload():
+def workload(name="event300k"):
     from paper_2609_31980_gb300 import synth
-    return synth.config2()
+    return synth.config3() if name == "event500k" else synth.config2()
 
 
 def algorithmic_query_bytes(N: int, D: int, K: int) -> int:
@@ -144,9 +144,10 @@ def run_ours(args):
     else:
         torch.cuda.set_device(0)
     dev = torch.device("cuda", torch.cuda.current_device())
-    w = workload()
+    w = workload(args.workload)
     pts_np = w.points
     N, D, r, K = pts_np.shape[0], w.D, w.r, w.K
+    path = args.path
     stream = torch.cuda.Stream()
     ctx = frnn.Context(stream=stream)
     if args.cell_mult:
@@ -162,7 +163,7 @@ def run_ours(args):
         d2 = torch.empty((N, K), dtype=torch.float32, device=dev)
         flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
     grid = ctx.build_grid(pts, r)
-    ctx.query(grid, pts, r, K, True, "grid", (counts, idx, d2))
+    ctx.query(grid, pts, r, K, True, path, (counts, idx, d2))
     ctx.sync()
 
     def step(ev=None):
@@ -171,7 +172,7 @@ def run_ours(args):
         ctx.build_grid(pts, r, grid=grid)
         if ev is not None:
             ev[1].record(stream)
-        ctx.query(grid, pts, r, K, True, "grid", (counts, idx, d2))
+        ctx.query(grid, pts, r, K, True, path, (counts, idx, d2))
         if ev is not None:
             ev[2].record(stream)
 
@@ -212,7 +213,7 @@ def run_ours(args):
     h_c = torch.empty(N, dtype=torch.int32).pin_memory()
     h_i = torch.empty((N, K), dtype=torch.int32).pin_memory()
     h_d = torch.empty((N, K), dtype=torch.float32).pin_memory()
-    e2e_args = (h_pts.numpy(), r, K, "grid", (h_c.numpy(), h_i.numpy(), h_d.numpy()))
+    e2e_args = (h_pts.numpy(), r, K, path, (h_c.numpy(), h_i.numpy(), h_d.numpy()))
     for _ in range(max(1, args.warmup)):
         ctx.self_query_host(*e2e_args)
     t0 = time.perf_counter()
@@ -238,7 +239,7 @@ def run_ours(args):
         "vs_baseline": None,
         "dtype": "f32",
         "data": "synthetic (seeded clusters + background shaped like a tracking event)",
-        "config": {"workload": w.name, "N": N, "D": D, "r": r, "K": K, "path": "grid",
+        "config": {"workload": w.name, "N": N, "D": D, "r": r, "K": K, "path": path,
                    "cell_mult": ctx.get_option(frnn.FRNN_OPT_CELL_MULT),
                    "exit_dims": ctx.get_option(frnn.FRNN_OPT_EXIT_DIMS),
                    "self_query": True, "l2": "flushed between timed steps (256 MB write)",
@@ -330,6 +331,8 @@ def main():
     ap.add_argument("--cell-mult", type=int, default=0, help="grid cell multiple m (0: library default)")
     ap.add_argument("--exit-dims", type=int, default=0, help="dims before the warp vote (0: default)")
     ap.add_argument("--grid-axes", type=int, default=0, help="0: last axes, 1: widest axes")
+    ap.add_argument("--path", default="grid", choices=["grid", "tc", "auto"])
+    ap.add_argument("--workload", default="event300k", choices=["event300k", "event500k"])
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -141,14 +141,16 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
         : "memory");
 }
 
+// try_wait suspends the thread until the phase completes or a time hint
+// (here 20 us) elapses, so waiting warps do not spin on the issue slots.
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
     uint32_t ok;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
         "selp.u32 %0, 1, 0, p;\n\t}"
         : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
+        : "r"(smem_u32(bar)), "r"(parity), "r"(20000)
         : "memory");
     return ok != 0;
 }
@@ -166,7 +168,7 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
     const uint64_t t0 = globaltimer_ns();
     for (uint32_t it = 1; it < kSpinLimit; ++it) {
         if (mbar_try_wait(bar, parity)) return true;
-        if ((it & 63u) == 0 && globaltimer_ns() - t0 > kWaitLimitNs) return false;
+        if ((it & 7u) == 0 && globaltimer_ns() - t0 > kWaitLimitNs) return false;
     }
     return false;
 }
@@ -186,5 +188,71 @@ inline int32_t host_float_to_ordered(float f) {
 }
 
 __host__ __device__ constexpr int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+// ------------------------------------------------------------ per-thread sort
+// A thread's neighbour list lives in shared memory as a column of a
+// transposed table: entry e at d2[e * stride], slot[e * stride] (slot = the
+// reference's sorted slot).  Sorting maps slots to original indices (the
+// tie-break key), builds 64-bit keys (d2 bits << 32 | index) (d2 >= +0, so
+// the unsigned order of the keys is the (d2, index) order) and runs a fixed
+// bitonic network in registers: no data-dependent branches, so the lanes of
+// a warp stay converged and the index loads are issued together.
+template <int S>
+__device__ __forceinline__ void sort_list_net(float* d2, int32_t* idx, int stride, int cnt,
+                                              const int32_t* perm) {
+    uint64_t k[S];
+#pragma unroll
+    for (int e = 0; e < S; ++e) {
+        k[e] = ~0ull;
+        if (e < cnt) {
+            const int32_t slot = idx[e * stride];
+            k[e] = ((uint64_t)__float_as_uint(d2[e * stride]) << 32) | (uint32_t)perm[slot];
+        }
+    }
+#pragma unroll
+    for (int kk = 2; kk <= S; kk <<= 1) {
+#pragma unroll
+        for (int j = kk >> 1; j > 0; j >>= 1) {
+#pragma unroll
+            for (int i = 0; i < S; ++i) {
+                const int l = i ^ j;
+                if (l > i) {
+                    const bool up = (i & kk) == 0;
+                    const uint64_t x = k[i], y = k[l];
+                    const bool sw = up ? (x > y) : (x < y);
+                    k[i] = sw ? y : x;
+                    k[l] = sw ? x : y;
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int e = 0; e < S; ++e) {
+        if (e < cnt) {
+            d2[e * stride] = __uint_as_float((uint32_t)(k[e] >> 32));
+            idx[e * stride] = (int32_t)(uint32_t)k[e];
+        }
+    }
+}
+
+// Sort one thread's list of cnt <= 32 entries (warp-uniform network size).
+__device__ __forceinline__ void sort_list(float* d2, int32_t* idx, int stride, int cnt,
+                                          const int32_t* perm) {
+    const unsigned full = __activemask();
+    int mx = cnt;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(full, mx, o));
+    if (mx <= 1) {
+        if (cnt == 1) idx[0] = perm[idx[0]];
+    } else if (mx <= 4) {
+        sort_list_net<4>(d2, idx, stride, cnt, perm);
+    } else if (mx <= 8) {
+        sort_list_net<8>(d2, idx, stride, cnt, perm);
+    } else if (mx <= 16) {
+        sort_list_net<16>(d2, idx, stride, cnt, perm);
+    } else {
+        sort_list_net<32>(d2, idx, stride, cnt, perm);
+    }
+}
 
 }  // namespace frnn

@@ -29,8 +29,9 @@
 //   * survivors are appended (d2, original index) to the lane's list in
 //     shared memory (the original index is looked up only for survivors: the
 //     paper's deferred lookup, Table 3);
-//   * at the end of the task every lane insertion-sorts its own list by
-//     (d2, index) in parallel, keeps the first K (count = min(degree, K)),
+//   * at the end of the task every lane sorts its own list by (d2, index)
+//     with a register bitonic network, keeps the first K (count =
+//     min(degree, K)),
 //     and the warp writes the rows coalesced with their padding.  Lists longer
 //     than 32 (never in the tracking-like workloads) go to an exact selection
 //     kernel; so does any degree > K beyond the list, keeping results exact
@@ -318,9 +319,9 @@ __global__ void __launch_bounds__(kQueryWarps * 32, 4) k_grid_query(QueryArgs a)
                         const float d = __fsub_rn(qk, cpf[2 * k]);
                         sv = __fadd_rn(sv, __fmul_rn(d, d));
                     }
-                    if (sv <= r2) {
+                    if (sv <= r2) {   // slot now, original index at the sort
                         Ld[wpos * kListStride + lane] = sv;
-                        Li[wpos * kListStride + lane] = a.rperm[cs];
+                        Li[wpos * kListStride + lane] = cs;
                         ++wpos;
                     }
                 }
@@ -351,28 +352,11 @@ __global__ void __launch_bounds__(kQueryWarps * 32, 4) k_grid_query(QueryArgs a)
             }
             return;
         }
-        // each lane sorts its own list by (d2, index): insertion sort, all
-        // lanes in parallel (the transposed layout keeps every access in the
-        // lane's own bank)
+        // each lane sorts its own list by (d2, original index), all lanes in
+        // parallel (register bitonic network, see sort_list)
         const bool spill = lost;
-        if (act && !spill) {
-            for (int e = 1; e < cnt; ++e) {
-                const float kd = Ld[e * kListStride + lane];
-                const int ki = Li[e * kListStride + lane];
-                int j = e - 1;
-                while (j >= 0) {
-                    const float dj = Ld[j * kListStride + lane];
-                    const int ij = Li[j * kListStride + lane];
-                    if (dj < kd || (dj == kd && ij < ki)) break;
-                    Ld[(j + 1) * kListStride + lane] = dj;
-                    Li[(j + 1) * kListStride + lane] = ij;
-                    --j;
-                }
-                Ld[(j + 1) * kListStride + lane] = kd;
-                Li[(j + 1) * kListStride + lane] = ki;
-            }
-            counts[qorig] = min(cnt, K);
-        }
+        sort_list(Ld + lane, Li + lane, kListStride, (act && !spill) ? cnt : 0, a.rperm);
+        if (act && !spill) counts[qorig] = min(cnt, K);
         if (act && spill) {
             // longer than the list: the exact selection kernel finishes this row
             const int pos = atomicAdd(a.ovf_count, 1);

@@ -33,17 +33,18 @@
 // is what the false-candidate rate measures.
 //
 // Kernel organisation (one persistent CTA per SM, 8 warps, 512 TMEM columns):
-//   * thread 0 is the producer: cp.async.bulk of the A tile (128 query rows)
-//     and, per chunk, of the B tile plus the float32 coordinates of the same
-//     candidates (for the recheck) into a 3-deep ring, then issues the MMAs
-//     (K/16 instructions, accumulator double-buffered in TMEM: 2 x 256 cols);
-//   * all 8 warps run the epilogue: warp w reads TMEM lanes 32 (w % 4).. and
-//     column half w / 4 with tcgen05.ld 32x32b.x32, tests 32 pairs with a
-//     3-input max tree, and only where a value reaches t(x) builds the bit
-//     mask and rechecks those candidates exactly from shared memory;
-//   * per (query, half) survivor lists in shared memory are merged, sorted by
-//     (d2, index) per query and written as coalesced rows.  Lists longer than
-//     the capacity go to the exact selection kernel (query.cu).
+//   * a producer warp issues cp.async.bulk copies of the A tile (128 query
+//     rows) and, per chunk of up to 128 candidates, of the B tile plus the
+//     float32 coordinates of the same candidates (for the recheck) into a
+//     3-deep ring, and the MMAs (K/16 instructions per chunk) into one of two
+//     TMEM accumulators (2 x 128 columns; two CTAs per SM share the 512);
+//   * four epilogue warps: warp w reads TMEM lanes 32w.. with tcgen05.ld
+//     32x32b.x32, tests 32 pairs per thread with a 3-input max tree, and where
+//     a value reaches t(x) compacts the warp's survivors so that all 32 lanes
+//     recheck them exactly from shared memory;
+//   * per-query survivor lists in shared memory are sorted by (d2, index)
+//     with a register network and written as coalesced rows.  Lists longer
+//     than the capacity go to the exact selection kernel (query.cu).
 // Every mbarrier wait is bounded; on a timeout the CTA records the status,
 // stops, waits (bounded) for its copies and MMAs in flight and frees TMEM.
 #include <cuda_bf16.h>
@@ -56,20 +57,45 @@
 namespace frnn {
 
 constexpr int kTcM = 128;        // queries per task = MMA M = TMEM lanes
-constexpr int kTcN = 256;        // candidates per chunk = max MMA N
-constexpr int kTcThreads = 256;  // 8 warps
-constexpr int kTcLStr = kTcThreads + 1;
+constexpr int kTcN = 128;        // candidates per chunk = MMA N (multiple of 32)
+constexpr int kTcAcc = 2;        // TMEM accumulators in flight (kTcAcc * kTcN = kTcCols)
+constexpr int kTcEpi = 128;      // epilogue threads: warp w < 4 owns TMEM lanes 32w..32w+31
+constexpr int kTcThreads = kTcEpi + 32;   // + one producer warp (bulk copies, MMA issue)
+constexpr int kTcLStr = kTcEpi + 1;
 constexpr int kTcMaxRows = 32;   // neighbour rows per task (m <= 2)
-constexpr int kTcRing = 3;       // operand ring depth
+constexpr int kTcCols = 256;     // TMEM columns per CTA: two accumulators (2 CTAs / SM)
+// (the producer warp is warp 4; epilogue warps 0..3 own the TMEM lane quarters)
+constexpr int kTcList = 30;      // per-query survivor list capacity (2 CTAs / SM up to D = 12)
 
 __host__ __device__ constexpr int tc_k_for(int D) { return ((3 * D + 2) + 15) / 16 * 16; }
-__host__ __device__ constexpr int tc_list_cap(int KS) { return KS >= 4 ? 30 : 32; }
 
-__host__ __device__ constexpr size_t tc_smem_bytes(int KS, int DP) {
-    return (size_t)kTcM * 16 * KS * 2                          // A tile
-           + (size_t)kTcRing * kTcN * 16 * KS * 2              // B ring
-           + (size_t)kTcRing * kTcN * DP * 4                   // float32 candidate ring
-           + (size_t)tc_list_cap(KS) * kTcLStr * 8;            // per-thread lists
+// shared memory outside the operand ring
+__host__ __device__ constexpr size_t tc_smem_fixed(int K, int DP);
+// operand ring depth: as deep as fits two CTAs per SM (<= 110 KB each), 3..8
+__host__ __device__ constexpr int tc_ring_for(int D);
+
+constexpr int kTcSurvCap = 32 * 32;   // survivor (row, column) pairs of one warp and 32 columns
+
+__host__ __device__ constexpr size_t tc_smem_fixed(int K, int DP) {
+    return (size_t)kTcM * K * 2                                // A tile
+           + (size_t)kTcList * kTcLStr * 8                     // per-query lists
+           + (size_t)kTcM * DP * 4                             // query coordinates
+           + (size_t)(kTcEpi / 32) * kTcSurvCap * 2;           // per-warp survivor buffers
+}
+__host__ __device__ constexpr size_t tc_slot_bytes(int K, int DP) {
+    return (size_t)kTcN * K * 2 + (size_t)kTcN * DP * 4;       // B tile + float32 candidates
+}
+__host__ __device__ constexpr int tc_ring_for(int D) {
+    int r = 8;
+    while (r > 3 && tc_smem_fixed(tc_k_for(D), padded_dim(D)) +
+                            (size_t)r * tc_slot_bytes(tc_k_for(D), padded_dim(D)) >
+                        110 * 1024)
+        --r;
+    return r;
+}
+__host__ __device__ constexpr size_t tc_smem_bytes(int D) {
+    return tc_smem_fixed(tc_k_for(D), padded_dim(D)) +
+           (size_t)tc_ring_for(D) * tc_slot_bytes(tc_k_for(D), padded_dim(D));
 }
 
 // element offset of (row s, column k) in the core-matrix layout of rows of K
@@ -95,58 +121,73 @@ __device__ __forceinline__ uint16_t bf16_bits(__nv_bfloat16 v) {
 
 // One thread per slot: centred split operands, norm, per-event max norm.
 // own: headers of this point set; ctr: headers whose centres to use.
-__global__ void k_tc_prep(const EventHdr* own, const EventHdr* ctr, int E, int D, int64_t n_total,
+template <int D>
+__global__ void k_tc_prep(const EventHdr* own, const EventHdr* ctr, int E, int64_t n_total,
                           const float* pts, uint16_t* tcA, uint16_t* tcB, float* tcn,
-                          int32_t* tcnu, int K) {
+                          int32_t* tcnu) {
+    constexpr int K = tc_k_for(D);
+    constexpr int DP = padded_dim(D);
     const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n_total) return;
     const int e = find_event_slot(own, E, s);
     const EventHdr& h = own[e];
     const bool real = s < h.pt_off + h.n && ctr[e].valid;
-    const int DP = padded_dim(D);
-    uint16_t ra[64], rb[64];
-#pragma unroll
-    for (int k = 0; k < 64; ++k) { ra[k] = 0; rb[k] = 0; }
+    uint16_t hi[D], lo[D];
     float n = 0.f;
-    if (real) {
-        const __nv_bfloat16 one = __float2bfloat16_rn(1.f);
 #pragma unroll
-        for (int k = 0; k < kMaxD; ++k) {
-            if (k < D) {
-                const float xc = __fsub_rn(pts[pair_index(s, k, DP)], ctr[e].ctr[k]);
-                const __nv_bfloat16 hi = __float2bfloat16_rn(xc);
-                const __nv_bfloat16 lo = __float2bfloat16_rn(__fsub_rn(xc, __bfloat162float(hi)));
-                const float xh = __fadd_rn(__bfloat162float(hi), __bfloat162float(lo));
-                n = __fmaf_rn(xh, xh, n);
-                ra[k] = bf16_bits(hi); ra[D + k] = bf16_bits(hi); ra[2 * D + k] = bf16_bits(lo);
-                rb[k] = bf16_bits(hi); rb[D + k] = bf16_bits(lo); rb[2 * D + k] = bf16_bits(hi);
-            }
+    for (int k = 0; k < D; ++k) {
+        hi[k] = 0;
+        lo[k] = 0;
+        if (real) {
+            const float xc = __fsub_rn(pts[pair_index(s, k, DP)], ctr[e].ctr[k]);
+            const __nv_bfloat16 bh = __float2bfloat16_rn(xc);
+            const __nv_bfloat16 bl = __float2bfloat16_rn(__fsub_rn(xc, __bfloat162float(bh)));
+            const float xh = __fadd_rn(__bfloat162float(bh), __bfloat162float(bl));
+            n = __fmaf_rn(xh, xh, n);
+            hi[k] = bf16_bits(bh);
+            lo[k] = bf16_bits(bl);
         }
-        const float mneg = -0.5f * n;
-        const __nv_bfloat16 mh = __float2bfloat16_rn(mneg);
-        const __nv_bfloat16 ml = __float2bfloat16_rn(__fsub_rn(mneg, __bfloat162float(mh)));
-        ra[3 * D] = bf16_bits(one);
-        ra[3 * D + 1] = bf16_bits(one);
-        rb[3 * D] = bf16_bits(mh);
-        rb[3 * D + 1] = bf16_bits(ml);
     }
-    // 8 bf16 (16 bytes) per core-matrix row segment
+    uint16_t one = 0, mh = 0, ml = 0;
+    if (real) {
+        const float mneg = -0.5f * n;
+        const __nv_bfloat16 bmh = __float2bfloat16_rn(mneg);
+        const __nv_bfloat16 bml = __float2bfloat16_rn(__fsub_rn(mneg, __bfloat162float(bmh)));
+        one = bf16_bits(__float2bfloat16_rn(1.f));
+        mh = bf16_bits(bmh);
+        ml = bf16_bits(bml);
+    }
+    // A = [hi, hi, lo, 1, 1, 0...], B = [hi, lo, hi, m_hi, m_lo, 0...]
+    auto a_el = [&](int j) -> uint32_t {
+        return j < D ? hi[j] : j < 2 * D ? hi[j - D] : j < 3 * D ? lo[j - 2 * D]
+               : (j == 3 * D || j == 3 * D + 1) ? one : 0;
+    };
+    auto b_el = [&](int j) -> uint32_t {
+        return j < D ? hi[j] : j < 2 * D ? lo[j - D] : j < 3 * D ? hi[j - 2 * D]
+               : j == 3 * D ? mh : j == 3 * D + 1 ? ml : 0;
+    };
+#pragma unroll
     for (int kg = 0; kg < K / 8; ++kg) {
         uint4 va, vb;
-        va.x = ra[8 * kg + 0] | ((uint32_t)ra[8 * kg + 1] << 16);
-        va.y = ra[8 * kg + 2] | ((uint32_t)ra[8 * kg + 3] << 16);
-        va.z = ra[8 * kg + 4] | ((uint32_t)ra[8 * kg + 5] << 16);
-        va.w = ra[8 * kg + 6] | ((uint32_t)ra[8 * kg + 7] << 16);
-        vb.x = rb[8 * kg + 0] | ((uint32_t)rb[8 * kg + 1] << 16);
-        vb.y = rb[8 * kg + 2] | ((uint32_t)rb[8 * kg + 3] << 16);
-        vb.z = rb[8 * kg + 4] | ((uint32_t)rb[8 * kg + 5] << 16);
-        vb.w = rb[8 * kg + 6] | ((uint32_t)rb[8 * kg + 7] << 16);
+        va.x = a_el(8 * kg + 0) | (a_el(8 * kg + 1) << 16);
+        va.y = a_el(8 * kg + 2) | (a_el(8 * kg + 3) << 16);
+        va.z = a_el(8 * kg + 4) | (a_el(8 * kg + 5) << 16);
+        va.w = a_el(8 * kg + 6) | (a_el(8 * kg + 7) << 16);
+        vb.x = b_el(8 * kg + 0) | (b_el(8 * kg + 1) << 16);
+        vb.y = b_el(8 * kg + 2) | (b_el(8 * kg + 3) << 16);
+        vb.z = b_el(8 * kg + 4) | (b_el(8 * kg + 5) << 16);
+        vb.w = b_el(8 * kg + 6) | (b_el(8 * kg + 7) << 16);
         const int64_t off = cm_off(s, 8 * kg, K);
         *reinterpret_cast<uint4*>(tcA + off) = va;
         *reinterpret_cast<uint4*>(tcB + off) = vb;
     }
     tcn[s] = n;
-    if (real) atomicMax(tcnu + e, float_to_ordered(n));
+    // per-event maximum: reduce across the warp first when its lanes share an
+    // event (almost always), one atomic per warp instead of one per point
+    const int32_t on = real ? float_to_ordered(n) : INT32_MIN;
+    const unsigned same = __match_any_sync(__activemask(), e);
+    const int32_t wmax = __reduce_max_sync(same, on);
+    if (real && (threadIdx.x & 31) == __ffs(same) - 1) atomicMax(tcnu + e, wmax);
 }
 
 // ------------------------------------------------------------- tcgen05 helpers
@@ -210,6 +251,22 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
     for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
 }
 
+// tcgen05.ld of 32 columns without the wait (several loads share one wait)
+__device__ __forceinline__ void tmem_ld32_nowait(uint32_t taddr, uint32_t (&r)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+        "%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+          "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+          "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
+          "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_wait_ld() {
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
 __device__ __forceinline__ float fmax3(float a, float b, float c) {
     float d;
     asm("max.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
@@ -262,49 +319,55 @@ __device__ __forceinline__ void chunk_info(const ChunkTab& t, int c, int& start,
     start = t.b8[L] + (c - t.pref[L]) * kTcN;
     const int e8 = (t.re[L] + 7) & ~7;
     n = min(kTcN, e8 - start);
-    n = (n + 15) & ~15;
+    n = (n + 31) & ~31;   // whole 32-column TMEM loads; extra rows are masked by [lo, hi)
     lo = t.rs[L];
     hi = t.re[L];
 }
 
-template <int KS>
-__global__ void __launch_bounds__(kTcThreads, 1) k_tc_query(TcArgs a) {
-    constexpr int K = 16 * KS;
-    constexpr int LCAP = tc_list_cap(KS);
+template <int D>
+__global__ void __launch_bounds__(kTcThreads, 2) k_tc_query(TcArgs a) {
+    constexpr int K = tc_k_for(D);
+    constexpr int KS = K / 16;
+    constexpr int DP = padded_dim(D);
+    constexpr int kTcRing = tc_ring_for(D);
     extern __shared__ __align__(1024) unsigned char smem[];
-    const int D = a.D;
-    const int DP = padded_dim(D);
     uint16_t* As = reinterpret_cast<uint16_t*>(smem);
     uint16_t* Bs = As + kTcM * K;
     float* Fs = reinterpret_cast<float*>(Bs + kTcRing * kTcN * K);
     float* Ld = Fs + kTcRing * kTcN * DP;
-    int32_t* Li = reinterpret_cast<int32_t*>(Ld + LCAP * kTcLStr);
+    int32_t* Li = reinterpret_cast<int32_t*>(Ld + kTcList * kTcLStr);
+    float* Qs = reinterpret_cast<float*>(Li + kTcList * kTcLStr);      // [128][DP]
+    uint16_t* Sv = reinterpret_cast<uint16_t*>(Qs + kTcM * DP);        // [4][kTcSurvCap]
 
-    __shared__ __align__(8) uint64_t bar_a, bar_b[kTcRing], bar_mma[2], bar_free[2];
+    // bar_b: chunk operands landed; bar_mma: accumulator ready; bar_acc:
+    // epilogue done with an accumulator; bar_slot: epilogue done with a ring slot
+    __shared__ __align__(8) uint64_t bar_a, bar_b[kTcRing], bar_mma[kTcAcc], bar_acc[kTcAcc],
+        bar_slot[kTcRing];
     __shared__ uint32_t s_taddr;
     __shared__ Task s_task;
     __shared__ int s_done, s_abort;
     __shared__ ChunkTab s_ct;
-    __shared__ int s_cnt[kTcThreads];
-    __shared__ int s_lost[kTcThreads];
-    __shared__ int s_qorig[kTcM];
+    __shared__ int s_cnt[kTcM];
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int quarter = warp & 3, half = warp >> 2;
-    const int row = 32 * quarter + lane;   // TMEM lane / query row in the tile
+    const bool producer = warp == kTcEpi / 32;
+    const int row = tid;   // TMEM lane / query row (epilogue threads)
 
     if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(
-                         smem_u32(&s_taddr))
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(&s_taddr)), "n"(kTcCols)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     if (tid == 0) {
         mbar_init(&bar_a, 1);
-        for (int i = 0; i < kTcRing; ++i) mbar_init(&bar_b[i], 1);
-        for (int i = 0; i < 2; ++i) {
+        for (int i = 0; i < kTcRing; ++i) {
+            mbar_init(&bar_b[i], 1);
+            mbar_init(&bar_slot[i], kTcEpi);
+        }
+        for (int i = 0; i < kTcAcc; ++i) {
             mbar_init(&bar_mma[i], 1);
-            mbar_init(&bar_free[i], kTcThreads);
+            mbar_init(&bar_acc[i], kTcEpi);
         }
         s_abort = 0;
         fence_mbar_init();
@@ -323,48 +386,17 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_query(TcArgs a) {
 
     uint32_t task_no = 0;
     uint32_t g0 = 0;          // global chunk counter at the start of the task
-    int issued_loads = 0;     // producer bookkeeping (thread 0): chunks loaded / MMAs issued
-    int issued_mma = 0;
     unsigned long long n_surv = 0, n_acc = 0;
 
-    // producer helpers (thread 0 only)
-    auto load_chunk = [&](int c, uint32_t g) {
-        int start, n, lo, hi;
-        chunk_info(s_ct, c, start, n, lo, hi);
-        const int slot = g % kTcRing;
-        const uint32_t bB = (uint32_t)n * K * 2;
-        const uint32_t bF = (uint32_t)n * DP * 4;
-        mbar_arrive_expect_tx(&bar_b[slot], bB + bF);
-        bulk_g2s(Bs + (size_t)slot * kTcN * K, a.tcB + cm_off(start, 0, K), bB, &bar_b[slot]);
-        bulk_g2s(Fs + (size_t)slot * kTcN * DP, a.rpts + (int64_t)(start >> 1) * 2 * DP, bF,
-                 &bar_b[slot]);
-    };
     auto abort_now = [&]() {
         atomicOr(a.status, kStatusTimeout);
         atomicExch(&s_abort, 1);
     };
     auto aborted = [&]() -> int { return *reinterpret_cast<volatile int*>(&s_abort); };
-    auto issue_mma = [&](int c, uint32_t g) -> bool {
-        const int slot = g % kTcRing;
-        if (!mbar_wait_bounded(&bar_b[slot], (g / kTcRing) & 1u)) return false;
-        if (g >= 2 && !mbar_wait_bounded(&bar_free[g & 1], ((g - 2) >> 1) & 1u)) return false;
-        tc_fence_after();
-        int start, n, lo, hi;
-        chunk_info(s_ct, c, start, n, lo, hi);
-        const uint32_t idesc = mma_idesc(n);
-        const uint32_t bbase = sB + (uint32_t)(slot * kTcN * K * 2);
-#pragma unroll
-        for (int ks = 0; ks < KS; ++ks) {
-            mma_bf16(taddr + (g & 1) * kTcN, smem_desc(sA + ks * 256, lbo, sbo),
-                     smem_desc(bbase + ks * 256, lbo, sbo), idesc, ks > 0 ? 1u : 0u);
-        }
-        mma_commit(&bar_mma[g & 1]);
-        return true;
-    };
 
     for (;;) {
         __syncthreads();
-        if (tid == 0) {
+        if (tid == kTcEpi) {
             const int t = atomicAdd(a.task_counter, 1);
             s_done = (t >= ntasks) || aborted();
             if (t < ntasks) s_task = a.tasks[t];
@@ -378,12 +410,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_query(TcArgs a) {
         float* od2 = a.counts ? a.dist2 : h.dist2;
         const int w0 = tk.qslot & ~7;
         const int qs = w0 + row;
-        const bool active = qs >= tk.qslot && qs < tk.qslot + tk.nq;
+        const bool active = !producer && qs >= tk.qslot && qs < tk.qslot + tk.nq;
         const int qorig = active ? a.qperm[qs] : 0;
-        if (half == 0) s_qorig[row] = qorig;
         if (!h.valid) {
             // grid built from non-finite input: empty rows (frnn_sync reports it)
-            if (half == 0 && active) {
+            if (active) {
                 for (int e = 0; e < Kout; ++e) {
                     oidx[(int64_t)qorig * Kout + e] = -1;
                     od2[(int64_t)qorig * Kout + e] = INFINITY;
@@ -392,8 +423,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_query(TcArgs a) {
             }
             continue;
         }
-        // neighbour rows and chunk table (warp 0)
-        if (warp == 0) {
+        if (producer) {
+            // neighbour rows and chunk table
             const int dims0 = h.dims[0], dims1 = h.dims[1], dims2 = h.dims[2], m = h.m;
             const int xa = a.qcell[tk.qslot] % dims0;
             const int xb = a.qcell[tk.qslot + tk.nq - 1] % dims0;
@@ -420,198 +451,248 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_query(TcArgs a) {
                 const int v = __shfl_up_sync(0xffffffffu, pre, o);
                 if (lane >= o) pre += v;
             }
-            if (lane < kTcMaxRows) {
-                s_ct.rs[lane] = rs;
-                s_ct.re[lane] = re;
-                s_ct.b8[lane] = b8;
-                s_ct.pref[lane] = pre - nch;
-            }
+            s_ct.rs[lane] = rs;
+            s_ct.re[lane] = re;
+            s_ct.b8[lane] = b8;
+            s_ct.pref[lane] = pre - nch;
             if (lane == 31) {
                 s_ct.nch = pre;
                 s_ct.nrows = nrows;
             }
+        } else {
+            // this thread's query: float32 coordinates (shared: the recheck
+            // reads them from any lane)
+#pragma unroll
+            for (int k = 0; k < D; ++k)
+                Qs[row * DP + k] = active ? a.qpts[pair_index(qs, k, DP)] : 0.f;
+            s_cnt[row] = 0;
         }
         __syncthreads();
         const int nch = s_ct.nch;
 
-        // this thread's query: float32 coordinates and the pass threshold
-        float q[kMaxD];
+        if (producer) {
+            // ---------------------------------------------------- producer
+            if (lane == 0 && nch > 0) {
+                // ring slot g % R is free once the epilogue of chunk g - R is done
+                auto slot_free_now = [&](uint32_t g) -> bool {
+                    if (g < (uint32_t)kTcRing) return true;
+                    uint32_t ok2;
+                    asm volatile(
+                        "{\n\t.reg .pred p;\n\t"
+                        "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                        "selp.u32 %0, 1, 0, p;\n\t}"
+                        : "=r"(ok2)
+                        : "r"(smem_u32(&bar_slot[g % kTcRing])),
+                          "r"(((g - kTcRing) / kTcRing) & 1u)
+                        : "memory");
+                    return ok2 != 0;
+                };
+                auto issue_load = [&](int c, uint32_t g) {
+                    int start, n, lo, hi;
+                    chunk_info(s_ct, c, start, n, lo, hi);
+                    const int slot = g % kTcRing;
+                    const uint32_t bB = (uint32_t)n * K * 2;
+                    const uint32_t bF = (uint32_t)n * DP * 4;
+                    mbar_arrive_expect_tx(&bar_b[slot], bB + bF);
+                    bulk_g2s(Bs + (size_t)slot * kTcN * K, a.tcB + cm_off(start, 0, K), bB,
+                             &bar_b[slot]);
+                    bulk_g2s(Fs + (size_t)slot * kTcN * DP, a.rpts + (int64_t)(start >> 1) * 2 * DP,
+                             bF, &bar_b[slot]);
+                };
+                const uint32_t bA = (uint32_t)kTcM * K * 2;
+                mbar_arrive_expect_tx(&bar_a, bA);
+                bulk_g2s(As, a.tcA + cm_off(w0, 0, K), bA, &bar_a);
+                int next_load = 0, issued_mma = 0;
+                bool ok = true;
+                // loads run ahead as far as ring slots are free
+                while (next_load < nch && next_load < kTcRing && slot_free_now(g0 + next_load)) {
+                    issue_load(next_load, g0 + next_load);
+                    ++next_load;
+                }
+                ok = mbar_wait_bounded(&bar_a, task_no & 1u);
+                for (int c = 0; ok && c < nch; ++c) {
+                    const uint32_t g = g0 + c;
+                    const int slot = g % kTcRing;
+                    while (ok && next_load <= c) {   // this chunk's operands must be on their way
+                        const uint32_t gl = g0 + next_load;
+                        if (gl >= (uint32_t)kTcRing)
+                            ok = mbar_wait_bounded(&bar_slot[gl % kTcRing],
+                                                   ((gl - kTcRing) / kTcRing) & 1u);
+                        if (ok) {
+                            issue_load(next_load, gl);
+                            ++next_load;
+                        }
+                    }
+                    // operands landed and the accumulator's previous epilogue done
+                    if (ok) ok = mbar_wait_bounded(&bar_b[slot], (g / kTcRing) & 1u);
+                    if (ok && g >= (uint32_t)kTcAcc)
+                        ok = mbar_wait_bounded(&bar_acc[g % kTcAcc], ((g - kTcAcc) / kTcAcc) & 1u);
+                    if (!ok) break;
+                    tc_fence_after();
+                    int start, n, lo, hi;
+                    chunk_info(s_ct, c, start, n, lo, hi);
+                    const uint32_t idesc = mma_idesc(n);
+                    const uint32_t bbase = sB + (uint32_t)(slot * kTcN * K * 2);
 #pragma unroll
-        for (int k = 0; k < kMaxD; ++k)
-            q[k] = (active && k < D) ? a.qpts[pair_index(qs, k, DP)] : 0.f;
-        float tx = INFINITY;
-        if (active) {
-            const double nu2 = fmax((double)ordered_to_float(a.nu_q[tk.ev]),
-                                    (double)ordered_to_float(a.nu_r[tk.ev]));
-            const double nu = sqrt(fmax(nu2, 0.0));
-            const double R = sqrt((double)r2 * (1.0 + 0x1p-18));
-            const double th = (R + 0x1p-14 * nu) * (R + 0x1p-14 * nu) + 0x1p-12 * nu2;
-            tx = __double2float_rd(((double)a.qn[qs] - th) * 0.5);
-        }
-        const int self_slot = a.self ? qs : -1;
-        int cnt = 0;
-        bool lost = false;
-
-        if (nch > 0 && tid == 0) {
-            // A tile + the first two chunks, then the first MMA
-            const uint32_t bA = (uint32_t)kTcM * K * 2;
-            mbar_arrive_expect_tx(&bar_a, bA);
-            bulk_g2s(As, a.tcA + cm_off(w0, 0, K), bA, &bar_a);
-            load_chunk(0, g0);
-            if (nch > 1) load_chunk(1, g0 + 1);
-            issued_loads = min(nch, 2);
-            issued_mma = 0;
-            if (!mbar_wait_bounded(&bar_a, task_no & 1u)) abort_now();
-            else if (!issue_mma(0, g0)) abort_now();
-            else issued_mma = 1;
-        }
-        for (int c = 0; c < nch; ++c) {
-            const uint32_t g = g0 + c;
-            if (tid == 0 && !aborted()) {
-                if (c + 1 < nch) {
-                    if (!issue_mma(c + 1, g + 1)) abort_now();
-                    else issued_mma = c + 2;
+                    for (int ks = 0; ks < KS; ++ks) {
+                        mma_bf16(taddr + (g % kTcAcc) * kTcN, smem_desc(sA + ks * 256, lbo, sbo),
+                                 smem_desc(bbase + ks * 256, lbo, sbo), idesc, ks > 0 ? 1u : 0u);
+                    }
+                    mma_commit(&bar_mma[g % kTcAcc]);
+                    issued_mma = c + 1;
+                    while (next_load < nch && next_load < c + 1 + kTcRing &&
+                           slot_free_now(g0 + next_load)) {
+                        issue_load(next_load, g0 + next_load);
+                        ++next_load;
+                    }
                 }
-                // the epilogue of chunk c-1 is done (waited inside issue_mma),
-                // so ring slot (c+2) % 3 is free again
-                if (!aborted() && c + 2 < nch) {
-                    load_chunk(c + 2, g + 2);
-                    issued_loads = c + 3;
-                }
-            }
-            // MMA done (accumulator ready) and the chunk's staged coordinates
-            // visible to this thread
-            if (!aborted()) {
-                if (!mbar_wait_bounded(&bar_mma[g & 1], (g >> 1) & 1u) ||
-                    !mbar_wait_bounded(&bar_b[g % kTcRing], (g / kTcRing) & 1u))
+                if (!ok) {
                     abort_now();
+                    // wait (bounded) for the copies and MMAs in flight
+                    for (int c = issued_mma; c < next_load; ++c)
+                        mbar_wait_bounded(&bar_b[(g0 + c) % kTcRing], ((g0 + c) / kTcRing) & 1u);
+                    if (issued_mma > 0)
+                        mbar_wait_bounded(&bar_mma[(g0 + issued_mma - 1) % kTcAcc],
+                                          ((g0 + issued_mma - 1) / kTcAcc) & 1u);
+                }
             }
             __syncwarp();
-            tc_fence_after();
-            if (!__shfl_sync(0xffffffffu, aborted(), 0)) {
-                int start, n, lo, hi;
-                chunk_info(s_ct, c, start, n, lo, hi);
-                const float* F = Fs + (size_t)(g % kTcRing) * kTcN * DP;
-                const uint32_t tbase = taddr + ((uint32_t)(32 * quarter) << 16) + (g & 1) * kTcN;
+        } else {
+            // ---------------------------------------------------- epilogue
+            float tx = INFINITY;
+            if (active) {
+                const double nu2 = fmax((double)ordered_to_float(a.nu_q[tk.ev]),
+                                        (double)ordered_to_float(a.nu_r[tk.ev]));
+                const double nu = sqrt(fmax(nu2, 0.0));
+                const double R = sqrt((double)r2 * (1.0 + 0x1p-18));
+                const double th = (R + 0x1p-14 * nu) * (R + 0x1p-14 * nu) + 0x1p-12 * nu2;
+                tx = __double2float_rd(((double)a.qn[qs] - th) * 0.5);
+            }
+            const int self_slot = a.self ? qs : -1;
+            uint16_t* sv = Sv + warp * kTcSurvCap;
+            for (int c = 0; c < nch; ++c) {
+                const uint32_t g = g0 + c;
+                // accumulator ready and the chunk's staged coordinates visible
+                if (!aborted()) {
+                    if (!mbar_wait_bounded(&bar_mma[g % kTcAcc], (g / kTcAcc) & 1u) ||
+                        !mbar_wait_bounded(&bar_b[g % kTcRing], (g / kTcRing) & 1u))
+                        abort_now();
+                }
+                __syncwarp();
+                tc_fence_after();
+                if (!__shfl_sync(0xffffffffu, aborted(), 0)) {
+                    int start, n, lo, hi;
+                    chunk_info(s_ct, c, start, n, lo, hi);
+                    const float* F = Fs + (size_t)(g % kTcRing) * kTcN * DP;
+                    const uint32_t tbase =
+                        taddr + ((uint32_t)(32 * warp) << 16) + (g % kTcAcc) * kTcN;
 #pragma unroll 1
-                for (int grp = 0; grp < 4; ++grp) {
-                    const int col0 = half * 128 + grp * 32;
-                    if (col0 >= n) break;                       // warp-uniform
-                    float v[32];
-                    __syncwarp();
-                    tmem_ld32(tbase + col0, v);
-                    const int nval = min(32, n - col0);
-                    float mx = -INFINITY;
+                    for (int col0 = 0; col0 < n; col0 += 32) {   // n: multiple of 32
+                        float v[32];
+                        __syncwarp();
+                        tmem_ld32(tbase + col0, v);
+                        float mx = fmax3(v[0], v[1], v[2]);
 #pragma unroll
-                    for (int j = 0; j < 32; j += 2) {
-                        const float v0 = j < nval ? v[j] : -INFINITY;
-                        const float v1 = j + 1 < nval ? v[j + 1] : -INFINITY;
-                        mx = fmax3(mx, v0, v1);
-                    }
-                    if (mx >= tx) {
+                        for (int j = 3; j < 31; j += 2) mx = fmax3(mx, v[j], v[j + 1]);
+                        mx = fmaxf(mx, v[31]);
+                        if (!__any_sync(0xffffffffu, mx >= tx)) continue;
+                        // columns of this group inside the chunk's own row range
+                        const int c0 = start + col0;
+                        const int jlo = max(lo - c0, 0), jhi = min(hi - c0, 32);
+                        uint32_t valid =
+                            jhi > jlo ? (((jhi - jlo) == 32 ? 0xffffffffu
+                                                            : ((1u << (jhi - jlo)) - 1u))
+                                         << jlo)
+                                      : 0u;
+                        if (self_slot >= c0 && self_slot < c0 + 32)
+                            valid &= ~(1u << (self_slot - c0));
                         uint32_t mask = 0;
+                        if (mx >= tx) {
 #pragma unroll
-                        for (int j = 0; j < 32; ++j)
-                            if (j < nval && v[j] >= tx) mask |= 1u << j;
+                            for (int j = 0; j < 32; ++j)
+                                if (v[j] >= tx) mask |= 1u << j;
+                            mask &= valid;
+                        }
+                        // compact the warp's (row, column) survivors, then
+                        // recheck them with all 32 lanes
+                        const int nb = __popc(mask);
+                        int off = nb;
+#pragma unroll
+                        for (int o = 1; o < 32; o <<= 1) {
+                            const int t2 = __shfl_up_sync(0xffffffffu, off, o);
+                            if (lane >= o) off += t2;
+                        }
+                        const int total = __shfl_sync(0xffffffffu, off, 31);
+                        off -= nb;
                         while (mask) {
                             const int j = __ffs(mask) - 1;
                             mask &= mask - 1;
-                            const int cs = start + col0 + j;
-                            if (cs < lo || cs >= hi || cs == self_slot) continue;
-                            ++n_surv;
-                            // exact contract from the staged float32 coordinates
-                            const float* f = F + ((cs - start) >> 1) * 2 * DP + (cs & 1);
-                            float sv = 0.f;
+                            sv[off++] = (uint16_t)((lane << 5) | j);
+                        }
+                        __syncwarp();
+                        n_surv += (lane == 0) ? total : 0;
+                        for (int b = 0; b < total; b += 32) {
+                            if (b + lane < total) {
+                                const int pr = sv[b + lane];
+                                const int r = warp * 32 + (pr >> 5);
+                                const int cs = c0 + (pr & 31);
+                                // exact contract from the staged float32 coordinates
+                                const float* f = F + ((cs - start) >> 1) * 2 * DP + (cs & 1);
+                                const float* qv = Qs + r * DP;
+                                float sd = 0.f;
 #pragma unroll
-                            for (int k = 0; k < kMaxD; ++k) {
-                                if (k < D) {
-                                    const float d = __fsub_rn(q[k], f[2 * k]);
-                                    sv = __fadd_rn(sv, __fmul_rn(d, d));
+                                for (int k = 0; k < D; ++k) {
+                                    const float d = __fsub_rn(qv[k], f[2 * k]);
+                                    sd = __fadd_rn(sd, __fmul_rn(d, d));
                                 }
-                            }
-                            if (sv <= r2) {
-                                ++n_acc;
-                                if (cnt < LCAP) {
-                                    Ld[cnt * kTcLStr + tid] = sv;
-                                    Li[cnt * kTcLStr + tid] = a.rperm[cs];
-                                } else {
-                                    lost = true;
+                                if (sd <= r2) {
+                                    ++n_acc;
+                                    const int pos = atomicAdd(&s_cnt[r], 1);
+                                    if (pos < kTcList) {   // slot now, original index at the sort
+                                        Ld[pos * kTcLStr + r] = sd;
+                                        Li[pos * kTcLStr + r] = cs;
+                                    }
                                 }
-                                ++cnt;
                             }
                         }
+                        __syncwarp();
                     }
                 }
+                tc_fence_before();
+                mbar_arrive(&bar_acc[g % kTcAcc]);
+                mbar_arrive(&bar_slot[g % kTcRing]);
             }
-            tc_fence_before();
-            mbar_arrive(&bar_free[g & 1]);
         }
         __syncthreads();
-        if (aborted()) {
-            // drain what thread 0 issued (bounded), then leave
-            if (tid == 0) {
-                for (int c = issued_mma; c < issued_loads; ++c)
-                    mbar_wait_bounded(&bar_b[(g0 + c) % kTcRing], ((g0 + c) / kTcRing) & 1u);
-                if (issued_mma > 0)
-                    mbar_wait_bounded(&bar_mma[(g0 + issued_mma - 1) & 1],
-                                      ((g0 + issued_mma - 1) >> 1) & 1u);
-            }
-            break;
-        }
+        if (aborted()) break;
         g0 += nch;
         if (nch > 0) ++task_no;
+        if (producer) continue;
 
-        // merge the two column halves of each row, sort, count
-        s_cnt[tid] = cnt;
-        s_lost[tid] = lost ? 1 : 0;
-        __syncthreads();
-        if (half == 0 && active) {
-            const int pt = tid + 128;
-            int c1 = s_cnt[pt];
-            bool l = lost || s_lost[pt] || cnt + c1 > LCAP;
-            if (!l) {
-                for (int e = 0; e < c1; ++e) {
-                    Ld[(cnt + e) * kTcLStr + tid] = Ld[e * kTcLStr + pt];
-                    Li[(cnt + e) * kTcLStr + tid] = Li[e * kTcLStr + pt];
-                }
-                cnt += c1;
-                for (int e = 1; e < cnt; ++e) {
-                    const float kd = Ld[e * kTcLStr + tid];
-                    const int ki = Li[e * kTcLStr + tid];
-                    int j = e - 1;
-                    while (j >= 0) {
-                        const float dj = Ld[j * kTcLStr + tid];
-                        const int ij = Li[j * kTcLStr + tid];
-                        if (dj < kd || (dj == kd && ij < ki)) break;
-                        Ld[(j + 1) * kTcLStr + tid] = dj;
-                        Li[(j + 1) * kTcLStr + tid] = ij;
-                        --j;
-                    }
-                    Ld[(j + 1) * kTcLStr + tid] = kd;
-                    Li[(j + 1) * kTcLStr + tid] = ki;
-                }
-                counts[qorig] = min(cnt, Kout);
-                s_cnt[tid] = cnt;
-                s_lost[tid] = 0;
+        // every query sorts its own list by (d2, original index), all threads
+        // in parallel (register bitonic network, see sort_list)
+        const int cnt = s_cnt[row];
+        const bool spill = active && cnt > kTcList;
+        sort_list(Ld + tid, Li + tid, kTcLStr, (active && !spill) ? cnt : 0, a.rperm);
+        if (active && !spill) counts[qorig] = min(cnt, Kout);
+        if (spill) {
+            // longer than the list: the exact selection kernel finishes this row
+            const int pos = atomicAdd(a.ovf_count, 1);
+            if (pos < a.ovf_cap) {
+                a.ovf[pos].qslot = qs;
+                a.ovf[pos].ev = tk.ev;
             } else {
-                s_lost[tid] = 1;
-                const int pos = atomicAdd(a.ovf_count, 1);
-                if (pos < a.ovf_cap) {
-                    a.ovf[pos].qslot = qs;
-                    a.ovf[pos].ev = tk.ev;
-                } else {
-                    atomicOr(a.status, kStatusCapacity);
-                }
+                atomicOr(a.status, kStatusCapacity);
             }
         }
-        if (half == 0 && !active) s_lost[tid] = 1;   // nothing to write for this row
-        __syncthreads();
-        // coalesced row writes: warp w writes rows 16w .. 16w + 15
-        for (int rr = 0; rr < 16; ++rr) {
-            const int r = warp * 16 + rr;
-            if (s_lost[r]) continue;
-            const int c = min(s_cnt[r], Kout);
-            const int qo = s_qorig[r];
+        __syncwarp();
+        // coalesced row writes: one of the warp's query rows at a time
+        const unsigned skip = __ballot_sync(0xffffffffu, !active || spill);
+        for (int ql = 0; ql < 32; ++ql) {
+            if (skip & (1u << ql)) continue;
+            const int r = warp * 32 + ql;
+            const int c = min(__shfl_sync(0xffffffffu, cnt, ql), Kout);
+            const int qo = __shfl_sync(0xffffffffu, qorig, ql);
             int32_t* irow = oidx + (int64_t)qo * Kout;
             float* drow = od2 + (int64_t)qo * Kout;
             for (int e = lane; e < Kout; e += 32) {
@@ -621,7 +702,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_query(TcArgs a) {
             }
         }
     }
-    if (a.stat_survivors) {
+    if (a.stat_survivors && !producer) {
         atomicAdd(a.stat_survivors, n_surv);
         atomicAdd(a.stat_accepted, n_acc);
     }
@@ -629,7 +710,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_query(TcArgs a) {
     __syncthreads();
     if (warp == 0) {
         tc_fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(taddr)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr),
+                     "n"(kTcCols)
                      : "memory");
     }
 }
@@ -699,8 +781,21 @@ frnn_status tc_prepare(GridBufs& g, const GridBufs& center_src, cudaStream_t st,
     const int K = tc_k_for(g.D);
     cudaMemsetAsync(g.tcnu, 0, sizeof(int32_t) * g.E, st);   // ordered(0.0f) == 0
     if (g.n_total > 0) {
-        k_tc_prep<<<(unsigned)ceil_div(g.n_total, 128), 128, 0, st>>>(
-            g.hdr, center_src.hdr, g.E, g.D, g.n_total, g.pts, g.tcA, g.tcB, g.tcn, g.tcnu, K);
+        const unsigned nb = (unsigned)ceil_div(g.n_total, 128);
+        switch (g.D) {
+#define FRNN_PREP(d)                                                                         \
+    case d:                                                                                  \
+        k_tc_prep<d><<<nb, 128, 0, st>>>(g.hdr, center_src.hdr, g.E, g.n_total, g.pts, g.tcA, \
+                                         g.tcB, g.tcn, g.tcnu);                              \
+        break;
+            FRNN_PREP(8) FRNN_PREP(9) FRNN_PREP(10) FRNN_PREP(11) FRNN_PREP(12)
+            FRNN_PREP(13) FRNN_PREP(14) FRNN_PREP(15) FRNN_PREP(16)
+#undef FRNN_PREP
+            default:
+                err = "tensor-core path needs 8 <= D <= 16";
+                return FRNN_ERR_UNSUPPORTED;
+        }
+        (void)K;
     }
     enqueue_tasks(g, kTcM, 8, g.tc_tasks, g.scalars + kScTcTasks, st);
     cudaError_t ce = cudaGetLastError();
@@ -749,21 +844,27 @@ frnn_status enqueue_tc_query(const QueryLaunch& q, cudaStream_t st, std::string&
     a.stat_accepted = q.tc_stats ? q.tc_stats + 1 : nullptr;
     cudaMemsetAsync(qs.scalars + kScOvfCount, 0, sizeof(int32_t), st);
     cudaMemsetAsync(qs.scalars + kScTcCounter, 0, sizeof(int32_t), st);
-    const size_t smem = tc_smem_bytes(KS, padded_dim(D));
     cudaError_t ce = cudaSuccess;
-    auto launch = [&](auto kern) {
+    auto launch = [&](auto kern, size_t smem) {
         ce = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (ce == cudaSuccess) {
-            kern<<<q.num_sms, kTcThreads, smem, st>>>(a);
+            kern<<<2 * q.num_sms, kTcThreads, smem, st>>>(a);
             ce = cudaGetLastError();
         }
     };
-    if (KS == 2) launch(k_tc_query<2>);
-    else if (KS == 3) launch(k_tc_query<3>);
-    else if (KS == 4) launch(k_tc_query<4>);
-    else {
-        err = "tensor-core path: unsupported D";
-        return FRNN_ERR_UNSUPPORTED;
+    switch (D) {
+        case 8: launch(k_tc_query<8>, tc_smem_bytes(8)); break;
+        case 9: launch(k_tc_query<9>, tc_smem_bytes(9)); break;
+        case 10: launch(k_tc_query<10>, tc_smem_bytes(10)); break;
+        case 11: launch(k_tc_query<11>, tc_smem_bytes(11)); break;
+        case 12: launch(k_tc_query<12>, tc_smem_bytes(12)); break;
+        case 13: launch(k_tc_query<13>, tc_smem_bytes(13)); break;
+        case 14: launch(k_tc_query<14>, tc_smem_bytes(14)); break;
+        case 15: launch(k_tc_query<15>, tc_smem_bytes(15)); break;
+        case 16: launch(k_tc_query<16>, tc_smem_bytes(16)); break;
+        default:
+            err = "tensor-core path needs 8 <= D <= 16";
+            return FRNN_ERR_UNSUPPORTED;
     }
     if (ce != cudaSuccess) {
         err = std::string("tensor-core query launch failed: ") + cudaGetErrorString(ce);
