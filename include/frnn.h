@@ -172,14 +172,41 @@ frnn_status frnn_sync(frnn_ctx* ctx);
  * "" when none).  ctx NULL gives the last frnn_create failure. */
 const char* frnn_last_error(const frnn_ctx* ctx);
 
+/*
+ * Autotuner.  Times the candidate configurations on the given point set (a
+ * representative event, device memory, self-query): cell multiple m in {1, 2}
+ * (cell edge ~ r/m, the grid's search reach +-m cells), the grid scan with its
+ * default and a later warp vote, and the tensor-core pre-filter (D >= 8).
+ * Each candidate is built and queried (first run untimed, best of three
+ * timed with CUDA events on the context's stream) and the fastest build +
+ * query is cached for the event size class (power-of-two bucket of N, D,
+ * power-of-two bucket of K).  Afterwards FRNN_PATH_AUTO queries, grid builds
+ * with the cell-multiple option at 0 (the default) and every event of
+ * frnn_query_batched use the cached choice of their size class.  Results
+ * never depend on the choice.  flags: FRNN_PATH_GRID or FRNN_PATH_TC limits
+ * the candidates to that path (0: all).  Synchronises; allocates temporary
+ * outputs (N + 2 N K words).  best (may be NULL) receives the winner.
+ */
+typedef struct frnn_tune_result {
+    int path;        /* FRNN_PATH_GRID or FRNN_PATH_TC */
+    int cell_mult;   /* m */
+    int exit_dims;   /* warp vote point of the grid scan (0 = default) */
+    float ms;        /* build + query time of the winner, milliseconds */
+} frnn_tune_result;
+
+frnn_status frnn_autotune(frnn_ctx* ctx, const float* refs, int64_t N, int D, float r, int K,
+                          unsigned flags, frnn_tune_result* best);
+
 /* Tunable options (none changes results, only speed). */
 typedef enum frnn_option {
-    FRNN_OPT_CELL_MULT = 1,   /* m in {1, 2}: cell edge ~ r/m, search +-m cells */
+    FRNN_OPT_CELL_MULT = 1,   /* m in {1, 2}: cell edge ~ r/m, search +-m cells;
+                                 0 (default): autotuned, else 1 */
     FRNN_OPT_GRID_AXES = 2,   /* 0: the last min(D,3) axes; 1: the 3 widest axes */
     FRNN_OPT_EXIT_DIMS = 3,   /* dims summed before the warp-uniform early exit
                                  (0 = library default) */
     FRNN_OPT_USE_GRAPH = 4,   /* 1 (default): batched calls replay a CUDA graph */
-    FRNN_OPT_AUTOTUNE = 5,    /* 1 (default): FRNN_PATH_AUTO consults the tuner */
+    FRNN_OPT_AUTOTUNE = 5,    /* 1 (default): FRNN_PATH_AUTO consults the tuner;
+                                 setting 0 also clears the tuned cache */
     FRNN_OPT_AUTO_TC = 6,     /* 1 (default): FRNN_PATH_AUTO takes the tensor-core
                                  path for D >= 8 */
     FRNN_OPT_TC_SURVIVORS = 7,/* read: candidates that passed the tensor-core

@@ -2,6 +2,7 @@
 // the single-event, cross-set, batched (CUDA-graph) and host-buffer paths.
 #include <cmath>
 #include <cstring>
+#include <map>
 #include <string>
 #include <unordered_set>
 #include <vector>
@@ -29,8 +30,8 @@ struct frnn_ctx {
     int32_t* h_status = nullptr;
     unsigned long long* d_tcstat = nullptr;   // [2] tensor-core survivors / exact accepts
     std::string err;
-    // options
-    int cell_mult = 1;
+    // options (cell_mult 0 / exit_dims 0: tuned value, else the library default)
+    int cell_mult = 0;
     int axes_mode = 0;
     int exit_dims = 0;
     int use_graph = 1;
@@ -42,6 +43,14 @@ struct frnn_ctx {
     frnn_grid* host_grid = nullptr;   // grid of the host-buffer path
     void* hp_buf = nullptr;   // device buffers of the host-buffer path
     size_t hp_bytes = 0;
+    // autotuner cache: (log2 N bucket, D, log2 K bucket) -> best configuration
+    struct Tuned {
+        int path;    // 0 grid, 1 tensor-core
+        int m;
+        int exit_dims;
+        float ms;
+    };
+    std::map<uint32_t, Tuned> tuned;
     // live grids built through this context (detached when it is destroyed)
     std::unordered_set<frnn_grid*> grids;
     // batched graph cache; captured and replayed on an internal stream fenced
@@ -114,10 +123,17 @@ static frnn_status alloc_accounted(frnn_ctx* c, GridBufs& g, int E, const int64_
 // Path choice: FRNN_PATH_TC forces the tensor-core pre-filter (D >= 8),
 // FRNN_PATH_GRID the scalar grid scan; FRNN_PATH_AUTO takes the tensor-core
 // path for D >= 8 unless the context's option says otherwise.
-static bool use_tc_path(const frnn_ctx* ctx, int D, unsigned flags) {
+static bool default_tc(const frnn_ctx* ctx, int D);
+static const frnn_ctx::Tuned* find_tuned(const frnn_ctx* ctx, int64_t N, int D, int K);
+static bool use_tc_path(const frnn_ctx* ctx, int D, unsigned flags, int64_t N = -1, int K = -1) {
     if (flags & FRNN_PATH_TC) return true;
     if (flags & FRNN_PATH_GRID) return false;
-    return D >= 8 && ctx->auto_tc;
+    if (D < 8) return false;
+    if (N >= 0) {
+        const frnn_ctx::Tuned* t = find_tuned(ctx, N, D, K);
+        if (t) return t->path == 1;
+    }
+    return default_tc(ctx, D);
 }
 
 // Build (or reuse) the tensor-core operands of a point set; accounted in the
@@ -132,6 +148,40 @@ static frnn_status prepare_tc(frnn_ctx* ctx, GridBufs& g, const GridBufs& center
     if (s != FRNN_OK) return fail(ctx, s, err);
     return FRNN_OK;
 }
+
+static int log2_bucket(int64_t x) {
+    int b = 0;
+    while (x > 1) {
+        x >>= 1;
+        ++b;
+    }
+    return b;
+}
+static uint32_t tune_key(int64_t N, int D, int K) {
+    return (uint32_t)log2_bucket(N) | ((uint32_t)D << 8) | ((uint32_t)log2_bucket(K) << 16);
+}
+// Tuned entry for this size class; K < 0 matches any K (grid builds do not know K).
+static const frnn_ctx::Tuned* find_tuned(const frnn_ctx* ctx, int64_t N, int D, int K) {
+    if (!ctx->autotune) return nullptr;
+    if (K >= 0) {
+        auto it = ctx->tuned.find(tune_key(N, D, K));
+        return it == ctx->tuned.end() ? nullptr : &it->second;
+    }
+    const uint32_t lo = (uint32_t)log2_bucket(N) | ((uint32_t)D << 8);
+    for (auto& kv : ctx->tuned)
+        if ((kv.first & 0xFFFFu) == lo) return &kv.second;
+    return nullptr;
+}
+// cell multiple for a build: explicit option, else tuned, else 1
+static int build_mult(const frnn_ctx* ctx, int64_t N, int D) {
+    if (ctx->cell_mult > 0) return ctx->cell_mult;
+    const frnn_ctx::Tuned* t = find_tuned(ctx, N, D, -1);
+    return t ? t->m : 1;
+}
+// default path when nothing is tuned: the tensor-core pre-filter pays off
+// from about D = 10 on (measured on the tracking-shaped events: slower at
+// D = 8, faster at D = 12)
+static bool default_tc(const frnn_ctx* ctx, int D) { return ctx->auto_tc && D >= 10; }
 
 extern "C" {
 
@@ -264,7 +314,7 @@ frnn_status frnn_build_grid(frnn_ctx* ctx, const float* refs, int64_t N, int D, 
     g->r = r;
     BuildOpts o;
     o.r = r;
-    o.m = ctx->cell_mult;
+    o.m = build_mult(ctx, N, D);
     o.axes_mode = ctx->axes_mode;
     std::string err;
     const float* ev_refs[1] = {refs};
@@ -314,6 +364,10 @@ frnn_status frnn_query(frnn_ctx* ctx, const frnn_grid* grid, const float* querie
     q.K = K;
     q.self = self ? 1 : 0;
     q.exit_dims = ctx->exit_dims;
+    if (q.exit_dims == 0 && !(flags & (FRNN_PATH_GRID | FRNN_PATH_TC))) {
+        const frnn_ctx::Tuned* t = find_tuned(ctx, grid->N, grid->D, K);
+        if (t) q.exit_dims = t->exit_dims;
+    }
     q.counts = counts;
     q.idx = idx;
     q.dist2 = dist2;
@@ -333,7 +387,7 @@ frnn_status frnn_query(frnn_ctx* ctx, const frnn_grid* grid, const float* querie
         if (s != FRNN_OK) return fail(ctx, s, err);
         q.qset = &ctx->qset;
     }
-    if (use_tc_path(ctx, grid->D, flags)) {
+    if (use_tc_path(ctx, grid->D, flags, grid->N, K)) {
         s = prepare_tc(ctx, rg, rg);
         if (s == FRNN_OK && !self) s = prepare_tc(ctx, ctx->qset, rg);
         if (s != FRNN_OK) return s;
@@ -362,15 +416,22 @@ static frnn_status enqueue_batched(frnn_ctx* ctx, const frnn_event* ev, int n_ev
                                    float r, int K, unsigned flags, bool capturing,
                                    cudaStream_t st) {
     std::vector<const float*> refs(n_events);
+    bool any_grid = false, any_tc = false;
     for (int e = 0; e < n_events; ++e) {
         refs[e] = ev[e].pts;
-        ctx->batch.h_hdr[e].counts = ev[e].counts;
-        ctx->batch.h_hdr[e].idx = ev[e].idx;
-        ctx->batch.h_hdr[e].dist2 = ev[e].dist2;
+        EventHdr& h = ctx->batch.h_hdr[e];
+        h.counts = ev[e].counts;
+        h.idx = ev[e].idx;
+        h.dist2 = ev[e].dist2;
+        // per event: autotuned cell multiple and path for its size class
+        h.m = build_mult(ctx, ev[e].n, D);
+        h.path = use_tc_path(ctx, D, flags, ev[e].n, K) ? 1 : 0;
+        any_grid |= h.path == 0 && ev[e].n > 0;
+        any_tc |= h.path == 1 && ev[e].n > 0;
     }
     BuildOpts o;
     o.r = r;
-    o.m = ctx->cell_mult;
+    o.m = 1;
     o.axes_mode = ctx->axes_mode;
     std::string err;
     frnn_status s = enqueue_build(ctx->batch, refs.data(), o, nullptr, ctx->d_status, st,
@@ -385,14 +446,19 @@ static frnn_status enqueue_batched(frnn_ctx* ctx, const frnn_event* ev, int n_ev
     q.exit_dims = ctx->exit_dims;
     q.d_status = ctx->d_status;
     q.num_sms = ctx->num_sms;
-    if (use_tc_path(ctx, D, flags)) {
+    const bool mixed = any_grid && any_tc;
+    if (any_grid || !any_tc) {
+        q.path_filter = mixed ? 0 : -1;
+        s = enqueue_grid_query(q, st, err);
+        if (s != FRNN_OK) return fail(ctx, s, err);
+    }
+    if (any_tc) {
         // operands were allocated before any capture; enqueue their build
         s = tc_prepare(ctx->batch, ctx->batch, st, err);
         if (s != FRNN_OK) return fail(ctx, s, err);
         q.tc_stats = ctx->d_tcstat;
+        q.path_filter = mixed ? 1 : -1;
         s = enqueue_tc_query(q, st, err);
-    } else {
-        s = enqueue_grid_query(q, st, err);
     }
     if (s != FRNN_OK) return fail(ctx, s, err);
     return FRNN_OK;
@@ -443,7 +509,10 @@ frnn_status frnn_query_batched(frnn_ctx* ctx, const frnn_event* ev, int n_events
     }
     frnn_status s = alloc_accounted(ctx, ctx->batch, n_events, n.data(), D, nullptr);
     if (s != FRNN_OK) return s;
-    if (use_tc_path(ctx, D, flags)) {
+    bool batch_tc = false;
+    for (int e = 0; e < n_events && !batch_tc; ++e)
+        batch_tc = ev[e].n > 0 && use_tc_path(ctx, D, flags, ev[e].n, K);
+    if (batch_tc) {
         // allocate the tensor-core operands outside any capture (no work enqueued)
         std::string err;
         s = tc_reserve(ctx->batch, err);
@@ -558,11 +627,97 @@ const char* frnn_last_error(const frnn_ctx* ctx) {
     return ctx->err.c_str();
 }
 
+frnn_status frnn_autotune(frnn_ctx* ctx, const float* refs, int64_t N, int D, float r, int K,
+                          unsigned flags, frnn_tune_result* best) {
+    if (!ctx) return FRNN_ERR_INVALID_ARG;
+    if (D < 1 || D > kMaxD) return fail(ctx, FRNN_ERR_INVALID_ARG, "D must be in 1..16");
+    if (N < 1 || N >= INT32_MAX || !refs)
+        return fail(ctx, FRNN_ERR_INVALID_ARG, "autotune needs N >= 1 device points");
+    if (K < 1 || K > kMaxK) return fail(ctx, FRNN_ERR_INVALID_ARG, "K must be in 1..1024");
+    if (!radius_ok(r)) return fail(ctx, FRNN_ERR_INVALID_ARG, "r must be finite, 2^-60..2^60");
+    const size_t ob = (size_t)N * (sizeof(int32_t) + (size_t)K * 8);
+    if (!budget_allows(ctx, 0, ob)) return fail(ctx, FRNN_ERR_BUDGET, "autotune outputs exceed budget");
+    void* out = nullptr;
+    if (cudaMalloc(&out, ob) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(ctx, FRNN_ERR_OUT_OF_MEMORY, "autotune outputs");
+    }
+    int32_t* counts = static_cast<int32_t*>(out);
+    int32_t* idx = counts + N;
+    float* dist2 = reinterpret_cast<float*>(idx + (size_t)N * K);
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    const int saved_m = ctx->cell_mult, saved_x = ctx->exit_dims;
+    frnn_tune_result bestr{FRNN_PATH_GRID, 1, 0, INFINITY};
+    frnn_status s = FRNN_OK;
+    frnn_grid* g = nullptr;
+    auto timed = [&](auto&& fn, float& ms) -> frnn_status {
+        float bestms = INFINITY;
+        for (int rep = 0; rep < 4; ++rep) {   // first run warms up
+            cudaEventRecord(e0, ctx->stream);
+            frnn_status st = fn();
+            if (st != FRNN_OK) return st;
+            cudaEventRecord(e1, ctx->stream);
+            if (cudaEventSynchronize(e1) != cudaSuccess) return FRNN_ERR_CUDA;
+            float t = 0.f;
+            cudaEventElapsedTime(&t, e0, e1);
+            if (rep > 0) bestms = std::min(bestms, t);
+        }
+        ms = bestms;
+        return frnn_sync(ctx);
+    };
+    for (int m = 1; m <= 2 && s == FRNN_OK; ++m) {
+        ctx->cell_mult = m;
+        float bms = 0.f;
+        s = timed([&] { return frnn_build_grid(ctx, refs, N, D, r, &g); }, bms);
+        if (s != FRNN_OK) break;
+        struct Cand { unsigned path; int exit_dims; };
+        std::vector<Cand> cands;
+        if (!(flags & FRNN_PATH_TC)) {
+            cands.push_back({FRNN_PATH_GRID, 0});
+            if (D >= 5) cands.push_back({FRNN_PATH_GRID, 3});
+        }
+        if (D >= 8 && !(flags & FRNN_PATH_GRID)) cands.push_back({FRNN_PATH_TC, 0});
+        if (cands.empty()) {
+            s = fail(ctx, FRNN_ERR_UNSUPPORTED, "the tensor-core path needs D >= 8");
+            break;
+        }
+        for (const Cand& c : cands) {
+            ctx->exit_dims = c.exit_dims;
+            float qms = 0.f;
+            s = timed([&] {
+                return frnn_query(ctx, g, refs, N, r, K, FRNN_SELF_QUERY | c.path, counts, idx,
+                                  dist2);
+            }, qms);
+            if (s != FRNN_OK) break;
+            if (bms + qms < bestr.ms) bestr = {(int)c.path, m, c.exit_dims, bms + qms};
+        }
+    }
+    ctx->cell_mult = saved_m;
+    ctx->exit_dims = saved_x;
+    if (g) frnn_grid_destroy(g);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(out);
+    if (s != FRNN_OK) return s;
+    ctx->tuned[tune_key(N, D, K)] = {bestr.path == FRNN_PATH_TC ? 1 : 0, bestr.cell_mult,
+                                     bestr.exit_dims, bestr.ms};
+    if (ctx->graph) {   // captured batches may now take other paths
+        cudaGraphExecDestroy(ctx->graph);
+        ctx->graph = nullptr;
+        ctx->g_ev.clear();
+    }
+    if (best) *best = bestr;
+    return FRNN_OK;
+}
+
 frnn_status frnn_set_option(frnn_ctx* ctx, frnn_option opt, int64_t value) {
     if (!ctx) return FRNN_ERR_INVALID_ARG;
     switch (opt) {
         case FRNN_OPT_CELL_MULT:
-            if (value < 1 || value > 2) return fail(ctx, FRNN_ERR_INVALID_ARG, "m must be 1 or 2");
+            if (value < 0 || value > 2)
+                return fail(ctx, FRNN_ERR_INVALID_ARG, "m must be 0 (tuned), 1 or 2");
             ctx->cell_mult = (int)value;
             return FRNN_OK;
         case FRNN_OPT_GRID_AXES:
@@ -577,7 +732,9 @@ frnn_status frnn_set_option(frnn_ctx* ctx, frnn_option opt, int64_t value) {
             ctx->use_graph = value ? 1 : 0;
             return FRNN_OK;
         case FRNN_OPT_AUTOTUNE:
+            // 0 also forgets every tuned configuration
             ctx->autotune = value ? 1 : 0;
+            if (!value) ctx->tuned.clear();
             return FRNN_OK;
         case FRNN_OPT_AUTO_TC:
             ctx->auto_tc = value ? 1 : 0;

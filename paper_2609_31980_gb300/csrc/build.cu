@@ -188,7 +188,7 @@ __global__ void k_params(EventHdr* hdr, int E, int D, const int32_t* bbox, float
     const int32_t* bb = bbox + (int64_t)e * kBBoxStride;
     const int naxes = D < 3 ? D : 3;
     h.naxes = naxes;
-    h.m = m;
+    h.m = h.m > 0 ? h.m : m;   // a per-event multiple (batched autotuning) wins
     int axes[3] = {0, 0, 0};
     if (axes_mode == 1 && D > naxes) {
         // the naxes widest coordinates (ties by lower index), in index order

@@ -122,6 +122,7 @@ struct QueryLaunch {
     int32_t* d_status;
     int num_sms;
     unsigned long long* tc_stats = nullptr;   // [2]: pre-filter survivors, exact accepts
+    int path_filter = -1;                     // batched: only events of this path
 };
 frnn_status enqueue_grid_query(const QueryLaunch& q, cudaStream_t st, std::string& err);
 

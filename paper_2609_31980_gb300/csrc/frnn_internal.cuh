@@ -55,7 +55,7 @@ struct EventHdr {
     float lo[3];           // per-axis minimum coordinate
     float hi[3];           // per-axis maximum coordinate
     float inv_h;           // 1 / cell edge (float; the value the cell ids use)
-    int32_t pad_;
+    int32_t path;          // batched queries: 0 = grid scan, 1 = tensor-core pre-filter
     float ctr[16];         // per-dimension centre of the bounding box (tensor-core operands)
     // query outputs for batched self-queries (row = original point index)
     int32_t* counts;
@@ -103,6 +103,7 @@ struct QueryArgs {
     int32_t* ovf_count;          // device scalar
     int32_t ovf_cap;
     int32_t exit_dims;           // dims summed before the warp early-exit vote
+    int32_t path_filter;         // -1: every event; else only events whose path matches
 };
 
 // ---------------------------------------------------------------- PTX helpers

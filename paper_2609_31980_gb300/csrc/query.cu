@@ -165,6 +165,7 @@ __global__ void __launch_bounds__(kQueryWarps * 32, 4) k_grid_query(QueryArgs a)
         if (t >= ntasks) break;
         const Task task = a.tasks[t];
         const EventHdr& h = a.ev[task.ev];
+        if (a.path_filter >= 0 && h.path != a.path_filter) continue;   // another launch's event
         int32_t* counts = a.counts ? a.counts : h.counts;
         int32_t* oidx = a.counts ? a.idx : h.idx;
         float* od2 = a.counts ? a.dist2 : h.dist2;
@@ -548,6 +549,7 @@ frnn_status enqueue_grid_query(const QueryLaunch& q, cudaStream_t st, std::strin
     a.ovf_count = qs.scalars + kScOvfCount;
     a.ovf_cap = (int32_t)std::max<int64_t>(qs.n_total, 1);
     a.exit_dims = q.exit_dims;
+    a.path_filter = q.path_filter;
     cudaMemsetAsync(qs.scalars + kScTaskCounter, 0, 2 * sizeof(int32_t), st);   // counter + ovf
     cudaError_t ce = cudaSuccess;
     switch (rs.D) {

@@ -300,6 +300,7 @@ struct TcArgs {
     Overflow* ovf;
     int32_t* ovf_count;
     int32_t ovf_cap;
+    int32_t path_filter;                  // -1: every event; else only events with this path
     unsigned long long* stat_survivors;   // pre-filter survivors (false-candidate rate)
     unsigned long long* stat_accepted;    // exact accepts
 };
@@ -405,6 +406,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_tc_query(TcArgs a) {
         if (s_done) break;
         const Task tk = s_task;
         const EventHdr& h = a.ev[tk.ev];
+        if (a.path_filter >= 0 && h.path != a.path_filter) continue;   // another launch's event
         int32_t* counts = a.counts ? a.counts : h.counts;
         int32_t* oidx = a.counts ? a.idx : h.idx;
         float* od2 = a.counts ? a.dist2 : h.dist2;
@@ -840,6 +842,7 @@ frnn_status enqueue_tc_query(const QueryLaunch& q, cudaStream_t st, std::string&
     a.ovf = qs.ovf;
     a.ovf_count = qs.scalars + kScOvfCount;
     a.ovf_cap = (int32_t)std::max<int64_t>(qs.n_total, 1);
+    a.path_filter = q.path_filter;
     a.stat_survivors = q.tc_stats;
     a.stat_accepted = q.tc_stats ? q.tc_stats + 1 : nullptr;
     cudaMemsetAsync(qs.scalars + kScOvfCount, 0, sizeof(int32_t), st);
@@ -890,6 +893,7 @@ frnn_status enqueue_tc_query(const QueryLaunch& q, cudaStream_t st, std::string&
     o.ovf = qs.ovf;
     o.ovf_count = qs.scalars + kScOvfCount;
     o.ovf_cap = a.ovf_cap;
+    o.path_filter = -1;   // the list only holds rows this launch queued
     return enqueue_overflow(o, q.num_sms, st, err);
 }
 

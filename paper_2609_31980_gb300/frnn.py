@@ -45,7 +45,13 @@ FRNN_OPT_TC_ACCEPTED = 8
 
 EXPORTED = ["frnn_version", "frnn_create", "frnn_destroy", "frnn_build_grid",
             "frnn_grid_destroy", "frnn_query", "frnn_query_batched", "frnn_self_query_host",
-            "frnn_sync", "frnn_last_error", "frnn_set_option", "frnn_get_option"]
+            "frnn_sync", "frnn_last_error", "frnn_set_option", "frnn_get_option",
+            "frnn_autotune"]
+
+
+class frnn_tune_result(ctypes.Structure):
+    _fields_ = [("path", ctypes.c_int), ("cell_mult", ctypes.c_int), ("exit_dims", ctypes.c_int),
+                ("ms", ctypes.c_float)]
 
 
 class frnn_event(ctypes.Structure):
@@ -67,6 +73,8 @@ _sigs = {
     "frnn_last_error": ([_vp], ctypes.c_char_p),
     "frnn_set_option": ([_vp, _int, _i64], _int),
     "frnn_get_option": ([_vp, _int, ctypes.POINTER(_i64)], _int),
+    "frnn_autotune": ([_vp, _vp, _i64, _int, _f32, _int, _u32, ctypes.POINTER(frnn_tune_result)],
+                      _int),
 }
 for _name, (_args, _res) in _sigs.items():
     _fn = getattr(_lib, _name)
@@ -242,6 +250,17 @@ class Context:
                                   _vp(d.ctypes.data))
         _check(self.handle, rc)
         return out
+
+    def autotune(self, points, r: float, K: int, path: str = "auto") -> dict:
+        """frnn_autotune on a representative [N, D] CUDA tensor; returns the
+        winning configuration (cached in the context for its size class)."""
+        _dev_f32(points, "points")
+        res = frnn_tune_result()
+        rc = frnn_autotune(self.handle, _vp(points.data_ptr()), points.shape[0], points.shape[1],
+                           float(r), int(K), PATHS[path], ctypes.byref(res))
+        _check(self.handle, rc)
+        return {"path": {FRNN_PATH_GRID: "grid", FRNN_PATH_TC: "tc"}.get(res.path, res.path),
+                "cell_mult": res.cell_mult, "exit_dims": res.exit_dims, "ms": res.ms}
 
     def sync(self):
         """frnn_sync: wait and raise the device status (non-finite input, ...)."""

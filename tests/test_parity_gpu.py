@@ -186,7 +186,7 @@ def test_grid_options_do_not_change_results(ctx, m, axes):
     try:
         _assert_rows_equal(_gpu_self(ctx, pts, 0.1, 64), want)
     finally:
-        ctx.set_option(frnn.FRNN_OPT_CELL_MULT, 1)
+        ctx.set_option(frnn.FRNN_OPT_CELL_MULT, 0)
         ctx.set_option(frnn.FRNN_OPT_GRID_AXES, 0)
 
 
@@ -352,3 +352,35 @@ def test_tc_path_batched_equals_alone(ctx):
         for p, (c, i, d) in zip(evs, outs):
             got = (c.cpu().numpy(), i.cpu().numpy(), d.cpu().numpy())
             _assert_rows_equal(got, _gpu_self(ctx, p, 0.1, 64, path="grid"))
+
+
+# ------------------------------------------------------------ autotuner
+
+def test_autotune_and_mixed_path_batches(ctx):
+    """Tune one size class to the tensor-core path and another to the grid
+    path; a batch holding both classes runs one launch per path inside its
+    graph, and every event equals its single-event result."""
+    import torch
+    from paper_2609_31980_gb300 import frnn
+    small = synth.event_mix(3000, 8, (42, 0))
+    large = synth.event_mix(9000, 8, (42, 1))
+    ts, tl = torch.from_numpy(small).cuda(), torch.from_numpy(large).cuda()
+    try:
+        a = ctx.autotune(ts, 0.1, 64, path="tc")
+        b = ctx.autotune(tl, 0.1, 64, path="grid")
+        assert a["path"] == "tc" and b["path"] == "grid"
+        assert a["cell_mult"] in (1, 2) and a["ms"] > 0
+        evs = [small, large, synth.event_mix(2500, 8, (42, 2)), synth.event_mix(12000, 8, (42, 3))]
+        tev = [torch.from_numpy(p).cuda() for p in evs]
+        for rep in range(2):
+            outs = ctx.query_batched(tev, 0.1, 64, path="auto")
+            ctx.sync()
+            for p, (c, i, d) in zip(evs, outs):
+                _assert_rows_equal((c.cpu().numpy(), i.cpu().numpy(), d.cpu().numpy()),
+                                   _gpu_self(ctx, p, 0.1, 64, path="grid"))
+        # auto single-event queries follow the tuned class and stay exact
+        _assert_rows_equal(_gpu_self(ctx, small, 0.1, 64, path="auto"),
+                           oracle.self_query(small, 0.1, 64))
+    finally:
+        ctx.set_option(frnn.FRNN_OPT_AUTOTUNE, 0)
+        ctx.set_option(frnn.FRNN_OPT_AUTOTUNE, 1)
