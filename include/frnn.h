@@ -164,6 +164,44 @@ frnn_status frnn_self_query_host(frnn_ctx* ctx, const float* refs_host, int64_t 
                                  float r, int K, unsigned flags, int32_t* counts_host,
                                  int32_t* idx_host, float* dist2_host);
 
+/*
+ * Serving loop with continuous batching.  Requests (independent events, host
+ * buffers) arrive at the given times; whenever one of n_slots device streams
+ * is free, the requests that have arrived are admitted in arrival order as
+ * one batch, as many as fit max_batch and the device bytes still free under
+ * mem_budget_bytes (0 = no cap; per request: input, outputs, its grid and
+ * operands, estimated from n, D and K).  Each batch is copied in, built and
+ * queried as one frnn_query_batched call and copied back on its own stream,
+ * overlapping with the batches still running; its grids stay resident until
+ * it completes.  Results are bit-identical to single-event queries.  Runs
+ * until every request completed (synchronous; real time, so arrival_s values
+ * pace the run).  A request larger than the whole budget is not run
+ * (latency -1) and the call returns FRNN_ERR_BUDGET after serving the rest.
+ * With n_slots = 1 and max_batch = 1 the loop serves one event at a time
+ * (the sequential baseline).
+ */
+typedef struct frnn_request {
+    const float* pts; /* host [n, D] float32 (page-locked memory copies faster) */
+    int64_t n;
+    int32_t* counts;  /* host [n] out */
+    int32_t* idx;     /* host [n, K] out */
+    float* dist2;     /* host [n, K] out */
+    double arrival_s; /* arrival time, seconds after the call starts (>= 0) */
+} frnn_request;
+
+typedef struct frnn_serve_stats {
+    double wall_s;                  /* first arrival to last completion */
+    double p50_ms, p99_ms, mean_ms, max_ms;   /* arrival -> results in host memory */
+    double events_per_s;            /* completed requests / wall_s */
+    int64_t completed, rejected;
+    int64_t peak_inflight_bytes;    /* estimated device bytes admitted at once */
+    int peak_inflight_batches;      /* batches on the device at once */
+} frnn_serve_stats;
+
+frnn_status frnn_serve_run(frnn_ctx* ctx, const frnn_request* reqs, int n_reqs, int D, float r,
+                           int K, size_t mem_budget_bytes, int n_slots, int max_batch,
+                           double* latency_ms, frnn_serve_stats* stats);
+
 /* Wait for the context's stream and report (then clear) the device status
  * word: FRNN_OK or the first device-side error since the last sync. */
 frnn_status frnn_sync(frnn_ctx* ctx);

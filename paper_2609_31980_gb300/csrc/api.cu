@@ -68,6 +68,20 @@ struct frnn_ctx {
 
 static thread_local std::string g_create_err;
 
+namespace frnn {
+void ctx_copy_tuning(frnn_ctx* dst, const frnn_ctx* src) {
+    dst->cell_mult = src->cell_mult;
+    dst->axes_mode = src->axes_mode;
+    dst->exit_dims = src->exit_dims;
+    dst->autotune = src->autotune;
+    dst->auto_tc = src->auto_tc;
+    dst->tuned = src->tuned;
+}
+void ctx_set_error(frnn_ctx* ctx, const char* msg) {
+    if (ctx) ctx->err = msg;
+}
+}  // namespace frnn
+
 static frnn_status fail(frnn_ctx* c, frnn_status s, const std::string& msg) {
     if (c) c->err = msg;
     return s;

@@ -136,4 +136,8 @@ frnn_status tc_reserve(GridBufs& g, std::string& err);
 void tc_free(GridBufs& g);
 frnn_status enqueue_overflow(const QueryArgs& a, int num_sms, cudaStream_t st, std::string& err);
 
+// Context helpers for the serving loop (defined with the context, api.cu).
+void ctx_copy_tuning(frnn_ctx* dst, const frnn_ctx* src);
+void ctx_set_error(frnn_ctx* ctx, const char* msg);
+
 }  // namespace frnn

@@ -46,12 +46,25 @@ FRNN_OPT_TC_ACCEPTED = 8
 EXPORTED = ["frnn_version", "frnn_create", "frnn_destroy", "frnn_build_grid",
             "frnn_grid_destroy", "frnn_query", "frnn_query_batched", "frnn_self_query_host",
             "frnn_sync", "frnn_last_error", "frnn_set_option", "frnn_get_option",
-            "frnn_autotune"]
+            "frnn_autotune", "frnn_serve_run"]
 
 
 class frnn_tune_result(ctypes.Structure):
     _fields_ = [("path", ctypes.c_int), ("cell_mult", ctypes.c_int), ("exit_dims", ctypes.c_int),
                 ("ms", ctypes.c_float)]
+
+
+class frnn_request(ctypes.Structure):
+    _fields_ = [("pts", ctypes.c_void_p), ("n", ctypes.c_int64), ("counts", ctypes.c_void_p),
+                ("idx", ctypes.c_void_p), ("dist2", ctypes.c_void_p), ("arrival_s", ctypes.c_double)]
+
+
+class frnn_serve_stats(ctypes.Structure):
+    _fields_ = [("wall_s", ctypes.c_double), ("p50_ms", ctypes.c_double),
+                ("p99_ms", ctypes.c_double), ("mean_ms", ctypes.c_double),
+                ("max_ms", ctypes.c_double), ("events_per_s", ctypes.c_double),
+                ("completed", ctypes.c_int64), ("rejected", ctypes.c_int64),
+                ("peak_inflight_bytes", ctypes.c_int64), ("peak_inflight_batches", ctypes.c_int)]
 
 
 class frnn_event(ctypes.Structure):
@@ -75,6 +88,9 @@ _sigs = {
     "frnn_get_option": ([_vp, _int, ctypes.POINTER(_i64)], _int),
     "frnn_autotune": ([_vp, _vp, _i64, _int, _f32, _int, _u32, ctypes.POINTER(frnn_tune_result)],
                       _int),
+    "frnn_serve_run": ([_vp, ctypes.POINTER(frnn_request), _int, _int, _f32, _int, ctypes.c_size_t,
+                        _int, _int, ctypes.POINTER(ctypes.c_double),
+                        ctypes.POINTER(frnn_serve_stats)], _int),
 }
 for _name, (_args, _res) in _sigs.items():
     _fn = getattr(_lib, _name)
@@ -261,6 +277,30 @@ class Context:
         _check(self.handle, rc)
         return {"path": {FRNN_PATH_GRID: "grid", FRNN_PATH_TC: "tc"}.get(res.path, res.path),
                 "cell_mult": res.cell_mult, "exit_dims": res.exit_dims, "ms": res.ms}
+
+    def serve(self, events, arrivals, r: float, K: int, budget_bytes: int = 0, slots: int = 4,
+              max_batch: int = 16, outs=None):
+        """frnn_serve_run over host (NumPy, ideally page-locked) events with
+        arrival times in seconds; returns (outputs, latencies_ms, stats)."""
+        import numpy as np
+        n = len(events)
+        D = events[0].shape[1] if n else 1
+        if outs is None:
+            outs = [(np.empty(len(p), np.int32), np.empty((len(p), K), np.int32),
+                     np.empty((len(p), K), np.float32)) for p in events]
+        arr = (frnn_request * max(n, 1))()
+        for i, (p, (c, ix, d)) in enumerate(zip(events, outs)):
+            if p.dtype != np.float32 or not p.flags.c_contiguous:
+                raise TypeError("events must be contiguous float32 [n, D] arrays")
+            arr[i] = frnn_request(p.ctypes.data, len(p), c.ctypes.data, ix.ctypes.data,
+                                  d.ctypes.data, float(arrivals[i]))
+        lat = (ctypes.c_double * max(n, 1))()
+        st = frnn_serve_stats()
+        rc = frnn_serve_run(self.handle, arr, n, D, float(r), int(K), int(budget_bytes),
+                            int(slots), int(max_batch), lat, ctypes.byref(st))
+        _check(self.handle, rc)
+        stats = {f: getattr(st, f) for f, _ in frnn_serve_stats._fields_}
+        return outs, np.array(lat[:n]), stats
 
     def sync(self):
         """frnn_sync: wait and raise the device status (non-finite input, ...)."""

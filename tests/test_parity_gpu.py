@@ -384,3 +384,39 @@ def test_autotune_and_mixed_path_batches(ctx):
     finally:
         ctx.set_option(frnn.FRNN_OPT_AUTOTUNE, 0)
         ctx.set_option(frnn.FRNN_OPT_AUTOTUNE, 1)
+
+
+# ------------------------------------------------------------ serving loop
+
+def test_serving_results_equal_alone_and_overlap(ctx):
+    """Continuous batching: requests arriving while others run are admitted
+    as slots free up; every result equals the single-event result bit for
+    bit, and batches overlapped on the device."""
+    import torch
+    g = np.random.default_rng(600)
+    sizes = g.integers(500, 12000, size=40)
+    events = [synth.event_mix(int(n), 8, (60, e)) for e, n in enumerate(sizes)]
+    arrivals = np.cumsum(g.exponential(2e-4, size=len(events)))
+    outs, lat, st = ctx.serve(events, arrivals, 0.1, 64, budget_bytes=2 * 10 ** 9, slots=4,
+                              max_batch=6)
+    assert st["completed"] == len(events) and st["rejected"] == 0
+    assert np.all(lat > 0) and st["p99_ms"] >= st["p50_ms"] > 0
+    assert st["peak_inflight_batches"] >= 2
+    for p, (c, i, d) in zip(events, outs):
+        _assert_rows_equal((c, i, d), _gpu_self(ctx, p, 0.1, 64, path="grid"))
+    # a small budget serialises the same stream (no request fits twice)
+    big = max(sizes)
+    outs2, lat2, st2 = ctx.serve(events[:8], arrivals[:8], 0.1, 64,
+                                 budget_bytes=int(big * (8 * 4 + 4 + 64 * 8) * 3.5), slots=4,
+                                 max_batch=6)
+    assert st2["completed"] == 8
+    for p, (c, i, d) in zip(events[:8], outs2):
+        _assert_rows_equal((c, i, d), _gpu_self(ctx, p, 0.1, 64, path="grid"))
+
+
+def test_serving_rejects_oversized_request(ctx):
+    from paper_2609_31980_gb300 import frnn
+    events = [synth.event_mix(2000, 8, (61, e)) for e in range(3)]
+    with pytest.raises(frnn.FrnnError) as ei:
+        ctx.serve(events, [0.0, 0.0, 0.0], 0.1, 64, budget_bytes=1000, slots=2, max_batch=2)
+    assert ei.value.status == -4
