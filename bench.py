@@ -261,12 +261,96 @@ def run_ours(args):
     }
     if clocks:
         res["clocks"] = clocks
+    if rank == 0 and not args.no_batched:
+        res["batched_vs_plain"] = run_batched(ctx, args, dev)
+    if rank == 0 and not args.no_serving:
+        res["serving"] = run_serving(ctx, args)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         res["cpu_baseline"] = cpu_baseline(pts_np, r, K, args.cpu_rows)
     if ws > 1:
         torch.distributed.destroy_process_group()
     ctx.close()
     return res if rank == 0 else None
+
+
+def run_batched(ctx, args, dev):
+    """64 uneven events (N ~ U[50k, 350k], D=8, the event mix): one batched
+    call (segmented build + persistent query launch, replayed from its CUDA
+    graph) against the same events one by one through the plain path."""
+    import torch
+    from paper_2609_31980_gb300 import synth
+    w = synth.config4(n_events=args.batch_events)
+    K, r = w.K, w.r
+    evs = [torch.from_numpy(p).to(dev) for p in w.events]
+    total = sum(len(p) for p in w.events)
+    outs = [(torch.empty(len(p), dtype=torch.int32, device=dev),
+             torch.empty((len(p), K), dtype=torch.int32, device=dev),
+             torch.empty((len(p), K), dtype=torch.float32, device=dev)) for p in w.events]
+    stream = ctx.stream
+    mk = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+    # plain: every event built and queried on its own
+    grids = [None] * len(evs)
+
+    def plain():
+        for e, p in enumerate(evs):
+            grids[e] = ctx.build_grid(p, r, grid=grids[e])
+            ctx.query(grids[e], p, r, K, True, args.batch_path, outs[e])
+
+    def batched():
+        ctx.query_batched(evs, r, K, path=args.batch_path, outs=outs)
+
+    res = {}
+    for name, fn in (("plain", plain), ("batched", batched)):
+        for _ in range(2):
+            fn()
+        ctx.sync()
+        a, b = mk(), mk()
+        a.record(stream)
+        for _ in range(args.batch_reps):
+            fn()
+        b.record(stream)
+        ctx.sync()
+        ms = a.elapsed_time(b) / args.batch_reps
+        res[name] = {"ms": ms, "queries_per_s": total / (ms / 1e3)}
+    pairs = int(sum(int(c.sum().item()) for c, _, _ in outs))
+    return {"workload": w.name, "events": len(evs), "queries": total, "neighbor_pairs": pairs,
+            "path": args.batch_path, "plain": res["plain"], "batched": res["batched"],
+            "batched_over_plain": res["plain"]["ms"] / res["batched"]["ms"]}
+
+
+def run_serving(ctx, args):
+    """A Poisson stream of events (N log-uniform on [20k, 400k], D=8, the
+    event mix) through the continuous-batching loop, against the same stream
+    served one event at a time (1 slot, batch of 1)."""
+    import torch
+    from paper_2609_31980_gb300 import synth
+    n_ev = args.serve_events
+    sizes = synth.serving_sizes(n_ev)
+    K, r = 64, 0.1
+    events, outs = [], []
+    for e in range(n_ev):
+        p = torch.from_numpy(synth.config5_event(e, sizes)).pin_memory()
+        events.append(p.numpy())
+        outs.append((torch.empty(len(p), dtype=torch.int32).pin_memory().numpy(),
+                     torch.empty((len(p), K), dtype=torch.int32).pin_memory().numpy(),
+                     torch.empty((len(p), K), dtype=torch.float32).pin_memory().numpy()))
+    budget = 40 * 10 ** 9
+    # sequential capacity: everything queued at t = 0, one event at a time
+    _, _, seq0 = ctx.serve(events, np.zeros(n_ev), r, K, budget, slots=1, max_batch=1, outs=outs)
+    cap = seq0["events_per_s"]
+    out = {"events": n_ev, "mean_N": float(np.mean(sizes)), "budget_bytes": budget,
+           "sequential_capacity_events_per_s": cap, "loads": []}
+    for load in args.serve_loads:
+        arr = synth.poisson_arrivals(n_ev, load * cap)
+        _, _, cb = ctx.serve(events, arr, r, K, budget, slots=args.serve_slots,
+                             max_batch=args.serve_batch, outs=outs)
+        _, _, sq = ctx.serve(events, arr, r, K, budget, slots=1, max_batch=1, outs=outs)
+        out["loads"].append({
+            "rate_x_sequential_capacity": load, "rate_hz": load * cap,
+            "continuous": {k: cb[k] for k in ("p50_ms", "p99_ms", "events_per_s",
+                                               "peak_inflight_batches", "peak_inflight_bytes")},
+            "sequential": {k: sq[k] for k in ("p50_ms", "p99_ms", "events_per_s")}})
+    return out
 
 
 def cpu_baseline(pts_np, r, K, rows):
@@ -332,6 +416,15 @@ def main():
     ap.add_argument("--exit-dims", type=int, default=0, help="dims before the warp vote (0: default)")
     ap.add_argument("--grid-axes", type=int, default=0, help="0: last axes, 1: widest axes")
     ap.add_argument("--path", default="grid", choices=["grid", "tc", "auto"])
+    ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--batch-events", type=int, default=64)
+    ap.add_argument("--batch-reps", type=int, default=3)
+    ap.add_argument("--batch-path", default="grid", choices=["grid", "tc", "auto"])
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--serve-events", type=int, default=48)
+    ap.add_argument("--serve-slots", type=int, default=4)
+    ap.add_argument("--serve-batch", type=int, default=8)
+    ap.add_argument("--serve-loads", type=float, nargs="*", default=[0.9, 1.5])
     ap.add_argument("--workload", default="event300k", choices=["event300k", "event500k"])
     args = ap.parse_args()
     if args.warmup < 3:
