@@ -202,6 +202,37 @@ frnn_status frnn_serve_run(frnn_ctx* ctx, const frnn_request* reqs, int n_reqs, 
                            int K, size_t mem_budget_bytes, int n_slots, int max_batch,
                            double* latency_ms, frnn_serve_stats* stats);
 
+/*
+ * Self-query that allocates nothing (the paper has no counterpart: it is an
+ * addition for callers that cannot allocate memory when they query).  Some
+ * callers cannot call cudaMalloc or any allocating routine at query time:
+ * a host loop that runs under a fixed, pre-reserved memory plan (embedded or
+ * real-time code, or a process that divides device memory among several
+ * engines in advance), or code that runs where an allocation is not allowed
+ * or would synchronise the device.  This call needs no context: the grid, the
+ * counters and the status word live in one fixed array of device memory
+ * (about 7 MB) that the library declares statically; every GPU that loads
+ * the library keeps that array until the process exits.
+ *   pts      device, [N, D] row-major float32; N <= 65536 (larger N returns
+ *            FRNN_ERR_INVALID_ARG at once), 1 <= D <= 16
+ *   r, K     as for frnn_query (grid path, self-query, reference j == i
+ *            excluded by index)
+ *   counts, idx, dist2   device outputs as for frnn_query
+ *   cuda_stream          stream to run on (NULL = legacy default stream)
+ * Synchronous: it waits for its work and returns the device status
+ * (FRNN_ERR_NONFINITE for a NaN or infinite coordinate).  Results are
+ * bit-identical to frnn_build_grid + frnn_query(FRNN_SELF_QUERY).
+ * Every call shares the one array and leaves its contents there (each call
+ * clears what must start at zero); calls whose work overlaps on the GPU
+ * (other streams or host threads) race on it and must be serialised by the
+ * caller.  The array's device address is looked up once per device, on the
+ * first call with that device current; make that first call before any
+ * stream capture begins.
+ */
+frnn_status frnn_self_query_noalloc(const float* pts, int64_t N, int D, float r, int K,
+                                    int32_t* counts, int32_t* idx, float* dist2,
+                                    void* cuda_stream);
+
 /* Wait for the context's stream and report (then clear) the device status
  * word: FRNN_OK or the first device-side error since the last sync. */
 frnn_status frnn_sync(frnn_ctx* ctx);

@@ -731,4 +731,34 @@ frnn_status enqueue_build(GridBufs& g, const float* const* refs, const BuildOpts
     return FRNN_OK;
 }
 
+// The same build as enqueue_build, for a point set whose per-event tables
+// (headers, block starts, cell offsets) some earlier work on the stream has
+// already written on the device: nothing is copied from the host.
+frnn_status enqueue_build_resident(GridBufs& g, const BuildOpts& o, int32_t* d_status,
+                                   cudaStream_t st, std::string& err) {
+    const int E = g.E, D = g.D;
+    const int32_t bbmin = host_float_to_ordered(INFINITY);
+    const int32_t bbmax = host_float_to_ordered(-INFINITY);
+    const int64_t init_n = std::max<int64_t>(g.L, (int64_t)E * kBBoxStride);
+    k_init<<<std::min<unsigned>(blocks_for(init_n, 256), 4096), 256, 0, st>>>(
+        g.cstart, g.L, g.bbox, E, g.scalars, bbmin, bbmax);
+    const size_t smem_pts = sizeof(float) * kBuildPtsPerBlock * D;
+    k_bbox<<<(unsigned)g.nblk, kBuildPtsPerBlock, smem_pts, st>>>(g.hdr, g.blk_start, E, D,
+                                                                 g.bbox, d_status);
+    k_params<<<blocks_for(E, 128), 128, 0, st>>>(g.hdr, E, D, g.bbox, o.r, o.m, o.axes_mode,
+                                                  g.cstart);
+    k_cellid<<<(unsigned)g.nblk, kBuildPtsPerBlock, smem_pts, st>>>(
+        g.hdr, g.blk_start, E, D, g.cstart, g.cid, g.rnk, 0, d_status);
+    enqueue_scan(g.cstart, g.L, g.parts, g.scalars + kScCellTotal, st);
+    k_scatter<<<(unsigned)g.nblk, kBuildPtsPerBlock, smem_pts, st>>>(
+        g.hdr, g.blk_start, E, D, g.DP, g.cstart, g.cid, g.rnk, g.pts, g.perm, g.cell);
+    enqueue_tasks(g, kTaskQueries, 1, g.tasks, g.scalars + kScNTasks, st);
+    cudaError_t ce = cudaGetLastError();
+    if (ce != cudaSuccess) {
+        err = std::string("grid build launch failed: ") + cudaGetErrorString(ce);
+        return FRNN_ERR_CUDA;
+    }
+    return FRNN_OK;
+}
+
 }  // namespace frnn

@@ -104,6 +104,10 @@ frnn_status enqueue_build(GridBufs& g, const float* const* refs, const BuildOpts
 // Task list: windows of W slots aligned to A within each row of cells.
 void enqueue_tasks(GridBufs& g, int W, int A, Task* out, int32_t* count_out, cudaStream_t st);
 
+// The build for per-event tables already resident on the device.
+frnn_status enqueue_build_resident(GridBufs& g, const BuildOpts& o, int32_t* d_status,
+                                   cudaStream_t st, std::string& err);
+
 // Exclusive scan of n int32 values in place; the total goes to *total.
 void enqueue_scan(int32_t* data, int64_t n, int32_t* parts, int32_t* total, cudaStream_t st);
 int64_t scan_parts_needed(int64_t n);

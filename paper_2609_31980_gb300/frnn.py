@@ -46,7 +46,7 @@ FRNN_OPT_TC_ACCEPTED = 8
 EXPORTED = ["frnn_version", "frnn_create", "frnn_destroy", "frnn_build_grid",
             "frnn_grid_destroy", "frnn_query", "frnn_query_batched", "frnn_self_query_host",
             "frnn_sync", "frnn_last_error", "frnn_set_option", "frnn_get_option",
-            "frnn_autotune", "frnn_serve_run"]
+            "frnn_autotune", "frnn_serve_run", "frnn_self_query_noalloc"]
 
 
 class frnn_tune_result(ctypes.Structure):
@@ -88,6 +88,7 @@ _sigs = {
     "frnn_get_option": ([_vp, _int, ctypes.POINTER(_i64)], _int),
     "frnn_autotune": ([_vp, _vp, _i64, _int, _f32, _int, _u32, ctypes.POINTER(frnn_tune_result)],
                       _int),
+    "frnn_self_query_noalloc": ([_vp, _i64, _int, _f32, _int, _vp, _vp, _vp, _vp], _int),
     "frnn_serve_run": ([_vp, ctypes.POINTER(frnn_request), _int, _int, _f32, _int, ctypes.c_size_t,
                         _int, _int, ctypes.POINTER(ctypes.c_double),
                         ctypes.POINTER(frnn_serve_stats)], _int),
