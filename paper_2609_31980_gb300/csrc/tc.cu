@@ -59,9 +59,11 @@ namespace frnn {
 constexpr int kTcM = 128;        // queries per task = MMA M = TMEM lanes
 constexpr int kTcN = 128;        // candidates per chunk = MMA N (multiple of 32)
 constexpr int kTcAcc = 2;        // TMEM accumulators in flight (kTcAcc * kTcN = kTcCols)
-constexpr int kTcEpi = 128;      // epilogue threads: warp w < 4 owns TMEM lanes 32w..32w+31
+constexpr int kTcEpi = 256;      // epilogue threads: warp w < 8 owns TMEM lanes 32 (w % 4)..
+                                 // and column half w / 4 of every chunk
 constexpr int kTcThreads = kTcEpi + 32;   // + one producer warp (bulk copies, MMA issue)
-constexpr int kTcLStr = kTcEpi + 1;
+constexpr int kTcLStr = kTcM + 1;         // list table: one column per query row
+constexpr int kTcMaxChunks = 128;         // chunk table entries kept in shared memory
 constexpr int kTcMaxRows = 32;   // neighbour rows per task (m <= 2)
 constexpr int kTcCols = 256;     // TMEM columns per CTA: two accumulators (2 CTAs / SM)
 // (the producer warp is warp 4; epilogue warps 0..3 own the TMEM lane quarters)
@@ -71,7 +73,7 @@ __host__ __device__ constexpr int tc_k_for(int D) { return ((3 * D + 2) + 15) / 
 
 // shared memory outside the operand ring
 __host__ __device__ constexpr size_t tc_smem_fixed(int K, int DP);
-// operand ring depth: as deep as fits two CTAs per SM (<= 110 KB each), 3..8
+// operand ring depth: as deep as fits two CTAs per SM (<= 110 KB each), 2..8
 __host__ __device__ constexpr int tc_ring_for(int D);
 
 constexpr int kTcSurvCap = 32 * 32;   // survivor (row, column) pairs of one warp and 32 columns
@@ -87,7 +89,7 @@ __host__ __device__ constexpr size_t tc_slot_bytes(int K, int DP) {
 }
 __host__ __device__ constexpr int tc_ring_for(int D) {
     int r = 8;
-    while (r > 3 && tc_smem_fixed(tc_k_for(D), padded_dim(D)) +
+    while (r > 2 && tc_smem_fixed(tc_k_for(D), padded_dim(D)) +
                             (size_t)r * tc_slot_bytes(tc_k_for(D), padded_dim(D)) >
                         110 * 1024)
         --r;
@@ -311,10 +313,11 @@ struct TcArgs {
 struct ChunkTab {
     int rs[kTcMaxRows], re[kTcMaxRows], b8[kTcMaxRows], pref[kTcMaxRows + 1];
     int nrows, nch;
+    int4 chunk[kTcMaxChunks];   // (start, n, lo, hi) of the first chunks
 };
 
-__device__ __forceinline__ void chunk_info(const ChunkTab& t, int c, int& start, int& n, int& lo,
-                                           int& hi) {
+__device__ __forceinline__ void chunk_info_slow(const ChunkTab& t, int c, int& start, int& n,
+                                                int& lo, int& hi) {
     int L = 0;
     while (L + 1 < t.nrows && t.pref[L + 1] <= c) ++L;
     start = t.b8[L] + (c - t.pref[L]) * kTcN;
@@ -323,6 +326,19 @@ __device__ __forceinline__ void chunk_info(const ChunkTab& t, int c, int& start,
     n = (n + 31) & ~31;   // whole 32-column TMEM loads; extra rows are masked by [lo, hi)
     lo = t.rs[L];
     hi = t.re[L];
+}
+
+__device__ __forceinline__ void chunk_info(const ChunkTab& t, int c, int& start, int& n, int& lo,
+                                           int& hi) {
+    if (c < kTcMaxChunks) {
+        const int4 v = t.chunk[c];
+        start = v.x;
+        n = v.y;
+        lo = v.z;
+        hi = v.w;
+    } else {
+        chunk_info_slow(t, c, start, n, lo, hi);
+    }
 }
 
 template <int D>
@@ -352,7 +368,8 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_tc_query(TcArgs a) {
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const bool producer = warp == kTcEpi / 32;
-    const int row = tid;   // TMEM lane / query row (epilogue threads)
+    const int half = (warp >> 2) & 1;          // column half of the chunk (epilogue warps)
+    const int row = 32 * (warp & 3) + lane;    // TMEM lane / query row
 
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
@@ -364,7 +381,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_tc_query(TcArgs a) {
         mbar_init(&bar_a, 1);
         for (int i = 0; i < kTcRing; ++i) {
             mbar_init(&bar_b[i], 1);
-            mbar_init(&bar_slot[i], kTcEpi);
+            mbar_init(&bar_slot[i], kTcEpi);   // every epilogue thread, every chunk
         }
         for (int i = 0; i < kTcAcc; ++i) {
             mbar_init(&bar_mma[i], 1);
@@ -461,7 +478,16 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_tc_query(TcArgs a) {
                 s_ct.nch = pre;
                 s_ct.nrows = nrows;
             }
-        } else {
+            // this lane's row: its chunks' (start, n, lo, hi)
+            for (int j = 0; j < nch; ++j) {
+                const int c = pre - nch + j;
+                if (c >= kTcMaxChunks) break;
+                const int start = b8 + j * kTcN;
+                int n = min(kTcN, e8 - start);
+                n = (n + 31) & ~31;
+                s_ct.chunk[c] = make_int4(start, n, rs, re);
+            }
+        } else if (half == 0) {
             // this thread's query: float32 coordinates (shared: the recheck
             // reads them from any lane)
 #pragma unroll
@@ -587,9 +613,10 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_tc_query(TcArgs a) {
                     chunk_info(s_ct, c, start, n, lo, hi);
                     const float* F = Fs + (size_t)(g % kTcRing) * kTcN * DP;
                     const uint32_t tbase =
-                        taddr + ((uint32_t)(32 * warp) << 16) + (g % kTcAcc) * kTcN;
+                        taddr + ((uint32_t)(32 * (warp & 3)) << 16) + (g % kTcAcc) * kTcN;
+                    const int cend = min(n, kTcN / 2 * (half + 1));
 #pragma unroll 1
-                    for (int col0 = 0; col0 < n; col0 += 32) {   // n: multiple of 32
+                    for (int col0 = kTcN / 2 * half; col0 < cend; col0 += 32) {   // n: multiple of 32
                         float v[32];
                         __syncwarp();
                         tmem_ld32(tbase + col0, v);
@@ -636,7 +663,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_tc_query(TcArgs a) {
                         for (int b = 0; b < total; b += 32) {
                             if (b + lane < total) {
                                 const int pr = sv[b + lane];
-                                const int r = warp * 32 + (pr >> 5);
+                                const int r = 32 * (warp & 3) + (pr >> 5);
                                 const int cs = c0 + (pr & 31);
                                 // exact contract from the staged float32 coordinates
                                 const float* f = F + ((cs - start) >> 1) * 2 * DP + (cs & 1);
@@ -675,9 +702,11 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_tc_query(TcArgs a) {
         // in parallel (register bitonic network, see sort_list)
         const int cnt = s_cnt[row];
         const bool spill = active && cnt > kTcList;
-        sort_list(Ld + tid, Li + tid, kTcLStr, (active && !spill) ? cnt : 0, a.rperm);
-        if (active && !spill) counts[qorig] = min(cnt, Kout);
-        if (spill) {
+        if (half == 0) {
+            sort_list(Ld + row, Li + row, kTcLStr, (active && !spill) ? cnt : 0, a.rperm);
+            if (active && !spill) counts[qorig] = min(cnt, Kout);
+        }
+        if (spill && half == 0) {
             // longer than the list: the exact selection kernel finishes this row
             const int pos = atomicAdd(a.ovf_count, 1);
             if (pos < a.ovf_cap) {
@@ -687,12 +716,14 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_tc_query(TcArgs a) {
                 atomicOr(a.status, kStatusCapacity);
             }
         }
-        __syncwarp();
-        // coalesced row writes: one of the warp's query rows at a time
-        const unsigned skip = __ballot_sync(0xffffffffu, !active || spill);
-        for (int ql = 0; ql < 32; ++ql) {
+        // rows sorted by the half-0 threads; then coalesced row writes, each
+        // epilogue warp 16 of the 128 rows
+        asm volatile("bar.sync 1, %0;" ::"n"(kTcEpi) : "memory");
+        const unsigned skip = __ballot_sync(0xffffffffu, !active || spill);   // rows 32(w%4)..
+        for (int qq = 0; qq < 16; ++qq) {
+            const int ql = 16 * half + qq;                 // lane of this row in the warp
             if (skip & (1u << ql)) continue;
-            const int r = warp * 32 + ql;
+            const int r = 32 * (warp & 3) + ql;
             const int c = min(__shfl_sync(0xffffffffu, cnt, ql), Kout);
             const int qo = __shfl_sync(0xffffffffu, qorig, ql);
             int32_t* irow = oidx + (int64_t)qo * Kout;
