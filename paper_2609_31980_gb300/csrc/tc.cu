@@ -878,6 +878,7 @@ frnn_status enqueue_tc_query(const QueryLaunch& q, cudaStream_t st, std::string&
     a.stat_accepted = q.tc_stats ? q.tc_stats + 1 : nullptr;
     cudaMemsetAsync(qs.scalars + kScOvfCount, 0, sizeof(int32_t), st);
     cudaMemsetAsync(qs.scalars + kScTcCounter, 0, sizeof(int32_t), st);
+    if (q.kev[0]) cudaEventRecord(q.kev[0], st);
     cudaError_t ce = cudaSuccess;
     auto launch = [&](auto kern, size_t smem) {
         ce = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -904,6 +905,7 @@ frnn_status enqueue_tc_query(const QueryLaunch& q, cudaStream_t st, std::string&
         err = std::string("tensor-core query launch failed: ") + cudaGetErrorString(ce);
         return FRNN_ERR_CUDA;
     }
+    if (q.kev[1]) cudaEventRecord(q.kev[1], st);
     // rows whose lists overflowed: exact selection kernel
     QueryArgs o{};
     o.ev = rs.hdr;

@@ -42,11 +42,13 @@ FRNN_OPT_AUTOTUNE = 5
 FRNN_OPT_AUTO_TC = 6
 FRNN_OPT_TC_SURVIVORS = 7
 FRNN_OPT_TC_ACCEPTED = 8
+FRNN_OPT_KERNEL_TIMING = 9
 
 EXPORTED = ["frnn_version", "frnn_create", "frnn_destroy", "frnn_build_grid",
             "frnn_grid_destroy", "frnn_query", "frnn_query_batched", "frnn_self_query_host",
             "frnn_sync", "frnn_last_error", "frnn_set_option", "frnn_get_option",
-            "frnn_autotune", "frnn_serve_run", "frnn_self_query_noalloc"]
+            "frnn_autotune", "frnn_serve_run", "frnn_self_query_noalloc",
+            "frnn_kernel_times"]
 
 
 class frnn_tune_result(ctypes.Structure):
@@ -86,6 +88,7 @@ _sigs = {
     "frnn_last_error": ([_vp], ctypes.c_char_p),
     "frnn_set_option": ([_vp, _int, _i64], _int),
     "frnn_get_option": ([_vp, _int, ctypes.POINTER(_i64)], _int),
+    "frnn_kernel_times": ([_vp, ctypes.POINTER(_f32), _int, ctypes.POINTER(_int)], _int),
     "frnn_autotune": ([_vp, _vp, _i64, _int, _f32, _int, _u32, ctypes.POINTER(frnn_tune_result)],
                       _int),
     "frnn_self_query_noalloc": ([_vp, _i64, _int, _f32, _int, _vp, _vp, _vp, _vp], _int),
@@ -302,6 +305,15 @@ class Context:
         _check(self.handle, rc)
         stats = {f: getattr(st, f) for f, _ in frnn_serve_stats._fields_}
         return outs, np.array(lat[:n]), stats
+
+    def kernel_times(self) -> list:
+        """frnn_kernel_times: main query kernel durations (ms) recorded since
+        the last read, when FRNN_OPT_KERNEL_TIMING is on."""
+        cap = 4096
+        buf = (_f32 * cap)()
+        n = _int(0)
+        _check(self.handle, frnn_kernel_times(self.handle, buf, cap, ctypes.byref(n)))
+        return [float(buf[i]) for i in range(min(n.value, cap))]
 
     def sync(self):
         """frnn_sync: wait and raise the device status (non-finite input, ...)."""

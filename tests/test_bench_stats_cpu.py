@@ -1,0 +1,28 @@
+"""Host statistics of the benchmark: the exact sign test against the binomial
+distribution and the bootstrap interval of the median."""
+import os
+import sys
+
+import numpy as np
+import pytest
+
+sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+import bench  # noqa: E402
+
+
+@pytest.mark.parametrize("wins,losses", [(0, 0), (30, 0), (0, 30), (20, 10), (15, 15), (3, 9)])
+def test_sign_test_matches_binomial(wins, losses):
+    stats = pytest.importorskip("scipy.stats")
+    a = [1.0] * wins + [3.0] * losses + [2.0] * 4      # 4 ties, dropped
+    b = [2.0] * (wins + losses + 4)
+    w, l, p = bench.sign_test(a, b)
+    assert (w, l) == (wins, losses)
+    ref = 1.0 if wins + losses == 0 else stats.binomtest(wins, wins + losses, 0.5).pvalue
+    assert p == pytest.approx(ref, rel=1e-12)
+
+
+def test_median_ci_brackets_the_median():
+    x = np.random.default_rng(3).normal(10.0, 1.0, size=30)
+    med, lo, hi = bench.median_ci(x, resamples=2000)
+    assert med == np.median(x) and lo <= med <= hi and hi - lo < 2.0
+    assert bench.median_ci([5.0] * 30, resamples=500) == (5.0, 5.0, 5.0)

@@ -318,6 +318,35 @@ def test_tc_path_event_500k_x12_equal_to_grid(ctx):
     _assert_rows_equal(tc, oracle.self_query(w.points, w.r, w.K, rows=rows), rows)
 
 
+@pytest.mark.parametrize("path", ["grid", "tc"])
+def test_kernel_timing_records_one_duration_per_query(ctx, path):
+    import time
+    import torch
+    from paper_2609_31980_gb300 import frnn
+    pts = torch.from_numpy(synth.clustered(300, 40, 20000, 8, 0.02, seed=510)).cuda()
+    K = 32
+    counts = torch.empty(len(pts), dtype=torch.int32, device="cuda")
+    idx = torch.empty((len(pts), K), dtype=torch.int32, device="cuda")
+    d2 = torch.empty((len(pts), K), dtype=torch.float32, device="cuda")
+    grid = ctx.build_grid(pts, 0.1)
+    ctx.set_option(frnn.FRNN_OPT_KERNEL_TIMING, 1)
+    assert ctx.get_option(frnn.FRNN_OPT_KERNEL_TIMING) == 1
+    ctx.query(grid, pts, 0.1, K, True, path, (counts, idx, d2))
+    ctx.sync()
+    t0 = time.perf_counter()
+    for _ in range(3):
+        ctx.query(grid, pts, 0.1, K, True, path, (counts, idx, d2))
+    ctx.sync()
+    wall_ms = (time.perf_counter() - t0) * 1e3
+    ms = ctx.kernel_times()
+    assert len(ms) == 4 and all(0.0 < t for t in ms) and sum(ms[1:]) <= wall_ms
+    assert ctx.kernel_times() == []           # the read clears the record
+    ctx.set_option(frnn.FRNN_OPT_KERNEL_TIMING, 0)
+    ctx.query(grid, pts, 0.1, K, True, path, (counts, idx, d2))
+    assert ctx.kernel_times() == []
+    grid.close()
+
+
 def test_tc_path_dense_and_duplicates(ctx):
     pts = np.repeat(synth.clustered(20, 40, 100, 8, 0.01, seed=502), 3, axis=0)
     for K in (8, 32, 100):
