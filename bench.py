@@ -314,6 +314,8 @@ def run_ours(args):
     }
     if clocks:
         res["clocks"] = clocks
+    if rank == 0 and not args.no_compact:
+        res["compact_rows"] = run_compact(ctx, grid, pts, r, K, path, stream)
     if rank == 0 and not args.no_batched:
         res["batched_vs_plain"] = run_batched(ctx, args, dev)
     if rank == 0 and not args.no_serving:
@@ -404,6 +406,48 @@ def run_batched(ctx, args, dev):
             "plain": res["plain"], "batched": res["batched"],
             "batched_over_plain": res["plain"]["ms_median"] / res["batched"]["ms_median"],
             "sign_test": {"batched_faster": wins, "plain_faster": losses, "p_two_sided": p}}
+
+
+def run_compact(ctx, grid, pts, r, K, path, stream, reps=20):
+    """Count-first compact rows (frnn_query_csr_count + frnn_query_csr_fill)
+    against the dense rows on the same grid, at the workload's K and at
+    K = 1000 (the paper's real-event setting, where dense rows are mostly
+    padding).  Device time per query (grid built once, outside)."""
+    import torch
+    N = pts.shape[0]
+    mk = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+    out = {}
+    for k in sorted({K, 1000}):
+        with torch.cuda.stream(stream):
+            dense = (torch.empty(N, dtype=torch.int32, device=pts.device),
+                     torch.empty((N, k), dtype=torch.int32, device=pts.device),
+                     torch.empty((N, k), dtype=torch.float32, device=pts.device))
+        res = {}
+        for name in ("dense", "compact"):
+            ts = []
+            for i in range(3 + reps):
+                a, b = mk(), mk()
+                a.record(stream)
+                if name == "dense":
+                    ctx.query(grid, pts, r, k, True, path, dense)
+                else:
+                    with torch.cuda.stream(stream):
+                        off, idx, d2, _ = ctx.query_csr(grid, pts, r, k, True, path)
+                b.record(stream)
+                ctx.sync()
+                if i >= 3:
+                    ts.append(a.elapsed_time(b))
+            res[name] = statistics.median(ts)
+        E = int(off[-1].item())
+        dense_bytes = N * 4 + 2 * N * k * 4
+        csr_bytes = (N + 1) * 8 + 2 * E * 4
+        out[f"K{k}"] = {"dense_ms": res["dense"], "compact_ms": res["compact"],
+                        "edges": E, "dense_output_bytes": dense_bytes,
+                        "compact_output_bytes": csr_bytes,
+                        "compact_matches_dense": bool(torch.equal(
+                            torch.diff(off).to(torch.int32), dense[0]))}
+        del dense
+    return out
 
 
 def run_serving(ctx, args):
@@ -508,6 +552,7 @@ def main():
     ap.add_argument("--grid-axes", type=int, default=0, help="0: last axes, 1: widest axes")
     ap.add_argument("--path", default="grid", choices=["grid", "tc", "auto"])
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-compact", action="store_true")
     ap.add_argument("--batch-events", type=int, default=64)
     ap.add_argument("--batch-reps", type=int, default=30, help="timed rounds of each")
     ap.add_argument("--batch-warmup", type=int, default=10)

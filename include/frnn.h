@@ -292,6 +292,42 @@ typedef enum frnn_option {
 frnn_status frnn_set_option(frnn_ctx* ctx, frnn_option opt, int64_t value);
 frnn_status frnn_get_option(const frnn_ctx* ctx, frnn_option opt, int64_t* value);
 
+/* Compact output, first pass: count-first exact allocation (Sec. 4: the
+ * temporary edge capacity of the real event fell from 4.35 GB to 148 MB; the
+ * compact output is one of the retained ideas of Sec. 6).  Runs the search of
+ * frnn_query (same arguments, same path choice, same results) once, keeps the
+ * sorted rows in the context, and writes
+ *   offsets  device int64 [M + 1]: row i's entries will occupy
+ *            [offsets[i], offsets[i+1]) of the fill pass's arrays;
+ *            offsets[i+1] - offsets[i] = min(degree_i, K); offsets[0] = 0
+ *   degree   device int32 [M] or NULL: the full number of in-radius
+ *            neighbours of each query (not truncated to K; saturates at
+ *            INT32_MAX), self excluded as in frnn_query
+ *   n_edges  host out: offsets[M], the entries the caller must allocate.
+ * Synchronises the context's stream (the count has to reach the host).  The
+ * context holds 8 * 32 + 4 bytes of staging per query, reused
+ * across calls (charged to the memory budget).  Errors: those of frnn_query
+ * (INVALID_ARG, UNSUPPORTED, BUDGET, OUT_OF_MEMORY, NONFINITE, CAPACITY,
+ * TIMEOUT, CUDA); NULL offsets or n_edges: INVALID_ARG. */
+frnn_status frnn_query_csr_count(frnn_ctx* ctx, const frnn_grid* grid, const float* queries,
+                                 int64_t M, float r, int K, unsigned flags, int64_t* offsets,
+                                 int32_t* degree, int64_t* n_edges);
+
+/* Compact output, second pass: writes the rows of the last
+ * frnn_query_csr_count on this context into
+ *   idx    device int32 [n_edges]: original reference indices, each row
+ *          sorted by (d2, index) ascending as in frnn_query, no padding
+ *   dist2  device float [n_edges]: the matching squared distances (bit-exact
+ *          float32 contract, Eq. 1)
+ * using the offsets array given to the count pass (still owned by the
+ * caller and unchanged).  Asynchronous on the context's stream.  Any other
+ * call on the context between the two passes (query, build, batched,
+ * host-buffer, autotune, grid destroy) discards the pending rows: then, or
+ * without a count pass, INVALID_ARG.  idx/dist2 may be NULL when n_edges was 0.
+ * The paper's interface has no separate fill call; the split lets the caller
+ * allocate exactly n_edges entries in between. */
+frnn_status frnn_query_csr_fill(frnn_ctx* ctx, int32_t* idx, float* dist2);
+
 /* Durations of the main query kernel of every frnn_query call made since the
  * last frnn_kernel_times call (or since FRNN_OPT_KERNEL_TIMING was set), in
  * milliseconds, in call order.  Synchronises the context's stream.

@@ -122,6 +122,18 @@ def self_query(points, r: float, K: int, rows=None):
     return frnn(pts[rows], pts, r, K, query_ids=rows)
 
 
+def csr(queries, refs, r: float, K: int, query_ids=None):
+    """Compact (CSR) form of ``frnn``'s result: row i holds its first
+    counts[i] = min(degree_i, K) entries, rows back to back (the paper's
+    count-first exact allocation, Sec. 4).  Returns ``offsets [M+1] int64,
+    idx [E] int32, dist2 [E] float32, degree [M] int64``."""
+    counts, idx, dist2, deg = frnn(queries, refs, r, K, query_ids)
+    offsets = np.zeros(len(counts) + 1, np.int64)
+    offsets[1:] = np.cumsum(counts, dtype=np.int64)
+    keep = np.arange(idx.shape[1])[None, :] < counts[:, None]
+    return offsets, idx[keep], dist2[keep], deg
+
+
 def degree(queries, refs, r: float, query_ids=None):
     """Untruncated degree under the FP32 contract (no sorting)."""
     q, p, ids = _prep(queries, refs, query_ids)

@@ -64,6 +64,18 @@ struct frnn_ctx {
     float g_r = 0.f;
     unsigned g_flags = 0;
     int g_opts[4] = {0, 0, 0, 0};
+    // compact output: staging rows of the pending count pass, and what the
+    // fill pass needs (valid until the next call on this context)
+    void* csr_buf = nullptr;
+    size_t csr_bytes = 0;
+    int32_t* csr_cnt = nullptr;     // [M] marked counts, original order
+    int32_t* csr_idx = nullptr;     // [M * kCsrStageW] staged rows
+    float* csr_d2 = nullptr;
+    int64_t* csr_parts = nullptr;
+    bool csr_pending = false;
+    QueryLaunch csr_q{};
+    int64_t csr_M = 0, csr_E = 0;
+    const int64_t* csr_off = nullptr;
     // kernel timing (FRNN_OPT_KERNEL_TIMING): event pairs, reused across reads
     int ktime = 0;
     std::vector<cudaEvent_t> kev;   // 2 per recorded call
@@ -276,6 +288,7 @@ frnn_status frnn_grid_destroy(frnn_grid* grid) {
     if (!grid) return FRNN_OK;
     if (grid->ctx) {
         cudaStreamSynchronize(grid->ctx->stream);
+        grid->ctx->csr_pending = false;
         grid->ctx->held -= std::min(grid->ctx->held, grid->g.bytes);
         grid->ctx->grids.erase(grid);
     } else {
@@ -309,6 +322,7 @@ frnn_status frnn_destroy(frnn_ctx* ctx) {
     grid_free(ctx->qset);
     grid_free(ctx->batch);
     if (ctx->hp_buf) cudaFree(ctx->hp_buf);
+    if (ctx->csr_buf) cudaFree(ctx->csr_buf);
     cudaFree(ctx->d_status);
     cudaFreeHost(ctx->h_status);
     delete ctx;
@@ -317,6 +331,7 @@ frnn_status frnn_destroy(frnn_ctx* ctx) {
 
 frnn_status frnn_build_grid(frnn_ctx* ctx, const float* refs, int64_t N, int D, float r,
                             frnn_grid** grid) {
+    if (ctx) ctx->csr_pending = false;
     if (!ctx) return FRNN_ERR_INVALID_ARG;
     if (!grid) return fail(ctx, FRNN_ERR_INVALID_ARG, "grid is NULL");
     if (D < 1 || D > kMaxD) return fail(ctx, FRNN_ERR_INVALID_ARG, "D must be in 1..16");
@@ -375,13 +390,16 @@ static frnn_status check_query_args(frnn_ctx* ctx, int64_t M, float r, int K, un
     return FRNN_OK;
 }
 
-frnn_status frnn_query(frnn_ctx* ctx, const frnn_grid* grid, const float* queries, int64_t M,
-                       float r, int K, unsigned flags, int32_t* counts, int32_t* idx,
-                       float* dist2) {
-    if (!ctx) return FRNN_ERR_INVALID_ARG;
-    if (!grid || grid->ctx != ctx) return fail(ctx, FRNN_ERR_INVALID_ARG, "grid is not of ctx");
-    frnn_status s = check_query_args(ctx, M, r, K, flags, counts, idx, dist2);
-    if (s != FRNN_OK) return s;
+// The search of frnn_query; csr != NULL: compact output's first pass (rows
+// to the staging area, counts marked, spilled rows counted and marked).
+struct CsrPass {
+    int32_t* degree;
+};
+static frnn_status query_impl(frnn_ctx* ctx, const frnn_grid* grid, const float* queries,
+                              int64_t M, float r, int K, unsigned flags, int32_t* counts,
+                              int32_t* idx, float* dist2, const CsrPass* csr,
+                              QueryLaunch* launched) {
+    frnn_status s;
     if (r > grid->r) return fail(ctx, FRNN_ERR_INVALID_ARG, "r exceeds the grid's radius");
     if (M > 0 && !queries) return fail(ctx, FRNN_ERR_INVALID_ARG, "queries is NULL");
     const bool self = (flags & FRNN_SELF_QUERY) != 0;
@@ -406,6 +424,11 @@ frnn_status frnn_query(frnn_ctx* ctx, const frnn_grid* grid, const float* querie
     q.dist2 = dist2;
     q.d_status = ctx->d_status;
     q.num_sms = ctx->num_sms;
+    if (csr) {
+        q.csr = 1;
+        q.ovf_mode = 1;
+        q.degree = csr->degree;
+    }
     if (ctx->ktime && ctx->kev_used < kMaxTimedCalls) {
         const size_t need = 2 * (size_t)(ctx->kev_used + 1);
         while (ctx->kev.size() < need) {
@@ -446,6 +469,109 @@ frnn_status frnn_query(frnn_ctx* ctx, const frnn_grid* grid, const float* querie
         s = enqueue_grid_query(q, ctx->stream, err);
     }
     if (s != FRNN_OK) return fail(ctx, s, err);
+    q.kev[0] = q.kev[1] = nullptr;
+    if (launched) *launched = q;
+    return FRNN_OK;
+}
+
+frnn_status frnn_query(frnn_ctx* ctx, const frnn_grid* grid, const float* queries, int64_t M,
+                       float r, int K, unsigned flags, int32_t* counts, int32_t* idx,
+                       float* dist2) {
+    if (!ctx) return FRNN_ERR_INVALID_ARG;
+    ctx->csr_pending = false;
+    if (!grid || grid->ctx != ctx) return fail(ctx, FRNN_ERR_INVALID_ARG, "grid is not of ctx");
+    frnn_status s = check_query_args(ctx, M, r, K, flags, counts, idx, dist2);
+    if (s != FRNN_OK) return s;
+    return query_impl(ctx, grid, queries, M, r, K, flags, counts, idx, dist2, nullptr, nullptr);
+}
+
+static frnn_status csr_reserve(frnn_ctx* ctx, int64_t M) {
+    auto al = [](size_t x) { return (x + 255) / 256 * 256; };
+    const size_t rows = (size_t)std::max<int64_t>(M, 1);
+    const size_t b_cnt = al(rows * 4), b_stage = al(rows * kCsrStageW * 4);
+    const size_t b_parts = al((size_t)csr_parts_needed(M) * 8);
+    const size_t need = b_cnt + 2 * b_stage + b_parts;
+    if (need > ctx->csr_bytes) {
+        if (!budget_allows(ctx, ctx->csr_bytes, need))
+            return fail(ctx, FRNN_ERR_BUDGET, "request exceeds the context's memory budget");
+        cudaStreamSynchronize(ctx->stream);
+        if (ctx->csr_buf) cudaFree(ctx->csr_buf);
+        ctx->held -= ctx->csr_bytes;
+        ctx->csr_buf = nullptr;
+        ctx->csr_bytes = 0;
+        if (cudaMalloc(&ctx->csr_buf, need) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(ctx, FRNN_ERR_OUT_OF_MEMORY, "cudaMalloc of the compact-output staging failed");
+        }
+        ctx->csr_bytes = need;
+        ctx->held += need;
+    }
+    char* b = static_cast<char*>(ctx->csr_buf);
+    ctx->csr_cnt = reinterpret_cast<int32_t*>(b);
+    ctx->csr_idx = reinterpret_cast<int32_t*>(b + b_cnt);
+    ctx->csr_d2 = reinterpret_cast<float*>(b + b_cnt + b_stage);
+    ctx->csr_parts = reinterpret_cast<int64_t*>(b + b_cnt + 2 * b_stage);
+    return FRNN_OK;
+}
+
+frnn_status frnn_query_csr_count(frnn_ctx* ctx, const frnn_grid* grid, const float* queries,
+                                 int64_t M, float r, int K, unsigned flags, int64_t* offsets,
+                                 int32_t* degree, int64_t* n_edges) {
+    if (!ctx) return FRNN_ERR_INVALID_ARG;
+    ctx->csr_pending = false;
+    if (!grid || grid->ctx != ctx) return fail(ctx, FRNN_ERR_INVALID_ARG, "grid is not of ctx");
+    if (!offsets || !n_edges) return fail(ctx, FRNN_ERR_INVALID_ARG, "offsets or n_edges is NULL");
+    int32_t dummy = 0;   // check_query_args wants row outputs: the staging is ours
+    frnn_status s = check_query_args(ctx, M, r, K, flags, &dummy, &dummy, reinterpret_cast<float*>(&dummy));
+    if (s != FRNN_OK) return s;
+    *n_edges = 0;
+    s = csr_reserve(ctx, M);
+    if (s != FRNN_OK) return s;
+    QueryLaunch q{};
+    if (M > 0) {
+        const CsrPass cp{degree};
+        s = query_impl(ctx, grid, queries, M, r, K, flags, ctx->csr_cnt, ctx->csr_idx,
+                       ctx->csr_d2, &cp, &q);
+        if (s != FRNN_OK) return s;
+    }
+    enqueue_csr_offsets(ctx->csr_cnt, M, ctx->csr_parts, offsets, ctx->stream);
+    int64_t* h_edges = reinterpret_cast<int64_t*>(ctx->h_status + 2);
+    cudaError_t e = cudaMemcpyAsync(h_edges, offsets + M, sizeof(int64_t), cudaMemcpyDeviceToHost,
+                                    ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "reading the edge count");
+    s = frnn_sync(ctx);
+    if (s != FRNN_OK) return s;
+    *n_edges = *h_edges;
+    ctx->csr_q = q;
+    ctx->csr_M = M;
+    ctx->csr_E = *h_edges;
+    ctx->csr_off = offsets;
+    ctx->csr_pending = true;
+    return FRNN_OK;
+}
+
+frnn_status frnn_query_csr_fill(frnn_ctx* ctx, int32_t* idx, float* dist2) {
+    if (!ctx) return FRNN_ERR_INVALID_ARG;
+    if (!ctx->csr_pending)
+        return fail(ctx, FRNN_ERR_INVALID_ARG,
+                    "no pending frnn_query_csr_count on this context (or another call came between)");
+    if (ctx->csr_E > 0 && (!idx || !dist2))
+        return fail(ctx, FRNN_ERR_INVALID_ARG, "idx or dist2 is NULL");
+    ctx->csr_pending = false;
+    if (ctx->csr_M == 0) return FRNN_OK;
+    enqueue_csr_gather(ctx->csr_cnt, ctx->csr_off, ctx->csr_idx, ctx->csr_d2, ctx->csr_M, idx,
+                       dist2, ctx->num_sms, ctx->stream);
+    QueryLaunch q = ctx->csr_q;
+    q.ovf_mode = 2;
+    q.row_off = ctx->csr_off;
+    q.idx = idx;
+    q.dist2 = dist2;
+    q.degree = nullptr;
+    std::string err;
+    frnn_status s = enqueue_overflow_only(q, ctx->stream, err);
+    if (s != FRNN_OK) return fail(ctx, s, err);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "compact-output gather launch");
     return FRNN_OK;
 }
 
@@ -528,6 +654,7 @@ static frnn_status launch_graph(frnn_ctx* ctx) {
 frnn_status frnn_query_batched(frnn_ctx* ctx, const frnn_event* ev, int n_events, int D,
                                float r, int K, unsigned flags) {
     if (!ctx) return FRNN_ERR_INVALID_ARG;
+    ctx->csr_pending = false;
     if (n_events < 0 || (n_events > 0 && !ev))
         return fail(ctx, FRNN_ERR_INVALID_ARG, "bad event list");
     if (D < 1 || D > kMaxD) return fail(ctx, FRNN_ERR_INVALID_ARG, "D must be in 1..16");

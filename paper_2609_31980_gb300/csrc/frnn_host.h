@@ -128,8 +128,25 @@ struct QueryLaunch {
     unsigned long long* tc_stats = nullptr;   // [2]: pre-filter survivors, exact accepts
     int path_filter = -1;                     // batched: only events of this path
     cudaEvent_t kev[2] = {nullptr, nullptr};  // optional: recorded around the main kernel
+    // compact output (csr.cu): staging mode of the main kernels and the
+    // selection kernel's mode (0 dense, 1 count, 2 rows at row_off)
+    int csr = 0;
+    int ovf_mode = 0;
+    int32_t* degree = nullptr;
+    const int64_t* row_off = nullptr;
 };
 frnn_status enqueue_grid_query(const QueryLaunch& q, cudaStream_t st, std::string& err);
+// The selection kernel alone over the rows the last query of q.qset listed
+// (compact output, second pass: q.ovf_mode 2, q.row_off).
+frnn_status enqueue_overflow_only(const QueryLaunch& q, cudaStream_t st, std::string& err);
+// Compact output (csr.cu): offsets[0..M] from the marked counts; the gather
+// of the staged rows.  parts: csr_parts_needed(M) int64 scratch.
+int64_t csr_parts_needed(int64_t M);
+void enqueue_csr_offsets(const int32_t* cnt, int64_t M, int64_t* parts, int64_t* offsets,
+                         cudaStream_t st);
+void enqueue_csr_gather(const int32_t* cnt, const int64_t* offsets, const int32_t* sidx,
+                        const float* sd2, int64_t M, int32_t* idx, float* dist2, int num_sms,
+                        cudaStream_t st);
 
 // Tensor-core path: prepare operands (and 128-query tasks) of a point set.
 // center_src: the grid whose per-event centres the operands use (the

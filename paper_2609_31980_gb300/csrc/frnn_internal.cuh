@@ -20,6 +20,11 @@ constexpr int kTaskQueries = 32;        // queries per warp task (one per lane)
 constexpr int kStatusNonFinite = 1;
 constexpr int kStatusTimeout = 2;
 constexpr int kStatusCapacity = 4;
+// compact (CSR) output: staging rows of kCsrStageW entries per query; a count
+// with kCsrSpill set belongs to a row the selection kernel writes itself
+constexpr int kCsrStageW = 32;
+constexpr int32_t kCsrSpill = 0x40000000;
+constexpr int32_t kCsrCountMask = 0x3fffffff;
 
 // Bounded waits: an mbarrier wait gives up after about two seconds of wall
 // time (%globaltimer), far above any legitimate wait, with an iteration cap as
@@ -104,6 +109,14 @@ struct QueryArgs {
     int32_t ovf_cap;
     int32_t exit_dims;           // dims summed before the warp early-exit vote
     int32_t path_filter;         // -1: every event; else only events whose path matches
+    // compact output.  csr = 1: rows go to idx/dist2 at row * kCsrStageW (no
+    // padding) and counts get kCsrSpill for rows left to the selection kernel.
+    // Selection kernel mode: 0 dense rows, 1 count only (counts | kCsrSpill and
+    // degree), 2 rows at row_off[query].
+    int32_t csr;
+    int32_t ovf_mode;
+    int32_t* degree;             // optional full degree per query (csr)
+    const int64_t* row_off;      // CSR row offsets (ovf_mode 2)
 };
 
 // ---------------------------------------------------------------- PTX helpers

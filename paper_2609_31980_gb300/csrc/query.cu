@@ -48,6 +48,7 @@ constexpr int kNBuf = 2;
 constexpr uint32_t kFull = 0xffffffffu;
 constexpr int kListCap = 32;      // per-lane neighbour list in shared memory
 constexpr int kListStride = 33;   // entry e of lane l at e*33 + l: conflict-free both ways
+static_assert(kListCap <= kCsrStageW, "a staged compact row holds a whole list");
 
 template <int D>
 struct QCfg {
@@ -175,7 +176,7 @@ __global__ void __launch_bounds__(kQueryWarps * 32, 4) k_grid_query(QueryArgs a)
         const int qorig = act ? a.qperm[qs] : 0;
         if (!h.valid) {
             // grid built from non-finite input: empty rows (frnn_sync reports it)
-            for (int ql = 0; ql < task.nq; ++ql) {
+            for (int ql = 0; ql < task.nq && !a.csr; ++ql) {
                 const int qo = __shfl_sync(kFull, qorig, ql);
                 for (int e = lane; e < K; e += 32) {
                     oidx[(int64_t)qo * K + e] = -1;
@@ -183,6 +184,7 @@ __global__ void __launch_bounds__(kQueryWarps * 32, 4) k_grid_query(QueryArgs a)
                 }
             }
             if (act) counts[qorig] = 0;
+            if (act && a.degree) a.degree[qorig] = 0;
             continue;
         }
         uint64_t qq[D];   // each query coordinate duplicated into both f32x2 lanes
@@ -358,6 +360,8 @@ __global__ void __launch_bounds__(kQueryWarps * 32, 4) k_grid_query(QueryArgs a)
         const bool spill = lost;
         sort_list(Ld + lane, Li + lane, kListStride, (act && !spill) ? cnt : 0, a.rperm);
         if (act && !spill) counts[qorig] = min(cnt, K);
+        if (act && spill && a.csr) counts[qorig] = kCsrSpill;   // counted by the selection kernel
+        if (act && !spill && a.degree) a.degree[qorig] = cnt;
         if (act && spill) {
             // longer than the list: the exact selection kernel finishes this row
             const int pos = atomicAdd(a.ovf_count, 1);
@@ -370,14 +374,17 @@ __global__ void __launch_bounds__(kQueryWarps * 32, 4) k_grid_query(QueryArgs a)
         }
         __syncwarp();
         // coalesced row writes: one query row at a time across the warp
+        // (compact output: the row's entries only, into its staging row)
         const unsigned spill_mask = __ballot_sync(kFull, spill);
+        const int rstride = a.csr ? kCsrStageW : K;
         for (int ql = 0; ql < task.nq; ++ql) {
             if (spill_mask & (1u << ql)) continue;
             const int c = min(__shfl_sync(kFull, cnt, ql), K);
             const int qo = __shfl_sync(kFull, qorig, ql);
-            int32_t* irow = oidx + (int64_t)qo * K;
-            float* drow = od2 + (int64_t)qo * K;
-            for (int e = lane; e < K; e += 32) {
+            int32_t* irow = oidx + (int64_t)qo * rstride;
+            float* drow = od2 + (int64_t)qo * rstride;
+            const int wlen = a.csr ? c : K;
+            for (int e = lane; e < wlen; e += 32) {
                 const bool real = e < c;
                 irow[e] = real ? Li[e * kListStride + ql] : -1;
                 drow[e] = real ? Ld[e * kListStride + ql] : INFINITY;
@@ -438,10 +445,11 @@ __global__ void __launch_bounds__(kOvfWarps * 32) k_overflow(QueryArgs a, int ca
         const int dims0 = h.dims[0], dims1 = h.dims[1], dims2 = h.dims[2], m = h.m;
         const int x = qc % dims0, y = (qc / dims0) % dims1, z = qc / (dims0 * dims1);
         const int self_slot = a.self ? qs : -1;
+        const bool count_only = a.ovf_mode == 1;
         int fill = 0;
         int64_t deg = 0;
         uint64_t thr = ~0ull;
-        for (int i = lane; i < cap; i += 32) buf[i] = ~0ull;
+        for (int i = lane; i < cap && !count_only; i += 32) buf[i] = ~0ull;
         __syncwarp();
         const int ylo = h.naxes >= 2 ? max(y - m, 0) : 0, yhi = h.naxes >= 2 ? min(y + m, dims1 - 1) : 0;
         const int zlo = h.naxes >= 3 ? max(z - m, 0) : 0, zhi = h.naxes >= 3 ? min(z + m, dims2 - 1) : 0;
@@ -463,11 +471,14 @@ __global__ void __launch_bounds__(kOvfWarps * 32) k_overflow(QueryArgs a, int ca
                             }
                         }
                         if (s <= a.r2) {
-                            key = make_key(s, a.rperm[cs]);
                             ++deg;
-                            if (key >= thr) key = ~0ull;
+                            if (!count_only) {
+                                key = make_key(s, a.rperm[cs]);
+                                if (key >= thr) key = ~0ull;
+                            }
                         }
                     }
+                    if (count_only) continue;
                     const unsigned bal = __ballot_sync(kFull, key != ~0ull);
                     if (key != ~0ull) buf[fill + __popc(bal & ((1u << lane) - 1u))] = key;
                     fill += __popc(bal);
@@ -481,17 +492,27 @@ __global__ void __launch_bounds__(kOvfWarps * 32) k_overflow(QueryArgs a, int ca
                 }
             }
         }
+        for (int o2 = 16; o2 > 0; o2 >>= 1) deg += __shfl_xor_sync(kFull, deg, o2);
+        const int32_t c = (int32_t)(deg < K ? deg : K);
+        if (count_only) {
+            // compact output, first pass: the row's count (marked) and degree
+            if (lane == 0) {
+                (a.counts ? a.counts : h.counts)[qo] = c | kCsrSpill;
+                if (a.degree) a.degree[qo] = (int32_t)(deg < INT32_MAX ? deg : INT32_MAX);
+            }
+            continue;
+        }
         smem_bitonic(buf, cap);
-        int32_t* irow = oidx + (int64_t)qo * K;
-        float* drow = od2 + (int64_t)qo * K;
-        for (int e = lane; e < K; e += 32) {
+        const bool csr_rows = a.ovf_mode == 2;
+        int32_t* irow = oidx + (csr_rows ? a.row_off[qo] : (int64_t)qo * K);
+        float* drow = od2 + (csr_rows ? a.row_off[qo] : (int64_t)qo * K);
+        for (int e = lane; e < (csr_rows ? c : K); e += 32) {
             const uint64_t v = buf[e];
             const bool real = v != ~0ull;
             irow[e] = real ? (int32_t)(uint32_t)v : -1;
             drow[e] = real ? __uint_as_float((uint32_t)(v >> 32)) : INFINITY;
         }
-        for (int o2 = 16; o2 > 0; o2 >>= 1) deg += __shfl_xor_sync(kFull, deg, o2);
-        if (lane == 0) (a.counts ? a.counts : h.counts)[qo] = (int32_t)(deg < K ? deg : K);
+        if (lane == 0 && !csr_rows) (a.counts ? a.counts : h.counts)[qo] = c;
         __syncwarp();
     }
 }
@@ -550,6 +571,10 @@ frnn_status enqueue_grid_query(const QueryLaunch& q, cudaStream_t st, std::strin
     a.ovf_cap = (int32_t)std::max<int64_t>(qs.n_total, 1);
     a.exit_dims = q.exit_dims;
     a.path_filter = q.path_filter;
+    a.csr = q.csr;
+    a.ovf_mode = q.ovf_mode;
+    a.degree = q.degree;
+    a.row_off = q.row_off;
     cudaMemsetAsync(qs.scalars + kScTaskCounter, 0, 2 * sizeof(int32_t), st);   // counter + ovf
     if (q.kev[0]) cudaEventRecord(q.kev[0], st);
     cudaError_t ce = cudaSuccess;
@@ -569,6 +594,36 @@ frnn_status enqueue_grid_query(const QueryLaunch& q, cudaStream_t st, std::strin
     }
     if (q.kev[1]) cudaEventRecord(q.kev[1], st);
     return enqueue_overflow(a, q.num_sms, st, err);
+}
+
+frnn_status enqueue_overflow_only(const QueryLaunch& q, cudaStream_t st, std::string& err) {
+    const GridBufs& qs = *q.qset;
+    const GridBufs& rs = *q.rset;
+    QueryArgs o{};
+    o.ev = rs.hdr;
+    o.qpts = qs.pts;
+    o.qperm = qs.perm;
+    o.qcell = qs.cell;
+    o.rpts = rs.pts;
+    o.rperm = rs.perm;
+    o.cstart = rs.cstart;
+    o.counts = q.counts;
+    o.idx = q.idx;
+    o.dist2 = q.dist2;
+    o.r2 = q.r2;
+    o.K = q.K;
+    o.self = q.self;
+    o.D = rs.D;
+    o.status = q.d_status;
+    o.ovf = qs.ovf;
+    o.ovf_count = qs.scalars + kScOvfCount;
+    o.ovf_cap = (int32_t)std::max<int64_t>(qs.n_total, 1);
+    o.path_filter = -1;
+    o.csr = q.csr;
+    o.ovf_mode = q.ovf_mode;
+    o.degree = q.degree;
+    o.row_off = q.row_off;
+    return enqueue_overflow(o, q.num_sms, st, err);
 }
 
 frnn_status enqueue_overflow(const QueryArgs& a, int num_sms, cudaStream_t st, std::string& err) {

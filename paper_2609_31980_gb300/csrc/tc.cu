@@ -68,6 +68,7 @@ constexpr int kTcMaxRows = 32;   // neighbour rows per task (m <= 2)
 constexpr int kTcCols = 256;     // TMEM columns per CTA: two accumulators (2 CTAs / SM)
 // (the producer warp is warp 4; epilogue warps 0..3 own the TMEM lane quarters)
 constexpr int kTcList = 30;      // per-query survivor list capacity (2 CTAs / SM up to D = 12)
+static_assert(kTcList <= kCsrStageW, "a staged compact row holds a whole list");
 
 __host__ __device__ constexpr int tc_k_for(int D) { return ((3 * D + 2) + 15) / 16 * 16; }
 
@@ -305,6 +306,8 @@ struct TcArgs {
     int32_t path_filter;                  // -1: every event; else only events with this path
     unsigned long long* stat_survivors;   // pre-filter survivors (false-candidate rate)
     unsigned long long* stat_accepted;    // exact accepts
+    int32_t csr;                          // compact output: staging rows (see QueryArgs)
+    int32_t* degree;
 };
 
 // Chunk geometry of a task: neighbour row L covers slot range [rs, re); its
@@ -434,11 +437,12 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_tc_query(TcArgs a) {
         if (!h.valid) {
             // grid built from non-finite input: empty rows (frnn_sync reports it)
             if (active) {
-                for (int e = 0; e < Kout; ++e) {
+                for (int e = 0; e < Kout && !a.csr; ++e) {
                     oidx[(int64_t)qorig * Kout + e] = -1;
                     od2[(int64_t)qorig * Kout + e] = INFINITY;
                 }
                 counts[qorig] = 0;
+                if (a.degree) a.degree[qorig] = 0;
             }
             continue;
         }
@@ -705,6 +709,8 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_tc_query(TcArgs a) {
         if (half == 0) {
             sort_list(Ld + row, Li + row, kTcLStr, (active && !spill) ? cnt : 0, a.rperm);
             if (active && !spill) counts[qorig] = min(cnt, Kout);
+            if (active && spill && a.csr) counts[qorig] = kCsrSpill;   // counted by the selection kernel
+            if (active && !spill && a.degree) a.degree[qorig] = cnt;
         }
         if (spill && half == 0) {
             // longer than the list: the exact selection kernel finishes this row
@@ -726,9 +732,10 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_tc_query(TcArgs a) {
             const int r = 32 * (warp & 3) + ql;
             const int c = min(__shfl_sync(0xffffffffu, cnt, ql), Kout);
             const int qo = __shfl_sync(0xffffffffu, qorig, ql);
-            int32_t* irow = oidx + (int64_t)qo * Kout;
-            float* drow = od2 + (int64_t)qo * Kout;
-            for (int e = lane; e < Kout; e += 32) {
+            const int rstride = a.csr ? kCsrStageW : Kout;   // compact: staging row, no padding
+            int32_t* irow = oidx + (int64_t)qo * rstride;
+            float* drow = od2 + (int64_t)qo * rstride;
+            for (int e = lane; e < (a.csr ? c : Kout); e += 32) {
                 const bool real = e < c;
                 irow[e] = real ? Li[e * kTcLStr + r] : -1;
                 drow[e] = real ? Ld[e * kTcLStr + r] : INFINITY;
@@ -876,6 +883,8 @@ frnn_status enqueue_tc_query(const QueryLaunch& q, cudaStream_t st, std::string&
     a.path_filter = q.path_filter;
     a.stat_survivors = q.tc_stats;
     a.stat_accepted = q.tc_stats ? q.tc_stats + 1 : nullptr;
+    a.csr = q.csr;
+    a.degree = q.degree;
     cudaMemsetAsync(qs.scalars + kScOvfCount, 0, sizeof(int32_t), st);
     cudaMemsetAsync(qs.scalars + kScTcCounter, 0, sizeof(int32_t), st);
     if (q.kev[0]) cudaEventRecord(q.kev[0], st);
@@ -927,6 +936,10 @@ frnn_status enqueue_tc_query(const QueryLaunch& q, cudaStream_t st, std::string&
     o.ovf_count = qs.scalars + kScOvfCount;
     o.ovf_cap = a.ovf_cap;
     o.path_filter = -1;   // the list only holds rows this launch queued
+    o.csr = q.csr;
+    o.ovf_mode = q.ovf_mode;
+    o.degree = q.degree;
+    o.row_off = q.row_off;
     return enqueue_overflow(o, q.num_sms, st, err);
 }
 

@@ -48,7 +48,7 @@ EXPORTED = ["frnn_version", "frnn_create", "frnn_destroy", "frnn_build_grid",
             "frnn_grid_destroy", "frnn_query", "frnn_query_batched", "frnn_self_query_host",
             "frnn_sync", "frnn_last_error", "frnn_set_option", "frnn_get_option",
             "frnn_autotune", "frnn_serve_run", "frnn_self_query_noalloc",
-            "frnn_kernel_times"]
+            "frnn_kernel_times", "frnn_query_csr_count", "frnn_query_csr_fill"]
 
 
 class frnn_tune_result(ctypes.Structure):
@@ -89,6 +89,9 @@ _sigs = {
     "frnn_set_option": ([_vp, _int, _i64], _int),
     "frnn_get_option": ([_vp, _int, ctypes.POINTER(_i64)], _int),
     "frnn_kernel_times": ([_vp, ctypes.POINTER(_f32), _int, ctypes.POINTER(_int)], _int),
+    "frnn_query_csr_count": ([_vp, _vp, _vp, _i64, _f32, _int, _u32, _vp, _vp,
+                              ctypes.POINTER(_i64)], _int),
+    "frnn_query_csr_fill": ([_vp, _vp, _vp], _int),
     "frnn_autotune": ([_vp, _vp, _i64, _int, _f32, _int, _u32, ctypes.POINTER(frnn_tune_result)],
                       _int),
     "frnn_self_query_noalloc": ([_vp, _i64, _int, _f32, _int, _vp, _vp, _vp, _vp], _int),
@@ -224,6 +227,32 @@ class Context:
                         _vp(dist2.data_ptr()))
         _check(self.handle, rc)
         return counts, idx, dist2
+
+    def query_csr(self, grid: Grid, queries, r: float, K: int, self_query: bool = True,
+                  path: str = "auto", degree: bool = False):
+        """frnn_query_csr_count + frnn_query_csr_fill (compact rows, exact
+        allocation); returns (offsets [M+1] int64, idx [E] int32,
+        dist2 [E] f32, degree [M] int32 or None)."""
+        torch = _torch()
+        _dev_f32(queries, "queries")
+        M = queries.shape[0]
+        dev = queries.device
+        offsets = torch.empty(M + 1, dtype=torch.int64, device=dev)
+        deg = torch.empty(M, dtype=torch.int32, device=dev) if degree else None
+        n_edges = _i64(0)
+        flags = PATHS[path] | (FRNN_SELF_QUERY if self_query else 0)
+        rc = frnn_query_csr_count(self.handle, grid.handle, _vp(queries.data_ptr()), M, float(r),
+                                  int(K), flags, _vp(offsets.data_ptr()),
+                                  _vp(deg.data_ptr()) if deg is not None else None,
+                                  ctypes.byref(n_edges))
+        _check(self.handle, rc)
+        E = int(n_edges.value)
+        idx = torch.empty(E, dtype=torch.int32, device=dev)
+        dist2 = torch.empty(E, dtype=torch.float32, device=dev)
+        rc = frnn_query_csr_fill(self.handle, _vp(idx.data_ptr()) if E else None,
+                                 _vp(dist2.data_ptr()) if E else None)
+        _check(self.handle, rc)
+        return offsets, idx, dist2, deg
 
     def self_query(self, points, r: float, K: int, path: str = "auto", out=None):
         """Build a grid on ``points`` and self-query it (one call each)."""

@@ -41,6 +41,17 @@ def test_ex1_line_hand_worked():
         np.testing.assert_array_equal(deg, [2, 2, 3, 1])
 
 
+def test_ex1_line_compact_rows_hand_worked():
+    g = _load("ex1_line_csr.json")
+    pts = np.array(g["points"], np.float32)
+    for case in g["cases"]:
+        off, idx, d2, deg = oracle.csr(pts, pts, g["r"], case["K"], query_ids=np.arange(len(pts)))
+        np.testing.assert_array_equal(off, case["offsets"])
+        np.testing.assert_array_equal(idx, case["idx"])
+        np.testing.assert_array_equal(_bits(d2), _bits([hexf(v) for v in case["dist2"]]))
+        np.testing.assert_array_equal(deg, case["degree"])
+
+
 def _pair(x, y, r):
     q = np.array([[hexf(v) for v in x]], np.float32)
     p = np.array([[hexf(v) for v in y]], np.float32)
