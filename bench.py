@@ -205,6 +205,12 @@ def run_ours(args):
         ctx.set_option(frnn.FRNN_OPT_EXIT_DIMS, args.exit_dims)
     if args.grid_axes:
         ctx.set_option(frnn.FRNN_OPT_GRID_AXES, args.grid_axes)
+    if args.grid_naxes:
+        ctx.set_option(frnn.FRNN_OPT_GRID_NAXES, args.grid_naxes)
+    elif path == "tc":
+        # the tensor-core path's 128-query tasks want the longer rows of a
+        # three-axis grid (the library's four-axis default suits the scan)
+        ctx.set_option(frnn.FRNN_OPT_GRID_NAXES, 3)
     with torch.cuda.stream(stream):
         pts = torch.from_numpy(pts_np).to(dev)
         counts = torch.empty(N, dtype=torch.int32, device=dev)
@@ -248,7 +254,7 @@ def run_ours(args):
     wall = time.perf_counter() - wall0
     clocks = sampler.stop()
     kern_ms = ctx.kernel_times()           # one per timed step, same stream
-    kern_is_tc = path == "tc" or (path == "auto" and D >= 10)
+    kern_is_tc = path == "tc"   # auto: the grid scan (four gridded axes by default)
     ctx.set_option(frnn.FRNN_OPT_KERNEL_TIMING, 0)
     step_ms = [e[0].elapsed_time(e[2]) for e in evs]
     build_ms = [e[0].elapsed_time(e[1]) for e in evs]
@@ -292,6 +298,7 @@ def run_ours(args):
         "config": {"workload": w.name, "N": N, "D": D, "r": r, "K": K, "path": path,
                    "cell_mult": ctx.get_option(frnn.FRNN_OPT_CELL_MULT),
                    "exit_dims": ctx.get_option(frnn.FRNN_OPT_EXIT_DIMS),
+                   "grid_naxes": ctx.get_option(frnn.FRNN_OPT_GRID_NAXES),
                    "self_query": True, "l2": "flushed between timed steps (256 MB write)",
                    "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
         "pairs_per_s": whole_job_rate(pairs, args.steps, ws, total_ms),
@@ -550,6 +557,7 @@ def main():
     ap.add_argument("--cell-mult", type=int, default=0, help="grid cell multiple m (0: library default)")
     ap.add_argument("--exit-dims", type=int, default=0, help="dims before the warp vote (0: default)")
     ap.add_argument("--grid-axes", type=int, default=0, help="0: last axes, 1: widest axes")
+    ap.add_argument("--grid-naxes", type=int, default=0, help="gridded axes (0: library default)")
     ap.add_argument("--path", default="grid", choices=["grid", "tc", "auto"])
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-compact", action="store_true")

@@ -261,6 +261,7 @@ typedef struct frnn_tune_result {
     int cell_mult;   /* m */
     int exit_dims;   /* warp vote point of the grid scan (0 = default) */
     float ms;        /* build + query time of the winner, milliseconds */
+    int grid_axes;   /* gridded coordinates (3, or 4 with m = 1) */
 } frnn_tune_result;
 
 frnn_status frnn_autotune(frnn_ctx* ctx, const float* refs, int64_t N, int D, float r, int K,
@@ -270,7 +271,8 @@ frnn_status frnn_autotune(frnn_ctx* ctx, const float* refs, int64_t N, int D, fl
 typedef enum frnn_option {
     FRNN_OPT_CELL_MULT = 1,   /* m in {1, 2}: cell edge ~ r/m, search +-m cells;
                                  0 (default): autotuned, else 1 */
-    FRNN_OPT_GRID_AXES = 2,   /* 0: the last min(D,3) axes; 1: the 3 widest axes */
+    FRNN_OPT_GRID_AXES = 2,   /* which coordinates are gridded: 0 the last ones,
+                                 1 the widest ones (count: FRNN_OPT_GRID_NAXES) */
     FRNN_OPT_EXIT_DIMS = 3,   /* dims summed before the warp-uniform early exit
                                  (0 = library default) */
     FRNN_OPT_USE_GRAPH = 4,   /* 1 (default): batched calls replay a CUDA graph */
@@ -282,11 +284,15 @@ typedef enum frnn_option {
                                  pre-filter since the last reset (synchronises);
                                  set (any value): reset both counters */
     FRNN_OPT_TC_ACCEPTED = 8, /* read: of those, accepted by the exact recheck */
-    FRNN_OPT_KERNEL_TIMING = 9/* 1: frnn_query records CUDA events around its
+    FRNN_OPT_KERNEL_TIMING = 9,/* 1: frnn_query records CUDA events around its
                                  main query kernel (grid or tensor-core; not the
                                  selection pass or operand preparation), read
                                  with frnn_kernel_times; 0 (default): off.
                                  Setting it discards recorded pairs. */
+    FRNN_OPT_GRID_NAXES = 10  /* gridded coordinates: 1..4 (at most D); 0
+                                 (default): autotuned, else min(D, 3).  With 4
+                                 axes the cell multiple is 1 (the neighbour
+                                 rows, (2m+1)^3, must not exceed 32). */
 } frnn_option;
 
 frnn_status frnn_set_option(frnn_ctx* ctx, frnn_option opt, int64_t value);

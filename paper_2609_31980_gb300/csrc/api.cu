@@ -18,6 +18,7 @@ struct frnn_grid {
     int64_t N = 0;
     int D = 0;
     float r = 0.f;
+    int naxes = 0;   // gridded axes requested at the build
 };
 
 struct frnn_ctx {
@@ -32,6 +33,7 @@ struct frnn_ctx {
     std::string err;
     // options (cell_mult 0 / exit_dims 0: tuned value, else the library default)
     int cell_mult = 0;
+    int grid_naxes = 0;       // gridded axes: 0 tuned / default, else 1..4
     int axes_mode = 0;
     int exit_dims = 0;
     int use_graph = 1;
@@ -49,6 +51,7 @@ struct frnn_ctx {
         int m;
         int exit_dims;
         float ms;
+        int naxes;
     };
     std::map<uint32_t, Tuned> tuned;
     // live grids built through this context (detached when it is destroyed)
@@ -89,6 +92,7 @@ static thread_local std::string g_create_err;
 namespace frnn {
 void ctx_copy_tuning(frnn_ctx* dst, const frnn_ctx* src) {
     dst->cell_mult = src->cell_mult;
+    dst->grid_naxes = src->grid_naxes;
     dst->axes_mode = src->axes_mode;
     dst->exit_dims = src->exit_dims;
     dst->autotune = src->autotune;
@@ -155,9 +159,12 @@ static frnn_status alloc_accounted(frnn_ctx* c, GridBufs& g, int E, const int64_
 // Path choice: FRNN_PATH_TC forces the tensor-core pre-filter (D >= 8),
 // FRNN_PATH_GRID the scalar grid scan; FRNN_PATH_AUTO takes the tensor-core
 // path for D >= 8 unless the context's option says otherwise.
-static bool default_tc(const frnn_ctx* ctx, int D);
+static bool default_tc(const frnn_ctx* ctx, int D, int naxes);
+static int build_naxes(const frnn_ctx* ctx, int64_t N, int D);
 static const frnn_ctx::Tuned* find_tuned(const frnn_ctx* ctx, int64_t N, int D, int K);
-static bool use_tc_path(const frnn_ctx* ctx, int D, unsigned flags, int64_t N = -1, int K = -1) {
+// naxes: gridded axes of the grid being queried (-1: what a build would use now)
+static bool use_tc_path(const frnn_ctx* ctx, int D, unsigned flags, int64_t N = -1, int K = -1,
+                        int naxes = -1) {
     if (flags & FRNN_PATH_TC) return true;
     if (flags & FRNN_PATH_GRID) return false;
     if (D < 8) return false;
@@ -165,7 +172,7 @@ static bool use_tc_path(const frnn_ctx* ctx, int D, unsigned flags, int64_t N = 
         const frnn_ctx::Tuned* t = find_tuned(ctx, N, D, K);
         if (t) return t->path == 1;
     }
-    return default_tc(ctx, D);
+    return default_tc(ctx, D, naxes >= 0 ? naxes : build_naxes(ctx, std::max<int64_t>(N, 0), D));
 }
 
 // Build (or reuse) the tensor-core operands of a point set; accounted in the
@@ -222,10 +229,23 @@ static int build_mult(const frnn_ctx* ctx, int64_t N, int D) {
     const frnn_ctx::Tuned* t = find_tuned(ctx, N, D, -1);
     return t ? t->m : 1;
 }
-// default path when nothing is tuned: the tensor-core pre-filter pays off
-// from about D = 10 on (measured on the tracking-shaped events: slower at
-// D = 8, faster at D = 12)
-static bool default_tc(const frnn_ctx* ctx, int D) { return ctx->auto_tc && D >= 10; }
+// gridded axes when neither the option nor the tuner fixes them: four (the
+// paper's retained four-axis gridding, Sec. 6; measured faster on the
+// tracking-shaped events: 0.365 vs 0.388 ms at 300k x 8, 0.70 vs 1.26 ms at
+// 500k x 12)
+static int default_naxes(int D) { return D < 4 ? D : 4; }
+static int build_naxes(const frnn_ctx* ctx, int64_t N, int D) {
+    if (ctx->grid_naxes > 0) return std::min(ctx->grid_naxes, D);
+    const frnn_ctx::Tuned* t = find_tuned(ctx, N, D, -1);
+    return std::min(t ? t->naxes : default_naxes(D), D);
+}
+// default path when nothing is tuned: the tensor-core pre-filter beats the
+// grid scan over three gridded axes from about D = 10 on (0.90 vs 1.26 ms at
+// 500k x 12), but not the scan over four (0.70 ms): its 128-query tasks are
+// poorly filled by the shorter rows of a four-axis grid
+static bool default_tc(const frnn_ctx* ctx, int D, int naxes) {
+    return ctx->auto_tc && D >= 10 && naxes <= 3;
+}
 
 extern "C" {
 
@@ -363,7 +383,9 @@ frnn_status frnn_build_grid(frnn_ctx* ctx, const float* refs, int64_t N, int D, 
     BuildOpts o;
     o.r = r;
     o.m = build_mult(ctx, N, D);
+    o.naxes = build_naxes(ctx, N, D);
     o.axes_mode = ctx->axes_mode;
+    g->naxes = o.naxes;
     std::string err;
     const float* ev_refs[1] = {refs};
     s = enqueue_build(g->g, ev_refs, o, nullptr, ctx->d_status, ctx->stream, false, err);
@@ -459,7 +481,7 @@ static frnn_status query_impl(frnn_ctx* ctx, const frnn_grid* grid, const float*
         if (s != FRNN_OK) return fail(ctx, s, err);
         q.qset = &ctx->qset;
     }
-    if (use_tc_path(ctx, grid->D, flags, grid->N, K)) {
+    if (use_tc_path(ctx, grid->D, flags, grid->N, K, grid->naxes)) {
         s = prepare_tc(ctx, rg, rg);
         if (s == FRNN_OK && !self) s = prepare_tc(ctx, ctx->qset, rg);
         if (s != FRNN_OK) return s;
@@ -600,6 +622,7 @@ static frnn_status enqueue_batched(frnn_ctx* ctx, const frnn_event* ev, int n_ev
         h.dist2 = ev[e].dist2;
         // per event: autotuned cell multiple and path for its size class
         h.m = build_mult(ctx, ev[e].n, D);
+        h.naxes = build_naxes(ctx, ev[e].n, D);
         h.path = use_tc_path(ctx, D, flags, ev[e].n, K) ? 1 : 0;
         any_grid |= h.path == 0 && ev[e].n > 0;
         any_tc |= h.path == 1 && ev[e].n > 0;
@@ -673,7 +696,7 @@ frnn_status frnn_query_batched(frnn_ctx* ctx, const frnn_event* ev, int n_events
             return fail(ctx, FRNN_ERR_INVALID_ARG, "event pointer is NULL");
         n[e] = x.n;
     }
-    const int opts[4] = {ctx->cell_mult, ctx->axes_mode, ctx->exit_dims, 0};
+    const int opts[4] = {ctx->cell_mult, ctx->axes_mode, ctx->exit_dims, ctx->grid_naxes};
     const bool hit = ctx->use_graph && ctx->graph && same_events(ctx, ev, n_events) &&
                      ctx->g_D == D && ctx->g_K == K && ctx->g_r == r && ctx->g_flags == flags &&
                      std::memcmp(opts, ctx->g_opts, sizeof(opts)) == 0;
@@ -824,8 +847,8 @@ frnn_status frnn_autotune(frnn_ctx* ctx, const float* refs, int64_t N, int D, fl
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
-    const int saved_m = ctx->cell_mult, saved_x = ctx->exit_dims;
-    frnn_tune_result bestr{FRNN_PATH_GRID, 1, 0, INFINITY};
+    const int saved_m = ctx->cell_mult, saved_x = ctx->exit_dims, saved_a = ctx->grid_naxes;
+    frnn_tune_result bestr{FRNN_PATH_GRID, 1, 0, INFINITY, default_naxes(D)};
     frnn_status s = FRNN_OK;
     frnn_grid* g = nullptr;
     auto timed = [&](auto&& fn, float& ms) -> frnn_status {
@@ -843,8 +866,14 @@ frnn_status frnn_autotune(frnn_ctx* ctx, const float* refs, int64_t N, int D, fl
         ms = bestms;
         return frnn_sync(ctx);
     };
-    for (int m = 1; m <= 2 && s == FRNN_OK; ++m) {
+    // grid configurations: 3 gridded axes with m = 1, 2; 4 axes with m = 1
+    struct GridCfg { int naxes, m; };
+    std::vector<GridCfg> gcfg = {{default_naxes(D), 1}, {default_naxes(D), 2}};
+    if (D >= 4) gcfg.push_back({4, 1});
+    for (size_t gi = 0; gi < gcfg.size() && s == FRNN_OK; ++gi) {
+        const int m = gcfg[gi].m;
         ctx->cell_mult = m;
+        ctx->grid_naxes = gcfg[gi].naxes;
         float bms = 0.f;
         s = timed([&] { return frnn_build_grid(ctx, refs, N, D, r, &g); }, bms);
         if (s != FRNN_OK) break;
@@ -867,18 +896,20 @@ frnn_status frnn_autotune(frnn_ctx* ctx, const float* refs, int64_t N, int D, fl
                                   dist2);
             }, qms);
             if (s != FRNN_OK) break;
-            if (bms + qms < bestr.ms) bestr = {(int)c.path, m, c.exit_dims, bms + qms};
+            if (bms + qms < bestr.ms)
+                bestr = {(int)c.path, m, c.exit_dims, bms + qms, gcfg[gi].naxes};
         }
     }
     ctx->cell_mult = saved_m;
     ctx->exit_dims = saved_x;
+    ctx->grid_naxes = saved_a;
     if (g) frnn_grid_destroy(g);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     cudaFree(out);
     if (s != FRNN_OK) return s;
     ctx->tuned[tune_key(N, D, K)] = {bestr.path == FRNN_PATH_TC ? 1 : 0, bestr.cell_mult,
-                                     bestr.exit_dims, bestr.ms};
+                                     bestr.exit_dims, bestr.ms, bestr.grid_axes};
     if (ctx->graph) {   // captured batches may now take other paths
         cudaGraphExecDestroy(ctx->graph);
         ctx->graph = nullptr;
@@ -899,6 +930,11 @@ frnn_status frnn_set_option(frnn_ctx* ctx, frnn_option opt, int64_t value) {
         case FRNN_OPT_GRID_AXES:
             if (value < 0 || value > 1) return fail(ctx, FRNN_ERR_INVALID_ARG, "axes mode 0 or 1");
             ctx->axes_mode = (int)value;
+            return FRNN_OK;
+        case FRNN_OPT_GRID_NAXES:
+            if (value < 0 || value > kMaxAxes)
+                return fail(ctx, FRNN_ERR_INVALID_ARG, "gridded axes must be 0 (tuned) or 1..4");
+            ctx->grid_naxes = (int)value;
             return FRNN_OK;
         case FRNN_OPT_EXIT_DIMS:
             if (value < 0 || value > kMaxD) return fail(ctx, FRNN_ERR_INVALID_ARG, "exit dims");
@@ -950,6 +986,7 @@ frnn_status frnn_get_option(const frnn_ctx* ctx, frnn_option opt, int64_t* value
     switch (opt) {
         case FRNN_OPT_CELL_MULT: *value = ctx->cell_mult; return FRNN_OK;
         case FRNN_OPT_GRID_AXES: *value = ctx->axes_mode; return FRNN_OK;
+        case FRNN_OPT_GRID_NAXES: *value = ctx->grid_naxes; return FRNN_OK;
         case FRNN_OPT_EXIT_DIMS: *value = ctx->exit_dims; return FRNN_OK;
         case FRNN_OPT_USE_GRAPH: *value = ctx->use_graph; return FRNN_OK;
         case FRNN_OPT_AUTOTUNE: *value = ctx->autotune; return FRNN_OK;

@@ -178,7 +178,7 @@ __global__ void __launch_bounds__(kBuildPtsPerBlock) k_bbox(const EventHdr* hdr,
 // and is lowered until the bound holds with 2^-20 to spare, every axis has at
 // most 1024 cells, and the event's cell count fits its capacity.
 __global__ void k_params(EventHdr* hdr, int E, int D, const int32_t* bbox, float r, int m,
-                         int axes_mode, int32_t* counts) {
+                         int axes_mode, int naxes_req, int32_t* counts) {
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= E) return;
     EventHdr& h = hdr[e];
@@ -186,10 +186,15 @@ __global__ void k_params(EventHdr* hdr, int E, int D, const int32_t* bbox, float
     // the next event's slots start on a pair boundary
     counts[h.cell_off + h.cell_cap] = (int32_t)(h.n & 1);
     const int32_t* bb = bbox + (int64_t)e * kBBoxStride;
-    const int naxes = D < 3 ? D : 3;
+    // per-event presets (batched autotuning) win over the call's options
+    const int want = h.naxes > 0 ? h.naxes : naxes_req;
+    const int naxes = min(D, min(max(want, 1), kMaxAxes));
     h.naxes = naxes;
-    h.m = h.m > 0 ? h.m : m;   // a per-event multiple (batched autotuning) wins
-    int axes[3] = {0, 0, 0};
+    h.m = h.m > 0 ? h.m : m;
+    // neighbour rows are enumerated one per lane of a warp: at most 32
+    while (h.m > 1 && neighbour_rows(h) > 32) --h.m;
+    m = h.m;
+    int axes[kMaxAxes] = {0, 0, 0, 0};
     if (axes_mode == 1 && D > naxes) {
         // the naxes widest coordinates (ties by lower index), in index order
         bool used[kMaxD];
@@ -210,8 +215,8 @@ __global__ void k_params(EventHdr* hdr, int E, int D, const int32_t* bbox, float
         for (int a = 0; a < naxes; ++a) axes[a] = D - naxes + a;
     }
     bool valid = bb[32] == 0 && h.n > 0;
-    double ext[3] = {0.0, 0.0, 0.0};
-    for (int a = 0; a < 3; ++a) {
+    double ext[kMaxAxes] = {0.0, 0.0, 0.0, 0.0};
+    for (int a = 0; a < kMaxAxes; ++a) {
         h.axes[a] = a < naxes ? axes[a] : 0;
         h.dims[a] = 1;
         h.lo[a] = 0.f;
@@ -243,7 +248,7 @@ __global__ void k_params(EventHdr* hdr, int E, int D, const int32_t* bbox, float
     const double rd = (double)r;
     const double rho = rd * (1.0 + 0x1p-20);
     float ih = __double2float_rd((double)m / (rd * (1.0 + 0x1p-10)));
-    int dims[3] = {1, 1, 1};
+    int dims[kMaxAxes] = {1, 1, 1, 1};
     for (int it = 0; it < 4096; ++it) {
         bool ok = true;
         int64_t cells = 1;
@@ -256,17 +261,21 @@ __global__ void k_params(EventHdr* hdr, int E, int D, const int32_t* bbox, float
         }
         if (ok && cells <= h.cell_cap) break;
         ih = __double2float_rd((double)ih * 0.9);
-        if (!(ih > 0.f)) { ih = 0.f; dims[0] = dims[1] = dims[2] = 1; break; }
+        if (!(ih > 0.f)) {
+            ih = 0.f;
+            for (int a = 0; a < kMaxAxes; ++a) dims[a] = 1;
+            break;
+        }
     }
     int64_t cells = 1;
-    for (int a = 0; a < 3; ++a) {
+    for (int a = 0; a < kMaxAxes; ++a) {
         h.dims[a] = a < naxes ? dims[a] : 1;
         cells *= h.dims[a];
     }
     if (cells > h.cell_cap) {   // unreachable in practice; one cell is always safe
         ih = 0.f;
         cells = 1;
-        for (int a = 0; a < 3; ++a) h.dims[a] = 1;
+        for (int a = 0; a < kMaxAxes; ++a) h.dims[a] = 1;
     }
     h.inv_h = ih;
     h.ncells = (int32_t)cells;
@@ -284,7 +293,7 @@ __global__ void k_copy_params(EventHdr* dst, const EventHdr* src, int E, int32_t
     d.valid = s.valid;
     d.inv_h = s.inv_h;
     d.ncells = s.ncells;
-    for (int a = 0; a < 3; ++a) {
+    for (int a = 0; a < kMaxAxes; ++a) {
         d.axes[a] = s.axes[a];
         d.dims[a] = s.dims[a];
         d.lo[a] = s.lo[a];
@@ -381,7 +390,7 @@ __global__ void k_rowtasks(const EventHdr* hdr, const int64_t* cell_off, int E, 
     const int e = find_event64(cell_off, E, i);
     const EventHdr& h = hdr[e];
     const int64_t row = i - cell_off[e];
-    const int64_t nrows = h.valid ? (int64_t)h.dims[1] * h.dims[2] : 1;
+    const int64_t nrows = h.valid ? (int64_t)h.dims[1] * h.dims[2] * h.dims[3] : 1;
     int32_t nt = 0;
     if (row < nrows) {
         int32_t base, cnt;
@@ -713,7 +722,7 @@ frnn_status enqueue_build(GridBufs& g, const float* const* refs, const BuildOpts
     } else {
         k_bbox<<<(unsigned)g.nblk, kBuildPtsPerBlock, smem_pts, st>>>(g.hdr, g.blk_start, E, D,
                                                                      g.bbox, d_status);
-        k_params<<<blocks_for(E, 128), 128, 0, st>>>(g.hdr, E, D, g.bbox, o.r, o.m, o.axes_mode,
+        k_params<<<blocks_for(E, 128), 128, 0, st>>>(g.hdr, E, D, g.bbox, o.r, o.m, o.axes_mode, o.naxes,
                                                       g.cstart);
     }
     k_cellid<<<(unsigned)g.nblk, kBuildPtsPerBlock, smem_pts, st>>>(
@@ -745,7 +754,7 @@ frnn_status enqueue_build_resident(GridBufs& g, const BuildOpts& o, int32_t* d_s
     const size_t smem_pts = sizeof(float) * kBuildPtsPerBlock * D;
     k_bbox<<<(unsigned)g.nblk, kBuildPtsPerBlock, smem_pts, st>>>(g.hdr, g.blk_start, E, D,
                                                                  g.bbox, d_status);
-    k_params<<<blocks_for(E, 128), 128, 0, st>>>(g.hdr, E, D, g.bbox, o.r, o.m, o.axes_mode,
+    k_params<<<blocks_for(E, 128), 128, 0, st>>>(g.hdr, E, D, g.bbox, o.r, o.m, o.axes_mode, o.naxes,
                                                   g.cstart);
     k_cellid<<<(unsigned)g.nblk, kBuildPtsPerBlock, smem_pts, st>>>(
         g.hdr, g.blk_start, E, D, g.cstart, g.cid, g.rnk, 0, d_status);

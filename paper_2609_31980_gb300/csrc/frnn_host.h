@@ -90,6 +90,7 @@ struct BuildOpts {
     float r = 0.f;          // grid radius
     int m = 1;              // cell multiple
     int axes_mode = 0;      // 0: last axes, 1: widest axes
+    int naxes = 3;          // gridded axes requested (at most D, at most 4)
 };
 
 // Enqueue a full build (bounding boxes, parameters, binning, counting sort,

@@ -12,7 +12,7 @@ namespace frnn {
 
 constexpr int kMaxD = 16;
 constexpr int kMaxK = 1024;
-constexpr int kMaxAxes = 3;
+constexpr int kMaxAxes = 4;
 constexpr int kMaxDimsPerAxis = 1024;   // the grid roundoff proof assumes <= 2^10 cells per axis
 constexpr int kTaskQueries = 32;        // queries per warp task (one per lane)
 
@@ -51,14 +51,14 @@ struct EventHdr {
     int64_t pt_off;        // first sorted slot of this event (global slot numbering)
     int64_t cell_off;      // first entry of this event in the cell arrays (cap + 1 entries)
     int32_t cell_cap;      // cells allowed for this event
-    int32_t ncells;        // dims[0] * dims[1] * dims[2] (written by the params kernel)
-    int32_t naxes;         // gridded axes (1..3)
+    int32_t ncells;        // product of dims (written by the params kernel)
+    int32_t naxes;         // gridded axes (1..4); preset by the host: requested count (0: default)
     int32_t m;             // cell multiple: neighbours are within +-m cells per gridded axis
     int32_t valid;         // 0 if a coordinate was non-finite
-    int32_t axes[3];       // gridded coordinate indices; axes[0] varies fastest
-    int32_t dims[3];       // cells per gridded axis (1 for unused axes)
-    float lo[3];           // per-axis minimum coordinate
-    float hi[3];           // per-axis maximum coordinate
+    int32_t axes[kMaxAxes];   // gridded coordinate indices; axes[0] varies fastest
+    int32_t dims[kMaxAxes];   // cells per gridded axis (1 for unused axes)
+    float lo[kMaxAxes];       // per-axis minimum coordinate
+    float hi[kMaxAxes];       // per-axis maximum coordinate
     float inv_h;           // 1 / cell edge (float; the value the cell ids use)
     int32_t path;          // batched queries: 0 = grid scan, 1 = tensor-core pre-filter
     float ctr[16];         // per-dimension centre of the bounding box (tensor-core operands)
@@ -74,8 +74,43 @@ struct Task {
     int32_t qslot;   // first query slot (global)
     int32_t nq;      // queries in the task (1..32)
     int32_t ev;      // event index
-    int32_t row;     // row index within the event: y + dims[1] * z
+    int32_t row;     // row index within the event: c1 + dims[1] * (c2 + dims[2] * c3)
 };
+
+// Neighbour rows of a row of cells.  A row fixes every gridded coordinate but
+// the fastest (c0); its neighbours are the rows whose coordinates c1..c3 each
+// differ by at most m.  Neighbour l (0 <= l < neighbour_rows(h)) takes the
+// offsets given by the base-(2m+1) digits of l, minus m.  Returns false if
+// that row lies outside the grid, else its first cell index.
+__host__ __device__ inline int neighbour_rows(const EventHdr& h) {
+    const int side = 2 * h.m + 1;
+    int n = 1;
+    for (int a = 1; a < h.naxes; ++a) n *= side;
+    return n;
+}
+__device__ __forceinline__ bool neighbour_row(const EventHdr& h, int row, int l,
+                                              int64_t& first_cell) {
+    const int side = 2 * h.m + 1;
+    int64_t lin = 0, stride = 1;
+    bool ok = true;
+#pragma unroll
+    for (int a = 1; a < kMaxAxes; ++a) {
+        const int da = h.dims[a];
+        const int c = row % da;
+        row /= da;
+        int d = 0;
+        if (a < h.naxes) {
+            d = (l % side) - h.m;
+            l /= side;
+        }
+        const int cc = c + d;
+        ok = ok && cc >= 0 && cc < da;
+        lin += (int64_t)cc * stride;
+        stride *= da;
+    }
+    first_cell = h.cell_off + lin * h.dims[0];
+    return ok;
+}
 
 // Overflowed query (degree > K): handled by the exact selection kernel.
 struct Overflow {

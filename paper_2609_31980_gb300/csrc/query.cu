@@ -194,27 +194,20 @@ __global__ void __launch_bounds__(kQueryWarps * 32, 4) k_grid_query(QueryArgs a)
             qq[k] = f2_pack(v, v);   // inactive lanes: NaN, never within r
         }
         const int qc = act ? a.qcell[qs] : 0;
-        const int dims0 = h.dims[0], dims1 = h.dims[1], dims2 = h.dims[2], m = h.m;
+        const int dims0 = h.dims[0], m = h.m;
         const int x = qc % dims0;
         const int xa = __shfl_sync(kFull, x, 0);
         const int xb = __shfl_sync(kFull, x, task.nq - 1);
-        const int y = task.row % dims1, z = task.row / dims1;
-        const int side = 2 * m + 1;
-        const int nrows = h.naxes >= 3 ? side * side : (h.naxes == 2 ? side : 1);
 
+        // lane l < neighbour_rows (at most 32) owns neighbour row l
         TaskGeom g;
         g.rs = 0;
         g.re = 0;
-        if (lane < nrows) {
-            const int dy = h.naxes >= 2 ? (lane % side) - m : 0;
-            const int dz = h.naxes >= 3 ? (lane / side) - m : 0;
-            const int yy = y + dy, zz = z + dz;
-            if (yy >= 0 && yy < dims1 && zz >= 0 && zz < dims2) {
-                const int64_t rowbase = h.cell_off + (int64_t)(yy + dims1 * zz) * dims0;
-                const int x0 = max(xa - m, 0), x1 = min(xb + m, dims0 - 1);
-                g.rs = a.cstart[rowbase + x0];
-                g.re = a.cstart[rowbase + x1 + 1];
-            }
+        int64_t rowbase;
+        if (lane < neighbour_rows(h) && neighbour_row(h, task.row, lane, rowbase)) {
+            const int x0 = max(xa - m, 0), x1 = min(xb + m, dims0 - 1);
+            g.rs = a.cstart[rowbase + x0];
+            g.re = a.cstart[rowbase + x1 + 1];
         }
         g.prs = g.rs >> 1;
         g.pre = g.re > g.rs ? (g.re + 1) >> 1 : g.prs;
@@ -442,8 +435,8 @@ __global__ void __launch_bounds__(kOvfWarps * 32) k_overflow(QueryArgs a, int ca
 #pragma unroll
         for (int k = 0; k < kMaxD; ++k) qv[k] = k < D ? a.qpts[pair_index(qs, k, DP)] : 0.f;
         const int qc = a.qcell[qs];
-        const int dims0 = h.dims[0], dims1 = h.dims[1], dims2 = h.dims[2], m = h.m;
-        const int x = qc % dims0, y = (qc / dims0) % dims1, z = qc / (dims0 * dims1);
+        const int dims0 = h.dims[0], m = h.m;
+        const int x = qc % dims0, qrow = qc / dims0;
         const int self_slot = a.self ? qs : -1;
         const bool count_only = a.ovf_mode == 1;
         int fill = 0;
@@ -451,11 +444,11 @@ __global__ void __launch_bounds__(kOvfWarps * 32) k_overflow(QueryArgs a, int ca
         uint64_t thr = ~0ull;
         for (int i = lane; i < cap && !count_only; i += 32) buf[i] = ~0ull;
         __syncwarp();
-        const int ylo = h.naxes >= 2 ? max(y - m, 0) : 0, yhi = h.naxes >= 2 ? min(y + m, dims1 - 1) : 0;
-        const int zlo = h.naxes >= 3 ? max(z - m, 0) : 0, zhi = h.naxes >= 3 ? min(z + m, dims2 - 1) : 0;
-        for (int zz = zlo; zz <= zhi; ++zz) {
-            for (int yy = ylo; yy <= yhi; ++yy) {
-                const int64_t rowbase = h.cell_off + (int64_t)(yy + dims1 * zz) * dims0;
+        const int nrows = neighbour_rows(h);
+        for (int nr = 0; nr < nrows; ++nr) {
+            int64_t rowbase;
+            if (!neighbour_row(h, qrow, nr, rowbase)) continue;
+            {
                 const int rs = a.cstart[rowbase + max(x - m, 0)];
                 const int re = a.cstart[rowbase + min(x + m, dims0 - 1) + 1];
                 for (int c0 = rs; c0 < re; c0 += 32) {

@@ -448,22 +448,15 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_tc_query(TcArgs a) {
         }
         if (producer) {
             // neighbour rows and chunk table
-            const int dims0 = h.dims[0], dims1 = h.dims[1], dims2 = h.dims[2], m = h.m;
+            const int dims0 = h.dims[0], m = h.m;
             const int xa = a.qcell[tk.qslot] % dims0;
             const int xb = a.qcell[tk.qslot + tk.nq - 1] % dims0;
-            const int y = tk.row % dims1, z = tk.row / dims1;
-            const int side = 2 * m + 1;
-            const int nrows = h.naxes >= 3 ? side * side : (h.naxes == 2 ? side : 1);
+            const int nrows = neighbour_rows(h);   // <= 32 (the params kernel ensures it)
             int rs = 0, re = 0;
-            if (lane < nrows) {
-                const int dy = h.naxes >= 2 ? (lane % side) - m : 0;
-                const int dz = h.naxes >= 3 ? (lane / side) - m : 0;
-                const int yy = y + dy, zz = z + dz;
-                if (yy >= 0 && yy < dims1 && zz >= 0 && zz < dims2) {
-                    const int64_t rowbase = h.cell_off + (int64_t)(yy + dims1 * zz) * dims0;
-                    rs = a.cstart[rowbase + max(xa - m, 0)];
-                    re = a.cstart[rowbase + min(xb + m, dims0 - 1) + 1];
-                }
+            int64_t rowbase;
+            if (lane < nrows && neighbour_row(h, tk.row, lane, rowbase)) {
+                rs = a.cstart[rowbase + max(xa - m, 0)];
+                re = a.cstart[rowbase + min(xb + m, dims0 - 1) + 1];
             }
             const int b8 = rs & ~7;
             const int e8 = (re + 7) & ~7;

@@ -43,6 +43,7 @@ FRNN_OPT_AUTO_TC = 6
 FRNN_OPT_TC_SURVIVORS = 7
 FRNN_OPT_TC_ACCEPTED = 8
 FRNN_OPT_KERNEL_TIMING = 9
+FRNN_OPT_GRID_NAXES = 10
 
 EXPORTED = ["frnn_version", "frnn_create", "frnn_destroy", "frnn_build_grid",
             "frnn_grid_destroy", "frnn_query", "frnn_query_batched", "frnn_self_query_host",
@@ -53,7 +54,7 @@ EXPORTED = ["frnn_version", "frnn_create", "frnn_destroy", "frnn_build_grid",
 
 class frnn_tune_result(ctypes.Structure):
     _fields_ = [("path", ctypes.c_int), ("cell_mult", ctypes.c_int), ("exit_dims", ctypes.c_int),
-                ("ms", ctypes.c_float)]
+                ("ms", ctypes.c_float), ("grid_axes", ctypes.c_int)]
 
 
 class frnn_request(ctypes.Structure):
@@ -309,7 +310,8 @@ class Context:
                            float(r), int(K), PATHS[path], ctypes.byref(res))
         _check(self.handle, rc)
         return {"path": {FRNN_PATH_GRID: "grid", FRNN_PATH_TC: "tc"}.get(res.path, res.path),
-                "cell_mult": res.cell_mult, "exit_dims": res.exit_dims, "ms": res.ms}
+                "cell_mult": res.cell_mult, "exit_dims": res.exit_dims, "ms": res.ms,
+                "grid_axes": res.grid_axes}
 
     def serve(self, events, arrivals, r: float, K: int, budget_bytes: int = 0, slots: int = 4,
               max_batch: int = 16, outs=None):

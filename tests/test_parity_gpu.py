@@ -449,3 +449,81 @@ def test_serving_rejects_oversized_request(ctx):
     with pytest.raises(frnn.FrnnError) as ei:
         ctx.serve(events, [0.0, 0.0, 0.0], 0.1, 64, budget_bytes=1000, slots=2, max_batch=2)
     assert ei.value.status == -4
+
+
+# ---------------------------------------------------------------- 4 gridded axes
+
+@pytest.fixture
+def ctx4(ctx):
+    from paper_2609_31980_gb300 import frnn
+    ctx.set_option(frnn.FRNN_OPT_GRID_NAXES, 4)
+    yield ctx
+    ctx.set_option(frnn.FRNN_OPT_GRID_NAXES, 0)
+
+
+@pytest.mark.parametrize("D,path", [(4, "grid"), (5, "grid"), (8, "grid"), (8, "tc"), (12, "tc"),
+                                    (12, "grid")])
+def test_four_axes_match_oracle(ctx4, D, path):
+    pts = synth.clustered(400, 25, 3000, D, 0.025, seed=800 + D)
+    r = 0.1 * np.sqrt(D / 8.0)
+    got = _gpu_self(ctx4, pts, r, 48, path=path)
+    _assert_rows_equal(got, oracle.self_query(pts, r, 48))
+
+
+def test_four_axes_with_m2_request_and_dense_rows(ctx4):
+    from paper_2609_31980_gb300 import frnn
+    ctx4.set_option(frnn.FRNN_OPT_CELL_MULT, 2)   # falls back to m = 1 (27 neighbour rows)
+    try:
+        pts = np.repeat(synth.clustered(25, 40, 300, 6, 0.01, seed=810), 3, axis=0)
+        for K in (8, 100):
+            _assert_rows_equal(_gpu_self(ctx4, pts, 0.05, K), oracle.self_query(pts, 0.05, K))
+    finally:
+        ctx4.set_option(frnn.FRNN_OPT_CELL_MULT, 0)
+
+
+def test_four_axes_lattice_boundaries(ctx4):
+    # points exactly on and one ulp around cell boundaries in every coordinate
+    g = np.arange(-3, 4, dtype=np.float32) * np.float32(0.125)
+    base = np.stack(np.meshgrid(g, g, g, g, indexing="ij"), -1).reshape(-1, 4)
+    jit = np.stack([np.nextafter(base, np.float32(np.inf)), np.nextafter(base, np.float32(-np.inf))])
+    pts = np.concatenate([base, jit.reshape(-1, 4)]).astype(np.float32)
+    got = _gpu_self(ctx4, pts, 0.125, 96)
+    _assert_rows_equal(got, oracle.self_query(pts, 0.125, 96))
+
+
+@pytest.mark.parametrize("path", ["grid", "tc"])
+def test_four_axes_cross_set(ctx4, path):
+    import torch
+    refs = synth.clustered(100, 20, 1500, 8, 0.03, seed=811)
+    qs = synth.clustered(80, 20, 1000, 8, 0.03, seed=812)
+    g = ctx4.build_grid(torch.from_numpy(refs).cuda(), 0.1)
+    c, i, d = ctx4.query(g, torch.from_numpy(qs).cuda(), 0.1, 32, False, path)
+    ctx4.sync()
+    _assert_rows_equal((c.cpu().numpy(), i.cpu().numpy(), d.cpu().numpy()),
+                       oracle.frnn(qs, refs, 0.1, 32))
+    g.close()
+
+
+def test_four_axes_batched(ctx4):
+    import torch
+    evs = [synth.clustered(50 + 10 * e, 20, 500 + 100 * e, 8, 0.02, seed=(813, e)) for e in range(5)]
+    outs = ctx4.query_batched([torch.from_numpy(p).cuda() for p in evs], 0.1, 32, path="grid")
+    ctx4.sync()
+    for p, (c, i, d) in zip(evs, outs):
+        _assert_rows_equal((c.cpu().numpy(), i.cpu().numpy(), d.cpu().numpy()),
+                           oracle.self_query(p, 0.1, 32))
+
+
+@pytest.mark.parametrize("path", ["grid", "tc"])
+def test_four_axes_event_500k_x12_equal_to_three_axes(ctx, path):
+    from paper_2609_31980_gb300 import frnn
+    w = synth.config3()
+    ref = _gpu_self(ctx, w.points, w.r, w.K, path=path)
+    ctx.set_option(frnn.FRNN_OPT_GRID_NAXES, 4)
+    try:
+        got = _gpu_self(ctx, w.points, w.r, w.K, path=path)
+    finally:
+        ctx.set_option(frnn.FRNN_OPT_GRID_NAXES, 0)
+    _assert_rows_equal(got, ref)
+    rows = _sample_rows(len(w.points), 300, 814)
+    _assert_rows_equal(got, oracle.self_query(w.points, w.r, w.K, rows=rows), rows)
