@@ -122,6 +122,7 @@ def profiled_traffic(path: str, wl: str):
     import hashlib
     key = (path, wl)
     known = {("grid", "event300k"): ("grid_query_event300k_x8.md", ["query.cu", "frnn_internal.cuh"]),
+             ("grid", "event500k"): ("grid_query_event500k_x12.md", ["query.cu", "frnn_internal.cuh"]),
              ("tc", "event500k"): ("tc_query_event500k_x12.md", ["tc.cu", "frnn_internal.cuh"])}
     if key not in known:
         return None
