@@ -12,30 +12,36 @@
 //   * a persistent grid; each warp takes warp tasks (32 cell-sorted queries in
 //     one row of cells) from an atomic counter;
 //   * the candidates of a task are the union of its lanes' neighbourhoods: per
-//     neighbour row one contiguous slot range; ranges are cut into tiles that
-//     lane 0 copies into the warp's shared-memory ring with cp.async.bulk,
-//     completion tracked by one mbarrier per buffer (prefetch depth kNBuf-1);
+//     neighbour row one contiguous slot range; the ranges, widened to pair
+//     boundaries, form one stream of candidate pairs cut into tiles of TILEP
+//     pairs; the row lanes copy their parts of a tile into the warp's
+//     shared-memory ring with cp.async.bulk, completion tracked by one
+//     mbarrier per buffer (prefetch depth kNBuf-1);
 //   * every lane screens every candidate of the tile (broadcast shared loads):
 //     warp-uniform control flow.  Points are stored pair-interleaved, so each
-//     16-byte shared load gives two dimensions of two candidates and the
-//     packed f32x2 instructions evaluate two candidates per instruction, each
-//     lane rounded exactly as the scalar contract;
-//   * exact early rejection: after the first `EXIT` dimensions the warp votes;
+//     16-byte shared load gives two dimensions of two candidates and one
+//     packed f32x2 instruction serves two candidates.  The packed arithmetic
+//     is only a conservative screen (proof below);
+//   * early rejection: after the first `EXIT` dimensions the warp votes;
 //     partial sums never decrease (round-to-nearest of non-negative terms), so
-//     if every lane's partial sum is already > r2 the candidate is rejected
-//     for all of them without changing any verdict (the paper's "roundoff-safe
-//     early rejection", Sec. 6).  Gridded axes are the last ones by default,
-//     so the first dimensions are the ungridded, most selective ones;
-//   * survivors are appended (d2, original index) to the lane's list in
-//     shared memory (the original index is looked up only for survivors: the
-//     paper's deferred lookup, Table 3);
-//   * at the end of the task every lane sorts its own list by (d2, index)
-//     with a register bitonic network, keeps the first K (count =
-//     min(degree, K)),
-//     and the warp writes the rows coalesced with their padding.  Lists longer
-//     than 32 (never in the tracking-like workloads) go to an exact selection
-//     kernel; so does any degree > K beyond the list, keeping results exact
-//     for dense inputs (the paper's Sec. 5 caveat on heap-free top-K).
+//     if every lane's partial sum already exceeds the screen bound the
+//     candidate is rejected for all of them without changing any verdict (the
+//     paper's "roundoff-safe early rejection", Sec. 6).  Gridded axes are the
+//     last ones by default, so the first dimensions are ungridded, the most
+//     selective ones;
+//   * a candidate that passes the whole screen is appended to the lane's list
+//     in shared memory as its stream position; at the end of the task the
+//     warp resolves every lane's entries together (row, slot, range filter)
+//     and recomputes each with the scalar contract, which alone decides
+//     membership and gives the distance (the paper's "conservative screening
+//     and canonical-order recomputation", Sec. 4.2); the original index is
+//     looked up only for the kept entries (the deferred lookup, Table 3);
+//   * every lane sorts its own list by (d2, index) with a register bitonic
+//     network and keeps the first K (count = min(degree, K)); the warp writes
+//     the rows coalesced with their padding.  Lists longer than 32 (never in
+//     the tracking-like workloads) go to an exact selection kernel, keeping
+//     results exact for dense inputs (the paper's Sec. 5 caveat on heap-free
+//     top-K).
 #include <algorithm>
 #include <cmath>
 
@@ -53,18 +59,22 @@ static_assert(kListCap <= kCsrStageW, "a staged compact row holds a whole list")
 template <int D>
 struct QCfg {
     static constexpr int DP = padded_dim(D);
-    // candidate pairs per tile: about 2 KB per buffer
-    static constexpr int TILEP = DP == 4 ? 64 : (DP == 8 ? 32 : (DP == 12 ? 24 : 16));
+    // candidate pairs per tile (1 KB per buffer up to D = 8, else about
+    // 2 KB) and CTAs per SM: up to D = 8 the smaller ring lets five CTAs
+    // (20 warps) share an SM, which the latency-bound scan prefers (measured
+    // 0.339 vs 0.349 ms at 300k x 8); above, the longer tiles win (0.633 vs
+    // 0.686 ms at 500k x 12)
+    static constexpr int TILEP = DP == 4 ? 32 : (DP == 8 ? 16 : (DP == 12 ? 24 : 16));
+    static constexpr int MINB = DP <= 8 ? 5 : 4;
     static constexpr int EXIT = D <= 4 ? D : 2;   // default vote point
 };
 
 __host__ __device__ constexpr size_t ring_floats(int DP, int TILEP) {
     return (size_t)kNBuf * TILEP * 2 * DP;
 }
+__host__ __device__ constexpr size_t warp_smem_bytes(int DP, int TILEP);
 __host__ __device__ constexpr size_t query_smem_bytes(int DP, int TILEP) {
-    return (size_t)kQueryWarps *
-           (ring_floats(DP, TILEP) * sizeof(float) + 2 * kListCap * kListStride * 4 +
-            kNBuf * sizeof(uint64_t));
+    return (size_t)kQueryWarps * warp_smem_bytes(DP, TILEP);
 }
 
 // ------------------------------------------------------------- packed f32x2
@@ -110,46 +120,79 @@ __device__ __forceinline__ uint64_t make_key(float d2, int32_t j) {
 
 // ------------------------------------------------------------- grid query
 
-struct TaskGeom {
-    int total_tiles;
-    int rs, re;     // this lane's neighbour-row slot range (original, unrounded)
-    int prs, pre;   // the same range in pairs, widened to pair boundaries
-    int tp;         // inclusive prefix of tiles over lanes
+// Per-warp shared memory: the tile ring, the per-lane lists, the task's
+// neighbour-row table, per-lane accept counters and the ring's mbarriers.
+struct WarpSmem {
+    float* ring;
+    float* Ld;
+    int32_t* Li;
+    int32_t* Rpp;    // [32] first stream pair of neighbour row l
+    int32_t* Rprs;   // [32] its first pair in slot space
+    int32_t* Rrs;    // [32] its slot range [rs, re)
+    int32_t* Rre;
+    int32_t* acc;    // [32] exactly accepted entries per lane
+    uint64_t* bars;  // [kNBuf]
 };
 
-template <int TILEP>
-__device__ __forceinline__ void tile_info(const TaskGeom& g, int t, int& basep, int& lenp,
-                                          int& lo, int& hi) {
-    const unsigned below = __ballot_sync(kFull, g.tp <= t);
-    const int L = __popc(below);
-    const int prs = __shfl_sync(kFull, g.prs, L);
-    const int pre = __shfl_sync(kFull, g.pre, L);
-    const int tp = __shfl_sync(kFull, g.tp, L);
-    lo = __shfl_sync(kFull, g.rs, L);
-    hi = __shfl_sync(kFull, g.re, L);
-    const int ntl = (pre - prs + TILEP - 1) / TILEP;
-    basep = prs + (t - (tp - ntl)) * TILEP;
-    lenp = min(TILEP, pre - basep);
+// rounded up to 128 bytes: every warp's ring (a bulk-copy destination) must
+// start on a 16-byte boundary
+__host__ __device__ constexpr size_t warp_smem_bytes(int DP, int TILEP) {
+    return (ring_floats(DP, TILEP) * sizeof(float) + 2 * kListCap * kListStride * 4 +
+            5 * 32 * 4 + kNBuf * sizeof(uint64_t) + 127) / 128 * 128;
+}
+
+__device__ __forceinline__ WarpSmem carve_warp(unsigned char* base, int DP, int TILEP) {
+    WarpSmem w;
+    w.ring = reinterpret_cast<float*>(base);
+    w.Ld = w.ring + ring_floats(DP, TILEP);
+    w.Li = reinterpret_cast<int32_t*>(w.Ld + kListCap * kListStride);
+    w.Rpp = w.Li + kListCap * kListStride;
+    w.Rprs = w.Rpp + 32;
+    w.Rrs = w.Rprs + 32;
+    w.Rre = w.Rrs + 32;
+    w.acc = w.Rre + 32;
+    w.bars = reinterpret_cast<uint64_t*>(w.acc + 32);
+    return w;
+}
+
+// One warp task: 32 queries in one row of cells; their candidates are the
+// slot ranges of the neighbour rows (lane l < neighbour_rows owns row l),
+// each widened to pair boundaries and concatenated into one stream of
+// candidate pairs.  Tile t of the stream (TILEP pairs) may span several rows:
+// every row lane that overlaps it copies its own part with cp.async.bulk,
+// all completing on the buffer's one mbarrier.  A tentative entry is stored
+// as its stream code 2 * pair + half; the row it came from, its slot, the
+// row-range filter and the exact recheck are resolved at the end of the task.
+template <int TILEP, int PAIRF>
+__device__ __forceinline__ void issue_tile(const WarpSmem& w, int t, int b, int pp, int np,
+                                           int prs, int P, const float* rpts, int lane) {
+    const int T0 = t * TILEP;
+    const int T1 = min(T0 + TILEP, P);
+    if (lane == 0)
+        mbar_arrive_expect_tx(&w.bars[b], (uint32_t)(T1 - T0) * PAIRF * sizeof(float));
+    __syncwarp();
+    const int lo_s = max(pp, T0), hi_s = min(pp + np, T1);
+    if (hi_s > lo_s) {
+        fence_proxy_async_smem();   // the buffer's previous contents were read generically
+        bulk_g2s(w.ring + (size_t)b * TILEP * PAIRF + (size_t)(lo_s - T0) * PAIRF,
+                 rpts + (int64_t)(prs + lo_s - pp) * PAIRF,
+                 (uint32_t)(hi_s - lo_s) * PAIRF * sizeof(float), &w.bars[b]);
+    }
 }
 
 template <int D, int EXIT>
-__global__ void __launch_bounds__(kQueryWarps * 32, 4) k_grid_query(QueryArgs a) {
+__global__ void __launch_bounds__(kQueryWarps * 32, QCfg<D>::MINB) k_grid_query(QueryArgs a) {
     using C = QCfg<D>;
     constexpr int DP = C::DP;
     constexpr int TILEP = C::TILEP;
     constexpr int PAIRF = 2 * DP;   // floats per candidate pair
     extern __shared__ __align__(128) unsigned char smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    float* ring = reinterpret_cast<float*>(smem) + (size_t)warp * ring_floats(DP, TILEP);
-    float* Ld = reinterpret_cast<float*>(smem) + (size_t)kQueryWarps * ring_floats(DP, TILEP) +
-                (size_t)warp * 2 * kListCap * kListStride;
-    int32_t* Li = reinterpret_cast<int32_t*>(Ld + kListCap * kListStride);
-    uint64_t* bars = reinterpret_cast<uint64_t*>(
-                         smem + (size_t)kQueryWarps * (ring_floats(DP, TILEP) * 4 +
-                                                       2 * kListCap * kListStride * 4)) +
-                     warp * kNBuf;
+    const WarpSmem w = carve_warp(smem + (size_t)warp * warp_smem_bytes(DP, TILEP), DP, TILEP);
+    float* Ld = w.Ld;
+    int32_t* Li = w.Li;
     if (lane == 0)
-        for (int b = 0; b < kNBuf; ++b) mbar_init(&bars[b], 1);
+        for (int b = 0; b < kNBuf; ++b) mbar_init(&w.bars[b], 1);
     fence_mbar_init();
     __syncwarp();
     uint32_t phase = 0;   // bit b: parity to wait for on buffer b
@@ -199,56 +242,70 @@ __global__ void __launch_bounds__(kQueryWarps * 32, 4) k_grid_query(QueryArgs a)
         const int xa = __shfl_sync(kFull, x, 0);
         const int xb = __shfl_sync(kFull, x, task.nq - 1);
 
-        // lane l < neighbour_rows (at most 32) owns neighbour row l
-        TaskGeom g;
-        g.rs = 0;
-        g.re = 0;
+        // neighbour row of this lane (lane < neighbour_rows <= 32) and its
+        // place in the candidate stream
+        const int nrows = neighbour_rows(h);
+        int rs = 0, re = 0;
         int64_t rowbase;
-        if (lane < neighbour_rows(h) && neighbour_row(h, task.row, lane, rowbase)) {
+        if (lane < nrows && neighbour_row(h, task.row, lane, rowbase)) {
             const int x0 = max(xa - m, 0), x1 = min(xb + m, dims0 - 1);
-            g.rs = a.cstart[rowbase + x0];
-            g.re = a.cstart[rowbase + x1 + 1];
+            rs = a.cstart[rowbase + x0];
+            re = a.cstart[rowbase + x1 + 1];
         }
-        g.prs = g.rs >> 1;
-        g.pre = g.re > g.rs ? (g.re + 1) >> 1 : g.prs;
-        const int ntl = (g.pre - g.prs + TILEP - 1) / TILEP;
-        int tp = ntl;
+        const int prs = rs >> 1;
+        const int np = re > rs ? ((re + 1) >> 1) - prs : 0;
+        int incl = np;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            const int v = __shfl_up_sync(kFull, tp, o);
-            if (lane >= o) tp += v;
+            const int v = __shfl_up_sync(kFull, incl, o);
+            if (lane >= o) incl += v;
         }
-        g.tp = tp;
-        g.total_tiles = __shfl_sync(kFull, tp, 31);
+        const int pp = incl - np;
+        const int P = __shfl_sync(kFull, incl, 31);
+        w.Rpp[lane] = pp;   // nondecreasing over lanes (empty rows repeat the next start)
+        w.Rprs[lane] = prs;
+        w.Rrs[lane] = rs;
+        w.Rre[lane] = re;
+        w.acc[lane] = 0;
+        // the query's own slot lies in the centre row (every offset zero); in
+        // a self-query it is excluded by its stream code
+        const int lc = (nrows - 1) >> 1;
+        const int pp_c = __shfl_sync(kFull, pp, lc), prs_c = __shfl_sync(kFull, prs, lc);
+        const int self_code = (a.self && act) ? 2 * (pp_c + (qs >> 1) - prs_c) + (qs & 1) : -1;
+        const int ntiles = (P + TILEP - 1) / TILEP;
 
-        int cnt = 0;          // confirmed + this tile's tentative entries
-        int kept = 0;         // confirmed (exactly rechecked) entries
+        int cnt = 0;          // tentative entries
         bool lost = false;    // an entry did not fit the list: the row goes to the selection kernel
-        const int self_slot = a.self ? qs : -1;
 
         // prologue: fill the ring
-        const int pre = min(kNBuf, g.total_tiles);
-        for (int tt = 0; tt < pre; ++tt) {
-            int basep, lenp, lo, hi;
-            tile_info<TILEP>(g, tt, basep, lenp, lo, hi);
-            if (lane == 0) {
-                const uint32_t bytes = (uint32_t)lenp * PAIRF * sizeof(float);
-                mbar_arrive_expect_tx(&bars[tt], bytes);
-                bulk_g2s(ring + (size_t)tt * TILEP * PAIRF, a.rpts + (int64_t)basep * PAIRF,
-                         bytes, &bars[tt]);
-            }
-        }
+        const int pre = min(kNBuf, ntiles);
+        for (int tt = 0; tt < pre; ++tt)
+            issue_tile<TILEP, PAIRF>(w, tt, tt, pp, np, prs, P, a.rpts, lane);
         int timed_out_at = -1;
-        for (int tt = 0; tt < g.total_tiles; ++tt) {
+        for (int tt = 0; tt < ntiles; ++tt) {
             const int b = tt % kNBuf;
-            int basep, lenp, lo, hi;
-            tile_info<TILEP>(g, tt, basep, lenp, lo, hi);
-            if (!mbar_wait_bounded(&bars[b], (phase >> b) & 1u)) {
+            if (!mbar_wait_bounded(&w.bars[b], (phase >> b) & 1u)) {
                 timed_out_at = tt;
                 break;
             }
             phase ^= 1u << b;
-            const float* tile = ring + (size_t)b * TILEP * PAIRF;
+            float* tile = w.ring + (size_t)b * TILEP * PAIRF;
+            const int T0 = tt * TILEP;
+            const int lenp = min(TILEP, P - T0);
+            {
+                // a row whose slot range starts (ends) inside a pair: put NaN
+                // into the first coordinate of the half outside the range, so
+                // it fails every screen (the neighbouring slot belongs to a
+                // cell outside the search range, or to another row's part)
+                const int lo_s = max(pp, T0), hi_s = min(pp + np, T0 + lenp);
+                if (hi_s > lo_s && (((lo_s == pp) && (rs & 1)) || ((hi_s == pp + np) && (re & 1)))) {
+                    if (lo_s == pp && (rs & 1)) tile[(lo_s - T0) * PAIRF] = __int_as_float(0x7fc00000);
+                    if (hi_s == pp + np && (re & 1))
+                        tile[(hi_s - 1 - T0) * PAIRF + 1] = __int_as_float(0x7fc00000);
+                    fence_proxy_async_smem();   // before the buffer is refilled by bulk copies
+                }
+                __syncwarp();
+            }
             // four candidate pairs per step: their first-stage screens are
             // independent, which hides the packed pipeline's latency
             for (int p0 = 0; p0 < lenp; p0 += 4) {
@@ -272,7 +329,7 @@ __global__ void __launch_bounds__(kQueryWarps * 32, 4) k_grid_query(QueryArgs a)
                     uint64_t s2 = sg[j];
                     float s0, s1;
                     f2_unpack(s2, s0, s1);
-                    if (!__any_sync(kFull, (s0 <= rs2) | (s1 <= rs2))) continue;
+                    if (!__any_sync(kFull, fminf(s0, s1) <= rs2)) continue;
                     if (EXIT < D) {
 #pragma unroll
                         for (int k = EXIT; k < D; ++k) {
@@ -281,16 +338,14 @@ __global__ void __launch_bounds__(kQueryWarps * 32, 4) k_grid_query(QueryArgs a)
                         }
                         f2_unpack(s2, s0, s1);
                     }
-                    if ((s0 <= rs2) | (s1 <= rs2)) {
-                        // tentative: remember the slot, recheck at the tile's end
-                        const int cs0 = 2 * (basep + p);
+                    if (fminf(s0, s1) <= rs2) {
+                        // tentative: remember the stream code, resolved at the task's end
+                        const int code0 = 2 * (T0 + p);
 #pragma unroll
                         for (int h2 = 0; h2 < 2; ++h2) {
-                            const int cs = cs0 + h2;
-                            // slots outside the row's own range were read only
-                            // because tiles start on pair boundaries: skip them
-                            if ((h2 ? s1 : s0) <= rs2 && cs >= lo && cs < hi && cs != self_slot) {
-                                if (cnt < kListCap) Li[cnt * kListStride + lane] = cs;
+                            const int code = code0 + h2;
+                            if ((h2 ? s1 : s0) <= rs2 && code != self_code) {
+                                if (cnt < kListCap) Li[cnt * kListStride + lane] = code;
                                 else lost = true;
                                 ++cnt;
                             }
@@ -298,63 +353,86 @@ __global__ void __launch_bounds__(kQueryWarps * 32, 4) k_grid_query(QueryArgs a)
                     }
                 }
             }
-            // exact recheck of this tile's tentative entries, every lane its
-            // own in parallel: the scalar contract in index order, no
-            // contraction; keep (d2, original index) of the accepted ones
-            if (!lost) {
-                const int tile_slot0 = 2 * basep;
-                int wpos = kept;
-                for (int e = kept; e < cnt; ++e) {
-                    const int cs = Li[e * kListStride + lane];
-                    const float* cpf = tile + (cs - tile_slot0 - (cs & 1)) * DP + (cs & 1);
-                    float sv = 0.f;
-#pragma unroll
-                    for (int k = 0; k < D; ++k) {
-                        float qk, qk2;
-                        f2_unpack(qq[k], qk, qk2);
-                        const float d = __fsub_rn(qk, cpf[2 * k]);
-                        sv = __fadd_rn(sv, __fmul_rn(d, d));
-                    }
-                    if (sv <= r2) {   // slot now, original index at the sort
-                        Ld[wpos * kListStride + lane] = sv;
-                        Li[wpos * kListStride + lane] = cs;
-                        ++wpos;
-                    }
-                }
-                cnt = kept = wpos;
-            }
             __syncwarp();
             const int nt = tt + kNBuf;
-            if (nt < g.total_tiles) {
-                int nbasep, nlenp, nlo, nhi;
-                tile_info<TILEP>(g, nt, nbasep, nlenp, nlo, nhi);
-                if (lane == 0) {
-                    fence_proxy_async_smem();
-                    const uint32_t bytes = (uint32_t)nlenp * PAIRF * sizeof(float);
-                    mbar_arrive_expect_tx(&bars[b], bytes);
-                    bulk_g2s(ring + (size_t)b * TILEP * PAIRF, a.rpts + (int64_t)nbasep * PAIRF,
-                             bytes, &bars[b]);
-                }
-            }
+            if (nt < ntiles) issue_tile<TILEP, PAIRF>(w, nt, b, pp, np, prs, P, a.rpts, lane);
         }
         if (timed_out_at >= 0) {
             // record, wait (bounded) for the copies still in flight, stop this warp
             if (lane == 0) atomicOr(a.status, kStatusTimeout);
-            const int issued = min(g.total_tiles, timed_out_at + kNBuf);
+            const int issued = min(ntiles, timed_out_at + kNBuf);
             for (int t2 = timed_out_at; t2 < issued; ++t2) {
                 const int b2 = t2 % kNBuf;
-                mbar_wait_bounded(&bars[b2], (phase >> b2) & 1u);
+                mbar_wait_bounded(&w.bars[b2], (phase >> b2) & 1u);
                 phase ^= 1u << b2;
             }
             return;
         }
-        // each lane sorts its own list by (d2, original index), all lanes in
-        // parallel (register bitonic network, see sort_list)
+
+        // exact recheck of every lane's tentative entries, spread over the
+        // whole warp: entry i of the task's concatenated lists goes to lane
+        // i % 32.  Each resolves its row (the last row whose stream part
+        // starts at or before the pair), its slot and the row-range filter
+        // (slots read only because parts start on pair boundaries are
+        // dropped), then applies the scalar contract in index order without
+        // contraction.  Accepted: (d2, slot); rejected: d2 = +inf, sorted last.
         const bool spill = lost;
+        const int own = spill ? 0 : cnt;
+        int cin = own;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(kFull, cin, o);
+            if (lane >= o) cin += v;
+        }
+        const int cex = cin - own;
+        const int T = __shfl_sync(kFull, cin, 31);
+        __syncwarp();
+        for (int base = 0; base < T; base += 32) {
+            const int i = base + lane;
+            // owner lane: the last lane whose entries start at or before i
+            int O = 0;
+#pragma unroll
+            for (int st = 16; st > 0; st >>= 1) {
+                const int v = __shfl_sync(kFull, cex, O + st);
+                if (v <= i) O += st;
+            }
+            const int e = i - __shfl_sync(kFull, cex, O);
+            if (i < T) {
+                const int code = Li[e * kListStride + O];
+                const int sp = code >> 1;
+                int L = 0;
+#pragma unroll
+                for (int st = 16; st > 0; st >>= 1)
+                    if (w.Rpp[L + st] <= sp) L += st;
+                const int slot = 2 * (w.Rprs[L] + sp - w.Rpp[L]) + (code & 1);
+                float sv = INFINITY;
+                if (slot >= w.Rrs[L] && slot < w.Rre[L]) {
+                    const int qo_slot = task.qslot + O;
+                    float acc = 0.f;
+#pragma unroll
+                    for (int k = 0; k < D; ++k) {
+                        const float d = __fsub_rn(a.qpts[pair_index(qo_slot, k, DP)],
+                                                  a.rpts[pair_index(slot, k, DP)]);
+                        acc = __fadd_rn(acc, __fmul_rn(d, d));
+                    }
+                    if (acc <= r2) {
+                        sv = acc;
+                        atomicAdd(&w.acc[O], 1);
+                    }
+                }
+                Ld[e * kListStride + O] = sv;
+                Li[e * kListStride + O] = sv <= r2 ? slot : 0;   // any valid slot sorts last
+            }
+        }
+        __syncwarp();
+        const int kept = w.acc[lane];
+        // each lane sorts its own list by (d2, original index), all lanes in
+        // parallel (register bitonic network, see sort_list); rejected
+        // entries (+inf) end up behind the kept ones
         sort_list(Ld + lane, Li + lane, kListStride, (act && !spill) ? cnt : 0, a.rperm);
-        if (act && !spill) counts[qorig] = min(cnt, K);
+        if (act && !spill) counts[qorig] = min(kept, K);
         if (act && spill && a.csr) counts[qorig] = kCsrSpill;   // counted by the selection kernel
-        if (act && !spill && a.degree) a.degree[qorig] = cnt;
+        if (act && !spill && a.degree) a.degree[qorig] = kept;
         if (act && spill) {
             // longer than the list: the exact selection kernel finishes this row
             const int pos = atomicAdd(a.ovf_count, 1);
@@ -372,7 +450,7 @@ __global__ void __launch_bounds__(kQueryWarps * 32, 4) k_grid_query(QueryArgs a)
         const int rstride = a.csr ? kCsrStageW : K;
         for (int ql = 0; ql < task.nq; ++ql) {
             if (spill_mask & (1u << ql)) continue;
-            const int c = min(__shfl_sync(kFull, cnt, ql), K);
+            const int c = min(__shfl_sync(kFull, kept, ql), K);
             const int qo = __shfl_sync(kFull, qorig, ql);
             int32_t* irow = oidx + (int64_t)qo * rstride;
             float* drow = od2 + (int64_t)qo * rstride;
@@ -516,6 +594,10 @@ template <int D>
 static cudaError_t launch_grid_query_d(const QueryArgs& a, int exit_dims, int num_sms,
                                        cudaStream_t st) {
     using C = QCfg<D>;
+    static_assert(warp_smem_bytes(C::DP, C::TILEP) % 16 == 0 &&
+                      (ring_floats(C::DP, C::TILEP) * sizeof(float)) % 16 == 0 &&
+                      (2 * C::DP * sizeof(float)) % 16 == 0,
+                  "bulk-copy destinations and sizes must be 16-byte multiples");
     const size_t smem = query_smem_bytes(C::DP, C::TILEP);
     auto kern = &k_grid_query<D, C::EXIT>;
     // other vote points are compiled for the tracking-like dimensions only
