@@ -135,7 +135,7 @@ static size_t predict_grid_bytes(int E, const int64_t* n, int D, const int64_t* 
     }
     nt = std::max<int64_t>(nt, 1);
     size_t b = 0;
-    b += sizeof(EventHdr) * E + 16 * (E + 1) + sizeof(int32_t) * kBBoxStride * E;
+    b += sizeof(EventHdr) * E + 16 * (E + 1) + sizeof(int32_t) * kBBoxStride * kBBoxCopies * E;
     b += (size_t)nt * (sizeof(float) * DP + 4 * sizeof(int32_t) + sizeof(Overflow));
     b += (size_t)L * 2 * sizeof(int32_t) + (size_t)tc * sizeof(Task);
     b += 64 * 1024 + 16 * 256;

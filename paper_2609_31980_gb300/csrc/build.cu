@@ -93,13 +93,18 @@ __global__ void k_init(int32_t* counts, int64_t L, int32_t* bbox, int E, int32_t
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t j = i; j < L; j += stride) counts[j] = 0;
-    for (int64_t j = i; j < (int64_t)E * kBBoxStride; j += stride) {
+    for (int64_t j = i; j < (int64_t)E * kBBoxCopies * kBBoxStride; j += stride) {
         int k = (int)(j % kBBoxStride);
         bbox[j] = k < 16 ? bb_min_init : (k < 32 ? bb_max_init : 0);
     }
     if (i < kScalars) scalars[i] = 0;
 }
 
+// Per-event bounding boxes.  One CTA per build block (256 points staged
+// through shared memory with 16-byte loads) reduces its points and merges the
+// result into one of kBBoxCopies copies of the event's box (copy = block mod
+// kBBoxCopies), so that no address takes more than a few dozen atomics; the
+// parameters kernel combines the copies.
 __global__ void __launch_bounds__(kBuildPtsPerBlock) k_bbox(const EventHdr* hdr,
                                                             const int32_t* blk_start, int E,
                                                             int D, int32_t* bbox,
@@ -145,6 +150,7 @@ __global__ void __launch_bounds__(kBuildPtsPerBlock) k_bbox(const EventHdr* hdr,
     }
     if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(&red_bad, 1);
     __syncthreads();
+    int32_t* bb = bbox + ((int64_t)e * kBBoxCopies + (blockIdx.x % kBBoxCopies)) * kBBoxStride;
     if (threadIdx.x < (unsigned)D) {
         const int k = threadIdx.x;
         float a = INFINITY, b = -INFINITY;
@@ -152,12 +158,11 @@ __global__ void __launch_bounds__(kBuildPtsPerBlock) k_bbox(const EventHdr* hdr,
             a = fminf(a, red_mn[k][w]);
             b = fmaxf(b, red_mx[k][w]);
         }
-        int32_t* bb = bbox + (int64_t)e * kBBoxStride;
         atomicMin(bb + k, float_to_ordered(a));
         atomicMax(bb + 16 + k, float_to_ordered(b));
     }
     if (threadIdx.x == 0 && red_bad) {
-        atomicOr(bbox + (int64_t)e * kBBoxStride + 32, 1);
+        atomicOr(bb + 32, 1);
         atomicOr(status, kStatusNonFinite);
     }
 }
@@ -177,15 +182,27 @@ __global__ void __launch_bounds__(kBuildPtsPerBlock) k_bbox(const EventHdr* hdr,
 // axis finds every accepted pair.  inv_h starts at fl_down(m / (r (1+2^-10)))
 // and is lowered until the bound holds with 2^-20 to spare, every axis has at
 // most 1024 cells, and the event's cell count fits its capacity.
-__global__ void k_params(EventHdr* hdr, int E, int D, const int32_t* bbox, float r, int m,
-                         int axes_mode, int naxes_req, int32_t* counts) {
-    const int e = blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= E) return;
+__global__ void __launch_bounds__(64) k_params(EventHdr* hdr, int E, int D, const int32_t* bbox,
+                                              float r, int m, int axes_mode, int naxes_req,
+                                              int32_t* counts) {
+    const int e = blockIdx.x;   // one CTA per event: its threads combine the box copies
+    __shared__ int32_t bb[kBBoxStride];
+    if (threadIdx.x < (unsigned)kBBoxStride) {
+        const int k = threadIdx.x;
+        const int32_t* b0 = bbox + (int64_t)e * kBBoxCopies * kBBoxStride + k;
+        int32_t v = b0[0];
+        for (int c = 1; c < kBBoxCopies; ++c) {
+            const int32_t x = b0[(int64_t)c * kBBoxStride];
+            v = k < 16 ? min(v, x) : (k < 32 ? max(v, x) : (v | x));
+        }
+        bb[k] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x != 0) return;
     EventHdr& h = hdr[e];
     // the last cell-array entry of the event counts its pair padding slot, so
     // the next event's slots start on a pair boundary
     counts[h.cell_off + h.cell_cap] = (int32_t)(h.n & 1);
-    const int32_t* bb = bbox + (int64_t)e * kBBoxStride;
     // per-event presets (batched autotuning) win over the call's options
     const int want = h.naxes > 0 ? h.naxes : naxes_req;
     const int naxes = min(D, min(max(want, 1), kMaxAxes));
@@ -338,30 +355,67 @@ __global__ void __launch_bounds__(kBuildPtsPerBlock) k_scatter(const EventHdr* h
                                                                const int32_t* cid,
                                                                const int32_t* rnk, float* pts,
                                                                int32_t* perm, int32_t* cell) {
-    extern __shared__ float sm[];
     const int e = find_event(blk_start, E, blockIdx.x);
     const EventHdr& h = hdr[e];
     const int64_t p0 = (int64_t)(blockIdx.x - blk_start[e]) * kBuildPtsPerBlock;
     const int np = (int)min((int64_t)kBuildPtsPerBlock, h.n - p0);
     if (p0 == 0 && threadIdx.x == 0 && (h.n & 1)) {
-        // pair padding slot: NaN coordinates are never within any radius
+        // pair padding slot (its coordinates are NaN, written by k_pack)
         const int64_t slot = h.pt_off + h.n;
-        for (int k = 0; k < DP; ++k) pts[pair_index(slot, k, DP)] = __int_as_float(0x7fc00000);
         perm[slot] = -1;
         cell[slot] = 0;
     }
-    if (np > 0) stage_floats(sm, h.refs + p0 * D, np * D);
-    __syncthreads();
     const int i = threadIdx.x;
     if (i >= np) return;
     const int64_t gi = h.pt_off + p0 + i;
     const int c = cid[gi];
     const int64_t slot = (int64_t)cstart[h.cell_off + c] + rnk[gi];
-    const float* p = sm + i * D;
-    float* dst = pts + pair_index(slot, 0, DP);
-    for (int k = 0; k < DP; ++k) dst[2 * k] = k < D ? p[k] : 0.f;
     perm[slot] = (int32_t)(p0 + i);
     cell[slot] = c;
+}
+
+// Cell-sorted coordinates, one thread per slot pair: the two points' input
+// rows are gathered and the pair's interleaved block (2 DP floats) is written
+// with 16-byte stores, consecutive pairs by consecutive threads.  A slot
+// without a point (an odd event's padding) gets NaN: never within any radius.
+__global__ void __launch_bounds__(256) k_pack(const EventHdr* hdr, int E, int64_t npairs, int D,
+                                              int DP, const int32_t* perm, float* pts) {
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= npairs) return;
+    // event of this pair: events occupy pair-aligned slot ranges
+    const int64_t s0 = 2 * q;
+    int lo = 0, hi = E - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (hdr[mid].pt_off <= s0) lo = mid; else hi = mid - 1;
+    }
+    const float* refs = hdr[lo].refs;
+    const int32_t i0 = perm[s0], i1 = perm[s0 + 1];
+    const float* a = i0 >= 0 ? refs + (int64_t)i0 * D : nullptr;
+    const float* b = i1 >= 0 ? refs + (int64_t)i1 * D : nullptr;
+    const float nan = __int_as_float(0x7fc00000);
+    float4* dst = reinterpret_cast<float4*>(pts + s0 * DP);
+    if ((D & 3) == 0 && (reinterpret_cast<uintptr_t>(refs) & 15) == 0) {
+        // rows of whole 16-byte vectors: two coordinates of each point per store
+        const float4 nan4 = make_float4(nan, nan, nan, nan);
+        for (int j = 0; j < D / 4; ++j) {
+            const float4 u = a ? __ldg(reinterpret_cast<const float4*>(a) + j) : nan4;
+            const float4 v = b ? __ldg(reinterpret_cast<const float4*>(b) + j) : nan4;
+            dst[2 * j] = make_float4(u.x, v.x, u.y, v.y);
+            dst[2 * j + 1] = make_float4(u.z, v.z, u.w, v.w);
+        }
+        for (int j = D / 2; j < DP / 2; ++j) dst[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+        return;
+    }
+    for (int j = 0; j < DP / 2; ++j) {
+        const int k0 = 2 * j, k1 = 2 * j + 1;
+        float4 v;
+        v.x = a ? (k0 < D ? __ldg(a + k0) : 0.f) : nan;
+        v.y = b ? (k0 < D ? __ldg(b + k0) : 0.f) : nan;
+        v.z = a ? (k1 < D ? __ldg(a + k1) : 0.f) : nan;
+        v.w = b ? (k1 < D ? __ldg(b + k1) : 0.f) : nan;
+        dst[j] = v;
+    }
 }
 
 // Per row of cells (all gridded coordinates but the fastest fixed): number of
@@ -444,9 +498,8 @@ void enqueue_tasks(GridBufs& g, int W, int A, Task* out, int32_t* count_out, cud
 // scans kScanItems consecutive values, then warp shuffles scan the thread
 // totals and a second warp pass scans the warp totals.
 
-constexpr int kScanThreads = 1024;
-constexpr int kScanItems = 8;
-constexpr int kScanChunk = kScanThreads * kScanItems;
+constexpr int kScanThreads = 256;
+constexpr int kScanItems = kScanChunk / kScanThreads;
 
 __device__ __forceinline__ int32_t block_exclusive_scan(int32_t v, int32_t* warp_tot,
                                                         int32_t* block_total) {
@@ -487,7 +540,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const int32_t* dat
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
     __syncthreads();
     if (threadIdx.x < 32) {
-        int32_t t = red[threadIdx.x];
+        int32_t t = threadIdx.x < kScanThreads / 32 ? red[threadIdx.x] : 0;
         for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
         if (threadIdx.x == 0) parts[blockIdx.x] = t;
     }
@@ -530,9 +583,52 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_single(int32_t* data, int
     scan_chunk(data, n, 0, 0, total);
 }
 
+// Down pass.  summed == 0: block b first sums the partials of the blocks
+// before it (used while there are at most kScanSumParts of them), then scans
+// its chunk with that offset; the last block also writes the total.
+// summed == 1: the partials were already scanned (k_scan_parts).
+constexpr int kScanSumParts = 512;
+
 __global__ void __launch_bounds__(kScanThreads) k_scan_down(int32_t* data, int64_t n,
-                                                            const int32_t* parts) {
-    scan_chunk(data, n, (int64_t)blockIdx.x * kScanChunk, parts[blockIdx.x], nullptr);
+                                                            const int32_t* parts, int32_t* total,
+                                                            int summed) {
+    if (summed) {
+        scan_chunk(data, n, (int64_t)blockIdx.x * kScanChunk, parts[blockIdx.x], nullptr);
+        return;
+    }
+    __shared__ int32_t red[kScanThreads / 32];
+    __shared__ int32_t offset;
+    int32_t v = 0;
+    for (int j = threadIdx.x; j < (int)blockIdx.x; j += kScanThreads) v += parts[j];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        int32_t t = threadIdx.x < kScanThreads / 32 ? red[threadIdx.x] : 0;
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+        if (threadIdx.x == 0) offset = t;
+    }
+    __syncthreads();
+    scan_chunk(data, n, (int64_t)blockIdx.x * kScanChunk, offset,
+               blockIdx.x == gridDim.x - 1 ? total : nullptr);
+}
+
+// One CTA: exclusive scan of the nb partials in place, chunk after chunk with
+// a running carry; writes the grand total.
+__global__ void __launch_bounds__(kScanThreads) k_scan_parts(int32_t* parts, int64_t nb,
+                                                             int32_t* total) {
+    __shared__ int32_t carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int64_t base = 0; base < nb; base += kScanChunk) {
+        const int32_t c = carry;
+        __shared__ int32_t ctot;
+        scan_chunk(parts, nb, base, c, &ctot);
+        __syncthreads();
+        if (threadIdx.x == 0) carry = ctot;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *total = carry;
 }
 
 int64_t scan_parts_needed(int64_t n) { return std::max<int64_t>(1, ceil_div(n, kScanChunk)); }
@@ -544,9 +640,12 @@ void enqueue_scan(int32_t* data, int64_t n, int32_t* parts, int32_t* total, cuda
         return;
     }
     k_scan_reduce<<<(unsigned)nb, kScanThreads, 0, st>>>(data, n, parts);
-    // nb <= kScanChunk is guaranteed by the capacity limits (2^26 entries)
-    k_scan_single<<<1, kScanThreads, 0, st>>>(parts, nb, total);
-    k_scan_down<<<(unsigned)nb, kScanThreads, 0, st>>>(data, n, parts);
+    if (nb <= kScanSumParts) {
+        k_scan_down<<<(unsigned)nb, kScanThreads, 0, st>>>(data, n, parts, total, 0);
+    } else {
+        k_scan_parts<<<1, kScanThreads, 0, st>>>(parts, nb, total);
+        k_scan_down<<<(unsigned)nb, kScanThreads, 0, st>>>(data, n, parts, total, 1);
+    }
 }
 
 // ------------------------------------------------------------------ host
@@ -619,7 +718,7 @@ frnn_status grid_alloc(GridBufs& g, int E, const int64_t* n, int D, std::string&
         const size_t o_hdr = take(sizeof(EventHdr) * E);
         const size_t o_blk = take(sizeof(int32_t) * (E + 1));
         const size_t o_coff = take(sizeof(int64_t) * (E + 1));
-        const size_t o_bbox = take(sizeof(int32_t) * kBBoxStride * E);
+        const size_t o_bbox = take(sizeof(int32_t) * kBBoxStride * kBBoxCopies * E);
         const size_t o_pts = take(sizeof(float) * DP * (cn + kTcRowPad));
         const size_t o_perm = take(sizeof(int32_t) * cn);
         const size_t o_cell = take(sizeof(int32_t) * cn);
@@ -664,7 +763,10 @@ frnn_status grid_alloc(GridBufs& g, int E, const int64_t* n, int D, std::string&
         g.cap_blk = nblk;
     }
     // page-locked mirror for the per-event tables
-    const size_t hbytes = sizeof(EventHdr) * E + sizeof(int32_t) * (E + 1) +
+    // (laid out like the device tables: header, block starts and cell offsets
+    // at the same relative offsets, so one copy uploads all three)
+    const size_t hbytes = (size_t)(reinterpret_cast<char*>(g.cell_off) -
+                                   reinterpret_cast<char*>(g.hdr)) +
                           sizeof(int64_t) * (E + 1) + 64;
     if (g.h_pinned_bytes < hbytes) {
         if (g.h_pinned) {
@@ -699,21 +801,23 @@ frnn_status enqueue_build(GridBufs& g, const float* const* refs, const BuildOpts
     // upload the per-event tables through the pinned mirror (wait until the
     // previous upload from it has been consumed)
     if (!capturing) cudaEventSynchronize(g.h_pinned_free);
+    // the three tables are adjacent on the device: mirror that layout in the
+    // pinned buffer and upload them with one copy
     char* hp = static_cast<char*>(g.h_pinned);
     const size_t s_hdr = sizeof(EventHdr) * E;
     const size_t s_blk = sizeof(int32_t) * (E + 1);
     const size_t s_coff = sizeof(int64_t) * (E + 1);
+    const size_t o_blk = reinterpret_cast<char*>(g.blk_start) - reinterpret_cast<char*>(g.hdr);
+    const size_t o_coff = reinterpret_cast<char*>(g.cell_off) - reinterpret_cast<char*>(g.hdr);
     memcpy(hp, g.h_hdr.data(), s_hdr);
-    memcpy(hp + s_hdr, g.h_blk_start.data(), s_blk);
-    memcpy(hp + s_hdr + s_blk, g.h_cell_off.data(), s_coff);
-    cudaMemcpyAsync(g.hdr, hp, s_hdr, cudaMemcpyHostToDevice, st);
-    cudaMemcpyAsync(g.blk_start, hp + s_hdr, s_blk, cudaMemcpyHostToDevice, st);
-    cudaMemcpyAsync(g.cell_off, hp + s_hdr + s_blk, s_coff, cudaMemcpyHostToDevice, st);
+    memcpy(hp + o_blk, g.h_blk_start.data(), s_blk);
+    memcpy(hp + o_coff, g.h_cell_off.data(), s_coff);
+    cudaMemcpyAsync(g.hdr, hp, o_coff + s_coff, cudaMemcpyHostToDevice, st);
     if (!capturing) cudaEventRecord(g.h_pinned_free, st);
 
     const int32_t bbmin = host_float_to_ordered(INFINITY);
     const int32_t bbmax = host_float_to_ordered(-INFINITY);
-    const int64_t init_n = std::max<int64_t>(g.L, (int64_t)E * kBBoxStride);
+    const int64_t init_n = std::max<int64_t>(g.L, (int64_t)E * kBBoxCopies * kBBoxStride);
     k_init<<<std::min<unsigned>(blocks_for(init_n, 256), 4096), 256, 0, st>>>(
         g.cstart, g.L, g.bbox, E, g.scalars, bbmin, bbmax);
     const size_t smem_pts = sizeof(float) * kBuildPtsPerBlock * D;
@@ -722,14 +826,17 @@ frnn_status enqueue_build(GridBufs& g, const float* const* refs, const BuildOpts
     } else {
         k_bbox<<<(unsigned)g.nblk, kBuildPtsPerBlock, smem_pts, st>>>(g.hdr, g.blk_start, E, D,
                                                                      g.bbox, d_status);
-        k_params<<<blocks_for(E, 128), 128, 0, st>>>(g.hdr, E, D, g.bbox, o.r, o.m, o.axes_mode, o.naxes,
+        k_params<<<(unsigned)E, 64, 0, st>>>(g.hdr, E, D, g.bbox, o.r, o.m, o.axes_mode, o.naxes,
                                                       g.cstart);
     }
     k_cellid<<<(unsigned)g.nblk, kBuildPtsPerBlock, smem_pts, st>>>(
         g.hdr, g.blk_start, E, D, g.cstart, g.cid, g.rnk, params_from ? 1 : 0, d_status);
     enqueue_scan(g.cstart, g.L, g.parts, g.scalars + kScCellTotal, st);
-    k_scatter<<<(unsigned)g.nblk, kBuildPtsPerBlock, smem_pts, st>>>(
+    k_scatter<<<(unsigned)g.nblk, kBuildPtsPerBlock, 0, st>>>(
         g.hdr, g.blk_start, E, D, g.DP, g.cstart, g.cid, g.rnk, g.pts, g.perm, g.cell);
+    if (g.n_total > 0)
+        k_pack<<<(unsigned)ceil_div(g.n_total / 2, 256), 256, 0, st>>>(g.hdr, E, g.n_total / 2, D,
+                                                                       g.DP, g.perm, g.pts);
     enqueue_tasks(g, kTaskQueries, 1, g.tasks, g.scalars + kScNTasks, st);
     g.tc_ready = false;   // tensor-core operands describe the previous contents
     cudaError_t ce = cudaGetLastError();
@@ -748,19 +855,22 @@ frnn_status enqueue_build_resident(GridBufs& g, const BuildOpts& o, int32_t* d_s
     const int E = g.E, D = g.D;
     const int32_t bbmin = host_float_to_ordered(INFINITY);
     const int32_t bbmax = host_float_to_ordered(-INFINITY);
-    const int64_t init_n = std::max<int64_t>(g.L, (int64_t)E * kBBoxStride);
+    const int64_t init_n = std::max<int64_t>(g.L, (int64_t)E * kBBoxCopies * kBBoxStride);
     k_init<<<std::min<unsigned>(blocks_for(init_n, 256), 4096), 256, 0, st>>>(
         g.cstart, g.L, g.bbox, E, g.scalars, bbmin, bbmax);
     const size_t smem_pts = sizeof(float) * kBuildPtsPerBlock * D;
     k_bbox<<<(unsigned)g.nblk, kBuildPtsPerBlock, smem_pts, st>>>(g.hdr, g.blk_start, E, D,
                                                                  g.bbox, d_status);
-    k_params<<<blocks_for(E, 128), 128, 0, st>>>(g.hdr, E, D, g.bbox, o.r, o.m, o.axes_mode, o.naxes,
+    k_params<<<(unsigned)E, 64, 0, st>>>(g.hdr, E, D, g.bbox, o.r, o.m, o.axes_mode, o.naxes,
                                                   g.cstart);
     k_cellid<<<(unsigned)g.nblk, kBuildPtsPerBlock, smem_pts, st>>>(
         g.hdr, g.blk_start, E, D, g.cstart, g.cid, g.rnk, 0, d_status);
     enqueue_scan(g.cstart, g.L, g.parts, g.scalars + kScCellTotal, st);
-    k_scatter<<<(unsigned)g.nblk, kBuildPtsPerBlock, smem_pts, st>>>(
+    k_scatter<<<(unsigned)g.nblk, kBuildPtsPerBlock, 0, st>>>(
         g.hdr, g.blk_start, E, D, g.DP, g.cstart, g.cid, g.rnk, g.pts, g.perm, g.cell);
+    if (g.n_total > 0)
+        k_pack<<<(unsigned)ceil_div(g.n_total / 2, 256), 256, 0, st>>>(g.hdr, E, g.n_total / 2, D,
+                                                                       g.DP, g.perm, g.pts);
     enqueue_tasks(g, kTaskQueries, 1, g.tasks, g.scalars + kScNTasks, st);
     cudaError_t ce = cudaGetLastError();
     if (ce != cudaSuccess) {

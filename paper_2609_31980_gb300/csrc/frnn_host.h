@@ -34,7 +34,7 @@ struct GridBufs {
     EventHdr* hdr = nullptr;       // [E]
     int32_t* blk_start = nullptr;  // [E + 1] first build block of each event
     int64_t* cell_off = nullptr;   // [E + 1] first cell-array entry of each event
-    int32_t* bbox = nullptr;       // [E * kBBoxStride] ordered-int min / max / flag
+    int32_t* bbox = nullptr;       // [E * kBBoxCopies * kBBoxStride] ordered-int min / max / flag
     float* pts = nullptr;          // [n_total * DP] cell-sorted coordinates
     int32_t* perm = nullptr;       // [n_total] slot -> original index in its event
     int32_t* cell = nullptr;       // [n_total] slot -> local cell id
@@ -66,6 +66,8 @@ struct GridBufs {
 };
 
 constexpr int kBBoxStride = 34;      // 16 minima, 16 maxima, non-finite flag, pad
+constexpr int kBBoxCopies = 32;      // copies of each event's box (spread the atomics)
+constexpr int kScanChunk = 2048;     // entries per block of the exclusive scan
 constexpr int kBuildPtsPerBlock = 256;
 // indices into GridBufs::scalars
 constexpr int kScNTasks = 0;        // number of warp tasks

@@ -43,9 +43,9 @@ constexpr size_t na_bytes(int64_t n, int D) {
     const int64_t cn = ((n + 1) & ~(int64_t)1) > 0 ? ((n + 1) & ~(int64_t)1) : 1;
     const int64_t L = na_cap(n) + 1;
     const int64_t tasks = n / kTaskQueries + na_cap(n) + 2;
-    const int64_t parts = (L + 8191) / 8192 > 0 ? (L + 8191) / 8192 : 1;
+    const int64_t parts = (L + kScanChunk - 1) / kScanChunk > 0 ? (L + kScanChunk - 1) / kScanChunk : 1;
     return na_al(sizeof(EventHdr)) + na_al(sizeof(int32_t) * 2) + na_al(sizeof(int64_t) * 2) +
-           na_al(sizeof(int32_t) * kBBoxStride) +
+           na_al(sizeof(int32_t) * kBBoxStride * kBBoxCopies) +
            na_al(sizeof(float) * padded_dim(D) * (cn + kTcRowPad)) + 4 * na_al(sizeof(int32_t) * cn) +
            2 * na_al(sizeof(int32_t) * L) + na_al(sizeof(Task) * tasks) +
            na_al(sizeof(Overflow) * cn) + na_al(sizeof(int32_t) * kScalars) +
@@ -97,7 +97,7 @@ static int32_t* carve(GridBufs& g, char* b, int64_t n, int D) {
     g.hdr = reinterpret_cast<EventHdr*>(take(sizeof(EventHdr)));
     g.blk_start = reinterpret_cast<int32_t*>(take(sizeof(int32_t) * 2));
     g.cell_off = reinterpret_cast<int64_t*>(take(sizeof(int64_t) * 2));
-    g.bbox = reinterpret_cast<int32_t*>(take(sizeof(int32_t) * kBBoxStride));
+    g.bbox = reinterpret_cast<int32_t*>(take(sizeof(int32_t) * kBBoxStride * kBBoxCopies));
     g.pts = reinterpret_cast<float*>(take(sizeof(float) * g.DP * (cn + kTcRowPad)));
     g.perm = reinterpret_cast<int32_t*>(take(sizeof(int32_t) * cn));
     g.cell = reinterpret_cast<int32_t*>(take(sizeof(int32_t) * cn));

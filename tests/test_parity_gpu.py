@@ -285,6 +285,31 @@ def test_batched_equals_alone_and_oracle(ctx):
                 _assert_rows_equal(got, oracle.self_query(p, 0.1, 64))
 
 
+def test_batched_many_events_long_cell_scan(ctx):
+    # 70 events: over 1.1 M cell entries, so the build's scans take the path
+    # that scans the block partials in a separate pass
+    import torch
+    g = np.random.default_rng(41)
+    sizes = g.integers(50, 3000, size=70)
+    evs = [synth.event_mix(int(n), 8, (41, e)) for e, n in enumerate(sizes)]
+    outs = ctx.query_batched([torch.from_numpy(p).cuda() for p in evs], 0.1, 32, path="grid")
+    ctx.sync()
+    for e, (p, (c, i, d)) in enumerate(zip(evs, outs)):
+        got = (c.cpu().numpy(), i.cpu().numpy(), d.cpu().numpy())
+        if e % 7 == 0:
+            _assert_rows_equal(got, oracle.self_query(p, 0.1, 32))
+        else:
+            _assert_rows_equal(got, _gpu_self(ctx, p, 0.1, 32))
+
+
+def test_single_event_2_5m_points_long_cell_scan(ctx):
+    pts = synth.uniform(2_500_000, 3, seed=42)
+    got = _gpu_self(ctx, pts, 0.004, 16)
+    rows = _sample_rows(len(pts), 200, 43)
+    _assert_rows_equal(got, oracle.self_query(pts, 0.004, 16, rows=rows), rows)
+    assert got[0].sum() > 0
+
+
 # ------------------------------------------------------------ tensor-core path
 
 @pytest.mark.parametrize("D", [8, 9, 11, 12, 16])
