@@ -334,6 +334,28 @@ frnn_status frnn_query_csr_count(frnn_ctx* ctx, const frnn_grid* grid, const flo
  * allocate exactly n_edges entries in between. */
 frnn_status frnn_query_csr_fill(frnn_ctx* ctx, int32_t* idx, float* dist2);
 
+/*
+ * The whole path with HOST buffers and compact output, in one call: copies
+ * refs to the device, builds the grid, runs the count pass of
+ * frnn_query_csr_count (self-query) and, if the rows fit, the fill pass, then
+ * copies the rows back; synchronises before it returns.  This is the shape of
+ * the paper's NumPy binding (Sec. 4.2: host transfers and compact host
+ * output).
+ *   refs_host     [N, D] float32 in
+ *   offsets_host  [N + 1] int64 out: row i at [offsets[i], offsets[i+1])
+ *   idx_host, dist2_host  [edge_cap] out (may be NULL when edge_cap is 0)
+ *   edge_cap      entries the caller provided; N * min(K, degree bound) or
+ *                 N * K always suffices
+ *   n_edges       out: offsets[N], the number of entries
+ * If n_edges > edge_cap the offsets are still written but no row is copied
+ * and the call returns FRNN_ERR_CAPACITY (retry with a larger buffer).
+ * Other errors: those of frnn_self_query_host.
+ */
+frnn_status frnn_self_query_host_csr(frnn_ctx* ctx, const float* refs_host, int64_t N, int D,
+                                     float r, int K, unsigned flags, int64_t* offsets_host,
+                                     int32_t* idx_host, float* dist2_host, int64_t edge_cap,
+                                     int64_t* n_edges);
+
 /* Durations of the main query kernel of every frnn_query call made since the
  * last frnn_kernel_times call (or since FRNN_OPT_KERNEL_TIMING was set), in
  * milliseconds, in call order.  Synchronises the context's stream.

@@ -45,6 +45,8 @@ struct frnn_ctx {
     frnn_grid* host_grid = nullptr;   // grid of the host-buffer path
     void* hp_buf = nullptr;   // device buffers of the host-buffer path
     size_t hp_bytes = 0;
+    void* hr_buf = nullptr;   // compact rows of the host-buffer path
+    size_t hr_bytes = 0;
     // autotuner cache: (log2 N bucket, D, log2 K bucket) -> best configuration
     struct Tuned {
         int path;    // 0 grid, 1 tensor-core
@@ -342,6 +344,7 @@ frnn_status frnn_destroy(frnn_ctx* ctx) {
     grid_free(ctx->qset);
     grid_free(ctx->batch);
     if (ctx->hp_buf) cudaFree(ctx->hp_buf);
+    if (ctx->hr_buf) cudaFree(ctx->hr_buf);
     if (ctx->csr_buf) cudaFree(ctx->csr_buf);
     cudaFree(ctx->d_status);
     cudaFreeHost(ctx->h_status);
@@ -798,6 +801,89 @@ frnn_status frnn_self_query_host(frnn_ctx* ctx, const float* refs_host, int64_t 
     cudaMemcpyAsync(counts_host, d_cnt, b_cnt, cudaMemcpyDeviceToHost, ctx->stream);
     cudaMemcpyAsync(idx_host, d_idx, b_row, cudaMemcpyDeviceToHost, ctx->stream);
     e = cudaMemcpyAsync(dist2_host, d_d2, b_row, cudaMemcpyDeviceToHost, ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "D2H copy");
+    return frnn_sync(ctx);
+}
+
+// Grow one of the context's device buffers of the host-buffer path (charged
+// to the budget; the stream is drained before the old buffer is freed).
+static frnn_status grow(frnn_ctx* ctx, void*& buf, size_t& bytes, size_t need, const char* what) {
+    if (need <= bytes) return FRNN_OK;
+    if (!budget_allows(ctx, bytes, need))
+        return fail(ctx, FRNN_ERR_BUDGET, "request exceeds the context's memory budget");
+    cudaStreamSynchronize(ctx->stream);
+    if (buf) cudaFree(buf);
+    ctx->held -= std::min(ctx->held, bytes);
+    buf = nullptr;
+    bytes = 0;
+    if (cudaMalloc(&buf, need) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(ctx, FRNN_ERR_OUT_OF_MEMORY, std::string("cudaMalloc of ") + what + " failed");
+    }
+    bytes = need;
+    ctx->held += need;
+    return FRNN_OK;
+}
+
+frnn_status frnn_self_query_host_csr(frnn_ctx* ctx, const float* refs_host, int64_t N, int D,
+                                     float r, int K, unsigned flags, int64_t* offsets_host,
+                                     int32_t* idx_host, float* dist2_host, int64_t edge_cap,
+                                     int64_t* n_edges) {
+    if (!ctx) return FRNN_ERR_INVALID_ARG;
+    if (D < 1 || D > kMaxD) return fail(ctx, FRNN_ERR_INVALID_ARG, "D must be in 1..16");
+    if (!offsets_host || !n_edges || edge_cap < 0)
+        return fail(ctx, FRNN_ERR_INVALID_ARG, "offsets_host or n_edges is NULL, or edge_cap < 0");
+    if (edge_cap > 0 && (!idx_host || !dist2_host))
+        return fail(ctx, FRNN_ERR_INVALID_ARG, "idx_host or dist2_host is NULL");
+    int32_t dummy = 0;
+    frnn_status s = check_query_args(ctx, N, r, K, flags | FRNN_SELF_QUERY, &dummy, &dummy,
+                                     reinterpret_cast<float*>(&dummy));
+    if (s != FRNN_OK) return s;
+    if (N > 0 && !refs_host) return fail(ctx, FRNN_ERR_INVALID_ARG, "refs_host is NULL");
+    *n_edges = 0;
+    if (N == 0) {
+        offsets_host[0] = 0;
+        return FRNN_OK;
+    }
+    auto al = [](size_t x) { return (x + 255) / 256 * 256; };
+    const size_t b_in = sizeof(float) * (size_t)N * D;
+    const size_t b_off = sizeof(int64_t) * (size_t)(N + 1);
+    s = grow(ctx, ctx->hp_buf, ctx->hp_bytes, al(b_in) + al(b_off), "host-path buffers");
+    if (s != FRNN_OK) return s;
+    float* d_in = static_cast<float*>(ctx->hp_buf);
+    int64_t* d_off = reinterpret_cast<int64_t*>(static_cast<char*>(ctx->hp_buf) + al(b_in));
+    cudaError_t e = cudaMemcpyAsync(d_in, refs_host, b_in, cudaMemcpyHostToDevice, ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "H2D copy");
+    s = frnn_build_grid(ctx, d_in, N, D, r, &ctx->host_grid);
+    if (s != FRNN_OK) return s;
+    int64_t E = 0;
+    s = frnn_query_csr_count(ctx, ctx->host_grid, d_in, N, r, K, flags | FRNN_SELF_QUERY, d_off,
+                             nullptr, &E);
+    if (s != FRNN_OK) return s;
+    *n_edges = E;
+    if (E > edge_cap) {
+        ctx->csr_pending = false;
+        e = cudaMemcpyAsync(offsets_host, d_off, b_off, cudaMemcpyDeviceToHost, ctx->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "D2H copy");
+        return fail(ctx, FRNN_ERR_CAPACITY, "more edges than edge_cap (n_edges has the count)");
+    }
+    const size_t b_rows = sizeof(int32_t) * (size_t)std::max<int64_t>(E, 1);
+    s = grow(ctx, ctx->hr_buf, ctx->hr_bytes, 2 * al(b_rows), "compact host-path rows");
+    if (s != FRNN_OK) return s;
+    int32_t* d_idx = static_cast<int32_t*>(ctx->hr_buf);
+    float* d_d2 = reinterpret_cast<float*>(static_cast<char*>(ctx->hr_buf) + al(b_rows));
+    // grow() drained the stream only when it reallocated; the pending rows
+    // survive it (no other call on the context came between)
+    s = frnn_query_csr_fill(ctx, d_idx, d_d2);
+    if (s != FRNN_OK) return s;
+    e = cudaMemcpyAsync(offsets_host, d_off, b_off, cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess && E > 0)
+        e = cudaMemcpyAsync(idx_host, d_idx, sizeof(int32_t) * (size_t)E, cudaMemcpyDeviceToHost,
+                            ctx->stream);
+    if (e == cudaSuccess && E > 0)
+        e = cudaMemcpyAsync(dist2_host, d_d2, sizeof(float) * (size_t)E, cudaMemcpyDeviceToHost,
+                            ctx->stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "D2H copy");
     return frnn_sync(ctx);
 }

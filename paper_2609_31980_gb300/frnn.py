@@ -43,13 +43,15 @@ FRNN_OPT_AUTO_TC = 6
 FRNN_OPT_TC_SURVIVORS = 7
 FRNN_OPT_TC_ACCEPTED = 8
 FRNN_OPT_KERNEL_TIMING = 9
+FRNN_ERR_CAPACITY = -8
 FRNN_OPT_GRID_NAXES = 10
 
 EXPORTED = ["frnn_version", "frnn_create", "frnn_destroy", "frnn_build_grid",
             "frnn_grid_destroy", "frnn_query", "frnn_query_batched", "frnn_self_query_host",
             "frnn_sync", "frnn_last_error", "frnn_set_option", "frnn_get_option",
             "frnn_autotune", "frnn_serve_run", "frnn_self_query_noalloc",
-            "frnn_kernel_times", "frnn_query_csr_count", "frnn_query_csr_fill"]
+            "frnn_kernel_times", "frnn_query_csr_count", "frnn_query_csr_fill",
+            "frnn_self_query_host_csr"]
 
 
 class frnn_tune_result(ctypes.Structure):
@@ -93,6 +95,8 @@ _sigs = {
     "frnn_query_csr_count": ([_vp, _vp, _vp, _i64, _f32, _int, _u32, _vp, _vp,
                               ctypes.POINTER(_i64)], _int),
     "frnn_query_csr_fill": ([_vp, _vp, _vp], _int),
+    "frnn_self_query_host_csr": ([_vp, _vp, _i64, _int, _f32, _int, _u32, _vp, _vp, _vp, _i64,
+                                  ctypes.POINTER(_i64)], _int),
     "frnn_autotune": ([_vp, _vp, _i64, _int, _f32, _int, _u32, ctypes.POINTER(frnn_tune_result)],
                       _int),
     "frnn_self_query_noalloc": ([_vp, _i64, _int, _f32, _int, _vp, _vp, _vp, _vp], _int),
@@ -300,6 +304,33 @@ class Context:
                                   _vp(d.ctypes.data))
         _check(self.handle, rc)
         return out
+
+    def self_query_host_csr(self, points_np, r: float, K: int, path: str = "auto", out=None):
+        """frnn_self_query_host_csr on NumPy arrays: returns (offsets [N+1],
+        idx [E], dist2 [E]) views; ``out`` = (offsets, idx, dist2) buffers,
+        idx/dist2 of any capacity (retried larger if too small)."""
+        import numpy as np
+        p = np.ascontiguousarray(points_np, dtype=np.float32)
+        N, D = p.shape
+        if out is None:
+            cap = N * min(K, 32)
+            out = (np.empty(N + 1, np.int64), np.empty(cap, np.int32), np.empty(cap, np.float32))
+        off, idx, d2 = out
+        ne = _i64(0)
+        for _ in range(2):
+            rc = frnn_self_query_host_csr(self.handle, _vp(p.ctypes.data), N, D, float(r), int(K),
+                                          PATHS[path], _vp(off.ctypes.data),
+                                          _vp(idx.ctypes.data) if len(idx) else None,
+                                          _vp(d2.ctypes.data) if len(d2) else None, len(idx),
+                                          ctypes.byref(ne))
+            if rc == FRNN_ERR_CAPACITY and ne.value > len(idx):
+                idx = np.empty(ne.value, np.int32)
+                d2 = np.empty(ne.value, np.float32)
+                continue
+            _check(self.handle, rc)
+            break
+        E = int(ne.value)
+        return off, idx[:E], d2[:E]
 
     def autotune(self, points, r: float, K: int, path: str = "auto") -> dict:
         """frnn_autotune on a representative [N, D] CUDA tensor; returns the

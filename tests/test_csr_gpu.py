@@ -152,3 +152,30 @@ def test_csr_event_500k_x12_k1000(ctx):
     rows = _sample(len(w.points), 400, 707)
     want = oracle.csr(w.points[rows], w.points, w.r, 1000, query_ids=rows)
     _assert_csr_equal(got, want, rows)
+
+
+def test_host_compact_call_matches_oracle_and_reports_capacity(ctx):
+    from paper_2609_31980_gb300 import frnn
+    pts = synth.clustered(200, 30, 3000, 8, 0.02, seed=720)
+    want = oracle.csr(pts, pts, 0.1, 48, query_ids=np.arange(len(pts)))
+    off, idx, d2 = ctx.self_query_host_csr(pts, 0.1, 48, "grid")
+    np.testing.assert_array_equal(off, want[0])
+    np.testing.assert_array_equal(idx, want[1])
+    np.testing.assert_array_equal(d2.view(np.uint32), want[2].view(np.uint32))
+    # too small a buffer: offsets still written, CAPACITY with the edge count
+    import ctypes
+    small_i = np.empty(5, np.int32)
+    small_d = np.empty(5, np.float32)
+    off2 = np.empty(len(pts) + 1, np.int64)
+    ne = ctypes.c_int64(0)
+    rc = frnn.frnn_self_query_host_csr(ctx.handle, ctypes.c_void_p(pts.ctypes.data), len(pts), 8,
+                                       0.1, 48, 0, ctypes.c_void_p(off2.ctypes.data),
+                                       ctypes.c_void_p(small_i.ctypes.data),
+                                       ctypes.c_void_p(small_d.ctypes.data), 5, ctypes.byref(ne))
+    assert rc == frnn.FRNN_ERR_CAPACITY and ne.value == want[0][-1]
+    np.testing.assert_array_equal(off2, want[0])
+    # the binding retries with a buffer of the right size
+    off3, idx3, _ = ctx.self_query_host_csr(pts, 0.1, 48, "grid", (off2, small_i, small_d))
+    np.testing.assert_array_equal(idx3, want[1])
+    empty = ctx.self_query_host_csr(np.zeros((0, 8), np.float32), 0.1, 48, "grid")
+    assert empty[0].tolist() == [0] and len(empty[1]) == 0
