@@ -356,6 +356,17 @@ frnn_status frnn_self_query_host_csr(frnn_ctx* ctx, const float* refs_host, int6
                                      int32_t* idx_host, float* dist2_host, int64_t edge_cap,
                                      int64_t* n_edges);
 
+/* Check of the device-side failure handling (no counterpart in the paper).
+ * Launches one warp on the context's stream that waits on an mbarrier which
+ * nothing ever completes, with the bounded wait every query kernel uses but a
+ * limit of limit_ns nanoseconds of %globaltimer time (1e6 .. 5e9).  The wait
+ * runs out, the warp records a timeout in the context's status word and
+ * exits; the call then synchronises and returns what frnn_sync returns:
+ * FRNN_ERR_TIMEOUT when the bound works.  The status word is cleared, so the
+ * context stays usable.  Errors: INVALID_ARG (NULL ctx, limit out of range),
+ * CUDA. */
+frnn_status frnn_check_wait_timeout(frnn_ctx* ctx, uint64_t limit_ns);
+
 /* Durations of the main query kernel of every frnn_query call made since the
  * last frnn_kernel_times call (or since FRNN_OPT_KERNEL_TIMING was set), in
  * milliseconds, in call order.  Synchronises the context's stream.

@@ -888,6 +888,16 @@ frnn_status frnn_self_query_host_csr(frnn_ctx* ctx, const float* refs_host, int6
     return frnn_sync(ctx);
 }
 
+frnn_status frnn_check_wait_timeout(frnn_ctx* ctx, uint64_t limit_ns) {
+    if (!ctx) return FRNN_ERR_INVALID_ARG;
+    if (limit_ns < 1000000ull || limit_ns > 5000000000ull)
+        return fail(ctx, FRNN_ERR_INVALID_ARG, "limit_ns must be in [1e6, 5e9]");
+    ctx->csr_pending = false;
+    const cudaError_t e = launch_wait_timeout(limit_ns, ctx->d_status, ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "wait-timeout check launch");
+    return frnn_sync(ctx);
+}
+
 frnn_status frnn_sync(frnn_ctx* ctx) {
     if (!ctx) return FRNN_ERR_INVALID_ARG;
     cudaError_t e = cudaMemcpyAsync(ctx->h_status, ctx->d_status, sizeof(int32_t),

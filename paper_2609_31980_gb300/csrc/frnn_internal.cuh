@@ -211,13 +211,14 @@ __device__ __forceinline__ uint64_t globaltimer_ns() {
 }
 
 // Bounded wait: returns false (and the caller records a timeout) if the phase
-// did not complete within kWaitLimitNs.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+// did not complete within limit_ns of %globaltimer time (or kSpinLimit polls).
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity,
+                                                  uint64_t limit_ns = kWaitLimitNs) {
     if (mbar_try_wait(bar, parity)) return true;
     const uint64_t t0 = globaltimer_ns();
     for (uint32_t it = 1; it < kSpinLimit; ++it) {
         if (mbar_try_wait(bar, parity)) return true;
-        if ((it & 7u) == 0 && globaltimer_ns() - t0 > kWaitLimitNs) return false;
+        if ((it & 7u) == 0 && globaltimer_ns() - t0 > limit_ns) return false;
     }
     return false;
 }

@@ -44,6 +44,8 @@ FRNN_OPT_TC_SURVIVORS = 7
 FRNN_OPT_TC_ACCEPTED = 8
 FRNN_OPT_KERNEL_TIMING = 9
 FRNN_ERR_CAPACITY = -8
+FRNN_ERR_TIMEOUT = -7
+FRNN_ERR_INVALID_ARG = -1
 FRNN_OPT_GRID_NAXES = 10
 
 EXPORTED = ["frnn_version", "frnn_create", "frnn_destroy", "frnn_build_grid",
@@ -51,7 +53,7 @@ EXPORTED = ["frnn_version", "frnn_create", "frnn_destroy", "frnn_build_grid",
             "frnn_sync", "frnn_last_error", "frnn_set_option", "frnn_get_option",
             "frnn_autotune", "frnn_serve_run", "frnn_self_query_noalloc",
             "frnn_kernel_times", "frnn_query_csr_count", "frnn_query_csr_fill",
-            "frnn_self_query_host_csr"]
+            "frnn_self_query_host_csr", "frnn_check_wait_timeout"]
 
 
 class frnn_tune_result(ctypes.Structure):
@@ -95,6 +97,7 @@ _sigs = {
     "frnn_query_csr_count": ([_vp, _vp, _vp, _i64, _f32, _int, _u32, _vp, _vp,
                               ctypes.POINTER(_i64)], _int),
     "frnn_query_csr_fill": ([_vp, _vp, _vp], _int),
+    "frnn_check_wait_timeout": ([_vp, ctypes.c_uint64], _int),
     "frnn_self_query_host_csr": ([_vp, _vp, _i64, _int, _f32, _int, _u32, _vp, _vp, _vp, _i64,
                                   ctypes.POINTER(_i64)], _int),
     "frnn_autotune": ([_vp, _vp, _i64, _int, _f32, _int, _u32, ctypes.POINTER(frnn_tune_result)],

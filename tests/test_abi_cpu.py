@@ -64,3 +64,4 @@ def test_null_context_is_rejected(lib_path):
     assert frnn.frnn_build_grid(None, None, 0, 3, 0.1, None) == -1
     n = ctypes.c_int(0)
     assert frnn.frnn_kernel_times(None, None, 0, ctypes.byref(n)) == -1
+    assert frnn.frnn_check_wait_timeout(None, 20_000_000) == -1
