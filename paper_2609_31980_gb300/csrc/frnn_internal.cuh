@@ -14,7 +14,7 @@ constexpr int kMaxD = 16;
 constexpr int kMaxK = 1024;
 constexpr int kMaxAxes = 4;
 constexpr int kMaxDimsPerAxis = 1024;   // the grid roundoff proof assumes <= 2^10 cells per axis
-constexpr int kTaskQueries = 32;        // queries per warp task (one per lane)
+constexpr int kTaskQueries = 16;        // queries per warp task (two lanes each)
 
 // Device status word bits (frnn_sync maps them to frnn_status).
 constexpr int kStatusNonFinite = 1;
@@ -68,11 +68,11 @@ struct EventHdr {
     float* dist2;
 };
 
-// One warp task: up to 32 consecutive cell-sorted query slots lying in one
+// One warp task: up to 16 consecutive cell-sorted query slots lying in one
 // row of cells (all gridded coordinates but the fastest equal).
 struct Task {
     int32_t qslot;   // first query slot (global)
-    int32_t nq;      // queries in the task (1..32)
+    int32_t nq;      // queries in the task (1..16 for warp tasks, 1..128 for tensor-core tiles)
     int32_t ev;      // event index
     int32_t row;     // row index within the event: c1 + dims[1] * (c2 + dims[2] * c3)
 };
@@ -241,12 +241,13 @@ __host__ __device__ constexpr int64_t ceil_div(int64_t a, int64_t b) { return (a
 
 // ------------------------------------------------------------ per-thread sort
 // A thread's neighbour list lives in shared memory as a column of a
-// transposed table: entry e at d2[e * stride], slot[e * stride] (slot = the
-// reference's sorted slot).  Sorting maps slots to original indices (the
-// tie-break key), builds 64-bit keys (d2 bits << 32 | index) (d2 >= +0, so
-// the unsigned order of the keys is the (d2, index) order) and runs a fixed
+// transposed table: entry e at d2[e * stride], idx[e * stride].  With perm,
+// idx holds the reference's sorted slot and sorting maps it to the original
+// index (the tie-break key); without, idx already holds the original index.
+// The sort builds 64-bit keys (d2 bits << 32 | index) (d2 >= +0, so the
+// unsigned order of the keys is the (d2, index) order) and runs a fixed
 // bitonic network in registers: no data-dependent branches, so the lanes of
-// a warp stay converged and the index loads are issued together.
+// a warp stay converged.
 template <int S>
 __device__ __forceinline__ void sort_list_net(float* d2, int32_t* idx, int stride, int cnt,
                                               const int32_t* perm) {
@@ -256,7 +257,8 @@ __device__ __forceinline__ void sort_list_net(float* d2, int32_t* idx, int strid
         k[e] = ~0ull;
         if (e < cnt) {
             const int32_t slot = idx[e * stride];
-            k[e] = ((uint64_t)__float_as_uint(d2[e * stride]) << 32) | (uint32_t)perm[slot];
+            k[e] = ((uint64_t)__float_as_uint(d2[e * stride]) << 32) |
+                   (uint32_t)(perm ? perm[slot] : slot);
         }
     }
 #pragma unroll
@@ -293,7 +295,7 @@ __device__ __forceinline__ void sort_list(float* d2, int32_t* idx, int stride, i
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(full, mx, o));
     if (mx <= 1) {
-        if (cnt == 1) idx[0] = perm[idx[0]];
+        if (cnt == 1 && perm) idx[0] = perm[idx[0]];
     } else if (mx <= 4) {
         sort_list_net<4>(d2, idx, stride, cnt, perm);
     } else if (mx <= 8) {

@@ -9,8 +9,11 @@
 //
 // Organisation on the GPU (differs from the paper's thread-per-query kernel,
 // whose profile showed dependent-load latency and divergence, Sec. 4.2):
-//   * a persistent grid; each warp takes warp tasks (32 cell-sorted queries in
-//     one row of cells) from an atomic counter;
+//   * a persistent grid; each warp takes warp tasks (16 cell-sorted queries in
+//     one row of cells) from an atomic counter; lanes q and q + 16 serve query
+//     q and split the candidates between them (even and odd pairs), so a warp
+//     screens the union of 16 neighbourhoods, not 32: fewer candidates per
+//     query (the union of a longer run of queries spans more cells);
 //   * the candidates of a task are the union of its lanes' neighbourhoods: per
 //     neighbour row one contiguous slot range; the ranges, widened to pair
 //     boundaries, form one stream of candidate pairs cut into tiles of TILEP
@@ -37,8 +40,9 @@
 //     and canonical-order recomputation", Sec. 4.2); the original index is
 //     looked up only for the kept entries (the deferred lookup, Table 3);
 //   * every lane sorts its own list by (d2, index) with a register bitonic
-//     network and keeps the first K (count = min(degree, K)); the warp writes
-//     the rows coalesced with their padding.  Lists longer than 32 (never in
+//     network, lane q merges lane q + 16's sorted list into its own, keeps the
+//     first K (count = min(degree, K)), and the warp writes the rows coalesced
+//     with their padding.  Lists longer than 32 (never in
 //     the tracking-like workloads) go to an exact selection kernel, keeping
 //     results exact for dense inputs (the paper's Sec. 5 caveat on heap-free
 //     top-K).
@@ -66,7 +70,8 @@ struct QCfg {
     // 0.686 ms at 500k x 12)
     static constexpr int TILEP = DP == 4 ? 32 : (DP == 8 ? 16 : (DP == 12 ? 24 : 16));
     static constexpr int MINB = DP <= 8 ? 5 : 4;
-    static constexpr int EXIT = D <= 4 ? D : 2;   // default vote point
+    // default vote point (measured: 2 and 3 tie at D = 8, 3 is best at D = 12)
+    static constexpr int EXIT = D <= 4 ? D : (D >= 10 ? 3 : 2);
 };
 
 __host__ __device__ constexpr size_t ring_floats(int DP, int TILEP) {
@@ -191,6 +196,10 @@ __global__ void __launch_bounds__(kQueryWarps * 32, QCfg<D>::MINB) k_grid_query(
     const WarpSmem w = carve_warp(smem + (size_t)warp * warp_smem_bytes(DP, TILEP), DP, TILEP);
     float* Ld = w.Ld;
     int32_t* Li = w.Li;
+    // lanes q and q + 16 serve the task's query q; lane q screens the stream's
+    // even candidate pairs, lane q + 16 the odd ones
+    const int qi = lane & (kTaskQueries - 1);
+    const int sh = lane / kTaskQueries;
     if (lane == 0)
         for (int b = 0; b < kNBuf; ++b) mbar_init(&w.bars[b], 1);
     fence_mbar_init();
@@ -214,8 +223,8 @@ __global__ void __launch_bounds__(kQueryWarps * 32, QCfg<D>::MINB) k_grid_query(
         int32_t* oidx = a.counts ? a.idx : h.idx;
         float* od2 = a.counts ? a.dist2 : h.dist2;
 
-        const bool act = lane < task.nq;
-        const int qs = task.qslot + lane;
+        const bool act = qi < task.nq;
+        const int qs = task.qslot + qi;
         const int qorig = act ? a.qperm[qs] : 0;
         if (!h.valid) {
             // grid built from non-finite input: empty rows (frnn_sync reports it)
@@ -226,8 +235,8 @@ __global__ void __launch_bounds__(kQueryWarps * 32, QCfg<D>::MINB) k_grid_query(
                     od2[(int64_t)qo * K + e] = INFINITY;
                 }
             }
-            if (act) counts[qorig] = 0;
-            if (act && a.degree) a.degree[qorig] = 0;
+            if (act && sh == 0) counts[qorig] = 0;
+            if (act && sh == 0 && a.degree) a.degree[qorig] = 0;
             continue;
         }
         uint64_t qq[D];   // each query coordinate duplicated into both f32x2 lanes
@@ -274,8 +283,7 @@ __global__ void __launch_bounds__(kQueryWarps * 32, QCfg<D>::MINB) k_grid_query(
         const int self_code = (a.self && act) ? 2 * (pp_c + (qs >> 1) - prs_c) + (qs & 1) : -1;
         const int ntiles = (P + TILEP - 1) / TILEP;
 
-        int cnt = 0;          // tentative entries
-        bool lost = false;    // an entry did not fit the list: the row goes to the selection kernel
+        int cnt = 0;          // tentative entries (more than kListCap: the row goes to the selection kernel)
 
         // prologue: fill the ring
         const int pre = min(kNBuf, ntiles);
@@ -306,25 +314,27 @@ __global__ void __launch_bounds__(kQueryWarps * 32, QCfg<D>::MINB) k_grid_query(
                 }
                 __syncwarp();
             }
-            // four candidate pairs per step: their first-stage screens are
-            // independent, which hides the packed pipeline's latency
-            for (int p0 = 0; p0 < lenp; p0 += 4) {
+            // eight candidate pairs per step, four per stream: their
+            // first-stage screens are independent, which hides the packed
+            // pipeline's latency
+            for (int p0 = 0; p0 < lenp; p0 += 8) {
                 uint64_t sg[4];
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
                     // pairs past the tile's end hold stale data: force them out
-                    const ulonglong2* cp = reinterpret_cast<const ulonglong2*>(tile + (p0 + j) * PAIRF);
+                    const int p = p0 + 2 * j + sh;
+                    const ulonglong2* cp = reinterpret_cast<const ulonglong2*>(tile + p * PAIRF);
                     uint64_t s2 = 0;
 #pragma unroll
                     for (int k = 0; k < EXIT; ++k) {
                         const ulonglong2 v = cp[k >> 1];
                         s2 = f2_screen(s2, qq[k], (k & 1) ? v.y : v.x);
                     }
-                    sg[j] = (p0 + j < lenp) ? s2 : 0x7f8000007f800000ull;   // +inf, +inf
+                    sg[j] = (p < lenp) ? s2 : 0x7f8000007f800000ull;   // +inf, +inf
                 }
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
-                    const int p = p0 + j;
+                    const int p = p0 + 2 * j + sh;
                     const ulonglong2* cp = reinterpret_cast<const ulonglong2*>(tile + p * PAIRF);
                     uint64_t s2 = sg[j];
                     float s0, s1;
@@ -338,19 +348,16 @@ __global__ void __launch_bounds__(kQueryWarps * 32, QCfg<D>::MINB) k_grid_query(
                         }
                         f2_unpack(s2, s0, s1);
                     }
-                    if (fminf(s0, s1) <= rs2) {
-                        // tentative: remember the stream code, resolved at the task's end
-                        const int code0 = 2 * (T0 + p);
-#pragma unroll
-                        for (int h2 = 0; h2 < 2; ++h2) {
-                            const int code = code0 + h2;
-                            if ((h2 ? s1 : s0) <= rs2 && code != self_code) {
-                                if (cnt < kListCap) Li[cnt * kListStride + lane] = code;
-                                else lost = true;
-                                ++cnt;
-                            }
-                        }
-                    }
+                    // tentative entries: the stream codes, resolved at the task's
+                    // end; appended without branches (predicated stores), so the
+                    // warp does not diverge here
+                    const int code0 = 2 * (T0 + p);
+                    const bool f0 = s0 <= rs2 && code0 != self_code;
+                    const bool f1 = s1 <= rs2 && code0 + 1 != self_code;
+                    const int c1 = cnt + (f0 ? 1 : 0);
+                    if (f0 && cnt < kListCap) Li[cnt * kListStride + lane] = code0;
+                    if (f1 && c1 < kListCap) Li[c1 * kListStride + lane] = code0 + 1;
+                    cnt = c1 + (f1 ? 1 : 0);
                 }
             }
             __syncwarp();
@@ -369,6 +376,7 @@ __global__ void __launch_bounds__(kQueryWarps * 32, QCfg<D>::MINB) k_grid_query(
             return;
         }
 
+        const bool lost = cnt > kListCap;   // an entry did not fit the list
         // exact recheck of every lane's tentative entries, spread over the
         // whole warp: entry i of the task's concatenated lists goes to lane
         // i % 32.  Each resolves its row (the last row whose stream part
@@ -376,8 +384,7 @@ __global__ void __launch_bounds__(kQueryWarps * 32, QCfg<D>::MINB) k_grid_query(
         // (slots read only because parts start on pair boundaries are
         // dropped), then applies the scalar contract in index order without
         // contraction.  Accepted: (d2, slot); rejected: d2 = +inf, sorted last.
-        const bool spill = lost;
-        const int own = spill ? 0 : cnt;
+        const int own = lost ? 0 : cnt;
         int cin = own;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
@@ -406,8 +413,10 @@ __global__ void __launch_bounds__(kQueryWarps * 32, QCfg<D>::MINB) k_grid_query(
                     if (w.Rpp[L + st] <= sp) L += st;
                 const int slot = 2 * (w.Rprs[L] + sp - w.Rpp[L]) + (code & 1);
                 float sv = INFINITY;
+                int32_t orig = 0;
                 if (slot >= w.Rrs[L] && slot < w.Rre[L]) {
-                    const int qo_slot = task.qslot + O;
+                    orig = a.rperm[slot];   // in flight with the coordinate loads
+                    const int qo_slot = task.qslot + (O & (kTaskQueries - 1));
                     float acc = 0.f;
 #pragma unroll
                     for (int k = 0; k < D; ++k) {
@@ -421,7 +430,7 @@ __global__ void __launch_bounds__(kQueryWarps * 32, QCfg<D>::MINB) k_grid_query(
                     }
                 }
                 Ld[e * kListStride + O] = sv;
-                Li[e * kListStride + O] = sv <= r2 ? slot : 0;   // any valid slot sorts last
+                Li[e * kListStride + O] = sv <= r2 ? orig : 0;   // rejected: +inf sorts last
             }
         }
         __syncwarp();
@@ -429,11 +438,39 @@ __global__ void __launch_bounds__(kQueryWarps * 32, QCfg<D>::MINB) k_grid_query(
         // each lane sorts its own list by (d2, original index), all lanes in
         // parallel (register bitonic network, see sort_list); rejected
         // entries (+inf) end up behind the kept ones
-        sort_list(Ld + lane, Li + lane, kListStride, (act && !spill) ? cnt : 0, a.rperm);
-        if (act && !spill) counts[qorig] = min(kept, K);
-        if (act && spill && a.csr) counts[qorig] = kCsrSpill;   // counted by the selection kernel
-        if (act && !spill && a.degree) a.degree[qorig] = kept;
-        if (act && spill) {
+        sort_list(Ld + lane, Li + lane, kListStride, (act && !lost) ? cnt : 0, nullptr);
+        // lane q merges lane q + 16's sorted entries into its own list, from
+        // the back (its column has room for both when the query fits at all)
+        const int kB = __shfl_sync(kFull, kept, qi + kTaskQueries);
+        const bool lostB = __shfl_sync(kFull, lost, qi + kTaskQueries);
+        const int total = kept + kB;
+        const bool spill_q = act && (lost || lostB || total > kListCap);
+        __syncwarp();
+        if (sh == 0 && act && !spill_q && kB > 0) {
+            const int cb = qi + kTaskQueries;
+            int i = kept - 1, j = kB - 1;
+            uint64_t ka = i >= 0 ? make_key(Ld[i * kListStride + qi], Li[i * kListStride + qi]) : 0;
+            uint64_t kb = make_key(Ld[j * kListStride + cb], Li[j * kListStride + cb]);
+            for (int k = total - 1; j >= 0; --k) {
+                if (i >= 0 && ka > kb) {
+                    Ld[k * kListStride + qi] = __uint_as_float((uint32_t)(ka >> 32));
+                    Li[k * kListStride + qi] = (int32_t)(uint32_t)ka;
+                    --i;
+                    if (i >= 0) ka = make_key(Ld[i * kListStride + qi], Li[i * kListStride + qi]);
+                } else {
+                    Ld[k * kListStride + qi] = __uint_as_float((uint32_t)(kb >> 32));
+                    Li[k * kListStride + qi] = (int32_t)(uint32_t)kb;
+                    --j;
+                    if (j >= 0) kb = make_key(Ld[j * kListStride + cb], Li[j * kListStride + cb]);
+                }
+            }
+        }
+        __syncwarp();
+        const bool spill = sh == 0 && spill_q;
+        if (sh == 0 && act && !spill) counts[qorig] = min(total, K);
+        if (spill && a.csr) counts[qorig] = kCsrSpill;   // counted by the selection kernel
+        if (sh == 0 && act && !spill && a.degree) a.degree[qorig] = total;
+        if (spill) {
             // longer than the list: the exact selection kernel finishes this row
             const int pos = atomicAdd(a.ovf_count, 1);
             if (pos < a.ovf_cap) {
@@ -450,7 +487,7 @@ __global__ void __launch_bounds__(kQueryWarps * 32, QCfg<D>::MINB) k_grid_query(
         const int rstride = a.csr ? kCsrStageW : K;
         for (int ql = 0; ql < task.nq; ++ql) {
             if (spill_mask & (1u << ql)) continue;
-            const int c = min(__shfl_sync(kFull, kept, ql), K);
+            const int c = min(__shfl_sync(kFull, total, ql), K);
             const int qo = __shfl_sync(kFull, qorig, ql);
             int32_t* irow = oidx + (int64_t)qo * rstride;
             float* drow = od2 + (int64_t)qo * rstride;
@@ -594,6 +631,7 @@ template <int D>
 static cudaError_t launch_grid_query_d(const QueryArgs& a, int exit_dims, int num_sms,
                                        cudaStream_t st) {
     using C = QCfg<D>;
+    static_assert(C::TILEP % 8 == 0, "eight candidate pairs per screening step");
     static_assert(warp_smem_bytes(C::DP, C::TILEP) % 16 == 0 &&
                       (ring_floats(C::DP, C::TILEP) * sizeof(float)) % 16 == 0 &&
                       (2 * C::DP * sizeof(float)) % 16 == 0,
@@ -603,6 +641,7 @@ static cudaError_t launch_grid_query_d(const QueryArgs& a, int exit_dims, int nu
     // other vote points are compiled for the tracking-like dimensions only
     if constexpr (D == 8 || D == 12) {
         if (exit_dims == 1) kern = &k_grid_query<D, 1>;
+        else if (exit_dims == 2) kern = &k_grid_query<D, 2>;
         else if (exit_dims == 3) kern = &k_grid_query<D, 3>;
         else if (exit_dims == 4) kern = &k_grid_query<D, 4>;
         else if (exit_dims >= 5) kern = &k_grid_query<D, 6>;
