@@ -182,24 +182,28 @@ __global__ void __launch_bounds__(kBuildPtsPerBlock) k_bbox(const EventHdr* hdr,
 // axis finds every accepted pair.  inv_h starts at fl_down(m / (r (1+2^-10)))
 // and is lowered until the bound holds with 2^-20 to spare, every axis has at
 // most 1024 cells, and the event's cell count fits its capacity.
-__global__ void __launch_bounds__(64) k_params(EventHdr* hdr, int E, int D, const int32_t* bbox,
-                                              float r, int m, int axes_mode, int naxes_req,
-                                              int32_t* counts) {
-    const int e = blockIdx.x;   // one CTA per event: its threads combine the box copies
+static_assert(kBBoxCopies == 32, "one copy per lane when the copies are combined");
+
+__global__ void __launch_bounds__(256) k_params(EventHdr* hdr, int E, int D, const int32_t* bbox,
+                                               float r, int m, int axes_mode, int naxes_req,
+                                               int32_t* counts) {
+    const int e = blockIdx.x;   // one CTA per event: its warps combine the box copies
     __shared__ int32_t bb[kBBoxStride];
-    if (threadIdx.x < (unsigned)kBBoxStride) {
-        const int k = threadIdx.x;
-        const int32_t* b0 = bbox + (int64_t)e * kBBoxCopies * kBBoxStride + k;
-        int32_t v = b0[0];
-        for (int c = 1; c < kBBoxCopies; ++c) {
-            const int32_t x = b0[(int64_t)c * kBBoxStride];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int k = warp; k < kBBoxStride; k += 8) {
+        // lane c holds copy c of entry k; a warp reduction combines them
+        int32_t v = bbox[((int64_t)e * kBBoxCopies + lane) * kBBoxStride + k];
+        for (int o = 16; o > 0; o >>= 1) {
+            const int32_t x = __shfl_xor_sync(0xffffffffu, v, o);
             v = k < 16 ? min(v, x) : (k < 32 ? max(v, x) : (v | x));
         }
-        bb[k] = v;
+        if (lane == 0) bb[k] = v;
     }
     __syncthreads();
     if (threadIdx.x != 0) return;
-    EventHdr& h = hdr[e];
+    // work on a private copy (global read-after-write chains are slow) and
+    // store it once at the end
+    EventHdr h = hdr[e];
     // the last cell-array entry of the event counts its pair padding slot, so
     // the next event's slots start on a pair boundary
     counts[h.cell_off + h.cell_cap] = (int32_t)(h.n & 1);
@@ -260,6 +264,7 @@ __global__ void __launch_bounds__(64) k_params(EventHdr* hdr, int E, int D, cons
     if (!valid) {
         h.inv_h = 0.f;
         h.ncells = 1;
+        hdr[e] = h;
         return;
     }
     const double rd = (double)r;
@@ -296,6 +301,7 @@ __global__ void __launch_bounds__(64) k_params(EventHdr* hdr, int E, int D, cons
     }
     h.inv_h = ih;
     h.ncells = (int32_t)cells;
+    hdr[e] = h;
 }
 
 // Cross-set binning: take the reference grid's parameters for each event.
@@ -826,7 +832,7 @@ frnn_status enqueue_build(GridBufs& g, const float* const* refs, const BuildOpts
     } else {
         k_bbox<<<(unsigned)g.nblk, kBuildPtsPerBlock, smem_pts, st>>>(g.hdr, g.blk_start, E, D,
                                                                      g.bbox, d_status);
-        k_params<<<(unsigned)E, 64, 0, st>>>(g.hdr, E, D, g.bbox, o.r, o.m, o.axes_mode, o.naxes,
+        k_params<<<(unsigned)E, 256, 0, st>>>(g.hdr, E, D, g.bbox, o.r, o.m, o.axes_mode, o.naxes,
                                                       g.cstart);
     }
     k_cellid<<<(unsigned)g.nblk, kBuildPtsPerBlock, smem_pts, st>>>(
@@ -861,7 +867,7 @@ frnn_status enqueue_build_resident(GridBufs& g, const BuildOpts& o, int32_t* d_s
     const size_t smem_pts = sizeof(float) * kBuildPtsPerBlock * D;
     k_bbox<<<(unsigned)g.nblk, kBuildPtsPerBlock, smem_pts, st>>>(g.hdr, g.blk_start, E, D,
                                                                  g.bbox, d_status);
-    k_params<<<(unsigned)E, 64, 0, st>>>(g.hdr, E, D, g.bbox, o.r, o.m, o.axes_mode, o.naxes,
+    k_params<<<(unsigned)E, 256, 0, st>>>(g.hdr, E, D, g.bbox, o.r, o.m, o.axes_mode, o.naxes,
                                                   g.cstart);
     k_cellid<<<(unsigned)g.nblk, kBuildPtsPerBlock, smem_pts, st>>>(
         g.hdr, g.blk_start, E, D, g.cstart, g.cid, g.rnk, 0, d_status);

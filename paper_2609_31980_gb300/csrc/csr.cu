@@ -116,26 +116,46 @@ __global__ void __launch_bounds__(kCsrThreads) k_csr_down(const int32_t* cnt, in
         offsets[M] = tot + (parts ? parts[blockIdx.x] : 0);
 }
 
-// One warp per 32 consecutive rows: their counts and offsets in one coalesced
-// load each, then each row's entries copied lane by lane (rows of one warp
-// are independent, so the loads of several rows are in flight together).
+// One warp per 32 consecutive rows.  Their entries are contiguous in the
+// output ([offsets[r0], offsets[r0 + 32]) minus the rows the selection
+// kernel writes), so the warp walks them as one flat range: entry t of the
+// range belongs to the row whose exclusive prefix (within the 32) is the last
+// one <= t (a binary search over the lanes' prefixes with shuffles); every
+// lane copies one entry per step and the stores of a step are contiguous.
 __global__ void __launch_bounds__(256) k_csr_gather(const int32_t* cnt, const int64_t* offsets,
                                                     const int32_t* sidx, const float* sd2,
                                                     int64_t M, int32_t* idx, float* dist2) {
     const int lane = threadIdx.x & 31;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w * 32 < M; w += nw) {
-        const int64_t i = w * 32 + lane;
+        const int64_t r0 = w * 32;
+        const int64_t i = r0 + lane;
         const int32_t c = i < M ? cnt[i] : 0;
-        const int64_t o = i < M ? offsets[i] : 0;
-#pragma unroll 8
-        for (int j = 0; j < 32; ++j) {
-            const int32_t cj = __shfl_sync(0xffffffffu, c, j);
-            const int64_t oj = __shfl_sync(0xffffffffu, o, j);
-            if ((cj & kCsrSpill) || lane >= cj) continue;
-            const int64_t src = (w * 32 + j) * kCsrStageW + lane;
-            idx[oj + lane] = sidx[src];
-            dist2[oj + lane] = sd2[src];
+        const int own = (c & kCsrSpill) ? 0 : c;   // spilled rows: written by the selection kernel
+        int incl = own;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += v;
+        }
+        const int excl = incl - own;
+        const int T = __shfl_sync(0xffffffffu, incl, 31);
+        const int64_t o_lane = i < M ? offsets[i] : 0;
+        for (int base = 0; base < T; base += 32) {
+            const int t = base + lane;
+            int R = 0;
+#pragma unroll
+            for (int st = 16; st > 0; st >>= 1) {
+                const int v = __shfl_sync(0xffffffffu, excl, R + st);
+                if (v <= t) R += st;
+            }
+            const int e = t - __shfl_sync(0xffffffffu, excl, R);
+            const int64_t dst = __shfl_sync(0xffffffffu, o_lane, R) + e;
+            if (t < T) {
+                const int64_t src = (r0 + R) * kCsrStageW + e;
+                idx[dst] = sidx[src];
+                dist2[dst] = sd2[src];
+            }
         }
     }
 }
