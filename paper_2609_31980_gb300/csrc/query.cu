@@ -19,7 +19,8 @@
 //     boundaries, form one stream of candidate pairs cut into tiles of TILEP
 //     pairs; the row lanes copy their parts of a tile into the warp's
 //     shared-memory ring with cp.async.bulk, completion tracked by one
-//     mbarrier per buffer (prefetch depth kNBuf-1);
+//     mbarrier per buffer (prefetch depth NBUF-1); once the last tile is
+//     consumed the ring is reused for the lists' distances;
 //   * every lane screens every candidate of the tile (broadcast shared loads):
 //     warp-uniform control flow.  Points are stored pair-interleaved, so each
 //     16-byte shared load gives two dimensions of two candidates and one
@@ -54,7 +55,7 @@
 namespace frnn {
 
 constexpr int kQueryWarps = 4;
-constexpr int kNBuf = 2;
+constexpr int kMaxNBuf = 4;
 constexpr uint32_t kFull = 0xffffffffu;
 constexpr int kListCap = 32;      // per-lane neighbour list in shared memory
 constexpr int kListStride = 33;   // entry e of lane l at e*33 + l: conflict-free both ways
@@ -64,22 +65,27 @@ template <int D>
 struct QCfg {
     static constexpr int DP = padded_dim(D);
     // candidate pairs per tile (1 KB per buffer up to D = 8, else about
-    // 2 KB) and CTAs per SM: up to D = 8 the smaller ring lets five CTAs
-    // (20 warps) share an SM, which the latency-bound scan prefers (measured
-    // 0.339 vs 0.349 ms at 300k x 8); above, the longer tiles win (0.633 vs
-    // 0.686 ms at 500k x 12)
+    // 2 KB) and CTAs per SM: up to D = 8 the smaller ring (shared with the
+    // list distances) lets six CTAs (24 warps, 80 registers) share an SM,
+    // which the latency-bound scan prefers (measured at 300k x 8: 0.311 ms
+    // with six, 0.321 with five, 0.349 with four CTAs and 2 KB tiles); above,
+    // the longer tiles win (0.633 vs 0.686 ms at 500k x 12)
     static constexpr int TILEP = DP == 4 ? 32 : (DP == 8 ? 16 : (DP == 12 ? 24 : 16));
-    static constexpr int MINB = DP <= 8 ? 5 : 4;
+    static constexpr int MINB = DP <= 8 ? 6 : 4;
+    // ring buffers: up to D = 8 four 1 KB tiles (three in flight; the ring
+    // doubles as the list distances afterwards, so the warp's shared memory
+    // stays small enough for five CTAs per SM), else two
+    static constexpr int NBUF = DP <= 8 ? 4 : 2;
     // default vote point (measured: 2 and 3 tie at D = 8, 3 is best at D = 12)
     static constexpr int EXIT = D <= 4 ? D : (D >= 10 ? 3 : 2);
 };
 
-__host__ __device__ constexpr size_t ring_floats(int DP, int TILEP) {
-    return (size_t)kNBuf * TILEP * 2 * DP;
+__host__ __device__ constexpr size_t ring_floats(int DP, int TILEP, int NB) {
+    return (size_t)NB * TILEP * 2 * DP;
 }
-__host__ __device__ constexpr size_t warp_smem_bytes(int DP, int TILEP);
-__host__ __device__ constexpr size_t query_smem_bytes(int DP, int TILEP) {
-    return (size_t)kQueryWarps * warp_smem_bytes(DP, TILEP);
+__host__ __device__ constexpr size_t warp_smem_bytes(int DP, int TILEP, int NB);
+__host__ __device__ constexpr size_t query_smem_bytes(int DP, int TILEP, int NB) {
+    return (size_t)kQueryWarps * warp_smem_bytes(DP, TILEP, NB);
 }
 
 // ------------------------------------------------------------- packed f32x2
@@ -136,21 +142,28 @@ struct WarpSmem {
     int32_t* Rrs;    // [32] its slot range [rs, re)
     int32_t* Rre;
     int32_t* acc;    // [32] exactly accepted entries per lane
-    uint64_t* bars;  // [kNBuf]
+    uint64_t* bars;  // [NBUF]
 };
 
-// rounded up to 128 bytes: every warp's ring (a bulk-copy destination) must
-// start on a 16-byte boundary
-__host__ __device__ constexpr size_t warp_smem_bytes(int DP, int TILEP) {
-    return (ring_floats(DP, TILEP) * sizeof(float) + 2 * kListCap * kListStride * 4 +
-            5 * 32 * 4 + kNBuf * sizeof(uint64_t) + 127) / 128 * 128;
+// The ring and the lists' distances share one region (the distances are
+// written only after the last tile is consumed).  Rounded up to 128 bytes:
+// every warp's ring (a bulk-copy destination) must start on a 16-byte
+// boundary.
+__host__ __device__ constexpr size_t ring_region_floats(int DP, int TILEP, int NB) {
+    return ring_floats(DP, TILEP, NB) > (size_t)kListCap * kListStride
+               ? ring_floats(DP, TILEP, NB)
+               : (size_t)kListCap * kListStride;
+}
+__host__ __device__ constexpr size_t warp_smem_bytes(int DP, int TILEP, int NB) {
+    return (ring_region_floats(DP, TILEP, NB) * sizeof(float) + kListCap * kListStride * 4 +
+            5 * 32 * 4 + NB * sizeof(uint64_t) + 127) / 128 * 128;
 }
 
-__device__ __forceinline__ WarpSmem carve_warp(unsigned char* base, int DP, int TILEP) {
+__device__ __forceinline__ WarpSmem carve_warp(unsigned char* base, int DP, int TILEP, int NB) {
     WarpSmem w;
     w.ring = reinterpret_cast<float*>(base);
-    w.Ld = w.ring + ring_floats(DP, TILEP);
-    w.Li = reinterpret_cast<int32_t*>(w.Ld + kListCap * kListStride);
+    w.Ld = w.ring;   // after the tiles
+    w.Li = reinterpret_cast<int32_t*>(w.ring + ring_region_floats(DP, TILEP, NB));
     w.Rpp = w.Li + kListCap * kListStride;
     w.Rprs = w.Rpp + 32;
     w.Rrs = w.Rprs + 32;
@@ -193,7 +206,9 @@ __global__ void __launch_bounds__(kQueryWarps * 32, QCfg<D>::MINB) k_grid_query(
     constexpr int PAIRF = 2 * DP;   // floats per candidate pair
     extern __shared__ __align__(128) unsigned char smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const WarpSmem w = carve_warp(smem + (size_t)warp * warp_smem_bytes(DP, TILEP), DP, TILEP);
+    constexpr int NB = C::NBUF;
+    const WarpSmem w =
+        carve_warp(smem + (size_t)warp * warp_smem_bytes(DP, TILEP, NB), DP, TILEP, NB);
     float* Ld = w.Ld;
     int32_t* Li = w.Li;
     // lanes q and q + 16 serve the task's query q; lane q screens the stream's
@@ -201,7 +216,7 @@ __global__ void __launch_bounds__(kQueryWarps * 32, QCfg<D>::MINB) k_grid_query(
     const int qi = lane & (kTaskQueries - 1);
     const int sh = lane / kTaskQueries;
     if (lane == 0)
-        for (int b = 0; b < kNBuf; ++b) mbar_init(&w.bars[b], 1);
+        for (int b = 0; b < NB; ++b) mbar_init(&w.bars[b], 1);
     fence_mbar_init();
     __syncwarp();
     uint32_t phase = 0;   // bit b: parity to wait for on buffer b
@@ -286,12 +301,12 @@ __global__ void __launch_bounds__(kQueryWarps * 32, QCfg<D>::MINB) k_grid_query(
         int cnt = 0;          // tentative entries (more than kListCap: the row goes to the selection kernel)
 
         // prologue: fill the ring
-        const int pre = min(kNBuf, ntiles);
+        const int pre = min(NB, ntiles);
         for (int tt = 0; tt < pre; ++tt)
             issue_tile<TILEP, PAIRF>(w, tt, tt, pp, np, prs, P, a.rpts, lane);
         int timed_out_at = -1;
         for (int tt = 0; tt < ntiles; ++tt) {
-            const int b = tt % kNBuf;
+            const int b = tt % NB;
             if (!mbar_wait_bounded(&w.bars[b], (phase >> b) & 1u)) {
                 timed_out_at = tt;
                 break;
@@ -361,15 +376,15 @@ __global__ void __launch_bounds__(kQueryWarps * 32, QCfg<D>::MINB) k_grid_query(
                 }
             }
             __syncwarp();
-            const int nt = tt + kNBuf;
+            const int nt = tt + NB;
             if (nt < ntiles) issue_tile<TILEP, PAIRF>(w, nt, b, pp, np, prs, P, a.rpts, lane);
         }
         if (timed_out_at >= 0) {
             // record, wait (bounded) for the copies still in flight, stop this warp
             if (lane == 0) atomicOr(a.status, kStatusTimeout);
-            const int issued = min(ntiles, timed_out_at + kNBuf);
+            const int issued = min(ntiles, timed_out_at + NB);
             for (int t2 = timed_out_at; t2 < issued; ++t2) {
-                const int b2 = t2 % kNBuf;
+                const int b2 = t2 % NB;
                 mbar_wait_bounded(&w.bars[b2], (phase >> b2) & 1u);
                 phase ^= 1u << b2;
             }
@@ -632,11 +647,12 @@ static cudaError_t launch_grid_query_d(const QueryArgs& a, int exit_dims, int nu
                                        cudaStream_t st) {
     using C = QCfg<D>;
     static_assert(C::TILEP % 8 == 0, "eight candidate pairs per screening step");
-    static_assert(warp_smem_bytes(C::DP, C::TILEP) % 16 == 0 &&
-                      (ring_floats(C::DP, C::TILEP) * sizeof(float)) % 16 == 0 &&
+    static_assert(C::NBUF <= kMaxNBuf, "phase bits and barriers per warp");
+    static_assert(warp_smem_bytes(C::DP, C::TILEP, C::NBUF) % 16 == 0 &&
+                      (ring_region_floats(C::DP, C::TILEP, C::NBUF) * sizeof(float)) % 16 == 0 &&
                       (2 * C::DP * sizeof(float)) % 16 == 0,
                   "bulk-copy destinations and sizes must be 16-byte multiples");
-    const size_t smem = query_smem_bytes(C::DP, C::TILEP);
+    const size_t smem = query_smem_bytes(C::DP, C::TILEP, C::NBUF);
     auto kern = &k_grid_query<D, C::EXIT>;
     // other vote points are compiled for the tracking-like dimensions only
     if constexpr (D == 8 || D == 12) {

@@ -190,6 +190,24 @@ def test_grid_options_do_not_change_results(ctx, m, axes):
         ctx.set_option(frnn.FRNN_OPT_GRID_AXES, 0)
 
 
+@pytest.mark.parametrize("naxes", [1, 2, 3, 4])
+@pytest.mark.parametrize("m", [1, 2])
+@pytest.mark.parametrize("axes", [0, 1])
+def test_gridded_axis_counts_do_not_change_results(ctx, naxes, m, axes):
+    from paper_2609_31980_gb300 import frnn
+    pts = synth.clustered(200, 30, 2000, 8, 0.02, seed=309)
+    want = oracle.self_query(pts, 0.1, 48)
+    ctx.set_option(frnn.FRNN_OPT_GRID_NAXES, naxes)
+    ctx.set_option(frnn.FRNN_OPT_CELL_MULT, m)
+    ctx.set_option(frnn.FRNN_OPT_GRID_AXES, axes)
+    try:
+        _assert_rows_equal(_gpu_self(ctx, pts, 0.1, 48), want)
+    finally:
+        ctx.set_option(frnn.FRNN_OPT_GRID_NAXES, 0)
+        ctx.set_option(frnn.FRNN_OPT_CELL_MULT, 0)
+        ctx.set_option(frnn.FRNN_OPT_GRID_AXES, 0)
+
+
 @pytest.mark.parametrize("e", [1, 3, 4, 6])
 def test_exit_dims_do_not_change_results(ctx, e):
     from paper_2609_31980_gb300 import frnn
