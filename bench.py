@@ -576,7 +576,7 @@ def main():
     ap.add_argument("--steps", type=int, default=400)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--cpu-rows", type=int, default=4000)
+    ap.add_argument("--cpu-rows", type=int, default=300000, help="oracle query rows (all: ~20 s on 16 cores)")
     ap.add_argument("--ref-rows", type=int, default=1000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cell-mult", type=int, default=0, help="grid cell multiple m (0: library default)")
