@@ -155,7 +155,10 @@ frnn_status frnn_query_batched(frnn_ctx* ctx, const frnn_event* ev, int n_events
  * The whole path with HOST buffers: copies refs to the device, builds the
  * grid, self-queries it and copies the results back, synchronising before it
  * returns (the host-side interface of Sec. 4.2's NumPy binding comparison).
- * Host buffers may be pageable; page-locked buffers copy faster.
+ * Host buffers may be pageable.  When all three output buffers are
+ * page-locked (cudaHostAlloc / cudaHostRegister), the query kernels write the
+ * rows straight into them over the host link instead of staging them in
+ * device memory and copying them back.
  *   refs_host [N, D] float32 in; counts_host [N], idx_host [N, K],
  *   dist2_host [N, K] out.  Device memory is taken from the context's
  *   workspace and reused across calls.

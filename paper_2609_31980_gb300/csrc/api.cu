@@ -116,6 +116,20 @@ static frnn_status cuda_fail(frnn_ctx* c, cudaError_t e, const char* what) {
     return fail(c, FRNN_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
 }
 
+// Device address of a page-locked host buffer (NULL if the buffer is pageable
+// or unknown to CUDA).  On a Grace-Blackwell node such memory is reachable
+// from the GPU over the coherent chip-to-chip link, so kernels can write
+// results straight into it instead of staging them in HBM and copying.
+static void* mapped_host(const void* p) {
+    if (!p) return nullptr;
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return at.type == cudaMemoryTypeHost ? at.devicePointer : nullptr;
+}
+
 static bool radius_ok(float r) {
     return std::isfinite(r) && r >= 0x1p-60f && r <= 0x1p60f;
 }
@@ -770,7 +784,13 @@ frnn_status frnn_self_query_host(frnn_ctx* ctx, const float* refs_host, int64_t 
     const size_t b_cnt = sizeof(int32_t) * (size_t)N;
     const size_t b_row = sizeof(int32_t) * (size_t)N * K;
     auto al = [](size_t x) { return (x + 255) / 256 * 256; };
-    const size_t need = al(b_in) + al(b_cnt) + 2 * al(b_row);
+    // page-locked outputs: the query writes them directly (no staging, no
+    // copy; 1.07 vs 1.31 ms end to end for the 300k x 8 event, K = 64)
+    int32_t* m_cnt = static_cast<int32_t*>(mapped_host(counts_host));
+    int32_t* m_idx = static_cast<int32_t*>(mapped_host(idx_host));
+    float* m_d2 = static_cast<float*>(mapped_host(dist2_host));
+    const bool direct = m_cnt && m_idx && m_d2;
+    const size_t need = al(b_in) + (direct ? 0 : al(b_cnt) + 2 * al(b_row));
     if (need > ctx->hp_bytes) {
         if (!budget_allows(ctx, ctx->hp_bytes, need))
             return fail(ctx, FRNN_ERR_BUDGET, "request exceeds the context's memory budget");
@@ -788,9 +808,10 @@ frnn_status frnn_self_query_host(frnn_ctx* ctx, const float* refs_host, int64_t 
     }
     char* b = static_cast<char*>(ctx->hp_buf);
     float* d_in = reinterpret_cast<float*>(b);
-    int32_t* d_cnt = reinterpret_cast<int32_t*>(b + al(b_in));
-    int32_t* d_idx = reinterpret_cast<int32_t*>(b + al(b_in) + al(b_cnt));
-    float* d_d2 = reinterpret_cast<float*>(b + al(b_in) + al(b_cnt) + al(b_row));
+    int32_t* d_cnt = direct ? m_cnt : reinterpret_cast<int32_t*>(b + al(b_in));
+    int32_t* d_idx = direct ? m_idx : reinterpret_cast<int32_t*>(b + al(b_in) + al(b_cnt));
+    float* d_d2 = direct ? m_d2
+                         : reinterpret_cast<float*>(b + al(b_in) + al(b_cnt) + al(b_row));
     cudaError_t e = cudaMemcpyAsync(d_in, refs_host, b_in, cudaMemcpyHostToDevice, ctx->stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "H2D copy");
     s = frnn_build_grid(ctx, d_in, N, D, r, &ctx->host_grid);
@@ -798,6 +819,7 @@ frnn_status frnn_self_query_host(frnn_ctx* ctx, const float* refs_host, int64_t 
     s = frnn_query(ctx, ctx->host_grid, d_in, N, r, K, flags | FRNN_SELF_QUERY, d_cnt, d_idx,
                    d_d2);
     if (s != FRNN_OK) return s;
+    if (direct) return frnn_sync(ctx);
     cudaMemcpyAsync(counts_host, d_cnt, b_cnt, cudaMemcpyDeviceToHost, ctx->stream);
     cudaMemcpyAsync(idx_host, d_idx, b_row, cudaMemcpyDeviceToHost, ctx->stream);
     e = cudaMemcpyAsync(dist2_host, d_d2, b_row, cudaMemcpyDeviceToHost, ctx->stream);
@@ -869,6 +891,9 @@ frnn_status frnn_self_query_host_csr(frnn_ctx* ctx, const float* refs_host, int6
         return fail(ctx, FRNN_ERR_CAPACITY, "more edges than edge_cap (n_edges has the count)");
     }
     const size_t b_rows = sizeof(int32_t) * (size_t)std::max<int64_t>(E, 1);
+    // the rows are gathered in HBM and copied back by the copy engine (measured
+    // faster here than gathering straight into page-locked host memory:
+    // 0.82 vs 0.95 ms for the 300k x 8 event)
     s = grow(ctx, ctx->hr_buf, ctx->hr_bytes, 2 * al(b_rows), "compact host-path rows");
     if (s != FRNN_OK) return s;
     int32_t* d_idx = static_cast<int32_t*>(ctx->hr_buf);

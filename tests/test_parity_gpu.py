@@ -254,6 +254,29 @@ def test_host_buffer_path(ctx):
     _assert_rows_equal((c, i, d), oracle.self_query(w.points, w.r, w.K))
 
 
+def test_host_buffer_paths_with_page_locked_buffers(ctx):
+    # page-locked outputs are written by the kernels directly (no copy back)
+    import torch
+    pts = synth.clustered(300, 30, 4000, 8, 0.02, seed=330)
+    N, K = len(pts), 40
+    want = oracle.self_query(pts, 0.1, K)
+    h_in = torch.from_numpy(pts).pin_memory()
+    out = (torch.full((N,), -7, dtype=torch.int32).pin_memory().numpy(),
+           torch.full((N, K), -7, dtype=torch.int32).pin_memory().numpy(),
+           torch.zeros((N, K), dtype=torch.float32).pin_memory().numpy())
+    got = ctx.self_query_host(h_in.numpy(), 0.1, K, "grid", out)
+    _assert_rows_equal(got, want)
+    wc = oracle.csr(pts, pts, 0.1, K, query_ids=np.arange(N))
+    cap = int(wc[0][-1]) + 5
+    c_out = (torch.empty(N + 1, dtype=torch.int64).pin_memory().numpy(),
+             torch.empty(cap, dtype=torch.int32).pin_memory().numpy(),
+             torch.empty(cap, dtype=torch.float32).pin_memory().numpy())
+    off, idx, d2 = ctx.self_query_host_csr(h_in.numpy(), 0.1, K, "grid", c_out)
+    np.testing.assert_array_equal(off, wc[0])
+    np.testing.assert_array_equal(idx, wc[1])
+    np.testing.assert_array_equal(d2.view(np.uint32), wc[2].view(np.uint32))
+
+
 def test_invalid_arguments(ctx):
     import torch
     from paper_2609_31980_gb300 import frnn
