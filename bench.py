@@ -503,8 +503,12 @@ def run_serving(ctx, args):
     ctx.serve(events[:8], np.zeros(8), r, K, budget, slots=args.serve_slots,
               max_batch=args.serve_batch, outs=outs[:8])
     # sequential capacity: everything queued at t = 0, one event at a time
-    _, _, seq0 = ctx.serve(events, np.zeros(n_ev), r, K, budget, slots=1, max_batch=1, outs=outs)
-    cap = seq0["events_per_s"]
+    # (the better of two runs)
+    cap = 0.0
+    for _ in range(2):
+        _, _, seq0 = ctx.serve(events, np.zeros(n_ev), r, K, budget, slots=1, max_batch=1,
+                               outs=outs)
+        cap = max(cap, seq0["events_per_s"])
     out = {"events": n_ev, "mean_N": float(np.mean(sizes)), "budget_bytes": budget,
            "sequential_capacity_events_per_s": cap, "loads": []}
     for load in args.serve_loads:
@@ -591,10 +595,10 @@ def main():
     ap.add_argument("--batch-warmup", type=int, default=10)
     ap.add_argument("--batch-path", default="grid", choices=["grid", "tc", "auto"])
     ap.add_argument("--no-serving", action="store_true")
-    ap.add_argument("--serve-events", type=int, default=48)
+    ap.add_argument("--serve-events", type=int, default=96)
     ap.add_argument("--serve-slots", type=int, default=4)
     ap.add_argument("--serve-batch", type=int, default=8)
-    ap.add_argument("--serve-loads", type=float, nargs="*", default=[0.9, 1.5])
+    ap.add_argument("--serve-loads", type=float, nargs="*", default=[0.9, 1.5, 3.0])
     ap.add_argument("--workload", default="event300k", choices=["event300k", "event500k"])
     args = ap.parse_args()
     if args.warmup < 3:

@@ -120,7 +120,8 @@ static frnn_status cuda_fail(frnn_ctx* c, cudaError_t e, const char* what) {
 // or unknown to CUDA).  On a Grace-Blackwell node such memory is reachable
 // from the GPU over the coherent chip-to-chip link, so kernels can write
 // results straight into it instead of staging them in HBM and copying.
-static void* mapped_host(const void* p) {
+namespace frnn {
+void* mapped_host(const void* p) {
     if (!p) return nullptr;
     cudaPointerAttributes at;
     if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
@@ -129,6 +130,7 @@ static void* mapped_host(const void* p) {
     }
     return at.type == cudaMemoryTypeHost ? at.devicePointer : nullptr;
 }
+}  // namespace frnn
 
 static bool radius_ok(float r) {
     return std::isfinite(r) && r >= 0x1p-60f && r <= 0x1p60f;

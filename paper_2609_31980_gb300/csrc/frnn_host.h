@@ -163,6 +163,8 @@ frnn_status enqueue_overflow(const QueryArgs& a, int num_sms, cudaStream_t st, s
 
 // Context helpers for the serving loop (defined with the context, api.cu).
 void ctx_copy_tuning(frnn_ctx* dst, const frnn_ctx* src);
+// Device address of a page-locked host buffer, or NULL (pageable / unknown).
+void* mapped_host(const void* p);
 // diag.cu: one warp waits (bounded by limit_ns) on a barrier nothing completes
 cudaError_t launch_wait_timeout(uint64_t limit_ns, int32_t* status, cudaStream_t st);
 // Grow the context's batched workspace (and the tensor-core operands when the

@@ -122,6 +122,7 @@ frnn_status frnn_serve_run(frnn_ctx* ctx, const frnn_request* reqs, int n_reqs, 
     std::vector<double> finish(n_reqs, -1.0);
     const double t0 = now_s();
     std::vector<frnn_event> evs;
+    std::vector<char> direct;
     auto launch = [&](Slot& s) -> frnn_status {
         const SchedBatch& b = s.batch;
         // device layout: per request input, counts, idx, dist2
@@ -142,6 +143,7 @@ frnn_status frnn_serve_run(frnn_ctx* ctx, const frnn_request* reqs, int n_reqs, 
         }
         char* p = static_cast<char*>(s.dbuf);
         evs.assign(b.reqs.size(), frnn_event{});
+        direct.assign(b.reqs.size(), 0);
         for (size_t i = 0; i < b.reqs.size(); ++i) {
             const frnn_request& q = reqs[b.reqs[i]];
             const int64_t n = q.n;
@@ -155,6 +157,16 @@ frnn_status frnn_serve_run(frnn_ctx* ctx, const frnn_request* reqs, int n_reqs, 
             p += al256((size_t)n * K * 4);
             ev.dist2 = reinterpret_cast<float*>(p);
             p += al256((size_t)n * K * 4);
+            // page-locked result buffers: the kernels write them directly
+            void* mc = mapped_host(q.counts);
+            void* mi = mapped_host(q.idx);
+            void* md = mapped_host(q.dist2);
+            if (mc && mi && md) {
+                ev.counts = static_cast<int32_t*>(mc);
+                ev.idx = static_cast<int32_t*>(mi);
+                ev.dist2 = static_cast<float*>(md);
+                direct[i] = 1;
+            }
             if (n > 0 && cudaMemcpyAsync(const_cast<float*>(ev.pts), q.pts, (size_t)n * D * 4,
                                          cudaMemcpyHostToDevice, s.stream) != cudaSuccess)
                 return FRNN_ERR_CUDA;
@@ -164,7 +176,7 @@ frnn_status frnn_serve_run(frnn_ctx* ctx, const frnn_request* reqs, int n_reqs, 
         for (size_t i = 0; i < b.reqs.size(); ++i) {
             const frnn_request& q = reqs[b.reqs[i]];
             const int64_t n = q.n;
-            if (n == 0) continue;
+            if (n == 0 || direct[i]) continue;
             cudaMemcpyAsync(q.counts, evs[i].counts, (size_t)n * 4, cudaMemcpyDeviceToHost,
                             s.stream);
             cudaMemcpyAsync(q.idx, evs[i].idx, (size_t)n * K * 4, cudaMemcpyDeviceToHost,
@@ -207,7 +219,7 @@ frnn_status frnn_serve_run(frnn_ctx* ctx, const frnn_request* reqs, int n_reqs, 
             // nothing to complete or admit right now: wait a little (for the
             // next arrival, or a completion on the GPU)
             const double wait = sched.next_arrival() - (now_s() - t0);
-            if (wait > 2e-4) std::this_thread::sleep_for(std::chrono::microseconds(100));
+            if (wait > 1e-4) std::this_thread::sleep_for(std::chrono::microseconds(20));
             else std::this_thread::yield();
         }
     }
