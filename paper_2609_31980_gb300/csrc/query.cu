@@ -56,6 +56,10 @@ namespace frnn {
 
 constexpr int kQueryWarps = 4;
 constexpr int kMaxNBuf = 4;
+// candidate streams per query: lanes q, q + G, q + 2G, ... (G = queries per
+// warp task) serve query q, each taking every kStreams-th candidate pair
+constexpr int kStreams = 32 / kTaskQueries;
+static_assert(kStreams * kTaskQueries == 32, "the lanes of a warp split evenly");
 constexpr uint32_t kFull = 0xffffffffu;
 constexpr int kListCap = 32;      // per-lane neighbour list in shared memory
 constexpr int kListStride = 33;   // entry e of lane l at e*33 + l: conflict-free both ways
@@ -211,9 +215,9 @@ __global__ void __launch_bounds__(kQueryWarps * 32, QCfg<D>::MINB) k_grid_query(
         carve_warp(smem + (size_t)warp * warp_smem_bytes(DP, TILEP, NB), DP, TILEP, NB);
     float* Ld = w.Ld;
     int32_t* Li = w.Li;
-    // lanes q and q + 16 serve the task's query q; lane q screens the stream's
-    // even candidate pairs, lane q + 16 the odd ones
-    const int qi = lane & (kTaskQueries - 1);
+    // lanes q, q + G, ... serve the task's query q (G = kTaskQueries); lane
+    // q + s G screens the candidate pairs p with p mod kStreams == s
+    const int qi = lane % kTaskQueries;
     const int sh = lane / kTaskQueries;
     if (lane == 0)
         for (int b = 0; b < NB; ++b) mbar_init(&w.bars[b], 1);
@@ -329,15 +333,15 @@ __global__ void __launch_bounds__(kQueryWarps * 32, QCfg<D>::MINB) k_grid_query(
                 }
                 __syncwarp();
             }
-            // eight candidate pairs per step, four per stream: their
-            // first-stage screens are independent, which hides the packed
-            // pipeline's latency
-            for (int p0 = 0; p0 < lenp; p0 += 8) {
+            // four candidate pairs per stream and step: their first-stage
+            // screens are independent, which hides the packed pipeline's
+            // latency
+            for (int p0 = 0; p0 < lenp; p0 += 4 * kStreams) {
                 uint64_t sg[4];
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
                     // pairs past the tile's end hold stale data: force them out
-                    const int p = p0 + 2 * j + sh;
+                    const int p = p0 + kStreams * j + sh;
                     const ulonglong2* cp = reinterpret_cast<const ulonglong2*>(tile + p * PAIRF);
                     uint64_t s2 = 0;
 #pragma unroll
@@ -349,7 +353,7 @@ __global__ void __launch_bounds__(kQueryWarps * 32, QCfg<D>::MINB) k_grid_query(
                 }
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
-                    const int p = p0 + 2 * j + sh;
+                    const int p = p0 + kStreams * j + sh;
                     const ulonglong2* cp = reinterpret_cast<const ulonglong2*>(tile + p * PAIRF);
                     uint64_t s2 = sg[j];
                     float s0, s1;
@@ -431,7 +435,7 @@ __global__ void __launch_bounds__(kQueryWarps * 32, QCfg<D>::MINB) k_grid_query(
                 int32_t orig = 0;
                 if (slot >= w.Rrs[L] && slot < w.Rre[L]) {
                     orig = a.rperm[slot];   // in flight with the coordinate loads
-                    const int qo_slot = task.qslot + (O & (kTaskQueries - 1));
+                    const int qo_slot = task.qslot + (O % kTaskQueries);
                     float acc = 0.f;
 #pragma unroll
                     for (int k = 0; k < D; ++k) {
@@ -454,30 +458,41 @@ __global__ void __launch_bounds__(kQueryWarps * 32, QCfg<D>::MINB) k_grid_query(
         // parallel (register bitonic network, see sort_list); rejected
         // entries (+inf) end up behind the kept ones
         sort_list(Ld + lane, Li + lane, kListStride, (act && !lost) ? cnt : 0, nullptr);
-        // lane q merges lane q + 16's sorted entries into its own list, from
-        // the back (its column has room for both when the query fits at all)
-        const int kB = __shfl_sync(kFull, kept, qi + kTaskQueries);
-        const bool lostB = __shfl_sync(kFull, lost, qi + kTaskQueries);
-        const int total = kept + kB;
-        const bool spill_q = act && (lost || lostB || total > kListCap);
+        // lane q merges the sorted entries of its query's other stream lanes
+        // into its own list, one after the other, each from the back (its
+        // column has room for all of them when the query fits at all)
+        int total = kept;
+        bool any_lost = lost;
+#pragma unroll
+        for (int st = 1; st < kStreams; ++st) {
+            total += __shfl_sync(kFull, kept, qi + st * kTaskQueries);
+            any_lost |= __shfl_sync(kFull, lost, qi + st * kTaskQueries);
+        }
+        const bool spill_q = act && (any_lost || total > kListCap);
         __syncwarp();
-        if (sh == 0 && act && !spill_q && kB > 0) {
-            const int cb = qi + kTaskQueries;
-            int i = kept - 1, j = kB - 1;
-            uint64_t ka = i >= 0 ? make_key(Ld[i * kListStride + qi], Li[i * kListStride + qi]) : 0;
-            uint64_t kb = make_key(Ld[j * kListStride + cb], Li[j * kListStride + cb]);
-            for (int k = total - 1; j >= 0; --k) {
-                if (i >= 0 && ka > kb) {
-                    Ld[k * kListStride + qi] = __uint_as_float((uint32_t)(ka >> 32));
-                    Li[k * kListStride + qi] = (int32_t)(uint32_t)ka;
-                    --i;
-                    if (i >= 0) ka = make_key(Ld[i * kListStride + qi], Li[i * kListStride + qi]);
-                } else {
-                    Ld[k * kListStride + qi] = __uint_as_float((uint32_t)(kb >> 32));
-                    Li[k * kListStride + qi] = (int32_t)(uint32_t)kb;
-                    --j;
-                    if (j >= 0) kb = make_key(Ld[j * kListStride + cb], Li[j * kListStride + cb]);
+        if (sh == 0 && act && !spill_q) {
+            int cur = kept;
+            for (int st = 1; st < kStreams; ++st) {
+                const int cb = qi + st * kTaskQueries;
+                const int kB = w.acc[cb];
+                if (kB == 0) continue;
+                int i = cur - 1, j = kB - 1;
+                uint64_t ka = i >= 0 ? make_key(Ld[i * kListStride + qi], Li[i * kListStride + qi]) : 0;
+                uint64_t kb = make_key(Ld[j * kListStride + cb], Li[j * kListStride + cb]);
+                for (int k = cur + kB - 1; j >= 0; --k) {
+                    if (i >= 0 && ka > kb) {
+                        Ld[k * kListStride + qi] = __uint_as_float((uint32_t)(ka >> 32));
+                        Li[k * kListStride + qi] = (int32_t)(uint32_t)ka;
+                        --i;
+                        if (i >= 0) ka = make_key(Ld[i * kListStride + qi], Li[i * kListStride + qi]);
+                    } else {
+                        Ld[k * kListStride + qi] = __uint_as_float((uint32_t)(kb >> 32));
+                        Li[k * kListStride + qi] = (int32_t)(uint32_t)kb;
+                        --j;
+                        if (j >= 0) kb = make_key(Ld[j * kListStride + cb], Li[j * kListStride + cb]);
+                    }
                 }
+                cur += kB;
             }
         }
         __syncwarp();
@@ -646,7 +661,7 @@ template <int D>
 static cudaError_t launch_grid_query_d(const QueryArgs& a, int exit_dims, int num_sms,
                                        cudaStream_t st) {
     using C = QCfg<D>;
-    static_assert(C::TILEP % 8 == 0, "eight candidate pairs per screening step");
+    static_assert(C::TILEP % (4 * kStreams) == 0, "whole screening steps per tile");
     static_assert(C::NBUF <= kMaxNBuf, "phase bits and barriers per warp");
     static_assert(warp_smem_bytes(C::DP, C::TILEP, C::NBUF) % 16 == 0 &&
                       (ring_region_floats(C::DP, C::TILEP, C::NBUF) * sizeof(float)) % 16 == 0 &&
