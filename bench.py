@@ -292,6 +292,9 @@ def run_ours(args):
     n_edges = int(off_np[-1])
     e2e_s = max_over_ranks(e2e_s, dev)
     e2e_c_s = max_over_ranks(e2e_c_s, dev)
+    if ws > 1:
+        # the remaining legs run on rank 0 alone and need no collective
+        torch.distributed.destroy_process_group()
     keep = np.arange(K)[None, :] < h_c.numpy()[:, None]
     ok_c = bool(np.array_equal(np.diff(off_np), h_c.numpy()) and
                 np.array_equal(ci_np, h_i.numpy()[keep]))
@@ -354,8 +357,6 @@ def run_ours(args):
         res["serving"] = run_serving(ctx, args)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         res["cpu_baseline"] = cpu_baseline(pts_np, r, K, args.cpu_rows)
-    if ws > 1:
-        torch.distributed.destroy_process_group()
     ctx.close()
     return res if rank == 0 else None
 
