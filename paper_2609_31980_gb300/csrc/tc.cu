@@ -674,9 +674,9 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_tc_query(TcArgs a) {
                                 if (sd <= r2) {
                                     ++n_acc;
                                     const int pos = atomicAdd(&s_cnt[r], 1);
-                                    if (pos < kTcList) {   // slot now, original index at the sort
+                                    if (pos < kTcList) {   // original index looked up here
                                         Ld[pos * kTcLStr + r] = sd;
-                                        Li[pos * kTcLStr + r] = cs;
+                                        Li[pos * kTcLStr + r] = a.rperm[cs];
                                     }
                                 }
                             }
@@ -700,7 +700,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_tc_query(TcArgs a) {
         const int cnt = s_cnt[row];
         const bool spill = active && cnt > kTcList;
         if (half == 0) {
-            sort_list(Ld + row, Li + row, kTcLStr, (active && !spill) ? cnt : 0, a.rperm);
+            sort_list(Ld + row, Li + row, kTcLStr, (active && !spill) ? cnt : 0, nullptr);
             if (active && !spill) counts[qorig] = min(cnt, Kout);
             if (active && spill && a.csr) counts[qorig] = kCsrSpill;   // counted by the selection kernel
             if (active && !spill && a.degree) a.degree[qorig] = cnt;
