@@ -321,6 +321,7 @@ def run_ours(args):
                    "cell_mult": ctx.get_option(frnn.FRNN_OPT_CELL_MULT),
                    "exit_dims": ctx.get_option(frnn.FRNN_OPT_EXIT_DIMS),
                    "grid_naxes": ctx.get_option(frnn.FRNN_OPT_GRID_NAXES),
+                   "gridded_axes": (ctx.get_option(frnn.FRNN_OPT_GRID_NAXES) or min(D, 4)),
                    "self_query": True, "l2": "flushed between timed steps (256 MB write)",
                    "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
         "pairs_per_s": whole_job_rate(pairs, args.steps, ws, total_ms),

@@ -273,7 +273,8 @@ frnn_status frnn_autotune(frnn_ctx* ctx, const float* refs, int64_t N, int D, fl
 /* Tunable options (none changes results, only speed). */
 typedef enum frnn_option {
     FRNN_OPT_CELL_MULT = 1,   /* m in {1, 2}: cell edge ~ r/m, search +-m cells;
-                                 0 (default): autotuned, else 1 */
+                                 0 (default): autotuned, else 2 on grids of at
+                                 most three axes and 1 on four-axis grids */
     FRNN_OPT_GRID_AXES = 2,   /* which coordinates are gridded: 0 the last ones,
                                  1 the widest ones (count: FRNN_OPT_GRID_NAXES) */
     FRNN_OPT_EXIT_DIMS = 3,   /* dims summed before the warp-uniform early exit
