@@ -90,6 +90,8 @@ __device__ __forceinline__ int point_cell(const float* p, const EventHdr& h) {
 
 __global__ void k_init(int32_t* counts, int64_t L, int32_t* bbox, int E, int32_t* scalars,
                        int32_t bb_min_init, int32_t bb_max_init) {
+    pdl_trigger();
+    pdl_wait();
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t j = i; j < L; j += stride) counts[j] = 0;
@@ -109,6 +111,8 @@ __global__ void __launch_bounds__(kBuildPtsPerBlock) k_bbox(const EventHdr* hdr,
                                                             const int32_t* blk_start, int E,
                                                             int D, int32_t* bbox,
                                                             int32_t* status) {
+    pdl_trigger();
+    pdl_wait();
     extern __shared__ float sm[];
     __shared__ float red_mn[kMaxD][kBuildPtsPerBlock / 32];
     __shared__ float red_mx[kMaxD][kBuildPtsPerBlock / 32];
@@ -187,17 +191,28 @@ static_assert(kBBoxCopies == 32, "one copy per lane when the copies are combined
 __global__ void __launch_bounds__(256) k_params(EventHdr* hdr, int E, int D, const int32_t* bbox,
                                                float r, int m, int axes_mode, int naxes_req,
                                                int32_t* counts) {
+    pdl_trigger();
+    pdl_wait();
     const int e = blockIdx.x;   // one CTA per event: its warps combine the box copies
     __shared__ int32_t bb[kBBoxStride];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int k = warp; k < kBBoxStride; k += 8) {
-        // lane c holds copy c of entry k; a warp reduction combines them
-        int32_t v = bbox[((int64_t)e * kBBoxCopies + lane) * kBBoxStride + k];
+    // lane c holds copy c of entry k; a warp reduction combines them (all of a
+    // warp's loads are issued before the first reduction)
+    constexpr int kPer = (kBBoxStride + 7) / 8;
+    int32_t v[kPer];
+#pragma unroll
+    for (int i = 0; i < kPer; ++i) {
+        const int k = warp + 8 * i;
+        v[i] = k < kBBoxStride ? bbox[((int64_t)e * kBBoxCopies + lane) * kBBoxStride + k] : 0;
+    }
+#pragma unroll
+    for (int i = 0; i < kPer; ++i) {
+        const int k = warp + 8 * i;
         for (int o = 16; o > 0; o >>= 1) {
-            const int32_t x = __shfl_xor_sync(0xffffffffu, v, o);
-            v = k < 16 ? min(v, x) : (k < 32 ? max(v, x) : (v | x));
+            const int32_t x = __shfl_xor_sync(0xffffffffu, v[i], o);
+            v[i] = k < 16 ? min(v[i], x) : (k < 32 ? max(v[i], x) : (v[i] | x));
         }
-        if (lane == 0) bb[k] = v;
+        if (lane == 0 && k < kBBoxStride) bb[k] = v[i];
     }
     __syncthreads();
     if (threadIdx.x != 0) return;
@@ -306,6 +321,8 @@ __global__ void __launch_bounds__(256) k_params(EventHdr* hdr, int E, int D, con
 
 // Cross-set binning: take the reference grid's parameters for each event.
 __global__ void k_copy_params(EventHdr* dst, const EventHdr* src, int E, int32_t* counts) {
+    pdl_trigger();
+    pdl_wait();
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= E) return;
     EventHdr& d = dst[e];
@@ -332,6 +349,8 @@ __global__ void __launch_bounds__(kBuildPtsPerBlock) k_cellid(const EventHdr* hd
                                                               int D, int32_t* counts,
                                                               int32_t* cid, int32_t* rnk,
                                                               int check_finite, int32_t* status) {
+    pdl_trigger();
+    pdl_wait();
     extern __shared__ float sm[];
     const int e = find_event(blk_start, E, blockIdx.x);
     const EventHdr& h = hdr[e];
@@ -361,6 +380,8 @@ __global__ void __launch_bounds__(kBuildPtsPerBlock) k_scatter(const EventHdr* h
                                                                const int32_t* cid,
                                                                const int32_t* rnk, float* pts,
                                                                int32_t* perm, int32_t* cell) {
+    pdl_trigger();
+    pdl_wait();
     const int e = find_event(blk_start, E, blockIdx.x);
     const EventHdr& h = hdr[e];
     const int64_t p0 = (int64_t)(blockIdx.x - blk_start[e]) * kBuildPtsPerBlock;
@@ -386,6 +407,8 @@ __global__ void __launch_bounds__(kBuildPtsPerBlock) k_scatter(const EventHdr* h
 // without a point (an odd event's padding) gets NaN: never within any radius.
 __global__ void __launch_bounds__(256) k_pack(const EventHdr* hdr, int E, int64_t npairs, int D,
                                               int DP, const int32_t* perm, float* pts) {
+    pdl_trigger();
+    pdl_wait();
     const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= npairs) return;
     // event of this pair: events occupy pair-aligned slot ranges
@@ -445,6 +468,8 @@ __device__ __forceinline__ void row_slots(const EventHdr& h, const int32_t* csta
 
 __global__ void k_rowtasks(const EventHdr* hdr, const int64_t* cell_off, int E, int64_t L,
                            const int32_t* cstart, int32_t* rtask, int W, int A) {
+    pdl_trigger();
+    pdl_wait();
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= L) return;
     const int e = find_event64(cell_off, E, i);
@@ -466,6 +491,8 @@ __global__ void k_rowtasks(const EventHdr* hdr, const int64_t* cell_off, int E, 
 __global__ void k_emit(const EventHdr* hdr, const int64_t* cell_off, int E, int64_t L,
                        const int32_t* cstart, const int32_t* rtask_start,
                        const int32_t* rtask_count_src, Task* tasks, int W, int A) {
+    pdl_trigger();
+    pdl_wait();
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= L) return;
     const int e = find_event64(cell_off, E, i);
@@ -492,9 +519,9 @@ __global__ void k_emit(const EventHdr* hdr, const int64_t* cell_off, int E, int6
 
 void enqueue_tasks(GridBufs& g, int W, int A, Task* out, int32_t* count_out, cudaStream_t st) {
     const unsigned nb = (unsigned)std::max<int64_t>(1, ceil_div(g.L, 256));
-    k_rowtasks<<<nb, 256, 0, st>>>(g.hdr, g.cell_off, g.E, g.L, g.cstart, g.rtask, W, A);
+    launch_pdl(k_rowtasks, dim3(nb), dim3(256), 0, st, g.hdr, g.cell_off, g.E, g.L, g.cstart, g.rtask, W, A);
     enqueue_scan(g.rtask, g.L, g.parts, count_out, st);
-    k_emit<<<nb, 256, 0, st>>>(g.hdr, g.cell_off, g.E, g.L, g.cstart, g.rtask, count_out, out, W,
+    launch_pdl(k_emit, dim3(nb), dim3(256), 0, st, g.hdr, g.cell_off, g.E, g.L, g.cstart, g.rtask, count_out, out, W,
                                A);
 }
 
@@ -535,6 +562,8 @@ __device__ __forceinline__ int32_t block_exclusive_scan(int32_t v, int32_t* warp
 
 __global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const int32_t* data, int64_t n,
                                                               int32_t* parts) {
+    pdl_trigger();
+    pdl_wait();
     __shared__ int32_t red[kScanThreads / 32];
     const int64_t base = (int64_t)blockIdx.x * kScanChunk;
     int32_t s = 0;
@@ -586,6 +615,8 @@ __device__ void scan_chunk(int32_t* data, int64_t n, int64_t base, int32_t offse
 
 __global__ void __launch_bounds__(kScanThreads) k_scan_single(int32_t* data, int64_t n,
                                                               int32_t* total) {
+    pdl_trigger();
+    pdl_wait();
     scan_chunk(data, n, 0, 0, total);
 }
 
@@ -598,6 +629,8 @@ constexpr int kScanSumParts = 512;
 __global__ void __launch_bounds__(kScanThreads) k_scan_down(int32_t* data, int64_t n,
                                                             const int32_t* parts, int32_t* total,
                                                             int summed) {
+    pdl_trigger();
+    pdl_wait();
     if (summed) {
         scan_chunk(data, n, (int64_t)blockIdx.x * kScanChunk, parts[blockIdx.x], nullptr);
         return;
@@ -623,6 +656,8 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_down(int32_t* data, int64
 // a running carry; writes the grand total.
 __global__ void __launch_bounds__(kScanThreads) k_scan_parts(int32_t* parts, int64_t nb,
                                                              int32_t* total) {
+    pdl_trigger();
+    pdl_wait();
     __shared__ int32_t carry;
     if (threadIdx.x == 0) carry = 0;
     __syncthreads();
@@ -642,15 +677,15 @@ int64_t scan_parts_needed(int64_t n) { return std::max<int64_t>(1, ceil_div(n, k
 void enqueue_scan(int32_t* data, int64_t n, int32_t* parts, int32_t* total, cudaStream_t st) {
     const int64_t nb = scan_parts_needed(n);
     if (nb == 1) {
-        k_scan_single<<<1, kScanThreads, 0, st>>>(data, n, total);
+        launch_pdl(k_scan_single, dim3(1), dim3(kScanThreads), 0, st, data, n, total);
         return;
     }
-    k_scan_reduce<<<(unsigned)nb, kScanThreads, 0, st>>>(data, n, parts);
+    launch_pdl(k_scan_reduce, dim3((unsigned)nb), dim3(kScanThreads), 0, st, data, n, parts);
     if (nb <= kScanSumParts) {
-        k_scan_down<<<(unsigned)nb, kScanThreads, 0, st>>>(data, n, parts, total, 0);
+        launch_pdl(k_scan_down, dim3((unsigned)nb), dim3(kScanThreads), 0, st, data, n, parts, total, 0);
     } else {
-        k_scan_parts<<<1, kScanThreads, 0, st>>>(parts, nb, total);
-        k_scan_down<<<(unsigned)nb, kScanThreads, 0, st>>>(data, n, parts, total, 1);
+        launch_pdl(k_scan_parts, dim3(1), dim3(kScanThreads), 0, st, parts, nb, total);
+        launch_pdl(k_scan_down, dim3((unsigned)nb), dim3(kScanThreads), 0, st, data, n, parts, total, 1);
     }
 }
 
@@ -824,24 +859,24 @@ frnn_status enqueue_build(GridBufs& g, const float* const* refs, const BuildOpts
     const int32_t bbmin = host_float_to_ordered(INFINITY);
     const int32_t bbmax = host_float_to_ordered(-INFINITY);
     const int64_t init_n = std::max<int64_t>(g.L, (int64_t)E * kBBoxCopies * kBBoxStride);
-    k_init<<<std::min<unsigned>(blocks_for(init_n, 256), 4096), 256, 0, st>>>(
+    launch_pdl(k_init, dim3(std::min<unsigned>(blocks_for(init_n, 256), 4096)), dim3(256), 0, st, 
         g.cstart, g.L, g.bbox, E, g.scalars, bbmin, bbmax);
     const size_t smem_pts = sizeof(float) * kBuildPtsPerBlock * D;
     if (params_from) {
-        k_copy_params<<<blocks_for(E, 128), 128, 0, st>>>(g.hdr, params_from->hdr, E, g.cstart);
+        launch_pdl(k_copy_params, dim3(blocks_for(E, 128)), dim3(128), 0, st, g.hdr, params_from->hdr, E, g.cstart);
     } else {
-        k_bbox<<<(unsigned)g.nblk, kBuildPtsPerBlock, smem_pts, st>>>(g.hdr, g.blk_start, E, D,
+        launch_pdl(k_bbox, dim3((unsigned)g.nblk), dim3(kBuildPtsPerBlock), smem_pts, st, g.hdr, g.blk_start, E, D,
                                                                      g.bbox, d_status);
-        k_params<<<(unsigned)E, 256, 0, st>>>(g.hdr, E, D, g.bbox, o.r, o.m, o.axes_mode, o.naxes,
+        launch_pdl(k_params, dim3((unsigned)E), dim3(256), 0, st, g.hdr, E, D, g.bbox, o.r, o.m, o.axes_mode, o.naxes,
                                                       g.cstart);
     }
-    k_cellid<<<(unsigned)g.nblk, kBuildPtsPerBlock, smem_pts, st>>>(
+    launch_pdl(k_cellid, dim3((unsigned)g.nblk), dim3(kBuildPtsPerBlock), smem_pts, st, 
         g.hdr, g.blk_start, E, D, g.cstart, g.cid, g.rnk, params_from ? 1 : 0, d_status);
     enqueue_scan(g.cstart, g.L, g.parts, g.scalars + kScCellTotal, st);
-    k_scatter<<<(unsigned)g.nblk, kBuildPtsPerBlock, 0, st>>>(
+    launch_pdl(k_scatter, dim3((unsigned)g.nblk), dim3(kBuildPtsPerBlock), 0, st, 
         g.hdr, g.blk_start, E, D, g.DP, g.cstart, g.cid, g.rnk, g.pts, g.perm, g.cell);
     if (g.n_total > 0)
-        k_pack<<<(unsigned)ceil_div(g.n_total / 2, 256), 256, 0, st>>>(g.hdr, E, g.n_total / 2, D,
+        launch_pdl(k_pack, dim3((unsigned)ceil_div(g.n_total / 2, 256)), dim3(256), 0, st, g.hdr, E, g.n_total / 2, D,
                                                                        g.DP, g.perm, g.pts);
     enqueue_tasks(g, kTaskQueries, 1, g.tasks, g.scalars + kScNTasks, st);
     g.tc_ready = false;   // tensor-core operands describe the previous contents
@@ -862,20 +897,20 @@ frnn_status enqueue_build_resident(GridBufs& g, const BuildOpts& o, int32_t* d_s
     const int32_t bbmin = host_float_to_ordered(INFINITY);
     const int32_t bbmax = host_float_to_ordered(-INFINITY);
     const int64_t init_n = std::max<int64_t>(g.L, (int64_t)E * kBBoxCopies * kBBoxStride);
-    k_init<<<std::min<unsigned>(blocks_for(init_n, 256), 4096), 256, 0, st>>>(
+    launch_pdl(k_init, dim3(std::min<unsigned>(blocks_for(init_n, 256), 4096)), dim3(256), 0, st, 
         g.cstart, g.L, g.bbox, E, g.scalars, bbmin, bbmax);
     const size_t smem_pts = sizeof(float) * kBuildPtsPerBlock * D;
-    k_bbox<<<(unsigned)g.nblk, kBuildPtsPerBlock, smem_pts, st>>>(g.hdr, g.blk_start, E, D,
+    launch_pdl(k_bbox, dim3((unsigned)g.nblk), dim3(kBuildPtsPerBlock), smem_pts, st, g.hdr, g.blk_start, E, D,
                                                                  g.bbox, d_status);
-    k_params<<<(unsigned)E, 256, 0, st>>>(g.hdr, E, D, g.bbox, o.r, o.m, o.axes_mode, o.naxes,
+    launch_pdl(k_params, dim3((unsigned)E), dim3(256), 0, st, g.hdr, E, D, g.bbox, o.r, o.m, o.axes_mode, o.naxes,
                                                   g.cstart);
-    k_cellid<<<(unsigned)g.nblk, kBuildPtsPerBlock, smem_pts, st>>>(
+    launch_pdl(k_cellid, dim3((unsigned)g.nblk), dim3(kBuildPtsPerBlock), smem_pts, st, 
         g.hdr, g.blk_start, E, D, g.cstart, g.cid, g.rnk, 0, d_status);
     enqueue_scan(g.cstart, g.L, g.parts, g.scalars + kScCellTotal, st);
-    k_scatter<<<(unsigned)g.nblk, kBuildPtsPerBlock, 0, st>>>(
+    launch_pdl(k_scatter, dim3((unsigned)g.nblk), dim3(kBuildPtsPerBlock), 0, st, 
         g.hdr, g.blk_start, E, D, g.DP, g.cstart, g.cid, g.rnk, g.pts, g.perm, g.cell);
     if (g.n_total > 0)
-        k_pack<<<(unsigned)ceil_div(g.n_total / 2, 256), 256, 0, st>>>(g.hdr, E, g.n_total / 2, D,
+        launch_pdl(k_pack, dim3((unsigned)ceil_div(g.n_total / 2, 256)), dim3(256), 0, st, g.hdr, E, g.n_total / 2, D,
                                                                        g.DP, g.perm, g.pts);
     enqueue_tasks(g, kTaskQueries, 1, g.tasks, g.scalars + kScNTasks, st);
     cudaError_t ce = cudaGetLastError();

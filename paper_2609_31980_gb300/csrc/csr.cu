@@ -61,6 +61,8 @@ __device__ int64_t block_scan64(int64_t v, int64_t* warp_tot, int64_t* total) {
 // per chunk of kCsrChunk counts: their sum
 __global__ void __launch_bounds__(kCsrThreads) k_csr_reduce(const int32_t* cnt, int64_t M,
                                                             int64_t* parts) {
+    pdl_trigger();
+    pdl_wait();
     __shared__ int64_t red[kCsrThreads / 32];
     const int64_t base = (int64_t)blockIdx.x * kCsrChunk;
     int64_t s = 0;
@@ -78,6 +80,8 @@ __global__ void __launch_bounds__(kCsrThreads) k_csr_reduce(const int32_t* cnt, 
 // one block: exclusive scan of the nb chunk sums in place, walking them in
 // blocks of kCsrThreads with a running carry
 __global__ void __launch_bounds__(kCsrThreads) k_csr_scan_parts(int64_t* parts, int64_t nb) {
+    pdl_trigger();
+    pdl_wait();
     __shared__ int64_t warp_tot[kCsrThreads / 32];
     __shared__ int64_t tot;
     int64_t carry = 0;
@@ -96,6 +100,8 @@ __global__ void __launch_bounds__(kCsrThreads) k_csr_scan_parts(int64_t* parts, 
 // the last chunk also writes offsets[M]
 __global__ void __launch_bounds__(kCsrThreads) k_csr_down(const int32_t* cnt, int64_t M,
                                                           const int64_t* parts, int64_t* offsets) {
+    pdl_trigger();
+    pdl_wait();
     __shared__ int64_t warp_tot[kCsrThreads / 32];
     __shared__ int64_t tot;
     const int64_t base = (int64_t)blockIdx.x * kCsrChunk + (int64_t)threadIdx.x * kCsrItems;
@@ -125,6 +131,8 @@ __global__ void __launch_bounds__(kCsrThreads) k_csr_down(const int32_t* cnt, in
 __global__ void __launch_bounds__(256) k_csr_gather(const int32_t* cnt, const int64_t* offsets,
                                                     const int32_t* sidx, const float* sd2,
                                                     int64_t M, int32_t* idx, float* dist2) {
+    pdl_trigger();
+    pdl_wait();
     const int lane = threadIdx.x & 31;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w * 32 < M; w += nw) {
@@ -166,10 +174,10 @@ void enqueue_csr_offsets(const int32_t* cnt, int64_t M, int64_t* parts, int64_t*
                          cudaStream_t st) {
     const int64_t nb = std::max<int64_t>(1, ceil_div(M, kCsrChunk));
     if (nb > 1) {
-        k_csr_reduce<<<(unsigned)nb, kCsrThreads, 0, st>>>(cnt, M, parts);
-        k_csr_scan_parts<<<1, kCsrThreads, 0, st>>>(parts, nb);
+        launch_pdl(k_csr_reduce, dim3((unsigned)nb), dim3(kCsrThreads), 0, st, cnt, M, parts);
+        launch_pdl(k_csr_scan_parts, dim3(1), dim3(kCsrThreads), 0, st, parts, nb);
     }
-    k_csr_down<<<(unsigned)nb, kCsrThreads, 0, st>>>(cnt, M, nb > 1 ? parts : nullptr, offsets);
+    launch_pdl(k_csr_down, dim3((unsigned)nb), dim3(kCsrThreads), 0, st, cnt, M, nb > 1 ? parts : nullptr, offsets);
 }
 
 int64_t csr_parts_needed(int64_t M) { return std::max<int64_t>(1, ceil_div(M, kCsrChunk)); }
@@ -180,7 +188,7 @@ void enqueue_csr_gather(const int32_t* cnt, const int64_t* offsets, const int32_
     if (M <= 0) return;
     const int64_t warps = ceil_div(M, 32);
     const int64_t blocks = std::min<int64_t>(ceil_div(warps, 8), (int64_t)num_sms * 8);
-    k_csr_gather<<<(unsigned)std::max<int64_t>(blocks, 1), 256, 0, st>>>(cnt, offsets, sidx, sd2, M,
+    launch_pdl(k_csr_gather, dim3((unsigned)std::max<int64_t>(blocks, 1)), dim3(256), 0, st, cnt, offsets, sidx, sd2, M,
                                                                          idx, dist2);
 }
 

@@ -163,6 +163,23 @@ frnn_status enqueue_overflow(const QueryArgs& a, int num_sms, cudaStream_t st, s
 
 // Context helpers for the serving loop (defined with the context, api.cu).
 void ctx_copy_tuning(frnn_ctx* dst, const frnn_ctx* src);
+// Launch a kernel with programmatic stream serialization (see pdl_wait).
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                              cudaStream_t st, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
+}
+
 // Device address of a page-locked host buffer, or NULL (pageable / unknown).
 void* mapped_host(const void* p);
 // diag.cu: one warp waits (bounded by limit_ns) on a barrier nothing completes

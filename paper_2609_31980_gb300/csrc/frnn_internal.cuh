@@ -223,6 +223,18 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
     return false;
 }
 
+// Programmatic dependent launch.  A kernel launched with programmatic stream
+// serialization (launch_pdl) may be scheduled while its predecessor on the
+// stream is still running: pdl_trigger() lets the successor launch,
+// pdl_wait() blocks until the predecessor grid has completed and its memory
+// writes are visible.  Every kernel of the build and query chain calls both
+// before touching its inputs; for a kernel launched the ordinary way they do
+// nothing.  This hides the launch gap between the chain's short kernels.
+__device__ __forceinline__ void pdl_trigger() {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 // Ordered-int encoding of float for atomic min/max (monotone in float order).
 __device__ __forceinline__ int32_t float_to_ordered(float f) {
     int32_t i = __float_as_int(f);

@@ -204,6 +204,8 @@ __device__ __forceinline__ void issue_tile(const WarpSmem& w, int t, int b, int 
 
 template <int D, int EXIT>
 __global__ void __launch_bounds__(kQueryWarps * 32, QCfg<D>::MINB) k_grid_query(QueryArgs a) {
+    pdl_trigger();
+    pdl_wait();
     using C = QCfg<D>;
     constexpr int DP = C::DP;
     constexpr int TILEP = C::TILEP;
@@ -563,6 +565,8 @@ __device__ void smem_bitonic(uint64_t* buf, int n) {
 }
 
 __global__ void __launch_bounds__(kOvfWarps * 32) k_overflow(QueryArgs a, int cap) {
+    pdl_trigger();
+    pdl_wait();
     extern __shared__ __align__(16) unsigned char smem_o[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     uint64_t* buf = reinterpret_cast<uint64_t*>(smem_o) + (size_t)warp * cap;
@@ -684,7 +688,7 @@ static cudaError_t launch_grid_query_d(const QueryArgs& a, int exit_dims, int nu
     ce = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kQueryWarps * 32, smem);
     if (ce != cudaSuccess) return ce;
     per_sm = std::max(per_sm, 1);
-    kern<<<num_sms * per_sm, kQueryWarps * 32, smem, st>>>(a);
+    launch_pdl(kern, dim3(num_sms * per_sm), dim3(kQueryWarps * 32), smem, st, a);
     return cudaGetLastError();
 }
 
@@ -779,7 +783,7 @@ frnn_status enqueue_overflow(const QueryArgs& a, int num_sms, cudaStream_t st, s
     cudaError_t ce =
         cudaFuncSetAttribute(k_overflow, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)osmem);
     if (ce == cudaSuccess) {
-        k_overflow<<<num_sms, kOvfWarps * 32, osmem, st>>>(a, cap);
+        launch_pdl(k_overflow, dim3(num_sms), dim3(kOvfWarps * 32), osmem, st, a, cap);
         ce = cudaGetLastError();
     }
     if (ce != cudaSuccess) {
