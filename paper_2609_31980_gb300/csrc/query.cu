@@ -68,18 +68,16 @@ static_assert(kListCap <= kCsrStageW, "a staged compact row holds a whole list")
 template <int D>
 struct QCfg {
     static constexpr int DP = padded_dim(D);
-    // candidate pairs per tile (1 KB per buffer up to D = 8, else about
-    // 2 KB) and CTAs per SM: up to D = 8 the smaller ring (shared with the
-    // list distances) lets six CTAs (24 warps, 80 registers) share an SM,
-    // which the latency-bound scan prefers (measured at 300k x 8: 0.311 ms
-    // with six, 0.321 with five, 0.349 with four CTAs and 2 KB tiles); above,
-    // the longer tiles win (0.633 vs 0.686 ms at 500k x 12)
-    static constexpr int TILEP = DP == 4 ? 32 : (DP == 8 ? 16 : (DP == 12 ? 24 : 16));
+    // candidate pairs per tile, ring buffers and CTAs per SM.  The ring (two
+    // tiles) doubles as the list distances once the tiles are consumed, so up
+    // to D = 8 a warp needs 9 KB of shared memory and six CTAs (24 warps, 80
+    // registers) share an SM, which the latency-bound scan prefers.  Measured
+    // at 300k x 8: 2 KB tiles with six CTAs 0.292 ms, 1 KB tiles 0.310 (and
+    // 0.321 with five CTAs), 3 KB tiles with five CTAs 0.298; at 500k x 12:
+    // 3 KB tiles 0.493 ms, 2.25 KB 0.512, 1.5 KB 0.548.
+    static constexpr int TILEP = DP == 4 ? 64 : (DP == 8 ? 32 : (DP == 12 ? 32 : 16));
     static constexpr int MINB = DP <= 8 ? 6 : 4;
-    // ring buffers: up to D = 8 four 1 KB tiles (three in flight; the ring
-    // doubles as the list distances afterwards, so the warp's shared memory
-    // stays small enough for five CTAs per SM), else two
-    static constexpr int NBUF = DP <= 8 ? 4 : 2;
+    static constexpr int NBUF = 2;
     // default vote point (measured: 2 and 3 tie at D = 8, 3 is best at D = 12)
     static constexpr int EXIT = D <= 4 ? D : (D >= 10 ? 3 : 2);
 };
