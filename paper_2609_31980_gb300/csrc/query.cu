@@ -40,10 +40,10 @@
 //     membership and gives the distance (the paper's "conservative screening
 //     and canonical-order recomputation", Sec. 4.2); the original index is
 //     looked up only for the kept entries (the deferred lookup, Table 3);
-//   * every lane sorts its own list by (d2, index) with a register bitonic
-//     network, lane q merges lane q + 16's sorted list into its own, keeps the
-//     first K (count = min(degree, K)), and the warp writes the rows coalesced
-//     with their padding.  Lists longer than 32 (never in
+//   * for each query the warp loads its lanes' entries (at most 32, one per
+//     lane), sorts them by (d2, index) with a bitonic network across the lanes
+//     (shuffles), and writes the first K (count = min(degree, K)) coalesced,
+//     with the padding.  Lists longer than 32 (never in
 //     the tracking-like workloads) go to an exact selection kernel, keeping
 //     results exact for dense inputs (the paper's Sec. 5 caveat on heap-free
 //     top-K).
@@ -454,54 +454,21 @@ __global__ void __launch_bounds__(kQueryWarps * 32, QCfg<D>::MINB) k_grid_query(
         }
         __syncwarp();
         const int kept = w.acc[lane];
-        // each lane sorts its own list by (d2, original index), all lanes in
-        // parallel (register bitonic network, see sort_list); rejected
-        // entries (+inf) end up behind the kept ones
-        sort_list(Ld + lane, Li + lane, kListStride, (act && !lost) ? cnt : 0, nullptr);
-        // lane q merges the sorted entries of its query's other stream lanes
-        // into its own list, one after the other, each from the back (its
-        // column has room for all of them when the query fits at all)
-        int total = kept;
-        bool any_lost = lost;
+        // per query: its lanes' entries together (rejected ones carry +inf)
+        int cnt_q = cnt, kept_q = kept;
+        bool lost_q = lost;
 #pragma unroll
         for (int st = 1; st < kStreams; ++st) {
-            total += __shfl_sync(kFull, kept, qi + st * kTaskQueries);
-            any_lost |= __shfl_sync(kFull, lost, qi + st * kTaskQueries);
+            cnt_q += __shfl_sync(kFull, cnt, qi + st * kTaskQueries);
+            kept_q += __shfl_sync(kFull, kept, qi + st * kTaskQueries);
+            lost_q |= __shfl_sync(kFull, lost, qi + st * kTaskQueries);
         }
-        const bool spill_q = act && (any_lost || total > kListCap);
-        __syncwarp();
-        if (sh == 0 && act && !spill_q) {
-            int cur = kept;
-            for (int st = 1; st < kStreams; ++st) {
-                const int cb = qi + st * kTaskQueries;
-                const int kB = w.acc[cb];
-                if (kB == 0) continue;
-                int i = cur - 1, j = kB - 1;
-                uint64_t ka = i >= 0 ? make_key(Ld[i * kListStride + qi], Li[i * kListStride + qi]) : 0;
-                uint64_t kb = make_key(Ld[j * kListStride + cb], Li[j * kListStride + cb]);
-                for (int k = cur + kB - 1; j >= 0; --k) {
-                    if (i >= 0 && ka > kb) {
-                        Ld[k * kListStride + qi] = __uint_as_float((uint32_t)(ka >> 32));
-                        Li[k * kListStride + qi] = (int32_t)(uint32_t)ka;
-                        --i;
-                        if (i >= 0) ka = make_key(Ld[i * kListStride + qi], Li[i * kListStride + qi]);
-                    } else {
-                        Ld[k * kListStride + qi] = __uint_as_float((uint32_t)(kb >> 32));
-                        Li[k * kListStride + qi] = (int32_t)(uint32_t)kb;
-                        --j;
-                        if (j >= 0) kb = make_key(Ld[j * kListStride + cb], Li[j * kListStride + cb]);
-                    }
-                }
-                cur += kB;
-            }
-        }
-        __syncwarp();
-        const bool spill = sh == 0 && spill_q;
-        if (sh == 0 && act && !spill) counts[qorig] = min(total, K);
+        // more than 32 entries: the exact selection kernel finishes the row
+        const bool spill = sh == 0 && act && (lost_q || cnt_q > kListCap);
+        if (sh == 0 && act && !spill) counts[qorig] = min(kept_q, K);
         if (spill && a.csr) counts[qorig] = kCsrSpill;   // counted by the selection kernel
-        if (sh == 0 && act && !spill && a.degree) a.degree[qorig] = total;
+        if (sh == 0 && act && !spill && a.degree) a.degree[qorig] = kept_q;
         if (spill) {
-            // longer than the list: the exact selection kernel finishes this row
             const int pos = atomicAdd(a.ovf_count, 1);
             if (pos < a.ovf_cap) {
                 a.ovf[pos].qslot = qs;
@@ -510,22 +477,48 @@ __global__ void __launch_bounds__(kQueryWarps * 32, QCfg<D>::MINB) k_grid_query(
                 atomicOr(a.status, kStatusCapacity);
             }
         }
-        __syncwarp();
-        // coalesced row writes: one query row at a time across the warp
-        // (compact output: the row's entries only, into its staging row)
+        // one query row at a time: lane l takes entry l of the query's lists,
+        // the warp sorts the 32 keys (d2 bits << 32 | original index; unused
+        // lanes hold the largest key) with a bitonic network across lanes, and
+        // lane l writes position l of the row (coalesced), then the padding
         const unsigned spill_mask = __ballot_sync(kFull, spill);
         const int rstride = a.csr ? kCsrStageW : K;
         for (int ql = 0; ql < task.nq; ++ql) {
             if (spill_mask & (1u << ql)) continue;
-            const int c = min(__shfl_sync(kFull, total, ql), K);
+            uint64_t key = ~0ull;
+            int base = 0;
+#pragma unroll
+            for (int st = 0; st < kStreams; ++st) {
+                const int col = ql + st * kTaskQueries;
+                const int c = __shfl_sync(kFull, cnt, col);
+                if (lane >= base && lane < base + c)
+                    key = make_key(Ld[(lane - base) * kListStride + col],
+                                   Li[(lane - base) * kListStride + col]);
+                base += c;
+            }
+#pragma unroll
+            for (int k2 = 2; k2 <= 32; k2 <<= 1) {
+#pragma unroll
+                for (int j = k2 >> 1; j > 0; j >>= 1) {
+                    const uint64_t other = __shfl_xor_sync(kFull, key, j);
+                    const bool take_min = ((lane & j) == 0) == ((lane & k2) == 0);
+                    key = take_min ? (other < key ? other : key) : (other > key ? other : key);
+                }
+            }
+            const int c = min(__shfl_sync(kFull, kept_q, ql), K);
             const int qo = __shfl_sync(kFull, qorig, ql);
             int32_t* irow = oidx + (int64_t)qo * rstride;
             float* drow = od2 + (int64_t)qo * rstride;
-            const int wlen = a.csr ? c : K;
-            for (int e = lane; e < wlen; e += 32) {
-                const bool real = e < c;
-                irow[e] = real ? Li[e * kListStride + ql] : -1;
-                drow[e] = real ? Ld[e * kListStride + ql] : INFINITY;
+            if (lane < c) {
+                irow[lane] = (int32_t)(uint32_t)key;
+                drow[lane] = __uint_as_float((uint32_t)(key >> 32));
+            } else if (!a.csr && lane < K) {
+                irow[lane] = -1;
+                drow[lane] = INFINITY;
+            }
+            for (int e = 32 + lane; e < K && !a.csr; e += 32) {
+                irow[e] = -1;
+                drow[e] = INFINITY;
             }
         }
         __syncwarp();
