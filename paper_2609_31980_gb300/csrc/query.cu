@@ -61,22 +61,27 @@ constexpr int kMaxNBuf = 4;
 constexpr int kStreams = 32 / kTaskQueries;
 static_assert(kStreams * kTaskQueries == 32, "the lanes of a warp split evenly");
 constexpr uint32_t kFull = 0xffffffffu;
-constexpr int kListCap = 32;      // per-lane neighbour list in shared memory
+// per-lane list in shared memory: a lane holds about half of its query's
+// entries, so 24 rarely overflows (an overflow only sends the row to the
+// selection kernel) and the smaller lists let seven CTAs share an SM
+constexpr int kListCap = 24;
+constexpr int kRowCap = 32;       // entries of one query sorted across the warp (one per lane)
 constexpr int kListStride = 33;   // entry e of lane l at e*33 + l: conflict-free both ways
-static_assert(kListCap <= kCsrStageW, "a staged compact row holds a whole list");
+static_assert(kRowCap <= kCsrStageW, "a staged compact row holds a whole row");
 
 template <int D>
 struct QCfg {
     static constexpr int DP = padded_dim(D);
     // candidate pairs per tile, ring buffers and CTAs per SM.  The ring (two
     // tiles) doubles as the list distances once the tiles are consumed, so up
-    // to D = 8 a warp needs 9 KB of shared memory and six CTAs (24 warps, 80
-    // registers) share an SM, which the latency-bound scan prefers.  Measured
-    // at 300k x 8: 2 KB tiles with six CTAs 0.292 ms, 1 KB tiles 0.310 (and
-    // 0.321 with five CTAs), 3 KB tiles with five CTAs 0.298; at 500k x 12:
-    // 3 KB tiles 0.493 ms, 2.25 KB 0.512, 1.5 KB 0.548.
+    // to D = 8 a warp needs under 8 KB of shared memory and seven CTAs (28
+    // warps, at most 72 registers) share an SM, which the latency-bound scan
+    // prefers.  Measured at 300k x 8 (before the warp-wide row sort): 2 KB
+    // tiles with six CTAs 0.292 ms, 1 KB tiles 0.310 (0.321 with five CTAs),
+    // 3 KB tiles with five CTAs 0.298; after it, seven CTAs 0.266 against six
+    // 0.270.  At 500k x 12: 3 KB tiles 0.493 ms, 2.25 KB 0.512, 1.5 KB 0.548.
     static constexpr int TILEP = DP == 4 ? 64 : (DP == 8 ? 32 : (DP == 12 ? 32 : 16));
-    static constexpr int MINB = DP <= 8 ? 6 : 4;
+    static constexpr int MINB = DP <= 8 ? 7 : 4;
     static constexpr int NBUF = 2;
     // default vote point (measured: 2 and 3 tie at D = 8, 3 is best at D = 12)
     static constexpr int EXIT = D <= 4 ? D : (D >= 10 ? 3 : 2);
@@ -464,7 +469,7 @@ __global__ void __launch_bounds__(kQueryWarps * 32, QCfg<D>::MINB) k_grid_query(
             lost_q |= __shfl_sync(kFull, lost, qi + st * kTaskQueries);
         }
         // more than 32 entries: the exact selection kernel finishes the row
-        const bool spill = sh == 0 && act && (lost_q || cnt_q > kListCap);
+        const bool spill = sh == 0 && act && (lost_q || cnt_q > kRowCap);
         if (sh == 0 && act && !spill) counts[qorig] = min(kept_q, K);
         if (spill && a.csr) counts[qorig] = kCsrSpill;   // counted by the selection kernel
         if (sh == 0 && act && !spill && a.degree) a.degree[qorig] = kept_q;
