@@ -501,8 +501,11 @@ __global__ void __launch_bounds__(kQueryWarps * 32, QCfg<D>::MINB) k_grid_query(
                                    Li[(lane - base) * kListStride + col]);
                 base += c;
             }
+            // the network only as wide as the row needs (base entries sit in
+            // lanes 0 .. base-1; wider stages would compare largest keys only)
 #pragma unroll
             for (int k2 = 2; k2 <= 32; k2 <<= 1) {
+                if ((k2 >> 1) >= base) break;
 #pragma unroll
                 for (int j = k2 >> 1; j > 0; j >>= 1) {
                     const uint64_t other = __shfl_xor_sync(kFull, key, j);
