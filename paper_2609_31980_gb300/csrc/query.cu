@@ -180,7 +180,7 @@ __device__ __forceinline__ WarpSmem carve_warp(unsigned char* base, int DP, int 
     return w;
 }
 
-// One warp task: 32 queries in one row of cells; their candidates are the
+// One warp task: 16 queries in one row of cells; their candidates are the
 // slot ranges of the neighbour rows (lane l < neighbour_rows owns row l),
 // each widened to pair boundaries and concatenated into one stream of
 // candidate pairs.  Tile t of the stream (TILEP pairs) may span several rows:
