@@ -336,6 +336,16 @@ __global__ void __launch_bounds__(kQueryWarps * 32, QCfg<D>::MINB) k_grid_query(
                         tile[(hi_s - 1 - T0) * PAIRF + 1] = __int_as_float(0x7fc00000);
                     fence_proxy_async_smem();   // before the buffer is refilled by bulk copies
                 }
+                // the last tile of the task: the pairs between its end and the
+                // end of the last screening step hold stale data; NaN makes
+                // them fail every screen (both halves)
+                const int pend = (lenp + 4 * kStreams - 1) / (4 * kStreams) * (4 * kStreams);
+                if (lane < pend - lenp) {
+                    float* f = tile + (size_t)(lenp + lane) * PAIRF;
+                    f[0] = __int_as_float(0x7fc00000);
+                    f[1] = __int_as_float(0x7fc00000);
+                    fence_proxy_async_smem();
+                }
                 __syncwarp();
             }
             // four candidate pairs per stream and step: their first-stage
@@ -345,7 +355,6 @@ __global__ void __launch_bounds__(kQueryWarps * 32, QCfg<D>::MINB) k_grid_query(
                 uint64_t sg[4];
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
-                    // pairs past the tile's end hold stale data: force them out
                     const int p = p0 + kStreams * j + sh;
                     const ulonglong2* cp = reinterpret_cast<const ulonglong2*>(tile + p * PAIRF);
                     uint64_t s2 = 0;
@@ -354,7 +363,7 @@ __global__ void __launch_bounds__(kQueryWarps * 32, QCfg<D>::MINB) k_grid_query(
                         const ulonglong2 v = cp[k >> 1];
                         s2 = f2_screen(s2, qq[k], (k & 1) ? v.y : v.x);
                     }
-                    sg[j] = (p < lenp) ? s2 : 0x7f8000007f800000ull;   // +inf, +inf
+                    sg[j] = s2;
                 }
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
