@@ -535,10 +535,26 @@ def cpu_baseline(pts_np, r, K, rows):
     t0 = time.perf_counter()
     oracle.self_query(pts_np, r, K, rows=sel)
     dt = time.perf_counter() - t0
-    return {"value": len(sel) / dt, "unit": "queries/s", "cores": oracle.num_threads(),
-            "kind": "oracle",
-            "sample": f"{len(sel)} of {len(pts_np)} query rows, each brute-forced against all "
-                      f"{len(pts_np)} points ({dt:.1f} s)"}
+    out = {"value": len(sel) / dt, "unit": "queries/s", "cores": oracle.num_threads(),
+           "kind": "oracle",
+           "sample": f"{len(sel)} of {len(pts_np)} query rows, each brute-forced against all "
+                     f"{len(pts_np)} points ({dt:.1f} s)"}
+    # the 4096 x 3 uniform set on one core and on all (a separate process, so
+    # that the OpenMP thread count can be fixed)
+    code = ("import sys, time; sys.path.insert(0, %r); from oracle import oracle; "
+            "from paper_2609_31980_gb300 import synth; w = synth.config1(); "
+            "oracle.self_query(w.points, w.r, w.K); t = time.perf_counter(); "
+            "oracle.self_query(w.points, w.r, w.K); "
+            "print(len(w.points) / (time.perf_counter() - t), oracle.num_threads())" % ROOT)
+    for tag, env in (("uniform4096x3_1core", {"OMP_NUM_THREADS": "1"}), ("uniform4096x3_all_cores", {})):
+        try:
+            pr = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True,
+                                timeout=120, env={**os.environ, **env})
+            v, c = pr.stdout.split()
+            out[tag] = {"queries_per_s": float(v), "cores": int(c)}
+        except Exception as e:   # noqa: BLE001 - a baseline detail, never fatal
+            out[tag] = {"error": str(e)[:100]}
+    return out
 
 
 def run_reference(args):
