@@ -519,7 +519,9 @@ __global__ void __launch_bounds__(kQueryWarps * 32, QCfg<D>::MINB) k_grid_query(
                 for (int j = k2 >> 1; j > 0; j >>= 1) {
                     const uint64_t other = __shfl_xor_sync(kFull, key, j);
                     const bool take_min = ((lane & j) == 0) == ((lane & k2) == 0);
-                    key = take_min ? (other < key ? other : key) : (other > key ? other : key);
+                    // one comparison: equal keys (rejected entries, empty lanes)
+                    // are interchangeable, all others are distinct
+                    key = (take_min == (other < key)) ? other : key;
                 }
             }
             const int c = min(__shfl_sync(kFull, kept_q, ql), K);
