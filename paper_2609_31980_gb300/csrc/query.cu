@@ -85,6 +85,11 @@ struct QCfg {
     static constexpr int NBUF = 2;
     // default vote point (measured: 2 and 3 tie at D = 8, 3 is best at D = 12)
     static constexpr int EXIT = D <= 4 ? D : (D >= 10 ? 3 : 2);
+    // sort two short query rows at once, one per half-warp.  Measured: 500k x
+    // 12 (about 12 neighbours per clustered query) 0.437 -> 0.424 ms; at 300k
+    // x 8 (about 25, rows rarely pair) the paired loop cost 0.8 %, so lower
+    // dimensions keep the one-row loop
+    static constexpr bool PAIR_ROWS = D >= 10;
 };
 
 __host__ __device__ constexpr size_t ring_floats(int DP, int TILEP, int NB) {
@@ -491,53 +496,112 @@ __global__ void __launch_bounds__(kQueryWarps * 32, QCfg<D>::MINB) k_grid_query(
                 atomicOr(a.status, kStatusCapacity);
             }
         }
-        // one query row at a time: lane l takes entry l of the query's lists,
-        // the warp sorts the 32 keys (d2 bits << 32 | original index; unused
-        // lanes hold the largest key) with a bitonic network across lanes, and
-        // lane l writes position l of the row (coalesced), then the padding
+        // one query row at a time (for D >= 10 two short rows at a time, one
+        // per half-warp): lane l takes entry l of the query's lists, the warp
+        // sorts the 32 keys (d2 bits << 32 | original index; unused lanes hold
+        // the largest key) with a bitonic network across lanes, and lane l
+        // writes position l of the row (coalesced), then the padding
         const unsigned spill_mask = __ballot_sync(kFull, spill);
         const int rstride = a.csr ? kCsrStageW : K;
-        for (int ql = 0; ql < task.nq; ++ql) {
-            if (spill_mask & (1u << ql)) continue;
-            uint64_t key = ~0ull;
-            int base = 0;
+        if constexpr (!C::PAIR_ROWS) {
+            for (int ql = 0; ql < task.nq; ++ql) {
+                if (spill_mask & (1u << ql)) continue;
+                uint64_t key = ~0ull;
+                int base = 0;
 #pragma unroll
-            for (int st = 0; st < kStreams; ++st) {
-                const int col = ql + st * kTaskQueries;
-                const int c = __shfl_sync(kFull, cnt, col);
-                if (lane >= base && lane < base + c)
-                    key = make_key(Ld[(lane - base) * kListStride + col],
-                                   Li[(lane - base) * kListStride + col]);
-                base += c;
-            }
-            // the network only as wide as the row needs (base entries sit in
-            // lanes 0 .. base-1; wider stages would compare largest keys only)
+                for (int st = 0; st < kStreams; ++st) {
+                    const int col = ql + st * kTaskQueries;
+                    const int c = __shfl_sync(kFull, cnt, col);
+                    if (lane >= base && lane < base + c)
+                        key = make_key(Ld[(lane - base) * kListStride + col],
+                                       Li[(lane - base) * kListStride + col]);
+                    base += c;
+                }
+                // the network only as wide as the row needs (base entries sit in
+                // lanes 0 .. base-1; wider stages would compare largest keys only)
 #pragma unroll
-            for (int k2 = 2; k2 <= 32; k2 <<= 1) {
-                if ((k2 >> 1) >= base) break;
+                for (int k2 = 2; k2 <= 32; k2 <<= 1) {
+                    if ((k2 >> 1) >= base) break;
 #pragma unroll
-                for (int j = k2 >> 1; j > 0; j >>= 1) {
-                    const uint64_t other = __shfl_xor_sync(kFull, key, j);
-                    const bool take_min = ((lane & j) == 0) == ((lane & k2) == 0);
-                    // one comparison: equal keys (rejected entries, empty lanes)
-                    // are interchangeable, all others are distinct
-                    key = (take_min == (other < key)) ? other : key;
+                    for (int j = k2 >> 1; j > 0; j >>= 1) {
+                        const uint64_t other = __shfl_xor_sync(kFull, key, j);
+                        const bool take_min = ((lane & j) == 0) == ((lane & k2) == 0);
+                        // one comparison: equal keys (rejected entries, empty lanes)
+                        // are interchangeable, all others are distinct
+                        key = (take_min == (other < key)) ? other : key;
+                    }
+                }
+                const int c = min(__shfl_sync(kFull, kept_q, ql), K);
+                const int qo = __shfl_sync(kFull, qorig, ql);
+                int32_t* irow = oidx + (int64_t)qo * rstride;
+                float* drow = od2 + (int64_t)qo * rstride;
+                if (lane < c) {
+                    irow[lane] = (int32_t)(uint32_t)key;
+                    drow[lane] = __uint_as_float((uint32_t)(key >> 32));
+                } else if (!a.csr && lane < K) {
+                    irow[lane] = -1;
+                    drow[lane] = INFINITY;
+                }
+                for (int e = 32 + lane; e < K && !a.csr; e += 32) {
+                    irow[e] = -1;
+                    drow[e] = INFINITY;
                 }
             }
-            const int c = min(__shfl_sync(kFull, kept_q, ql), K);
-            const int qo = __shfl_sync(kFull, qorig, ql);
-            int32_t* irow = oidx + (int64_t)qo * rstride;
-            float* drow = od2 + (int64_t)qo * rstride;
-            if (lane < c) {
-                irow[lane] = (int32_t)(uint32_t)key;
-                drow[lane] = __uint_as_float((uint32_t)(key >> 32));
-            } else if (!a.csr && lane < K) {
-                irow[lane] = -1;
-                drow[lane] = INFINITY;
-            }
-            for (int e = 32 + lane; e < K && !a.csr; e += 32) {
-                irow[e] = -1;
-                drow[e] = INFINITY;
+        } else {
+            // two rows at a time, one per half-warp, when both hold at most
+            // 16 entries (the network then stays within each half and both
+            // halves end ascending); otherwise one row per warp as above
+            for (int ql = 0; ql < task.nq;) {
+                if (spill_mask & (1u << ql)) {
+                    ++ql;
+                    continue;
+                }
+                const int ql1 = ql + 1;   // <= 16: a valid lane
+                const int n0 = __shfl_sync(kFull, cnt_q, ql);
+                const int n1 = __shfl_sync(kFull, cnt_q, ql1);
+                const bool two =
+                    n0 <= 16 && ql1 < task.nq && !(spill_mask & (1u << ql1)) && n1 <= 16;
+                const int hw = two ? 16 : 32;   // lanes per row
+                const int row = two ? ql + (lane >> 4) : ql;
+                const int hl = two ? (lane & 15) : lane;
+                const int width = two ? max(n0, n1) : n0;
+                uint64_t key = ~0ull;
+                int base = 0;
+#pragma unroll
+                for (int st = 0; st < kStreams; ++st) {
+                    const int col = row + st * kTaskQueries;
+                    const int c = __shfl_sync(kFull, cnt, col);
+                    if (hl >= base && hl < base + c)
+                        key = make_key(Ld[(hl - base) * kListStride + col],
+                                       Li[(hl - base) * kListStride + col]);
+                    base += c;
+                }
+#pragma unroll
+                for (int k2 = 2; k2 <= 32; k2 <<= 1) {
+                    if ((k2 >> 1) >= width) break;
+#pragma unroll
+                    for (int j = k2 >> 1; j > 0; j >>= 1) {
+                        const uint64_t other = __shfl_xor_sync(kFull, key, j);
+                        const bool take_min = ((hl & j) == 0) == ((hl & k2) == 0);
+                        key = (take_min == (other < key)) ? other : key;
+                    }
+                }
+                const int c = min(__shfl_sync(kFull, kept_q, row), K);
+                const int qo = __shfl_sync(kFull, qorig, row);
+                int32_t* irow = oidx + (int64_t)qo * rstride;
+                float* drow = od2 + (int64_t)qo * rstride;
+                if (hl < c) {
+                    irow[hl] = (int32_t)(uint32_t)key;
+                    drow[hl] = __uint_as_float((uint32_t)(key >> 32));
+                } else if (!a.csr && hl < K) {
+                    irow[hl] = -1;
+                    drow[hl] = INFINITY;
+                }
+                for (int e = hw + hl; e < K && !a.csr; e += hw) {
+                    irow[e] = -1;
+                    drow[e] = INFINITY;
+                }
+                ql += two ? 2 : 1;
             }
         }
         __syncwarp();
