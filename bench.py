@@ -157,7 +157,7 @@ def launches_per_step(N: int, path: str = "grid") -> int:
     cap = max(16384, N // 2 + 1)
     L = cap + 1
     scan = 1 if (L + 2047) // 2048 == 1 else 2
-    build = 1 + 1 + 1 + 1 + scan + 1 + 1 + 1 + scan + 1   # init bbox params cellid scan scatter pack rowtasks scan emit
+    build = 1 + 1 + 1 + scan + 1 + 1 + 1 + scan + 1    # init bbox cellid scan scatter pack rowtasks scan emit
     if path == "tc":
         # operand preparation + 128-query tasks (rowtasks scan emit), tc query, selection pass
         return build + 1 + (1 + scan + 1) + 2

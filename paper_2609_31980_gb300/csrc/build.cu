@@ -9,13 +9,16 @@
 // choose_params below).
 //
 // Steps, all on the device, no host synchronisation:
-//   k_init      zero the cell counts, reset bounding boxes
-//   k_bbox      per-event per-axis min / max (+ non-finite flag), float4 staged
-//   k_params    per event: gridded axes, cell edge, cells per axis
+//   k_init      zero the cell counts, reset bounding boxes (and, for one event,
+//               write the per-event tables passed by value)
+//   k_bbox      per-event per-axis min / max (+ non-finite flag), float4 staged;
+//               the event's last block to finish derives the grid parameters:
+//               gridded axes, cell edge, cells per axis
 //   k_cellid    cell id of every point and its rank inside the cell (atomics)
 //   scan        exclusive warp-shuffle prefix scan of the counts -> cell starts
-//   k_scatter   write cell-sorted padded rows, slot -> original index, slot -> cell
-//   k_rowtasks  per row of cells: number of 32-query warp tasks
+//   k_scatter   slot -> original index, slot -> cell
+//   k_pack      cell-sorted pair-interleaved coordinates
+//   k_rowtasks  per row of cells: number of 16-query warp tasks
 //   scan        -> task starts
 //   k_emit      write the tasks
 #include <algorithm>
@@ -26,6 +29,19 @@
 namespace frnn {
 
 // ------------------------------------------------------------------ helpers
+
+// Entry of each event's box copy 0 that counts its finished k_bbox blocks.
+constexpr int kBBoxDone = 33;
+static_assert(kBBoxDone >= 33 && kBBoxDone < kBBoxStride, "after the minima, maxima and flag");
+
+// The tables of a one-event build (header, block starts, cell offsets), passed
+// to k_init by value instead of being copied from the host.
+struct OneEventTables {
+    EventHdr hdr;
+    int64_t cell_end;   // cell_off[1]
+    int32_t nblk;       // blk_start[1]
+    int32_t set;        // 0: the tables are already on the device
+};
 
 __device__ __forceinline__ int find_event(const int32_t* starts, int E, int b) {
     // largest e with starts[e] <= b
@@ -89,28 +105,44 @@ __device__ __forceinline__ int point_cell(const float* p, const EventHdr& h) {
 // ------------------------------------------------------------------ kernels
 
 __global__ void k_init(int32_t* counts, int64_t L, int32_t* bbox, int E, int32_t* scalars,
-                       int32_t bb_min_init, int32_t bb_max_init) {
+                       int32_t bb_min_init, int32_t bb_max_init, OneEventTables t1,
+                       EventHdr* hdr, int32_t* blk_start, int64_t* cell_off) {
     pdl_trigger();
-    pdl_wait();
+    pdl_wait();   // the previous work on the stream may still read the tables
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t1.set && i == 0) {
+        hdr[0] = t1.hdr;
+        blk_start[0] = 0;
+        blk_start[1] = t1.nblk;
+        cell_off[0] = 0;
+        cell_off[1] = t1.cell_end;
+    }
     int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t j = i; j < L; j += stride) counts[j] = 0;
     for (int64_t j = i; j < (int64_t)E * kBBoxCopies * kBBoxStride; j += stride) {
         int k = (int)(j % kBBoxStride);
-        bbox[j] = k < 16 ? bb_min_init : (k < 32 ? bb_max_init : 0);
+        bbox[j] = k < 16 ? bb_min_init : (k < 32 ? bb_max_init : 0);   // flag, block counter: 0
     }
     if (i < kScalars) scalars[i] = 0;
 }
 
+__device__ void event_params(EventHdr* hdr, int e, int D, const int32_t* bbox, float r, int m,
+                             int axes_mode, int naxes_req, int32_t* counts);
+
 // Per-event bounding boxes.  One CTA per build block (256 points staged
 // through shared memory with 16-byte loads) reduces its points and merges the
 // result into one of kBBoxCopies copies of the event's box (copy = block mod
-// kBBoxCopies), so that no address takes more than a few dozen atomics; the
-// parameters kernel combines the copies.
-__global__ void __launch_bounds__(kBuildPtsPerBlock) k_bbox(const EventHdr* hdr,
+// kBBoxCopies), so that no address takes more than a few dozen atomics.  The
+// event's last block to finish (a counter beside copy 0, taken after a memory
+// fence) combines the copies and derives the grid parameters.
+// (at most 40 registers, as without the parameter step: six CTAs per SM; the
+// one-thread parameter code may spill)
+__global__ void __launch_bounds__(kBuildPtsPerBlock, 6) k_bbox(EventHdr* hdr,
                                                             const int32_t* blk_start, int E,
                                                             int D, int32_t* bbox,
-                                                            int32_t* status) {
+                                                            int32_t* status, float r, int m,
+                                                            int axes_mode, int naxes_req,
+                                                            int32_t* counts) {
     pdl_trigger();
     pdl_wait();
     extern __shared__ float sm[];
@@ -169,9 +201,22 @@ __global__ void __launch_bounds__(kBuildPtsPerBlock) k_bbox(const EventHdr* hdr,
         atomicOr(bb + 32, 1);
         atomicOr(status, kStatusNonFinite);
     }
+    __shared__ int s_last;
+    __threadfence();   // this block's box updates before its count
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const int nb = blk_start[e + 1] - blk_start[e];
+        int32_t* done = bbox + (int64_t)e * kBBoxCopies * kBBoxStride + kBBoxDone;
+        s_last = atomicAdd(done, 1) == nb - 1;
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();   // every other block's updates before the reads
+    event_params(hdr, e, D, bbox, r, m, axes_mode, naxes_req, counts);
 }
 
-// Grid parameters of one event (one thread per event).
+// Grid parameters of one event (one CTA: its warps combine the box copies,
+// then one thread derives the parameters).
 //
 // Roundoff-safe cell assignment (proof).  Let u = 2^-24.  If the contract
 // accepts (x, y), every rounded square t_a = fl(fl(x_a - y_a)^2) is <= the
@@ -188,12 +233,10 @@ __global__ void __launch_bounds__(kBuildPtsPerBlock) k_bbox(const EventHdr* hdr,
 // most 1024 cells, and the event's cell count fits its capacity.
 static_assert(kBBoxCopies == 32, "one copy per lane when the copies are combined");
 
-__global__ void __launch_bounds__(256) k_params(EventHdr* hdr, int E, int D, const int32_t* bbox,
-                                               float r, int m, int axes_mode, int naxes_req,
-                                               int32_t* counts) {
-    pdl_trigger();
-    pdl_wait();
-    const int e = blockIdx.x;   // one CTA per event: its warps combine the box copies
+static_assert(kBuildPtsPerBlock == 256, "eight warps combine the box copies");
+
+__device__ void event_params(EventHdr* hdr, int e, int D, const int32_t* bbox, float r, int m,
+                             int axes_mode, int naxes_req, int32_t* counts) {
     __shared__ int32_t bb[kBBoxStride];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     // lane c holds copy c of entry k; a warp reduction combines them (all of a
@@ -203,7 +246,8 @@ __global__ void __launch_bounds__(256) k_params(EventHdr* hdr, int E, int D, con
 #pragma unroll
     for (int i = 0; i < kPer; ++i) {
         const int k = warp + 8 * i;
-        v[i] = k < kBBoxStride ? bbox[((int64_t)e * kBBoxCopies + lane) * kBBoxStride + k] : 0;
+        // L2 reads: the copies were updated by other blocks' atomics
+        v[i] = k < kBBoxStride ? __ldcg(bbox + ((int64_t)e * kBBoxCopies + lane) * kBBoxStride + k) : 0;
     }
 #pragma unroll
     for (int i = 0; i < kPer; ++i) {
@@ -831,6 +875,24 @@ static inline unsigned blocks_for(int64_t n, int t) {
     return (unsigned)std::max<int64_t>(1, ceil_div(n, t));
 }
 
+// Cell ids, the cell-start scan, slot maps, coordinates, the warp tasks.
+static void enqueue_sort(GridBufs& g, size_t smem_pts, int check_finite, int32_t* d_status,
+                         cudaStream_t st) {
+    const int E = g.E, D = g.D;
+    launch_pdl(k_cellid, dim3((unsigned)g.nblk), dim3(kBuildPtsPerBlock), smem_pts, st, 
+        g.hdr, g.blk_start, E, D, g.cstart, g.cid, g.rnk, check_finite, d_status);
+    enqueue_scan(g.cstart, g.L, g.parts, g.scalars + kScCellTotal, st);
+    launch_pdl(k_scatter, dim3((unsigned)g.nblk), dim3(kBuildPtsPerBlock), 0, st, 
+        g.hdr, g.blk_start, E, D, g.DP, g.cstart, g.cid, g.rnk, g.pts, g.perm, g.cell);
+    if (g.n_total > 0)
+        launch_pdl(k_pack, dim3((unsigned)ceil_div(g.n_total / 2, 256)), dim3(256), 0, st, g.hdr, E, g.n_total / 2, D,
+                                                                       g.DP, g.perm, g.pts);
+    // warp tasks in row order (numbered by a scan: the query takes them in
+    // this order, so concurrent warps work on neighbouring cells; tasks
+    // appended by atomics in arbitrary order made the query 2.9 % slower)
+    enqueue_tasks(g, kTaskQueries, 1, g.tasks, g.scalars + kScNTasks, st);
+}
+
 frnn_status enqueue_build(GridBufs& g, const float* const* refs, const BuildOpts& o,
                           const GridBufs* params_from, int32_t* d_status, cudaStream_t st,
                           bool capturing, std::string& err) {
@@ -839,6 +901,16 @@ frnn_status enqueue_build(GridBufs& g, const float* const* refs, const BuildOpts
         g.h_hdr[e].refs = refs[e];
         g.h_hdr[e].valid = 1;
     }
+    // one event outside a capture: k_init writes the tables from its
+    // arguments (no copy on the stream, so the chain stays one run of
+    // programmatically dependent kernels)
+    OneEventTables t1{};
+    if (E == 1 && !capturing) {
+        t1.hdr = g.h_hdr[0];
+        t1.cell_end = g.h_cell_off[1];
+        t1.nblk = g.h_blk_start[1];
+        t1.set = 1;
+    } else {
     // upload the per-event tables through the pinned mirror (wait until the
     // previous upload from it has been consumed)
     if (!capturing) cudaEventSynchronize(g.h_pinned_free);
@@ -855,30 +927,21 @@ frnn_status enqueue_build(GridBufs& g, const float* const* refs, const BuildOpts
     memcpy(hp + o_coff, g.h_cell_off.data(), s_coff);
     cudaMemcpyAsync(g.hdr, hp, o_coff + s_coff, cudaMemcpyHostToDevice, st);
     if (!capturing) cudaEventRecord(g.h_pinned_free, st);
+    }
 
     const int32_t bbmin = host_float_to_ordered(INFINITY);
     const int32_t bbmax = host_float_to_ordered(-INFINITY);
     const int64_t init_n = std::max<int64_t>(g.L, (int64_t)E * kBBoxCopies * kBBoxStride);
     launch_pdl(k_init, dim3(std::min<unsigned>(blocks_for(init_n, 256), 4096)), dim3(256), 0, st, 
-        g.cstart, g.L, g.bbox, E, g.scalars, bbmin, bbmax);
+        g.cstart, g.L, g.bbox, E, g.scalars, bbmin, bbmax, t1, g.hdr, g.blk_start, g.cell_off);
     const size_t smem_pts = sizeof(float) * kBuildPtsPerBlock * D;
     if (params_from) {
         launch_pdl(k_copy_params, dim3(blocks_for(E, 128)), dim3(128), 0, st, g.hdr, params_from->hdr, E, g.cstart);
     } else {
         launch_pdl(k_bbox, dim3((unsigned)g.nblk), dim3(kBuildPtsPerBlock), smem_pts, st, g.hdr, g.blk_start, E, D,
-                                                                     g.bbox, d_status);
-        launch_pdl(k_params, dim3((unsigned)E), dim3(256), 0, st, g.hdr, E, D, g.bbox, o.r, o.m, o.axes_mode, o.naxes,
-                                                      g.cstart);
+                   g.bbox, d_status, o.r, o.m, o.axes_mode, o.naxes, g.cstart);
     }
-    launch_pdl(k_cellid, dim3((unsigned)g.nblk), dim3(kBuildPtsPerBlock), smem_pts, st, 
-        g.hdr, g.blk_start, E, D, g.cstart, g.cid, g.rnk, params_from ? 1 : 0, d_status);
-    enqueue_scan(g.cstart, g.L, g.parts, g.scalars + kScCellTotal, st);
-    launch_pdl(k_scatter, dim3((unsigned)g.nblk), dim3(kBuildPtsPerBlock), 0, st, 
-        g.hdr, g.blk_start, E, D, g.DP, g.cstart, g.cid, g.rnk, g.pts, g.perm, g.cell);
-    if (g.n_total > 0)
-        launch_pdl(k_pack, dim3((unsigned)ceil_div(g.n_total / 2, 256)), dim3(256), 0, st, g.hdr, E, g.n_total / 2, D,
-                                                                       g.DP, g.perm, g.pts);
-    enqueue_tasks(g, kTaskQueries, 1, g.tasks, g.scalars + kScNTasks, st);
+    enqueue_sort(g, smem_pts, params_from ? 1 : 0, d_status, st);
     g.tc_ready = false;   // tensor-core operands describe the previous contents
     cudaError_t ce = cudaGetLastError();
     if (ce != cudaSuccess) {
@@ -898,21 +961,11 @@ frnn_status enqueue_build_resident(GridBufs& g, const BuildOpts& o, int32_t* d_s
     const int32_t bbmax = host_float_to_ordered(-INFINITY);
     const int64_t init_n = std::max<int64_t>(g.L, (int64_t)E * kBBoxCopies * kBBoxStride);
     launch_pdl(k_init, dim3(std::min<unsigned>(blocks_for(init_n, 256), 4096)), dim3(256), 0, st, 
-        g.cstart, g.L, g.bbox, E, g.scalars, bbmin, bbmax);
+        g.cstart, g.L, g.bbox, E, g.scalars, bbmin, bbmax, OneEventTables{}, g.hdr, g.blk_start, g.cell_off);
     const size_t smem_pts = sizeof(float) * kBuildPtsPerBlock * D;
     launch_pdl(k_bbox, dim3((unsigned)g.nblk), dim3(kBuildPtsPerBlock), smem_pts, st, g.hdr, g.blk_start, E, D,
-                                                                 g.bbox, d_status);
-    launch_pdl(k_params, dim3((unsigned)E), dim3(256), 0, st, g.hdr, E, D, g.bbox, o.r, o.m, o.axes_mode, o.naxes,
-                                                  g.cstart);
-    launch_pdl(k_cellid, dim3((unsigned)g.nblk), dim3(kBuildPtsPerBlock), smem_pts, st, 
-        g.hdr, g.blk_start, E, D, g.cstart, g.cid, g.rnk, 0, d_status);
-    enqueue_scan(g.cstart, g.L, g.parts, g.scalars + kScCellTotal, st);
-    launch_pdl(k_scatter, dim3((unsigned)g.nblk), dim3(kBuildPtsPerBlock), 0, st, 
-        g.hdr, g.blk_start, E, D, g.DP, g.cstart, g.cid, g.rnk, g.pts, g.perm, g.cell);
-    if (g.n_total > 0)
-        launch_pdl(k_pack, dim3((unsigned)ceil_div(g.n_total / 2, 256)), dim3(256), 0, st, g.hdr, E, g.n_total / 2, D,
-                                                                       g.DP, g.perm, g.pts);
-    enqueue_tasks(g, kTaskQueries, 1, g.tasks, g.scalars + kScNTasks, st);
+               g.bbox, d_status, o.r, o.m, o.axes_mode, o.naxes, g.cstart);
+    enqueue_sort(g, smem_pts, 0, d_status, st);
     cudaError_t ce = cudaGetLastError();
     if (ce != cudaSuccess) {
         err = std::string("grid build launch failed: ") + cudaGetErrorString(ce);

@@ -65,7 +65,7 @@ struct GridBufs {
     std::vector<int64_t> h_cell_off;
 };
 
-constexpr int kBBoxStride = 34;      // 16 minima, 16 maxima, non-finite flag, pad
+constexpr int kBBoxStride = 34;      // 16 minima, 16 maxima, non-finite flag, finished blocks
 constexpr int kBBoxCopies = 32;      // copies of each event's box (spread the atomics)
 constexpr int kScanChunk = 2048;     // entries per block of the exclusive scan
 constexpr int kBuildPtsPerBlock = 256;
