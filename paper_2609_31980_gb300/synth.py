@@ -45,6 +45,17 @@ def clustered(n_clusters: int, per_cluster: int, n_background: int, d: int,
     return allp.astype(np.float32)
 
 
+def mixed_degrees(d: int, seed, sigma: float = 0.025) -> np.ndarray:
+    """2,500 points: 60 clusters of 8, 40 of 20 and 12 of 60 points plus 500
+    uniform background points in ``[-1, 1]^d``, shuffled.  At r = 0.12 and
+    d = 10 or 12 a query has a few, about ten, or 30 to 60 neighbours (or
+    none), so all row lengths a warp handles occur side by side."""
+    parts = [clustered(nc, pc, 0, d, sigma, seed=(seed, pc)) for nc, pc in ((60, 8), (40, 20), (12, 60))]
+    parts.append(uniform(500, d, seed=(seed, 0), lo=-1.0, hi=1.0))
+    pts = np.concatenate(parts)
+    return pts[_rng((seed, 1)).permutation(len(pts))]
+
+
 def event_mix(n: int, d: int, seed, per_cluster: int = 30, frac_clustered: float = 0.8,
               sigma: float = 0.02) -> np.ndarray:
     """One tracking-event-shaped set of ``n`` points: ``frac_clustered`` of

@@ -81,6 +81,16 @@ def test_csr_rows_beyond_the_lists(ctx, path, K):
     assert want[3].max() > 32
 
 
+@pytest.mark.parametrize("D", [10, 12])
+@pytest.mark.parametrize("K", [7, 40])
+def test_csr_mixed_row_lengths_high_dimensions(ctx, D, K):
+    # short rows sorted two at a time next to long and overflowing rows
+    pts = synth.mixed_degrees(D, 700 + D)
+    got = _csr(ctx, pts, 0.12, K)
+    want = oracle.csr(pts, pts, 0.12, K, query_ids=np.arange(len(pts)))
+    _assert_csr_equal(got, want)
+
+
 @pytest.mark.parametrize("path", ["grid", "tc"])
 def test_csr_cross_set(ctx, path):
     refs = synth.clustered(200, 25, 3000, 8, 0.03, seed=702)

@@ -126,6 +126,20 @@ def test_k_values_with_truncation(ctx, K):
     _assert_rows_equal(got, want)
 
 
+@pytest.mark.parametrize("D", [10, 12])
+@pytest.mark.parametrize("K", [1, 7, 16, 17, 40])
+def test_mixed_row_lengths_high_dimensions(ctx, D, K):
+    # rows of at most 16 entries are sorted two at a time (one per half-warp)
+    # from D = 10 on; next to them rows of 17 to 32 entries and rows that the
+    # selection kernel finishes, for K below, at and above each length
+    pts = synth.mixed_degrees(D, 700 + D)
+    want = oracle.self_query(pts, 0.12, K)
+    deg = want[3]
+    assert (deg <= 16).sum() > 1000 and ((deg > 16) & (deg <= 32)).sum() > 100
+    assert (deg > 32).sum() > 100
+    _assert_rows_equal(_gpu_self(ctx, pts, 0.12, K), want)
+
+
 def test_all_points_in_one_cell(ctx):
     pts = synth.uniform(3000, 3, seed=301, lo=0.0, hi=0.01)
     got = _gpu_self(ctx, pts, 0.05, 32)
