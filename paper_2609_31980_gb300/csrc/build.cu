@@ -494,7 +494,7 @@ __global__ void __launch_bounds__(256) k_pack(const EventHdr* hdr, int E, int64_
 // Per row of cells (all gridded coordinates but the fastest fixed): number of
 // query tasks.  A task is the intersection of the row's slot range with a
 // window of W slots; windows start at the row's first slot rounded down to a
-// multiple of A (A = 1 for the 32-query warp tasks of the grid path, A = 8 for
+// multiple of A (A = 1 for the 16-query warp tasks of the grid path, A = 8 for
 // the 128-query tensor-core tiles, whose operand rows come in groups of 8).
 // Entry i of the cell arrays doubles as row slot i.
 __device__ __forceinline__ void row_slots(const EventHdr& h, const int32_t* cstart, int64_t row,

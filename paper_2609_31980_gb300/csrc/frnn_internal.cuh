@@ -51,7 +51,7 @@ struct EventHdr {
     int64_t pt_off;        // first sorted slot of this event (global slot numbering)
     int64_t cell_off;      // first entry of this event in the cell arrays (cap + 1 entries)
     int32_t cell_cap;      // cells allowed for this event
-    int32_t ncells;        // product of dims (written by the params kernel)
+    int32_t ncells;        // product of dims (written by the parameter step)
     int32_t naxes;         // gridded axes (1..4); preset by the host: requested count (0: default)
     int32_t m;             // cell multiple: neighbours are within +-m cells per gridded axis
     int32_t valid;         // 0 if a coordinate was non-finite

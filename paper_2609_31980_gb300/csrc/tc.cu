@@ -451,7 +451,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_tc_query(TcArgs a) {
             const int dims0 = h.dims[0], m = h.m;
             const int xa = a.qcell[tk.qslot] % dims0;
             const int xb = a.qcell[tk.qslot + tk.nq - 1] % dims0;
-            const int nrows = neighbour_rows(h);   // <= 32 (the params kernel ensures it)
+            const int nrows = neighbour_rows(h);   // <= 32 (the grid parameters ensure it)
             int rs = 0, re = 0;
             int64_t rowbase;
             if (lane < nrows && neighbour_row(h, tk.row, lane, rowbase)) {
@@ -845,7 +845,6 @@ frnn_status enqueue_tc_query(const QueryLaunch& q, cudaStream_t st, std::string&
     const GridBufs& rs = *q.rset;
     const int D = rs.D;
     const int K = tc_k_for(D);
-    const int KS = K / 16;
     TcArgs a{};
     a.ev = rs.hdr;
     a.tasks = qs.tc_tasks;
