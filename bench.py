@@ -115,10 +115,11 @@ def workload(name="event300k"):
     return synth.config3() if name == "event500k" else synth.config2()
 
 
-def profiled_traffic(path: str, wl: str):
-    """DRAM bytes per launch of the dominant kernel from its committed ncu
-    summary of the same workload, or None when there is none or the kernel's
-    sources changed since the capture."""
+def profile_summary(path: str, wl: str):
+    """Counters of the dominant kernel from its committed ncu summary of the
+    same workload: DRAM bytes per launch ("traffic") and executed warp
+    instructions per launch ("warp_instructions"); None when there is no
+    summary or the kernel's sources changed since the capture."""
     import hashlib
     key = (path, wl)
     known = {("grid", "event300k"): ("grid_query_event300k_x8.md", ["query.cu", "frnn_internal.cuh"]),
@@ -134,14 +135,37 @@ def profiled_traffic(path: str, wl: str):
     for s_ in srcs:
         with open(os.path.join(ROOT, "paper_2609_31980_gb300", "csrc", s_), "rb") as fh:
             h.update(fh.read())
-    traffic, sha = None, None
+    out, sha = {"traffic": None, "warp_instructions": None}, None
     with open(f) as fh:
         for line in fh:
             if line.startswith("traffic_bytes_per_launch:"):
-                traffic = int(line.split(":")[1])
+                out["traffic"] = int(line.split(":")[1])
             elif line.startswith("source_sha256_16"):
                 sha = line.split(":")[-1].strip()
-    return traffic if sha == h.hexdigest()[:16] else None
+            elif line.startswith("| smsp__inst_executed.sum |"):
+                # "| smsp__inst_executed.sum | 195.3 M warp instructions |"
+                out["warp_instructions"] = float(line.split("|")[2].split()[0]) * 1e6
+    return out if sha == h.hexdigest()[:16] else None
+
+
+def profiled_traffic(path: str, wl: str):
+    """DRAM bytes per launch of the dominant kernel (see profile_summary)."""
+    p = profile_summary(path, wl)
+    return p["traffic"] if p else None
+
+
+def issue_roofline(warp_instructions, kernel_ms: float, sms: int, sm_mhz: float):
+    """Instruction issue of the dominant kernel against the issue ceiling:
+    every SM has four schedulers, each issuing at most one warp instruction
+    per clock.  Rates in tera warp instructions per second."""
+    if not warp_instructions or kernel_ms <= 0 or sms <= 0 or sm_mhz <= 0:
+        return None
+    achieved = warp_instructions / (kernel_ms / 1e3) / 1e12
+    peak = sms * 4 * sm_mhz * 1e6 / 1e12
+    return {"warp_instructions": warp_instructions, "achieved": achieved, "peak": peak,
+            "unit": "T warp instructions/s", "frac": achieved / peak, "sms": sms,
+            "sm_mhz": sm_mhz, "source": "instruction count of the committed ncu summary, "
+            "time of this run"}
 
 
 def algorithmic_query_bytes(N: int, D: int, K: int) -> int:
@@ -304,6 +328,7 @@ def run_ours(args):
     q_med = statistics.median(query_ms)
     k_mean = sum(kern_ms) / len(kern_ms)
     achieved = qbytes / (k_mean / 1e3) / 1e9
+    prof = profile_summary("tc" if kern_is_tc else "grid", args.workload)
     res = {
         "metric": METRIC,
         "value": value,
@@ -334,7 +359,11 @@ def run_ours(args):
                      "kernel_ms_mean": k_mean,
                      "frac": achieved / hbm_peak, "peak_kind": peak_kind,
                      "algorithmic_bytes": qbytes,
-                     "traffic": profiled_traffic("tc" if kern_is_tc else "grid", args.workload)},
+                     "traffic": (prof or {}).get("traffic"),
+                     # the kernel is bound by instruction issue, not HBM
+                     "issue": issue_roofline((prof or {}).get("warp_instructions"), k_mean,
+                                             torch.cuda.get_device_properties(dev).multi_processor_count,
+                                             (clocks or {}).get("sm_max_mhz") or 2070.0)},
         "e2e": {"value": N * ws / e2e_c_s, "unit": "queries/s",
                 "h2d_bytes_per_step": N * D * 4,
                 "d2h_bytes_per_step": (N + 1) * 8 + 2 * n_edges * 4,

@@ -26,3 +26,25 @@ def test_median_ci_brackets_the_median():
     med, lo, hi = bench.median_ci(x, resamples=2000)
     assert med == np.median(x) and lo <= med <= hi and hi - lo < 2.0
     assert bench.median_ci([5.0] * 30, resamples=500) == (5.0, 5.0, 5.0)
+
+
+def test_issue_roofline_arithmetic():
+    # 152 SMs x 4 schedulers x 2.07 GHz = 1.25856 T warp instructions/s
+    r = bench.issue_roofline(195.3e6, 0.25, 152, 2070.0)
+    assert r["peak"] == pytest.approx(1.25856)
+    assert r["achieved"] == pytest.approx(195.3e6 / 0.25e-3 / 1e12)
+    assert r["frac"] == pytest.approx(r["achieved"] / r["peak"])
+    assert bench.issue_roofline(None, 0.25, 152, 2070.0) is None
+    assert bench.issue_roofline(1e6, 0.0, 152, 2070.0) is None
+
+
+def test_profile_summaries_parse():
+    # a summary is used only while it matches the kernel's sources; when it
+    # does, both counters are present and plausible
+    for path, wl in (("grid", "event300k"), ("grid", "event500k"), ("tc", "event500k")):
+        p = bench.profile_summary(path, wl)
+        if p is None:
+            continue
+        assert p["traffic"] > 10e6 and 10e6 < p["warp_instructions"] < 10e9
+        assert bench.profiled_traffic(path, wl) == p["traffic"]
+    assert bench.profile_summary("grid", "no-such-workload") is None
