@@ -329,6 +329,7 @@ def run_ours(args):
     k_mean = sum(kern_ms) / len(kern_ms)
     achieved = qbytes / (k_mean / 1e3) / 1e9
     prof = profile_summary("tc" if kern_is_tc else "grid", args.workload)
+    sm_count = int(getattr(torch.cuda.get_device_properties(dev), "multi_processor_count", 0))
     res = {
         "metric": METRIC,
         "value": value,
@@ -362,8 +363,7 @@ def run_ours(args):
                      "traffic": (prof or {}).get("traffic"),
                      # the kernel is bound by instruction issue, not HBM
                      "issue": issue_roofline((prof or {}).get("warp_instructions"), k_mean,
-                                             torch.cuda.get_device_properties(dev).multi_processor_count,
-                                             (clocks or {}).get("sm_max_mhz") or 2070.0)},
+                                             sm_count, (clocks or {}).get("sm_max_mhz") or 2070.0)},
         "e2e": {"value": N * ws / e2e_c_s, "unit": "queries/s",
                 "h2d_bytes_per_step": N * D * 4,
                 "d2h_bytes_per_step": (N + 1) * 8 + 2 * n_edges * 4,
