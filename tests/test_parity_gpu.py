@@ -340,6 +340,22 @@ def test_batched_equals_alone_and_oracle(ctx):
                 _assert_rows_equal(got, oracle.self_query(p, 0.1, 64))
 
 
+def test_batch_64_uneven_events_full_size_sampled(ctx):
+    # the batched workload at full size (64 events, N ~ U[50k, 350k], 14.1 M
+    # points) in the batched launch the benchmark times; per event 16 sampled
+    # rows against the oracle's brute force over that event
+    import torch
+    w = synth.config4()
+    evs = [torch.from_numpy(p).cuda() for p in w.events]
+    outs = ctx.query_batched(evs, w.r, w.K, path="grid")
+    ctx.sync()
+    for e, (p, (c, i, d)) in enumerate(zip(w.events, outs)):
+        rows = _sample_rows(len(p), 16, 900 + e)
+        rt = torch.from_numpy(rows).cuda()
+        got = (c[rt].cpu().numpy(), i[rt].cpu().numpy(), d[rt].cpu().numpy())
+        _assert_rows_equal(got, oracle.self_query(p, w.r, w.K, rows=rows))
+
+
 def test_batched_many_events_long_cell_scan(ctx):
     # 70 events: over 1.1 M cell entries, so the build's scans take the path
     # that scans the block partials in a separate pass
