@@ -30,6 +30,9 @@ CFLAGS = ["-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp",
 
 _lock = threading.Lock()
 _lib = None
+# The tests of the pins themselves run them against copies of this oracle with
+# one mistake planted; such a copy is loaded from this path instead.
+_OVERRIDE = os.environ.get("FRNN_ORACLE_LIB")
 
 
 def build(force: bool = False) -> str:
@@ -49,7 +52,7 @@ def _load():
     global _lib
     with _lock:
         if _lib is None:
-            lib = ctypes.CDLL(build())
+            lib = ctypes.CDLL(_OVERRIDE or build())
             i64, f32p = ctypes.c_int64, ctypes.c_void_p
             lib.frnn_oracle_query.argtypes = [f32p, f32p, i64, f32p, i64, ctypes.c_int,
                                               ctypes.c_float, ctypes.c_int,

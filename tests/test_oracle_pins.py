@@ -6,8 +6,9 @@ with its citation), closed-form lattice shell counts, invariants of Eq. 1
 (symmetry, truncation prefix, relabelling, exact power-of-two scaling) and the
 float32 rounding-error bound of the FP64 audit.  A plausible slip in the oracle
 (a dropped or transposed term, a wrong sign, '<' for '<=', another summation
-order, a fused multiply-add, a wrong tie-break, a self-pair kept) fails at
-least one of them.
+order, a fused multiply-add, a wrong tie-break, a self-pair kept, the radius
+compared unrounded) fails at least one of them; tests/test_oracle_mutants.py
+plants such mistakes and checks that.
 """
 import json
 import os
@@ -66,6 +67,17 @@ def test_ex2_inclusive_boundary():
         assert inside == case["inside"]
         if inside:
             assert _bits(d2) == _bits(hexf(case["d2"]))
+
+
+def test_ex5_radius_enters_as_its_rounded_square():
+    from fractions import Fraction
+    g = _load("ex5_radius_square.json")
+    r, d2_want = hexf(g["r"]), hexf(g["d2"])
+    # the fixture's premise, from its hand-worked numbers: fl(r*r) lies above r^2
+    assert Fraction(float(d2_want)) == Fraction(10737419, 2 ** 30) > Fraction(float(r)) ** 2
+    inside, d2 = _pair(g["x"], g["y"], r)
+    assert inside == g["inside"]
+    assert _bits(d2) == _bits(d2_want)
 
 
 def test_ex3_index_order_summation_and_audit():
