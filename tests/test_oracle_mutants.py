@@ -13,7 +13,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 SRC = os.path.join(ROOT, "oracle", "frnn_oracle.c")
 
 # name -> (text in the oracle, replacement); the first occurrence is replaced
-# (in frnn_oracle_query, the function the pins call)
+# (for the shared lines: in frnn_oracle_query)
 MUTANTS = {
     "strict boundary": ("if (s <= r2) {", "if (s < r2) {"),
     "radius not squared in float": ("    const float r2 = r * r;\n    int failed = 0;",
@@ -33,6 +33,12 @@ MUTANTS = {
     "off-by-one truncation": ("int64_t keep = deg < K ? deg : K;", "int64_t keep = deg < K ? deg : K - 1;"),
     "query row stride": ("const float* q = queries + i * (int64_t)D;\n            int64_t deg = 0;",
                          "const float* q = queries + i;\n            int64_t deg = 0;"),
+    # the degree-only and FP64-audit functions
+    "degree strict boundary": ("if (contract_d2(q, refs + j * (int64_t)D, D) <= r2) ++deg;",
+                               "if (contract_d2(q, refs + j * (int64_t)D, D) < r2) ++deg;"),
+    "audit in float": ("double d = (double)q[k] - (double)p[k];", "float d = q[k] - p[k];"),
+    "audit strict boundary": ("int in64 = s <= r64;", "int in64 = s < r64;"),
+    "audit verdicts swapped": ("if (in32 && !in64) ++a32;", "if (in64 && !in32) ++a32;"),
 }
 
 

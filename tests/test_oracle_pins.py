@@ -80,6 +80,17 @@ def test_ex5_radius_enters_as_its_rounded_square():
     assert _bits(d2) == _bits(d2_want)
 
 
+def test_fp64_audit_is_inclusive_at_exactly_r():
+    # a pair at exactly distance r is inside in both arithmetics, so it is no
+    # crossing: ex2 (every value exact) and ex5 (d^2 = r^2 exactly in double)
+    for name in ("ex2_boundary.json", "ex5_radius_square.json"):
+        g = _load(name)
+        q = np.array([[hexf(v) for v in g["x"]]], np.float32)
+        p = np.array([[hexf(v) for v in g["y"]]], np.float32)
+        r = hexf(g["cases"][0]["r"]) if "cases" in g else hexf(g["r"])
+        assert oracle.fp64_audit(q, p, float(r)) == (0, 0, 0)
+
+
 def test_ex3_index_order_summation_and_audit():
     g = _load("ex3_order.json")
     r = hexf(g["r"])
