@@ -65,3 +65,19 @@ def test_null_context_is_rejected(lib_path):
     n = ctypes.c_int(0)
     assert frnn.frnn_kernel_times(None, None, 0, ctypes.byref(n)) == -1
     assert frnn.frnn_check_wait_timeout(None, 20_000_000) == -1
+
+
+def test_plain_c_caller_compiles_links_and_runs(lib_path, tmp_path):
+    """The header is plain C11 (warnings are errors) and a C program links
+    against the library; without a GPU it reports the missing device cleanly,
+    with one it checks a hand-worked self-query."""
+    import subprocess
+    exe = tmp_path / "abi_example"
+    lib_dir = os.path.dirname(lib_path)
+    subprocess.run(["gcc", "-std=c11", "-Wall", "-Wextra", "-Werror", "-pedantic",
+                    "-I", os.path.join(ROOT, "include"), os.path.join(ROOT, "tests", "abi_example.c"),
+                    "-o", str(exe), "-L", lib_dir, "-lfrnn", f"-Wl,-rpath,{lib_dir}"], check=True)
+    p = subprocess.run([str(exe)], capture_output=True, text=True, timeout=120)
+    assert p.returncode in (0, 3), p.stdout + p.stderr
+    if p.returncode == 0:
+        assert p.stdout.strip() == "ok"
