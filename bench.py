@@ -386,7 +386,8 @@ def run_ours(args):
     if rank == 0 and not args.no_serving:
         res["serving"] = run_serving(ctx, args)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        res["cpu_baseline"] = cpu_baseline(pts_np, r, K, args.cpu_rows)
+        res["cpu_baseline"] = cpu_baseline(pts_np, r, K, args.cpu_rows,
+                                           gpu=(h_c.numpy(), h_i.numpy(), h_d.numpy()))
     ctx.close()
     return res if rank == 0 else None
 
@@ -555,19 +556,31 @@ def run_serving(ctx, args):
     return out
 
 
-def cpu_baseline(pts_np, r, K, rows):
-    """The oracle (brute force, FP32 contract) on a bounded sample of queries."""
+def cpu_baseline(pts_np, r, K, rows, gpu=None):
+    """The oracle (brute force, FP32 contract) on a bounded sample of queries;
+    with ``gpu`` = the library's dense result (counts, idx, dist2) of the same
+    event, the sampled rows are also compared with it element by element."""
     from oracle import oracle
     g = np.random.default_rng(0)
     sel = np.sort(g.choice(len(pts_np), size=min(rows, len(pts_np)), replace=False))
     oracle.self_query(pts_np, r, K, rows=sel[:64])     # warm (page-in, thread pool)
     t0 = time.perf_counter()
-    oracle.self_query(pts_np, r, K, rows=sel)
+    want = oracle.self_query(pts_np, r, K, rows=sel)
     dt = time.perf_counter() - t0
     out = {"value": len(sel) / dt, "unit": "queries/s", "cores": oracle.num_threads(),
            "kind": "oracle",
            "sample": f"{len(sel)} of {len(pts_np)} query rows, each brute-forced against all "
                      f"{len(pts_np)} points ({dt:.1f} s)"}
+    if gpu is not None:
+        try:
+            gc, gi, gd = gpu
+            same = (np.array_equal(gc[sel], want[0]) and np.array_equal(gi[sel], want[1]) and
+                    np.array_equal(np.ascontiguousarray(gd[sel]).view(np.uint32),
+                                   want[2].view(np.uint32)))
+            out["gpu_rows_equal"] = {"rows": int(len(sel)), "equal": bool(same),
+                                     "compared": "counts, indices, distance bits"}
+        except Exception as e:   # noqa: BLE001 - a report, never fatal
+            out["gpu_rows_equal"] = {"error": str(e)[:100]}
     # the 4096 x 3 uniform set on one core and on all (a separate process, so
     # that the OpenMP thread count can be fixed)
     code = ("import sys, time; sys.path.insert(0, %r); from oracle import oracle; "

@@ -48,3 +48,18 @@ def test_profile_summaries_parse():
         assert p["traffic"] > 10e6 and 10e6 < p["warp_instructions"] < 10e9
         assert bench.profiled_traffic(path, wl) == p["traffic"]
     assert bench.profile_summary("grid", "no-such-workload") is None
+
+
+def test_cpu_baseline_compares_sampled_rows_with_the_library_result():
+    # the oracle's own full result stands in for the library's: equal; one
+    # index changed in a sampled row: not equal
+    from oracle import oracle
+    from paper_2609_31980_gb300 import synth
+    pts = synth.clustered(50, 20, 500, 8, 0.02, seed=9)
+    c, i, d, _ = oracle.self_query(pts, 0.1, 16)
+    out = bench.cpu_baseline(pts, 0.1, 16, len(pts), gpu=(c, i, d))
+    assert out["gpu_rows_equal"]["equal"] and out["gpu_rows_equal"]["rows"] == len(pts)
+    assert out["kind"] == "oracle" and out["cores"] >= 1
+    i2 = i.copy()
+    i2[5, 0] += 1
+    assert not bench.cpu_baseline(pts, 0.1, 16, len(pts), gpu=(c, i2, d))["gpu_rows_equal"]["equal"]
