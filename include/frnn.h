@@ -98,10 +98,11 @@ frnn_status frnn_destroy(frnn_ctx* ctx);
  *   grid  in/out.  If *grid is NULL a new grid is allocated.  If *grid is a
  *         grid from this context with D equal and capacity >= N, it is rebuilt
  *         in place without allocating (the previous contents are replaced).
- * The grid bins at most 3 coordinates with cells of edge (r/m)(1+2^-10),
- * m = the cell-multiple option, enlarged when needed so that the cell count
- * stays bounded; the choice never changes results (the cell assignment is
- * proven conservative).  A non-finite coordinate makes frnn_sync return
+ * The grid bins at most 4 coordinates (the last min(D, 4) by default; see
+ * FRNN_OPT_GRID_NAXES and FRNN_OPT_GRID_AXES) with cells of edge
+ * (r/m)(1+2^-10), m = the cell-multiple option, enlarged when needed so that
+ * the cell count stays bounded; the choice never changes results (the cell
+ * assignment is proven conservative).  A non-finite coordinate makes frnn_sync return
  * FRNN_ERR_NONFINITE and later queries on the grid return no neighbours.
  */
 frnn_status frnn_build_grid(frnn_ctx* ctx, const float* refs, int64_t N, int D, float r,
@@ -246,9 +247,11 @@ const char* frnn_last_error(const frnn_ctx* ctx);
 
 /*
  * Autotuner.  Times the candidate configurations on the given point set (a
- * representative event, device memory, self-query): cell multiple m in {1, 2}
- * (cell edge ~ r/m, the grid's search reach +-m cells), the grid scan with its
- * default and a later warp vote, and the tensor-core pre-filter (D >= 8).
+ * representative event, device memory, self-query): grids over three
+ * coordinates with cell multiple m in {1, 2} (cell edge ~ r/m, the grid's
+ * search reach +-m cells) and over four with m = 1; on each, the grid scan
+ * with its default and a later warp vote (D >= 5), and the tensor-core
+ * pre-filter (D >= 8).
  * Each candidate is built and queried (first run untimed, best of three
  * timed with CUDA events on the context's stream) and the fastest build +
  * query is cached for the event size class (power-of-two bucket of N, D,
@@ -294,7 +297,7 @@ typedef enum frnn_option {
                                  with frnn_kernel_times; 0 (default): off.
                                  Setting it discards recorded pairs. */
     FRNN_OPT_GRID_NAXES = 10  /* gridded coordinates: 1..4 (at most D); 0
-                                 (default): autotuned, else min(D, 3).  With 4
+                                 (default): autotuned, else min(D, 4).  With 4
                                  axes the cell multiple is 1 (the neighbour
                                  rows, (2m+1)^3, must not exceed 32). */
 } frnn_option;

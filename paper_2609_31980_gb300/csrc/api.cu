@@ -993,9 +993,10 @@ frnn_status frnn_autotune(frnn_ctx* ctx, const float* refs, int64_t N, int D, fl
         ms = bestms;
         return frnn_sync(ctx);
     };
-    // grid configurations: 3 gridded axes with m = 1, 2; 4 axes with m = 1
+    // grid configurations: 3 gridded axes (all of them for D < 3) with m = 1,
+    // 2; 4 axes with m = 1 (the only multiple four axes allow)
     struct GridCfg { int naxes, m; };
-    std::vector<GridCfg> gcfg = {{default_naxes(D), 1}, {default_naxes(D), 2}};
+    std::vector<GridCfg> gcfg = {{std::min(D, 3), 1}, {std::min(D, 3), 2}};
     if (D >= 4) gcfg.push_back({4, 1});
     for (size_t gi = 0; gi < gcfg.size() && s == FRNN_OK; ++gi) {
         const int m = gcfg[gi].m;
