@@ -3,10 +3,10 @@
 //
 // The uniform grid / cell list is the method of the original FRNN the paper
 // starts from (Sec. 2: uniform-grid kernel, spacing chosen so that r is an
-// integer multiple of it).  Here at most 3 coordinates are gridded; the cell
+// integer multiple of it).  Here at most 4 coordinates are gridded; the cell
 // assignment is "roundoff-safe" (Table 1): it provably never separates two
 // points the float32 contract accepts by more than m cells per axis (proof at
-// choose_params below).
+// event_params below).
 //
 // Steps, all on the device, no host synchronisation:
 //   k_init      zero the cell counts, reset bounding boxes (and, for one event,
