@@ -85,6 +85,24 @@ def test_event_300k_x8_sampled(ctx):
             assert len(pos) == 1 and d[j, pos[0]].view(np.uint32) == d[q, e].view(np.uint32)
 
 
+@pytest.mark.slow
+def test_event_300k_x8_every_row(ctx):
+    # the benchmark's event at full size, every row against the oracle
+    # (about 20 s of brute force on 16 host cores)
+    w = synth.config2()
+    _assert_rows_equal(_gpu_self(ctx, w.points, w.r, w.K), oracle.self_query(w.points, w.r, w.K))
+
+
+@pytest.mark.slow
+def test_event_500k_x12_every_row_both_paths(ctx):
+    # the high-dimensional event at full size, every row, grid and
+    # tensor-core paths (about 80 s of brute force on 16 host cores)
+    w = synth.config3()
+    want = oracle.self_query(w.points, w.r, w.K)
+    _assert_rows_equal(_gpu_self(ctx, w.points, w.r, w.K, path="grid"), want)
+    _assert_rows_equal(_gpu_self(ctx, w.points, w.r, w.K, path="tc"), want)
+
+
 def test_event_40k_x12_full(ctx):
     pts = synth.clustered(1280, 25, 8000, 12, 0.025, seed=23)
     got = _gpu_self(ctx, pts, 0.12, 128)
