@@ -270,6 +270,30 @@ def test_fp64_audit_crossings_lie_inside_rounding_band():
     assert oracle.fp64_audit(q, p, 1.0)[0] == 1
 
 
+@pytest.mark.parametrize("D", [5, 12, 16])
+def test_cross_polytope_closed_form(D):
+    # the origin and the 2D points +-e_k (all values exact in float32): at
+    # r = 1 the origin's neighbours are the 2D unit points at d2 = 1 (ordered
+    # by index), every unit point's only neighbour is the origin (the nearest
+    # other unit points are at d2 = 2, the opposite one at 4); at r = 2 a unit
+    # point also reaches the 2D - 2 others at d2 = 2 and its opposite at 4
+    pts = np.zeros((2 * D + 1, D), np.float32)
+    for k in range(D):
+        pts[1 + 2 * k, k] = 1.0
+        pts[2 + 2 * k, k] = -1.0
+    c, i, d, deg = oracle.self_query(pts, 1.0, 2 * D + 1)
+    assert deg[0] == 2 * D and (i[0, :2 * D] == np.arange(1, 2 * D + 1)).all()
+    assert (d[0, :2 * D] == 1.0).all()
+    assert (deg[1:] == 1).all() and (i[1:, 0] == 0).all() and (d[1:, 0] == 1.0).all()
+    c, i, d, deg = oracle.self_query(pts, 2.0, 2 * D + 1)
+    assert (deg[1:] == 2 * D).all()
+    for q in range(1, 2 * D + 1):
+        opposite = q + 1 if q % 2 else q - 1
+        assert i[q, 0] == 0 and d[q, 0] == 1.0
+        assert (d[q, 1:2 * D - 1] == 2.0).all()
+        assert i[q, 2 * D - 1] == opposite and d[q, 2 * D - 1] == 4.0
+
+
 def test_empty_inputs():
     pts = np.zeros((0, 3), np.float32)
     counts, idx, d2, deg = oracle.frnn(pts, pts, 0.1, 4)
