@@ -135,13 +135,15 @@ def profile_summary(path: str, wl: str):
     for s_ in srcs:
         with open(os.path.join(ROOT, "paper_2609_31980_gb300", "csrc", s_), "rb") as fh:
             h.update(fh.read())
-    out, sha = {"traffic": None, "warp_instructions": None}, None
+    out, sha = {"traffic": None, "warp_instructions": None, "tensor_pipe_pct": None}, None
     with open(f) as fh:
         for line in fh:
             if line.startswith("traffic_bytes_per_launch:"):
                 out["traffic"] = int(line.split(":")[1])
             elif line.startswith("source_sha256_16"):
                 sha = line.split(":")[-1].strip()
+            elif line.startswith("tensor_pipe_active_pct:"):
+                out["tensor_pipe_pct"] = float(line.split(":")[1])
             elif line.startswith("| smsp__inst_executed.sum |"):
                 # "| smsp__inst_executed.sum | 195.3 M warp instructions |"
                 out["warp_instructions"] = float(line.split("|")[2].split()[0]) * 1e6
@@ -204,6 +206,88 @@ def whole_job_rate(units_per_rank: int, steps: int, ws: int, total_ms: float) ->
     """Units all ranks processed over the slowest rank's time (weak scaling:
     every rank runs its own replica of the workload)."""
     return units_per_rank * ws * steps / (total_ms / 1e3)
+
+
+def time_config(frnn, pts_np, r, K, path, dev, steps=20, warmup=3, opts=None, tc_stats=False):
+    """Build + query of one event in one configuration (a fresh context with
+    the given options): median step and build ms (CUDA events on the
+    context's stream, L2 flushed between steps), mean main-kernel ms, and
+    for the tensor-core path the pre-filter's false-candidate rate."""
+    import torch
+    stream = torch.cuda.Stream()
+    ctx = frnn.Context(stream=stream)
+    for k, v in (opts or {}).items():
+        ctx.set_option(k, v)
+    N = pts_np.shape[0]
+    with torch.cuda.stream(stream):
+        pts = torch.from_numpy(pts_np).to(dev)
+        out = (torch.empty(N, dtype=torch.int32, device=dev),
+               torch.empty((N, K), dtype=torch.int32, device=dev),
+               torch.empty((N, K), dtype=torch.float32, device=dev))
+        flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
+    grid = ctx.build_grid(pts, r)
+    for _ in range(warmup):
+        ctx.build_grid(pts, r, grid=grid)
+        ctx.query(grid, pts, r, K, True, path, out)
+    ctx.sync()
+    if tc_stats:
+        ctx.set_option(frnn.FRNN_OPT_TC_SURVIVORS, 0)   # reset the pre-filter counters
+    ctx.set_option(frnn.FRNN_OPT_KERNEL_TIMING, 1)
+    mk = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+    evs = [(mk(), mk(), mk()) for _ in range(steps)]
+    for k in range(steps):
+        with torch.cuda.stream(stream):
+            flush.fill_(float(k))
+        evs[k][0].record(stream)
+        ctx.build_grid(pts, r, grid=grid)
+        evs[k][1].record(stream)
+        ctx.query(grid, pts, r, K, True, path, out)
+        evs[k][2].record(stream)
+    ctx.sync()
+    kern = ctx.kernel_times()
+    res = {"step_ms_median": statistics.median(e[0].elapsed_time(e[2]) for e in evs),
+           "build_ms_median": statistics.median(e[0].elapsed_time(e[1]) for e in evs),
+           "kernel_ms_mean": sum(kern) / max(len(kern), 1),
+           "queries_per_s": N / (statistics.median(e[0].elapsed_time(e[2]) for e in evs) / 1e3),
+           "neighbor_pairs": int(out[0].sum().item())}
+    if tc_stats:
+        surv = ctx.get_option(frnn.FRNN_OPT_TC_SURVIVORS)
+        acc = ctx.get_option(frnn.FRNN_OPT_TC_ACCEPTED)
+        res["prefilter_survivors"] = surv
+        res["exact_accepted"] = acc
+        res["false_candidate_rate"] = (surv - acc) / surv if surv else None
+    res["gridded_axes"] = ctx.get_option(frnn.FRNN_OPT_GRID_NAXES) or min(pts_np.shape[1], 4)
+    res["cell_mult"] = ctx.get_option(frnn.FRNN_OPT_CELL_MULT)
+    ctx.close()
+    del out, pts, flush
+    return res
+
+
+def run_design_points(args, dev):
+    """Other configurations of the same path, each timed on its own:
+    the 300k x 8 event on grids over three coordinates (cell multiple 1 and 2;
+    the library's default grids four), the uniform 4096 x 3 set, and the
+    500k x 12 event on the grid scan against the tensor-core pre-filter
+    (false-candidate rate of the pre-filter; tensor-pipe activity from the
+    committed ncu summary of that kernel)."""
+    from paper_2609_31980_gb300 import frnn, synth
+    out = {}
+    w2 = synth.config2()
+    for m in (1, 2):
+        out[f"event300k_3axes_m{m}"] = time_config(
+            frnn, w2.points, w2.r, w2.K, "grid", dev,
+            opts={frnn.FRNN_OPT_GRID_NAXES: 3, frnn.FRNN_OPT_CELL_MULT: m})
+    w1 = synth.config1()
+    out["uniform4096x3"] = time_config(frnn, w1.points, w1.r, w1.K, "grid", dev)
+    w3 = synth.config3()
+    g3 = time_config(frnn, w3.points, w3.r, w3.K, "grid", dev)
+    t3 = time_config(frnn, w3.points, w3.r, w3.K, "tc", dev,
+                     opts={frnn.FRNN_OPT_GRID_NAXES: 3}, tc_stats=True)
+    prof = profile_summary("tc", "event500k") or {}
+    t3["tensor_pipe_active_pct"] = prof.get("tensor_pipe_pct")
+    out["event500k_x12"] = {"workload": w3.name, "grid": g3, "tc": t3,
+                            "tc_kernel_over_grid_kernel": t3["kernel_ms_mean"] / g3["kernel_ms_mean"]}
+    return out
 
 
 def run_ours(args):
@@ -382,7 +466,11 @@ def run_ours(args):
     if rank == 0 and not args.no_compact:
         res["compact_rows"] = run_compact(ctx, grid, pts, r, K, path, stream)
     if rank == 0 and not args.no_batched:
-        res["batched_vs_plain"] = run_batched(ctx, args, dev)
+        res["batched_vs_plain"] = run_batched(ctx, args, dev, args.batch_path)
+        if not args.no_tuned_batch:
+            res["batched_vs_plain_tuned"] = run_batched_tuned(args, dev)
+    if rank == 0 and not args.no_design_points:
+        res["design_points"] = run_design_points(args, dev)
     if rank == 0 and not args.no_serving:
         res["serving"] = run_serving(ctx, args)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -414,7 +502,31 @@ def sign_test(a, b):
     return wins, losses, min(1.0, p)
 
 
-def run_batched(ctx, args, dev):
+def run_batched_tuned(args, dev):
+    """The batched leg with the autotuner's choices: one representative event
+    per size class of the batch (power-of-two bucket of N) is tuned with
+    frnn_autotune, then batched and plain calls take FRNN_PATH_AUTO."""
+    import torch
+    from paper_2609_31980_gb300 import frnn, synth
+    w = synth.config4(n_events=args.batch_events)
+    stream = torch.cuda.Stream()
+    ctx = frnn.Context(stream=stream)
+    classes = {}
+    for p in w.events:
+        classes.setdefault(int(np.log2(max(len(p), 1))), p)
+    tuned = {}
+    for b, p in sorted(classes.items()):
+        with torch.cuda.stream(stream):
+            t = torch.from_numpy(p).to(dev)
+        tuned[f"N in [2^{b}, 2^{b + 1})"] = dict(ctx.autotune(t, w.r, w.K), representative_N=len(p))
+        del t
+    res = run_batched(ctx, args, dev, "auto")
+    res["tuned_classes"] = tuned
+    ctx.close()
+    return res
+
+
+def run_batched(ctx, args, dev, path):
     """64 uneven events (N ~ U[50k, 350k], D=8, the event mix): one batched
     call (segmented build + persistent query launch, replayed from its CUDA
     graph) against the same events one by one through the plain path.
@@ -430,6 +542,7 @@ def run_batched(ctx, args, dev):
     outs = [(torch.empty(len(p), dtype=torch.int32, device=dev),
              torch.empty((len(p), K), dtype=torch.int32, device=dev),
              torch.empty((len(p), K), dtype=torch.float32, device=dev)) for p in w.events]
+    torch.cuda.synchronize()   # the copies above ran on torch's stream, not the context's
     stream = ctx.stream
     mk = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
     # plain: every event built and queried on its own
@@ -438,10 +551,10 @@ def run_batched(ctx, args, dev):
     def plain():
         for e, p in enumerate(evs):
             grids[e] = ctx.build_grid(p, r, grid=grids[e])
-            ctx.query(grids[e], p, r, K, True, args.batch_path, outs[e])
+            ctx.query(grids[e], p, r, K, True, path, outs[e])
 
     def batched():
-        ctx.query_batched(evs, r, K, path=args.batch_path, outs=outs)
+        ctx.query_batched(evs, r, K, path=path, outs=outs)
 
     fns = {"plain": plain, "batched": batched}
     for _ in range(args.batch_warmup):
@@ -466,7 +579,7 @@ def run_batched(ctx, args, dev):
     wins, losses, p = sign_test(times["batched"], times["plain"])
     pairs = int(sum(int(c.sum().item()) for c, _, _ in outs))
     return {"workload": w.name, "events": len(evs), "queries": total, "neighbor_pairs": pairs,
-            "path": args.batch_path, "rounds": args.batch_reps, "warmup": args.batch_warmup,
+            "path": path, "rounds": args.batch_reps, "warmup": args.batch_warmup,
             "plain": res["plain"], "batched": res["batched"],
             "batched_over_plain": res["plain"]["ms_median"] / res["batched"]["ms_median"],
             "sign_test": {"batched_faster": wins, "plain_faster": losses, "p_two_sided": p}}
@@ -514,24 +627,53 @@ def run_compact(ctx, grid, pts, r, K, path, stream, reps=20):
     return out
 
 
+def _serving_inputs(n_ev, sizes, D):
+    """All events of the serving stream in one page-locked host buffer
+    (drawn by a pool of spawned processes: about 250 M points in total)."""
+    import multiprocessing as mp
+    import torch
+    from paper_2609_31980_gb300 import synth
+    offs = np.zeros(n_ev + 1, np.int64)
+    offs[1:] = np.cumsum(sizes[:n_ev])
+    flat = torch.empty(int(offs[-1]) * D, dtype=torch.float32, pin_memory=True)
+    fv = flat.numpy()
+    workers = max(1, min(16, len(os.sched_getaffinity(0))))
+    with mp.get_context("spawn").Pool(workers) as pool:
+        for e, p in enumerate(pool.imap(synth.config5_event_args, [(e, sizes) for e in range(n_ev)],
+                                        chunksize=4)):
+            fv[offs[e] * D:offs[e + 1] * D] = p.reshape(-1)
+    return [fv[offs[e] * D:offs[e + 1] * D].reshape(-1, D) for e in range(n_ev)], flat
+
+
 def run_serving(ctx, args):
-    """A Poisson stream of events (N log-uniform on [20k, 400k], D=8, the
-    event mix) through the continuous-batching loop, against the same stream
-    served one event at a time (1 slot, batch of 1)."""
+    """The serving workload: a Poisson stream of 2,000 events (N log-uniform
+    on [20k, 400k], D=8, the event mix, r=0.1, K=64) through the
+    continuous-batching loop under a 40 GB budget, against the same stream
+    served one event at a time (1 slot, batch of 1), at several offered loads
+    (multiples of the measured one-at-a-time capacity).
+
+    Inputs are page-locked host buffers.  Results go to a pool of
+    page-locked output buffers: request e writes buffer e mod P (P > the
+    requests one batch round can hold), so host memory stays bounded; two
+    requests far apart in arrival order may share a buffer, which is harmless
+    here because this leg only times the loop (served results are compared
+    with the oracle and the single-event path by the tests)."""
     import torch
     from paper_2609_31980_gb300 import synth
     n_ev = args.serve_events
-    sizes = synth.serving_sizes(n_ev)
-    K, r = 64, 0.1
-    events, outs = [], []
-    for e in range(n_ev):
-        p = torch.from_numpy(synth.config5_event(e, sizes)).pin_memory()
-        events.append(p.numpy())
-        outs.append((torch.empty(len(p), dtype=torch.int32).pin_memory().numpy(),
-                     torch.empty((len(p), K), dtype=torch.int32).pin_memory().numpy(),
-                     torch.empty((len(p), K), dtype=torch.float32).pin_memory().numpy()))
+    sizes = synth.serving_sizes(2000)[:n_ev]
+    K, r, D = 64, 0.1, 8
+    t0 = time.perf_counter()
+    events, _flat = _serving_inputs(n_ev, sizes, D)
+    gen_s = time.perf_counter() - t0
+    P = min(n_ev, max(args.serve_pool, args.serve_slots * args.serve_batch + 2))
+    pool_n = [int(sizes[j::P].max()) for j in range(P)]
+    pool = [(torch.empty(n, dtype=torch.int32, pin_memory=True).numpy(),
+             torch.empty((n, K), dtype=torch.int32, pin_memory=True).numpy(),
+             torch.empty((n, K), dtype=torch.float32, pin_memory=True).numpy()) for n in pool_n]
+    outs = [tuple(a[:len(events[e])] for a in pool[e % P]) for e in range(n_ev)]
     budget = 40 * 10 ** 9
-    # warm-up (module loading, first launches), not measured
+    # warm-up (module loading, first launches, slot workspaces), not measured
     ctx.serve(events[:8], np.zeros(8), r, K, budget, slots=args.serve_slots,
               max_batch=args.serve_batch, outs=outs[:8])
     # sequential capacity: everything queued at t = 0, one event at a time
@@ -541,7 +683,10 @@ def run_serving(ctx, args):
         _, _, seq0 = ctx.serve(events, np.zeros(n_ev), r, K, budget, slots=1, max_batch=1,
                                outs=outs)
         cap = max(cap, seq0["events_per_s"])
-    out = {"events": n_ev, "mean_N": float(np.mean(sizes)), "budget_bytes": budget,
+    out = {"workload": f"serving-{n_ev}ev-logU20k-400k-x8-r0.1-k64", "events": n_ev,
+           "mean_N": float(np.mean(sizes)), "points": int(np.sum(sizes)),
+           "budget_bytes": budget, "slots": args.serve_slots, "max_batch": args.serve_batch,
+           "output_pool_buffers": P, "input_generation_s": gen_s,
            "sequential_capacity_events_per_s": cap, "loads": []}
     for load in args.serve_loads:
         arr = synth.poisson_arrivals(n_ev, load * cap)
@@ -550,9 +695,10 @@ def run_serving(ctx, args):
         _, _, sq = ctx.serve(events, arr, r, K, budget, slots=1, max_batch=1, outs=outs)
         out["loads"].append({
             "rate_x_sequential_capacity": load, "rate_hz": load * cap,
-            "continuous": {k: cb[k] for k in ("p50_ms", "p99_ms", "events_per_s",
+            "continuous": {k: cb[k] for k in ("p50_ms", "p99_ms", "events_per_s", "completed",
                                                "peak_inflight_batches", "peak_inflight_bytes")},
-            "sequential": {k: sq[k] for k in ("p50_ms", "p99_ms", "events_per_s")}})
+            "sequential": {k: sq[k] for k in ("p50_ms", "p99_ms", "events_per_s", "completed")}})
+    del pool, outs, events, _flat
     return out
 
 
@@ -655,7 +801,10 @@ def main():
     ap.add_argument("--batch-warmup", type=int, default=10)
     ap.add_argument("--batch-path", default="grid", choices=["grid", "tc", "auto"])
     ap.add_argument("--no-serving", action="store_true")
-    ap.add_argument("--serve-events", type=int, default=96)
+    ap.add_argument("--no-design-points", action="store_true")
+    ap.add_argument("--no-tuned-batch", action="store_true")
+    ap.add_argument("--serve-events", type=int, default=2000)
+    ap.add_argument("--serve-pool", type=int, default=48, help="page-locked output buffers")
     ap.add_argument("--serve-slots", type=int, default=4)
     ap.add_argument("--serve-batch", type=int, default=8)
     ap.add_argument("--serve-loads", type=float, nargs="*", default=[0.9, 1.5, 3.0])

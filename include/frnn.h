@@ -70,7 +70,10 @@ typedef struct frnn_grid frnn_grid;
 const char* frnn_version(void);
 
 /*
- * Create a context on the current CUDA device.
+ * Create a context on the current CUDA device.  The context owns the reused,
+ * pre-allocated device workspace of Sec. 4.1 (all intermediate buffers of a
+ * search live in it, so a repeated search allocates nothing) and keeps
+ * inputs and outputs device-resident.
  *   cuda_stream       cudaStream_t to enqueue on (NULL = the legacy default
  *                     stream).  Not owned.
  *   mem_budget_bytes  cap on device memory the context may hold for grids and
@@ -81,7 +84,8 @@ const char* frnn_version(void);
  */
 frnn_status frnn_create(frnn_ctx** out, void* cuda_stream, size_t mem_budget_bytes);
 
-/* Synchronise the context's stream and free everything it owns.  Grids built
+/* Release the workspace of frnn_create (Sec. 4.1).
+ * Synchronise the context's stream and free everything it owns.  Grids built
  * through it are detached: they can no longer be queried, and must still be
  * released with frnn_grid_destroy.  NULL is accepted. */
 frnn_status frnn_destroy(frnn_ctx* ctx);
@@ -108,7 +112,9 @@ frnn_status frnn_destroy(frnn_ctx* ctx);
 frnn_status frnn_build_grid(frnn_ctx* ctx, const float* refs, int64_t N, int D, float r,
                             frnn_grid** grid);
 
-/* Free a grid (after its pending work completes).  NULL is accepted. */
+/* Free a grid (after its pending work completes).  NULL is accepted.  A grid
+ * is the device-resident cell structure of Sec. 2's uniform-grid method; it
+ * stays resident between queries until this call. */
 frnn_status frnn_grid_destroy(frnn_grid* grid);
 
 /*
@@ -138,8 +144,11 @@ typedef struct frnn_event {
 } frnn_event;
 
 /*
- * Self-query of many independent events of uneven size (each event is its own
- * point set; no pair crosses events).  All events' grids are built by one set
+ * Self-query of many independent events of uneven size.  The paper evaluates
+ * one tracking event at a time (Sec. 4.1) and has no batched interface: this
+ * call applies Eq. 1 to every event of a batch, with the same result as one
+ * call per event.  Each event is its own point set; no pair crosses events.
+ * All events' grids are built by one set
  * of segmented launches and all queries run in one persistent launch, the
  * whole sequence captured once in a CUDA graph and replayed while the event
  * list (pointers and sizes) stays the same.  Results per event are bit-identical
@@ -229,16 +238,21 @@ frnn_status frnn_serve_run(frnn_ctx* ctx, const frnn_request* reqs, int n_reqs, 
  * Every call shares the one array and leaves its contents there (each call
  * clears what must start at zero); calls whose work overlaps on the GPU
  * (other streams or host threads) race on it and must be serialised by the
- * caller.  The array's device address is looked up once per device, on the
- * first call with that device current; make that first call before any
- * stream capture begins.
+ * caller.  Each call looks the array's device address up with the caller's
+ * device current.  The first call on a device also loads the library's
+ * device code there, which places the array: make that first call before
+ * any stream capture begins.  Error paths may allocate host memory for
+ * their message; the query itself allocates nothing.
  */
 frnn_status frnn_self_query_noalloc(const float* pts, int64_t N, int D, float r, int K,
                                     int32_t* counts, int32_t* idx, float* dist2,
                                     void* cuda_stream);
 
 /* Wait for the context's stream and report (then clear) the device status
- * word: FRNN_OK or the first device-side error since the last sync. */
+ * word: FRNN_OK or the first device-side error since the last sync.  The
+ * paper specifies no error interface; this call exists because the work is
+ * asynchronous (device-resident input and output, Sec. 4.1) and device-side
+ * conditions can only be read back after it. */
 frnn_status frnn_sync(frnn_ctx* ctx);
 
 /* Text of the last error on this context (static storage of the context;

@@ -30,9 +30,7 @@ CFLAGS = ["-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp",
 
 _lock = threading.Lock()
 _lib = None
-# The tests of the pins themselves run them against copies of this oracle with
-# one mistake planted; such a copy is loaded from this path instead.
-_OVERRIDE = os.environ.get("FRNN_ORACLE_LIB")
+_lib_path = None   # set only by use_library()
 
 
 def build(force: bool = False) -> str:
@@ -48,11 +46,23 @@ def build(force: bool = False) -> str:
     return _LIB_PATH
 
 
+def use_library(path: str) -> None:
+    """Load the checker from ``path`` instead of building this file.  Only the
+    test of the pins calls it (through pytest's ``--oracle-lib`` option), to
+    run the pins against a copy of the oracle with one mistake planted; it must
+    be called before the first oracle call of the process."""
+    global _lib_path
+    with _lock:
+        if _lib is not None:
+            raise RuntimeError("the oracle library is already loaded")
+        _lib_path = path
+
+
 def _load():
     global _lib
     with _lock:
         if _lib is None:
-            lib = ctypes.CDLL(_OVERRIDE or build())
+            lib = ctypes.CDLL(_lib_path or build())
             i64, f32p = ctypes.c_int64, ctypes.c_void_p
             lib.frnn_oracle_query.argtypes = [f32p, f32p, i64, f32p, i64, ctypes.c_int,
                                               ctypes.c_float, ctypes.c_int,

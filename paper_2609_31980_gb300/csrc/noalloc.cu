@@ -3,14 +3,14 @@
 // Some callers cannot allocate memory when they run a query: code that runs
 // under a fixed, pre-reserved memory plan (an embedded or real-time host
 // loop that must not call into the allocator, a process whose device memory
-// is carved up in advance among several engines), or code that runs where
-// allocation is not allowed or would synchronise the device (for example
-// inside a stream callback, or between the launches of a latency-critical
-// pipeline).  frnn_self_query_noalloc serves them: its grid and counters
-// live in one fixed-size array in device memory that the library declares
-// at file scope, so the call issues no cudaMalloc, cudaFree, page-locked
-// allocation or library allocation at all; the caller provides the points
-// and the output rows.
+// is carved up in advance among several engines), or code between the
+// launches of a latency-critical pipeline, where cudaMalloc or cudaFree
+// would synchronise the whole device.  frnn_self_query_noalloc serves them:
+// its grid and counters live in one fixed-size array in device memory that
+// the library declares at file scope, so the call issues no cudaMalloc,
+// cudaFree, page-locked allocation or library allocation at all; the caller
+// provides the points and the output rows.  The call is synchronous: it
+// waits for its own work and reads the device status word back.
 //
 // The array holds the grid of at most kNoAllocMaxPoints points in up to 16
 // dimensions (about 7 MB).  Every GPU that loads the library keeps it until
@@ -19,11 +19,13 @@
 // work overlaps on the GPU (other streams, other host threads) race on the
 // array and give wrong results: serialise them.
 //
-// The device address of the array is looked up with cudaGetSymbolAddress
-// the first time the entry point runs on a device (with that device
-// current) and kept per device; that first call should come before any
-// stream capture begins.
-#include <mutex>
+// In host code the array's name stands for a host-side shadow, not a device
+// address; every call looks the device address up with cudaGetSymbolAddress,
+// with the caller's device current, and passes that pointer to the kernels.
+// The first call on a device also loads the library's device code there,
+// which places the array; make that first call before any stream capture
+// begins.  Looking the address up on every call (instead of caching it)
+// keeps it right after a device reset, which places the array anew.
 #include <string>
 
 #include "frnn_host.h"
@@ -112,32 +114,17 @@ static int32_t* carve(GridBufs& g, char* b, int64_t n, int D) {
     return reinterpret_cast<int32_t*>(take(sizeof(int32_t) * 16));
 }
 
-// per-device address of the scratch array (looked up once per device)
-static std::mutex g_na_mutex;
-static void* g_na_addr[64];
-
-static void* scratch_address(int dev) {
-    std::lock_guard<std::mutex> lock(g_na_mutex);
-    if (dev < 0 || dev >= 64) return nullptr;
-    if (!g_na_addr[dev]) {
-        void* p = nullptr;
-        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess || !p) {
-            cudaGetLastError();
-            return nullptr;
-        }
-        g_na_addr[dev] = p;
+// Device address of the scratch array on the current device, or NULL.  The
+// lookup allocates nothing once the device code is loaded.
+static void* scratch_address() {
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p) {
+        cudaGetLastError();
+        return nullptr;
     }
-    return g_na_addr[dev];
+    return p;
 }
-
-// Error text of the internal helpers.  Reserved once when the library loads,
-// so filling it on an error path needs no allocation (messages are short).
-struct NaErr {
-    std::string s;
-    NaErr() { s.reserve(1024); }
-};
-static NaErr g_na_err_holder;
 
 }  // namespace frnn
 
@@ -153,7 +140,7 @@ frnn_status frnn_self_query_noalloc(const float* pts, int64_t N, int D, float r,
         return FRNN_ERR_INVALID_ARG;
     if (N > 0 && (!pts || !counts || !idx || !dist2)) return FRNN_ERR_INVALID_ARG;
     if (N == 0) return FRNN_OK;
-    std::string& err = g_na_err_holder.s;
+    std::string err;   // text of the build/launch helpers; only filled on an error path
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
     int dev = 0, sms = 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||
@@ -161,7 +148,7 @@ frnn_status frnn_self_query_noalloc(const float* pts, int64_t N, int D, float r,
         cudaGetLastError();
         return FRNN_ERR_CUDA;
     }
-    char* base = static_cast<char*>(scratch_address(dev));
+    char* base = static_cast<char*>(scratch_address());
     if (!base) return FRNN_ERR_CUDA;
     GridBufs g;
     int32_t* status = carve(g, base, N, D);

@@ -41,8 +41,9 @@ def clustered(n_clusters: int, per_cluster: int, n_background: int, d: int,
     pts += g.normal(0.0, sigma, size=pts.shape)
     bg = g.uniform(-box, box, size=(n_background, d))
     allp = np.concatenate([pts, bg], axis=0)
-    g.shuffle(allp, axis=0)
-    return allp.astype(np.float32)
+    # rows in the order of a Fisher-Yates permutation: the same points and
+    # generator state as shuffling the rows in place, about ten times faster
+    return allp[g.permutation(len(allp))].astype(np.float32)
 
 
 def mixed_degrees(d: int, seed, sigma: float = 0.025) -> np.ndarray:
@@ -135,3 +136,8 @@ def config5_event(e: int, sizes: np.ndarray) -> np.ndarray:
     """Event ``e`` of the serving stream (drawn on demand: 2000 events do not
     all need to live in memory at once)."""
     return event_mix(int(sizes[e]), 8, (5, e))
+
+
+def config5_event_args(args) -> np.ndarray:
+    """config5_event(*args): one picklable argument, for process pools."""
+    return config5_event(*args)

@@ -52,8 +52,9 @@ def test_pins_catch_planted_mistake(name, tmp_path):
     c.write_text(src.replace(a, b, 1))
     so = tmp_path / "liboracle_mutant.so"
     subprocess.run(["gcc", *oracle.CFLAGS, "-o", str(so), str(c), "-lm"], check=True)
-    env = dict(os.environ, FRNN_ORACLE_LIB=str(so), OMP_NUM_THREADS="4")
+    env = dict(os.environ, OMP_NUM_THREADS="4")
     p = subprocess.run([sys.executable, "-m", "pytest", "-q", "-p", "no:cacheprovider",
+                        f"--oracle-lib={so}",
                         os.path.join(ROOT, "tests", "test_oracle_pins.py")],
                        cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
     # exit status 1: some pin failed (not an error in collecting or running them)

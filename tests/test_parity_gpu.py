@@ -358,20 +358,32 @@ def test_batched_equals_alone_and_oracle(ctx):
                 _assert_rows_equal(got, oracle.self_query(p, 0.1, 64))
 
 
-def test_batch_64_uneven_events_full_size_sampled(ctx):
+def test_batch_64_uneven_events_full_size(ctx):
     # the batched workload at full size (64 events, N ~ U[50k, 350k], 14.1 M
-    # points) in the batched launch the benchmark times; per event 16 sampled
-    # rows against the oracle's brute force over that event
+    # points) in the batched launch the benchmark times.  Every row of every
+    # event equals the plain single-event path (compared on the device: counts,
+    # indices and distance bits), and per event 256 sampled rows equal the
+    # oracle's brute force over that event
     import torch
     w = synth.config4()
     evs = [torch.from_numpy(p).cuda() for p in w.events]
     outs = ctx.query_batched(evs, w.r, w.K, path="grid")
     ctx.sync()
-    for e, (p, (c, i, d)) in enumerate(zip(w.events, outs)):
-        rows = _sample_rows(len(p), 16, 900 + e)
+    grid = None
+    for e, (p, t, (c, i, d)) in enumerate(zip(w.events, evs, outs)):
+        grid = ctx.build_grid(t, w.r, grid=grid)
+        pc, pi, pd = ctx.query(grid, t, w.r, w.K, True, "grid")
+        ctx.sync()
+        assert torch.equal(c, pc), f"event {e}: batched counts differ from the plain path"
+        assert torch.equal(i, pi), f"event {e}: batched indices differ from the plain path"
+        assert torch.equal(d.view(torch.int32), pd.view(torch.int32)), \
+            f"event {e}: batched distances differ from the plain path"
+        del pc, pi, pd
+        rows = _sample_rows(len(p), 256, 900 + e)
         rt = torch.from_numpy(rows).cuda()
         got = (c[rt].cpu().numpy(), i[rt].cpu().numpy(), d[rt].cpu().numpy())
         _assert_rows_equal(got, oracle.self_query(p, w.r, w.K, rows=rows))
+    grid.close()
 
 
 def test_batched_many_events_long_cell_scan(ctx):
@@ -515,12 +527,14 @@ def test_autotune_and_mixed_path_batches(ctx):
         assert a["cell_mult"] in (1, 2) and a["ms"] > 0
         evs = [small, large, synth.event_mix(2500, 8, (42, 2)), synth.event_mix(12000, 8, (42, 3))]
         tev = [torch.from_numpy(p).cuda() for p in evs]
+        wants = [oracle.self_query(p, 0.1, 64) for p in evs]
         for rep in range(2):
             outs = ctx.query_batched(tev, 0.1, 64, path="auto")
             ctx.sync()
-            for p, (c, i, d) in zip(evs, outs):
-                _assert_rows_equal((c.cpu().numpy(), i.cpu().numpy(), d.cpu().numpy()),
-                                   _gpu_self(ctx, p, 0.1, 64, path="grid"))
+            for p, want, (c, i, d) in zip(evs, wants, outs):
+                got = (c.cpu().numpy(), i.cpu().numpy(), d.cpu().numpy())
+                _assert_rows_equal(got, _gpu_self(ctx, p, 0.1, 64, path="grid"))
+                _assert_rows_equal(got, want)
         # auto single-event queries follow the tuned class and stay exact
         _assert_rows_equal(_gpu_self(ctx, small, 0.1, 64, path="auto"),
                            oracle.self_query(small, 0.1, 64))
@@ -545,16 +559,20 @@ def test_serving_results_equal_alone_and_overlap(ctx):
     assert st["completed"] == len(events) and st["rejected"] == 0
     assert np.all(lat > 0) and st["p99_ms"] >= st["p50_ms"] > 0
     assert st["peak_inflight_batches"] >= 2
-    for p, (c, i, d) in zip(events, outs):
+    for e, (p, (c, i, d)) in enumerate(zip(events, outs)):
         _assert_rows_equal((c, i, d), _gpu_self(ctx, p, 0.1, 64, path="grid"))
+        if e % 5 == 0:   # a seeded subset against the oracle, every row
+            _assert_rows_equal((c, i, d), oracle.self_query(p, 0.1, 64))
     # a small budget serialises the same stream (no request fits twice)
     big = max(sizes)
     outs2, lat2, st2 = ctx.serve(events[:8], arrivals[:8], 0.1, 64,
                                  budget_bytes=int(big * (8 * 4 + 4 + 64 * 8) * 3.5), slots=4,
                                  max_batch=6)
     assert st2["completed"] == 8
-    for p, (c, i, d) in zip(events[:8], outs2):
+    for e, (p, (c, i, d)) in enumerate(zip(events[:8], outs2)):
         _assert_rows_equal((c, i, d), _gpu_self(ctx, p, 0.1, 64, path="grid"))
+        if e % 3 == 0:
+            _assert_rows_equal((c, i, d), oracle.self_query(p, 0.1, 64))
 
 
 def test_serving_rejects_oversized_request(ctx):
