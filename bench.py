@@ -178,16 +178,27 @@ def algorithmic_query_bytes(N: int, D: int, K: int) -> int:
     return N * DP * 4 * 2 + N * 4 + N * 4 + N * K * 8
 
 
-def launches_per_step(N: int, path: str = "grid") -> int:
+def _cell_cap(N: int, D: int) -> int:
+    """Cells the library allows an N-point grid with its default axes
+    (mirrors cell_cap_for in build.cu: 24 N for five axes, 2 N for four)."""
+    na = min(D, 5)
+    c = 24 * N if na >= 5 else (2 * N if na == 4 else N // 2 + 1)
+    return min(max(16384, c), (1 << 27) if na >= 5 else (1 << 24))
+
+
+def _scan_launches(L: int) -> int:
+    nb = (L + 2047) // 2048
+    return 1 if nb == 1 else (2 if nb <= 512 else 3)
+
+
+def launches_per_step(N: int, D: int, path: str = "grid") -> int:
     """Kernels one build + query launches (mirrors the library's host code)."""
-    cap = max(16384, N // 2 + 1)
-    L = cap + 1
-    scan = 1 if (L + 2047) // 2048 == 1 else 2
-    build = 1 + 1 + 1 + scan + 1 + 1 + 1 + scan + 1    # init bbox cellid scan scatter pack rowtasks scan emit
+    L = _cell_cap(N, D) + 1
+    build = 5 + _scan_launches(L)          # init bbox cellid scan(s) scatter pack
     if path == "tc":
         # operand preparation + 128-query tasks (rowtasks scan emit), tc query, selection pass
-        return build + 1 + (1 + scan + 1) + 2
-    return build + 2                                   # grid query + selection pass
+        return build + 1 + (1 + _scan_launches(L) + 1) + 2
+    return build + 2                       # grid query + selection pass
 
 
 def max_over_ranks(x: float, device) -> float:
@@ -458,7 +469,7 @@ def run_ours(args):
                       "d2h_bytes_per_step": N * 4 + 2 * N * K * 4,
                       "ms_per_step": e2e_s * 1e3, "output": "dense rows (frnn_self_query_host)",
                       "matches_device_path": bool(ok_e2e)},
-        "gpu_launches": launches_per_step(N, "tc" if kern_is_tc else "grid") * args.steps,
+        "gpu_launches": launches_per_step(N, D, "tc" if kern_is_tc else "grid") * args.steps,
         "wall_s": wall,
     }
     if clocks:

@@ -144,31 +144,38 @@ static bool budget_allows(frnn_ctx* c, size_t old_bytes, size_t new_bytes) {
 // Predicted device bytes of a GridBufs layout (mirrors grid_alloc's layout).
 static size_t predict_grid_bytes(int E, const int64_t* n, int D, const int64_t* caps) {
     const int DP = padded_dim(D);
-    int64_t nt = 0, L = 0, tc = 0;
+    int64_t nt = 0, L = 0;
     for (int e = 0; e < E; ++e) {
-        const int64_t cap = caps ? caps[e] : cell_cap_for(n[e]);
-        nt += n[e];
-        L += cap + 1;
-        tc += n[e] / kTaskQueries + cap + 2;
+        nt += n[e] + 1;
+        L += caps[e] + 1;
     }
     nt = std::max<int64_t>(nt, 1);
     size_t b = 0;
     b += sizeof(EventHdr) * E + 16 * (E + 1) + sizeof(int32_t) * kBBoxStride * kBBoxCopies * E;
-    b += (size_t)nt * (sizeof(float) * DP + 4 * sizeof(int32_t) + sizeof(Overflow));
-    b += (size_t)L * 2 * sizeof(int32_t) + (size_t)tc * sizeof(Task);
+    b += (size_t)(nt + kTcRowPad) * sizeof(float) * DP +
+         (size_t)nt * (4 * sizeof(int32_t) + sizeof(Overflow));
+    b += (size_t)L * sizeof(int32_t) + (size_t)(L / 2048 + 1) * sizeof(int32_t);
     b += 64 * 1024 + 16 * 256;
     return b;
 }
 
+static int build_naxes(const frnn_ctx* ctx, int64_t N, int D);
+// gridded axes a cell budget is sized for: the requested count, or for the
+// automatic choice (0) the most the build may take
+static int cap_axes(int naxes, int D) { return naxes > 0 ? naxes : std::min(D, kMaxAxes); }
+
 static frnn_status alloc_accounted(frnn_ctx* c, GridBufs& g, int E, const int64_t* n, int D,
-                                   const int64_t* caps) {
+                                   const int64_t* caps_in) {
+    std::vector<int64_t> caps(E);
+    for (int e = 0; e < E; ++e)
+        caps[e] = caps_in ? caps_in[e] : cell_cap_for(n[e], cap_axes(build_naxes(c, n[e], D), D));
     const size_t old_bytes = g.bytes;
-    const size_t need = predict_grid_bytes(E, n, D, caps);
+    const size_t need = predict_grid_bytes(E, n, D, caps.data());
     const bool reuse = g.base && need <= g.bytes;
     if (!reuse && !budget_allows(c, old_bytes, need))
         return fail(c, FRNN_ERR_BUDGET, "request exceeds the context's memory budget");
     std::string err;
-    frnn_status s = grid_alloc(g, E, n, D, err, caps);
+    frnn_status s = grid_alloc(g, E, n, D, err, caps.data());
     c->held = c->held - old_bytes + g.bytes;
     if (s != FRNN_OK) return fail(c, s, err);
     return FRNN_OK;
@@ -178,7 +185,6 @@ static frnn_status alloc_accounted(frnn_ctx* c, GridBufs& g, int E, const int64_
 // FRNN_PATH_GRID the scalar grid scan; FRNN_PATH_AUTO takes the tensor-core
 // path for D >= 8 unless the context's option says otherwise.
 static bool default_tc(const frnn_ctx* ctx, int D, int naxes);
-static int build_naxes(const frnn_ctx* ctx, int64_t N, int D);
 static const frnn_ctx::Tuned* find_tuned(const frnn_ctx* ctx, int64_t N, int D, int K);
 // naxes: gridded axes of the grid being queried (-1: what a build would use now)
 static bool use_tc_path(const frnn_ctx* ctx, int D, unsigned flags, int64_t N = -1, int K = -1,
@@ -212,7 +218,8 @@ static frnn_status prepare_tc(frnn_ctx* ctx, GridBufs& g, const GridBufs& center
     if (g.tc_ready && &g == &center_src) return FRNN_OK;
     const size_t before = g.tc_bytes;
     std::string err;
-    frnn_status s = tc_prepare(g, center_src, capturing ? ctx->gstream : ctx->stream, err);
+    frnn_status s = tc_prepare(g, center_src, ctx->d_status, capturing ? ctx->gstream : ctx->stream,
+                               err);
     ctx->held = ctx->held - std::min(ctx->held, before) + g.tc_bytes;
     if (s != FRNN_OK) return fail(ctx, s, err);
     return FRNN_OK;
@@ -246,16 +253,15 @@ static int build_mult(const frnn_ctx* ctx, int64_t N, int D) {
     if (ctx->cell_mult > 0) return ctx->cell_mult;
     const frnn_ctx::Tuned* t = find_tuned(ctx, N, D, -1);
     if (t) return t->m;
-    // default: cells of r/2 when at most three coordinates are gridded (a
-    // finer grid pays there: 0.374 vs 0.398 ms at 300k x 8, 0.85 vs 1.06 ms
-    // at 500k x 12), cells of r with four (the 27 neighbour rows of m = 1)
-    return build_naxes(ctx, N, D) <= 3 ? 2 : 1;
+    // default: cells of r/2 when at most three coordinates are gridded on
+    // request (a finer grid pays there), cells of r otherwise
+    const int na = build_naxes(ctx, N, D);
+    return (na >= 1 && na <= 3 && D > 3) ? 2 : 1;
 }
-// gridded axes when neither the option nor the tuner fixes them: four (the
-// paper's retained four-axis gridding, Sec. 6; measured faster on the
-// tracking-shaped events: 0.365 vs 0.388 ms at 300k x 8, 0.70 vs 1.26 ms at
-// 500k x 12)
-static int default_naxes(int D) { return D < 4 ? D : 4; }
+// gridded axes when neither the option nor the tuner fixes them: 0, the
+// build's automatic choice (five axes, or four when the cell budget makes
+// five-axis cells too coarse; all of them for D < 5)
+static int default_naxes(int) { return 0; }
 static int build_naxes(const frnn_ctx* ctx, int64_t N, int D) {
     if (ctx->grid_naxes > 0) return std::min(ctx->grid_naxes, D);
     const frnn_ctx::Tuned* t = find_tuned(ctx, N, D, -1);
@@ -266,7 +272,7 @@ static int build_naxes(const frnn_ctx* ctx, int64_t N, int D) {
 // 500k x 12), but not the scan over four (0.70 ms): its 128-query tasks are
 // poorly filled by the shorter rows of a four-axis grid
 static bool default_tc(const frnn_ctx* ctx, int D, int naxes) {
-    return ctx->auto_tc && D >= 10 && naxes <= 3;
+    return ctx->auto_tc && D >= 10 && naxes >= 1 && naxes <= 3;
 }
 
 extern "C" {
@@ -675,7 +681,7 @@ static frnn_status enqueue_batched(frnn_ctx* ctx, const frnn_event* ev, int n_ev
     }
     if (any_tc) {
         // operands were allocated before any capture; enqueue their build
-        s = tc_prepare(ctx->batch, ctx->batch, st, err);
+        s = tc_prepare(ctx->batch, ctx->batch, ctx->d_status, st, err);
         if (s != FRNN_OK) return fail(ctx, s, err);
         q.tc_stats = ctx->d_tcstat;
         q.path_filter = mixed ? 1 : -1;
@@ -975,7 +981,7 @@ frnn_status frnn_autotune(frnn_ctx* ctx, const float* refs, int64_t N, int D, fl
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     const int saved_m = ctx->cell_mult, saved_x = ctx->exit_dims, saved_a = ctx->grid_naxes;
-    frnn_tune_result bestr{FRNN_PATH_GRID, 1, 0, INFINITY, default_naxes(D)};
+    frnn_tune_result bestr{FRNN_PATH_GRID, 1, 0, INFINITY, std::min(D, kMaxAxes)};
     frnn_status s = FRNN_OK;
     frnn_grid* g = nullptr;
     auto timed = [&](auto&& fn, float& ms) -> frnn_status {
@@ -993,11 +999,22 @@ frnn_status frnn_autotune(frnn_ctx* ctx, const float* refs, int64_t N, int D, fl
         ms = bestms;
         return frnn_sync(ctx);
     };
-    // grid configurations: 3 gridded axes (all of them for D < 3) with m = 1,
-    // 2; 4 axes with m = 1 (the only multiple four axes allow)
+    // grid configurations: five gridded axes with cells of r, four with
+    // cells of r and r/2, three with cells of r/2 and r/3 (all of them for
+    // smaller D); the neighbour rows, (2m+1)^(axes-1), stay within 128
     struct GridCfg { int naxes, m; };
-    std::vector<GridCfg> gcfg = {{std::min(D, 3), 1}, {std::min(D, 3), 2}};
-    if (D >= 4) gcfg.push_back({4, 1});
+    std::vector<GridCfg> gcfg;
+    auto add_cfg = [&](int na, int m) {
+        na = std::min(na, D);
+        for (const GridCfg& c : gcfg)
+            if (c.naxes == na && c.m == m) return;
+        gcfg.push_back({na, m});
+    };
+    add_cfg(5, 1);
+    add_cfg(4, 1);
+    add_cfg(4, 2);
+    add_cfg(3, 2);
+    add_cfg(3, 3);
     for (size_t gi = 0; gi < gcfg.size() && s == FRNN_OK; ++gi) {
         const int m = gcfg[gi].m;
         ctx->cell_mult = m;
@@ -1007,10 +1024,7 @@ frnn_status frnn_autotune(frnn_ctx* ctx, const float* refs, int64_t N, int D, fl
         if (s != FRNN_OK) break;
         struct Cand { unsigned path; int exit_dims; };
         std::vector<Cand> cands;
-        if (!(flags & FRNN_PATH_TC)) {
-            cands.push_back({FRNN_PATH_GRID, 0});
-            if (D >= 5) cands.push_back({FRNN_PATH_GRID, 3});
-        }
+        if (!(flags & FRNN_PATH_TC)) cands.push_back({FRNN_PATH_GRID, 0});
         if (D >= 8 && !(flags & FRNN_PATH_GRID)) cands.push_back({FRNN_PATH_TC, 0});
         if (cands.empty()) {
             s = fail(ctx, FRNN_ERR_UNSUPPORTED, "the tensor-core path needs D >= 8");
@@ -1051,8 +1065,8 @@ frnn_status frnn_set_option(frnn_ctx* ctx, frnn_option opt, int64_t value) {
     if (!ctx) return FRNN_ERR_INVALID_ARG;
     switch (opt) {
         case FRNN_OPT_CELL_MULT:
-            if (value < 0 || value > 2)
-                return fail(ctx, FRNN_ERR_INVALID_ARG, "m must be 0 (tuned), 1 or 2");
+            if (value < 0 || value > 3)
+                return fail(ctx, FRNN_ERR_INVALID_ARG, "m must be 0 (tuned), 1, 2 or 3");
             ctx->cell_mult = (int)value;
             return FRNN_OK;
         case FRNN_OPT_GRID_AXES:
@@ -1061,7 +1075,7 @@ frnn_status frnn_set_option(frnn_ctx* ctx, frnn_option opt, int64_t value) {
             return FRNN_OK;
         case FRNN_OPT_GRID_NAXES:
             if (value < 0 || value > kMaxAxes)
-                return fail(ctx, FRNN_ERR_INVALID_ARG, "gridded axes must be 0 (tuned) or 1..4");
+                return fail(ctx, FRNN_ERR_INVALID_ARG, "gridded axes must be 0 (tuned) or 1..5");
             ctx->grid_naxes = (int)value;
             return FRNN_OK;
         case FRNN_OPT_EXIT_DIMS:

@@ -17,10 +17,8 @@
 //   k_cellid    cell id of every point and its rank inside the cell (atomics)
 //   scan        exclusive warp-shuffle prefix scan of the counts -> cell starts
 //   k_scatter   slot -> original index, slot -> cell
-//   k_pack      cell-sorted pair-interleaved coordinates
-//   k_rowtasks  per row of cells: number of 16-query warp tasks
-//   scan        -> task starts
-//   k_emit      write the tasks
+//   k_pack      cell-sorted coordinates, one row of DP floats per slot
+// (the tensor-core path adds its 128-query tiles: k_rowtasks, a scan, k_emit)
 #include <algorithm>
 #include <cmath>
 
@@ -235,6 +233,103 @@ static_assert(kBBoxCopies == 32, "one copy per lane when the copies are combined
 
 static_assert(kBuildPtsPerBlock == 256, "eight warps combine the box copies");
 
+// One candidate grid: k gridded axes (the last k coordinates, or the k
+// widest), cell multiple m, the cell edge fitted to the proof's condition,
+// 1024 cells per axis and the event's cell budget (inv_h starts at
+// fl_down(m / (r (1+2^-10))) and is lowered until all three hold), and the
+// expected fraction of the event a query's neighbourhood covers if the
+// points were spread evenly: the product over the gridded axes of
+// min(1, (2m+1) cells / extent).  The parameter step keeps the candidate
+// with the smallest fraction; the choice never changes results.
+struct GridFit {
+    int naxes = 1, m = 1;
+    int axes[kMaxAxes] = {0, 0, 0, 0, 0};
+    int dims[kMaxAxes] = {1, 1, 1, 1, 1};
+    float inv_h = 0.f;
+    int32_t ncells = 1;
+    float frac = INFINITY;
+};
+
+__device__ void grid_fit(GridFit& f, const int32_t* bb, int D, int k, int m, int axes_mode,
+                         float r, int32_t cap, bool valid) {
+    f.naxes = k;
+    // neighbour rows, (2m+1)^(k-1), are enumerated 32 per round: at most kMaxNbrRows
+    int mm = max(m, 1);
+    for (;;) {
+        int rows = 1;
+        for (int a = 1; a < k; ++a) rows *= 2 * mm + 1;
+        if (rows <= kMaxNbrRows || mm == 1) break;
+        --mm;
+    }
+    f.m = mm;
+    if (axes_mode == 1 && D > k) {
+        // the k widest coordinates (ties by lower index), in index order
+        bool used[kMaxD];
+        for (int j = 0; j < kMaxD; ++j) used[j] = false;
+        for (int a = 0; a < k; ++a) {
+            int best = -1;
+            float bw = -1.f;
+            for (int j = 0; j < D; ++j) {
+                if (used[j]) continue;
+                float w = ordered_to_float(bb[16 + j]) - ordered_to_float(bb[j]);
+                if (!(w <= bw)) { best = j; bw = w; }   // NaN-safe: first wins on NaN
+            }
+            used[best] = true;
+        }
+        int a = 0;
+        for (int j = 0; j < D; ++j) if (used[j]) f.axes[a++] = j;
+    } else {
+        for (int a = 0; a < k; ++a) f.axes[a] = D - k + a;
+    }
+    if (!valid) {
+        f.frac = 1.f;
+        return;
+    }
+    double ext[kMaxAxes] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    for (int a = 0; a < k; ++a)
+        ext[a] = (double)ordered_to_float(bb[16 + f.axes[a]]) - (double)ordered_to_float(bb[f.axes[a]]);
+    const double rd = (double)r;
+    const double rho = rd * (1.0 + 0x1p-20);
+    float ih = __double2float_rd((double)mm / (rd * (1.0 + 0x1p-10)));
+    int dims[kMaxAxes] = {1, 1, 1, 1, 1};
+    for (int it = 0; it < 4096; ++it) {
+        bool ok = true;
+        int64_t cells = 1;
+        for (int a = 0; a < k; ++a) {
+            double c = floor(ext[a] * (double)ih) + 1.0;
+            if (c > kMaxDimsPerAxis) { ok = false; break; }
+            dims[a] = (int)c;
+            cells *= dims[a];
+            if ((double)ih * (rho + 0x1p-21 * ext[a]) + 0x1p-148 >= (double)mm - 0x1p-20) ok = false;
+        }
+        if (ok && cells <= cap) break;
+        ih = __double2float_rd((double)ih * 0.9);
+        if (!(ih > 0.f)) {
+            ih = 0.f;
+            for (int a = 0; a < kMaxAxes; ++a) dims[a] = 1;
+            break;
+        }
+    }
+    int64_t cells = 1;
+    for (int a = 0; a < kMaxAxes; ++a) {
+        f.dims[a] = a < k ? dims[a] : 1;
+        cells *= f.dims[a];
+    }
+    if (cells > cap) {   // unreachable in practice; one cell is always safe
+        ih = 0.f;
+        cells = 1;
+        for (int a = 0; a < kMaxAxes; ++a) f.dims[a] = 1;
+    }
+    f.inv_h = ih;
+    f.ncells = (int32_t)cells;
+    double frac = 1.0;
+    for (int a = 0; a < k; ++a) {
+        const double span = ih > 0.f ? (2.0 * mm + 1.0) / (double)ih : INFINITY;
+        if (ext[a] > 0.0) frac *= fmin(1.0, span / ext[a]);
+    }
+    f.frac = (float)frac;
+}
+
 __device__ void event_params(EventHdr* hdr, int e, int D, const int32_t* bbox, float r, int m,
                              int axes_mode, int naxes_req, int32_t* counts) {
     __shared__ int32_t bb[kBBoxStride];
@@ -266,51 +361,35 @@ __device__ void event_params(EventHdr* hdr, int e, int D, const int32_t* bbox, f
     // the last cell-array entry of the event counts its pair padding slot, so
     // the next event's slots start on a pair boundary
     counts[h.cell_off + h.cell_cap] = (int32_t)(h.n & 1);
-    // per-event presets (batched autotuning) win over the call's options
+    // per-event presets (batched autotuning) win over the call's options;
+    // 0 = automatic: the widest count up to kMaxAxes, or one fewer axis when
+    // the cell budget makes that grid's neighbourhoods smaller
     const int want = h.naxes > 0 ? h.naxes : naxes_req;
-    const int naxes = min(D, min(max(want, 1), kMaxAxes));
-    h.naxes = naxes;
-    h.m = h.m > 0 ? h.m : m;
-    // neighbour rows are enumerated one per lane of a warp: at most 32
-    while (h.m > 1 && neighbour_rows(h) > 32) --h.m;
-    m = h.m;
-    int axes[kMaxAxes] = {0, 0, 0, 0};
-    if (axes_mode == 1 && D > naxes) {
-        // the naxes widest coordinates (ties by lower index), in index order
-        bool used[kMaxD];
-        for (int k = 0; k < kMaxD; ++k) used[k] = false;
-        for (int a = 0; a < naxes; ++a) {
-            int best = -1;
-            float bw = -1.f;
-            for (int k = 0; k < D; ++k) {
-                if (used[k]) continue;
-                float w = ordered_to_float(bb[16 + k]) - ordered_to_float(bb[k]);
-                if (!(w <= bw)) { best = k; bw = w; }   // NaN-safe: first wins on NaN
-            }
-            used[best] = true;
-        }
-        int a = 0;
-        for (int k = 0; k < D; ++k) if (used[k]) axes[a++] = k;
-    } else {
-        for (int a = 0; a < naxes; ++a) axes[a] = D - naxes + a;
-    }
+    const int m_req = h.m > 0 ? h.m : m;
     bool valid = bb[32] == 0 && h.n > 0;
-    double ext[kMaxAxes] = {0.0, 0.0, 0.0, 0.0};
-    for (int a = 0; a < kMaxAxes; ++a) {
-        h.axes[a] = a < naxes ? axes[a] : 0;
-        h.dims[a] = 1;
-        h.lo[a] = 0.f;
-        h.hi[a] = 0.f;
-        if (a < naxes && valid) {
-            float lo = ordered_to_float(bb[axes[a]]);
-            float hi = ordered_to_float(bb[16 + axes[a]]);
-            if (!isfinite(lo) || !isfinite(hi)) valid = false;
-            h.lo[a] = lo;
-            h.hi[a] = hi;
-            ext[a] = (double)hi - (double)lo;
-        }
+    for (int k = 0; k < D && valid; ++k) {
+        if (!isfinite(ordered_to_float(bb[k])) || !isfinite(ordered_to_float(bb[16 + k]))) valid = false;
     }
+    const int kmax = min(D, kMaxAxes);
+    int k_hi = want > 0 ? min(D, min(want, kMaxAxes)) : kmax;
+    int k_lo = want > 0 ? k_hi : max(1, kmax - 1);
+    GridFit best;
+    best.frac = INFINITY;
+    for (int k = k_hi; k >= k_lo; --k) {
+        GridFit f;
+        grid_fit(f, bb, D, k, m_req, axes_mode, r, h.cell_cap, valid);
+        if (f.frac < best.frac) best = f;
+    }
+    const int naxes = best.naxes;
+    h.naxes = naxes;
+    h.m = best.m;
     h.valid = valid ? 1 : 0;
+    for (int a = 0; a < kMaxAxes; ++a) {
+        h.axes[a] = a < naxes ? best.axes[a] : 0;
+        h.dims[a] = a < naxes ? best.dims[a] : 1;
+        h.lo[a] = a < naxes && valid ? ordered_to_float(bb[best.axes[a]]) : 0.f;
+        h.hi[a] = a < naxes && valid ? ordered_to_float(bb[16 + best.axes[a]]) : 0.f;
+    }
     for (int k = 0; k < kMaxD; ++k) {
         float c = 0.f;
         if (valid && k < D) {
@@ -320,46 +399,10 @@ __device__ void event_params(EventHdr* hdr, int e, int D, const int32_t* bbox, f
         }
         h.ctr[k] = c;
     }
-    if (!valid) {
-        h.inv_h = 0.f;
-        h.ncells = 1;
-        hdr[e] = h;
-        return;
-    }
-    const double rd = (double)r;
-    const double rho = rd * (1.0 + 0x1p-20);
-    float ih = __double2float_rd((double)m / (rd * (1.0 + 0x1p-10)));
-    int dims[kMaxAxes] = {1, 1, 1, 1};
-    for (int it = 0; it < 4096; ++it) {
-        bool ok = true;
-        int64_t cells = 1;
-        for (int a = 0; a < naxes; ++a) {
-            double c = floor(ext[a] * (double)ih) + 1.0;
-            if (c > kMaxDimsPerAxis) { ok = false; break; }
-            dims[a] = (int)c;
-            cells *= dims[a];
-            if ((double)ih * (rho + 0x1p-21 * ext[a]) + 0x1p-148 >= (double)m - 0x1p-20) ok = false;
-        }
-        if (ok && cells <= h.cell_cap) break;
-        ih = __double2float_rd((double)ih * 0.9);
-        if (!(ih > 0.f)) {
-            ih = 0.f;
-            for (int a = 0; a < kMaxAxes; ++a) dims[a] = 1;
-            break;
-        }
-    }
-    int64_t cells = 1;
-    for (int a = 0; a < kMaxAxes; ++a) {
-        h.dims[a] = a < naxes ? dims[a] : 1;
-        cells *= h.dims[a];
-    }
-    if (cells > h.cell_cap) {   // unreachable in practice; one cell is always safe
-        ih = 0.f;
-        cells = 1;
+    h.inv_h = valid ? best.inv_h : 0.f;
+    h.ncells = valid ? best.ncells : 1;
+    if (!valid)
         for (int a = 0; a < kMaxAxes; ++a) h.dims[a] = 1;
-    }
-    h.inv_h = ih;
-    h.ncells = (int32_t)cells;
     hdr[e] = h;
 }
 
@@ -445,48 +488,39 @@ __global__ void __launch_bounds__(kBuildPtsPerBlock) k_scatter(const EventHdr* h
     cell[slot] = c;
 }
 
-// Cell-sorted coordinates, one thread per slot pair: the two points' input
-// rows are gathered and the pair's interleaved block (2 DP floats) is written
-// with 16-byte stores, consecutive pairs by consecutive threads.  A slot
-// without a point (an odd event's padding) gets NaN: never within any radius.
-__global__ void __launch_bounds__(256) k_pack(const EventHdr* hdr, int E, int64_t npairs, int D,
+// Cell-sorted coordinates, one thread per slot: the point's input row is
+// gathered and written as one row of DP floats (zero padding) with 16-byte
+// stores, consecutive slots by consecutive threads.  A slot without a point
+// (an odd event's padding) gets NaN: never within any radius.
+__global__ void __launch_bounds__(256) k_pack(const EventHdr* hdr, int E, int64_t nslots, int D,
                                               int DP, const int32_t* perm, float* pts) {
     pdl_trigger();
     pdl_wait();
-    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (q >= npairs) return;
-    // event of this pair: events occupy pair-aligned slot ranges
-    const int64_t s0 = 2 * q;
+    const int64_t s0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s0 >= nslots) return;
+    // event of this slot: events occupy pair-aligned slot ranges
     int lo = 0, hi = E - 1;
     while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
         if (hdr[mid].pt_off <= s0) lo = mid; else hi = mid - 1;
     }
     const float* refs = hdr[lo].refs;
-    const int32_t i0 = perm[s0], i1 = perm[s0 + 1];
+    const int32_t i0 = perm[s0];
     const float* a = i0 >= 0 ? refs + (int64_t)i0 * D : nullptr;
-    const float* b = i1 >= 0 ? refs + (int64_t)i1 * D : nullptr;
     const float nan = __int_as_float(0x7fc00000);
     float4* dst = reinterpret_cast<float4*>(pts + s0 * DP);
     if ((D & 3) == 0 && (reinterpret_cast<uintptr_t>(refs) & 15) == 0) {
-        // rows of whole 16-byte vectors: two coordinates of each point per store
         const float4 nan4 = make_float4(nan, nan, nan, nan);
-        for (int j = 0; j < D / 4; ++j) {
-            const float4 u = a ? __ldg(reinterpret_cast<const float4*>(a) + j) : nan4;
-            const float4 v = b ? __ldg(reinterpret_cast<const float4*>(b) + j) : nan4;
-            dst[2 * j] = make_float4(u.x, v.x, u.y, v.y);
-            dst[2 * j + 1] = make_float4(u.z, v.z, u.w, v.w);
-        }
-        for (int j = D / 2; j < DP / 2; ++j) dst[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int j = 0; j < D / 4; ++j)
+            dst[j] = a ? __ldg(reinterpret_cast<const float4*>(a) + j) : nan4;
         return;
     }
-    for (int j = 0; j < DP / 2; ++j) {
-        const int k0 = 2 * j, k1 = 2 * j + 1;
+    for (int j = 0; j < DP / 4; ++j) {
         float4 v;
-        v.x = a ? (k0 < D ? __ldg(a + k0) : 0.f) : nan;
-        v.y = b ? (k0 < D ? __ldg(b + k0) : 0.f) : nan;
-        v.z = a ? (k1 < D ? __ldg(a + k1) : 0.f) : nan;
-        v.w = b ? (k1 < D ? __ldg(b + k1) : 0.f) : nan;
+        v.x = a ? (4 * j + 0 < D ? __ldg(a + 4 * j + 0) : 0.f) : nan;
+        v.y = a ? (4 * j + 1 < D ? __ldg(a + 4 * j + 1) : 0.f) : nan;
+        v.z = a ? (4 * j + 2 < D ? __ldg(a + 4 * j + 2) : 0.f) : nan;
+        v.w = a ? (4 * j + 3 < D ? __ldg(a + 4 * j + 3) : 0.f) : nan;
         dst[j] = v;
     }
 }
@@ -519,7 +553,8 @@ __global__ void k_rowtasks(const EventHdr* hdr, const int64_t* cell_off, int E, 
     const int e = find_event64(cell_off, E, i);
     const EventHdr& h = hdr[e];
     const int64_t row = i - cell_off[e];
-    const int64_t nrows = h.valid ? (int64_t)h.dims[1] * h.dims[2] * h.dims[3] : 1;
+    int64_t nrows = 1;   // rows: every gridded coordinate but the fastest
+    for (int a = 1; a < kMaxAxes && h.valid; ++a) nrows *= h.dims[a];
     int32_t nt = 0;
     if (row < nrows) {
         int32_t base, cnt;
@@ -534,7 +569,8 @@ __global__ void k_rowtasks(const EventHdr* hdr, const int64_t* cell_off, int E, 
 
 __global__ void k_emit(const EventHdr* hdr, const int64_t* cell_off, int E, int64_t L,
                        const int32_t* cstart, const int32_t* rtask_start,
-                       const int32_t* rtask_count_src, Task* tasks, int W, int A) {
+                       const int32_t* rtask_count_src, Task* tasks, int64_t task_cap, int W,
+                       int A, int32_t* status) {
     pdl_trigger();
     pdl_wait();
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -549,6 +585,10 @@ __global__ void k_emit(const EventHdr* hdr, const int64_t* cell_off, int E, int6
     row_slots(h, cstart, row, base, cnt);
     const int32_t w0 = base & ~(A - 1);
     for (int32_t t = t0; t < t1; ++t) {
+        if (t >= task_cap) {   // never with the tensor-core path's capacity; guarded all the same
+            atomicOr(status, kStatusCapacity);
+            return;
+        }
         const int32_t ws = w0 + (t - t0) * W;
         const int32_t a = max(ws, base);
         const int32_t b = min(ws + W, base + cnt);
@@ -561,12 +601,13 @@ __global__ void k_emit(const EventHdr* hdr, const int64_t* cell_off, int E, int6
     }
 }
 
-void enqueue_tasks(GridBufs& g, int W, int A, Task* out, int32_t* count_out, cudaStream_t st) {
+void enqueue_tasks(GridBufs& g, int W, int A, Task* out, int64_t out_cap, int32_t* count_out,
+                   int32_t* d_status, cudaStream_t st) {
     const unsigned nb = (unsigned)std::max<int64_t>(1, ceil_div(g.L, 256));
     launch_pdl(k_rowtasks, dim3(nb), dim3(256), 0, st, g.hdr, g.cell_off, g.E, g.L, g.cstart, g.rtask, W, A);
     enqueue_scan(g.rtask, g.L, g.parts, count_out, st);
-    launch_pdl(k_emit, dim3(nb), dim3(256), 0, st, g.hdr, g.cell_off, g.E, g.L, g.cstart, g.rtask, count_out, out, W,
-                               A);
+    launch_pdl(k_emit, dim3(nb), dim3(256), 0, st, g.hdr, g.cell_off, g.E, g.L, g.cstart, g.rtask,
+               count_out, out, out_cap, W, A, d_status);
 }
 
 // ------------------------------------------------------------------ scan
@@ -735,9 +776,17 @@ void enqueue_scan(int32_t* data, int64_t n, int32_t* parts, int32_t* total, cuda
 
 // ------------------------------------------------------------------ host
 
-int64_t cell_cap_for(int64_t n) {
-    int64_t c = std::max<int64_t>(16384, n / 2 + 1);
-    return std::min<int64_t>(c, (int64_t)1 << 24);
+// Five gridded axes at a cell edge of about r need about (extent / r)^5
+// cells (5.2 M for the 300k x 8 tracking-like event, whose coordinates span
+// [-1.06, 1.06] at r = 0.1), four about (extent / r)^4; the budget grows with
+// n so that the cells stay near r on such events, and the parameter step
+// falls back to one axis fewer when the budget would make the five-axis
+// cells too coarse.
+int64_t cell_cap_for(int64_t n, int naxes) {
+    const int64_t per = naxes >= 5 ? 24 : (naxes == 4 ? 2 : 0);
+    int64_t c = per ? per * n : n / 2 + 1;
+    c = std::max<int64_t>(16384, c);
+    return std::min<int64_t>(c, naxes >= 5 ? ((int64_t)1 << 27) : ((int64_t)1 << 24));
 }
 
 static size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
@@ -751,19 +800,21 @@ void grid_free(GridBufs& g) {
 }
 
 frnn_status grid_alloc(GridBufs& g, int E, const int64_t* n, int D, std::string& err,
-                       const int64_t* caps) {
+                       const int64_t* caps, int naxes) {
     const int DP = padded_dim(D);
-    int64_t n_total = 0, L = 0, task_cap = 0, nblk = 0;
+    int64_t n_total = 0, L = 0, task_cap = 0, nblk = 0, nchunks = 0;
     g.h_hdr.assign(E, EventHdr{});
     g.h_blk_start.assign(E + 1, 0);
     g.h_cell_off.assign(E + 1, 0);
     for (int e = 0; e < E; ++e) {
-        const int64_t cap = caps ? caps[e] : cell_cap_for(n[e]);
+        const int64_t cap = caps ? caps[e] : cell_cap_for(n[e], naxes);
         EventHdr& h = g.h_hdr[e];
         h.n = n[e];
         h.pt_off = n_total;
         h.cell_off = L;
         h.cell_cap = (int32_t)cap;
+        h.qchunk0 = (int32_t)nchunks;
+        nchunks += ceil_div(n[e], kChunkQ);
         g.h_blk_start[e] = (int32_t)nblk;
         g.h_cell_off[e] = L;
         n_total += (n[e] + 1) & ~(int64_t)1;   // pair-aligned event regions
@@ -773,8 +824,8 @@ frnn_status grid_alloc(GridBufs& g, int E, const int64_t* n, int D, std::string&
     }
     g.h_blk_start[E] = (int32_t)nblk;
     g.h_cell_off[E] = L;
-    if (n_total >= INT32_MAX || L >= ((int64_t)1 << 26) || task_cap >= INT32_MAX ||
-        nblk >= INT32_MAX) {
+    if (n_total >= INT32_MAX || L >= ((int64_t)1 << 30) || task_cap >= INT32_MAX ||
+        nblk >= INT32_MAX || nchunks >= INT32_MAX) {
         err = "problem too large for one call (points, cells or tasks exceed the limits)";
         return FRNN_ERR_INVALID_ARG;
     }
@@ -786,8 +837,9 @@ frnn_status grid_alloc(GridBufs& g, int E, const int64_t* n, int D, std::string&
     g.task_cap = task_cap;
     g.nblk = nblk;
     g.nparts = scan_parts_needed(L);
-    const bool fits = g.base && g.cap_n >= n_total && g.cap_L >= L && g.cap_tasks >= task_cap &&
-                      g.cap_E >= E && g.cap_blk >= nblk;
+    g.nchunks = nchunks;
+    const bool fits = g.base && g.cap_n >= n_total && g.cap_L >= L && g.cap_E >= E &&
+                      g.cap_blk >= nblk;
     const int64_t cn = std::max<int64_t>(n_total, 1);
     if (!fits) {
         if (g.base) {
@@ -810,8 +862,6 @@ frnn_status grid_alloc(GridBufs& g, int E, const int64_t* n, int D, std::string&
         const size_t o_cid = take(sizeof(int32_t) * cn);
         const size_t o_rnk = take(sizeof(int32_t) * cn);
         const size_t o_cst = take(sizeof(int32_t) * L);
-        const size_t o_rt = take(sizeof(int32_t) * L);
-        const size_t o_tasks = take(sizeof(Task) * task_cap);
         const size_t o_ovf = take(sizeof(Overflow) * cn);
         const size_t o_sc = take(sizeof(int32_t) * kScalars);
         const size_t o_parts = take(sizeof(int32_t) * g.nparts);
@@ -836,8 +886,8 @@ frnn_status grid_alloc(GridBufs& g, int E, const int64_t* n, int D, std::string&
         g.cid = reinterpret_cast<int32_t*>(b + o_cid);
         g.rnk = reinterpret_cast<int32_t*>(b + o_rnk);
         g.cstart = reinterpret_cast<int32_t*>(b + o_cst);
-        g.rtask = reinterpret_cast<int32_t*>(b + o_rt);
-        g.tasks = reinterpret_cast<Task*>(b + o_tasks);
+        g.rtask = nullptr;   // the tensor-core operands carry the task builder's scratch
+        g.tasks = nullptr;
         g.ovf = reinterpret_cast<Overflow*>(b + o_ovf);
         g.scalars = reinterpret_cast<int32_t*>(b + o_sc);
         g.parts = reinterpret_cast<int32_t*>(b + o_parts);
@@ -875,7 +925,7 @@ static inline unsigned blocks_for(int64_t n, int t) {
     return (unsigned)std::max<int64_t>(1, ceil_div(n, t));
 }
 
-// Cell ids, the cell-start scan, slot maps, coordinates, the warp tasks.
+// Cell ids, the cell-start scan, slot maps, coordinates.
 static void enqueue_sort(GridBufs& g, size_t smem_pts, int check_finite, int32_t* d_status,
                          cudaStream_t st) {
     const int E = g.E, D = g.D;
@@ -885,12 +935,9 @@ static void enqueue_sort(GridBufs& g, size_t smem_pts, int check_finite, int32_t
     launch_pdl(k_scatter, dim3((unsigned)g.nblk), dim3(kBuildPtsPerBlock), 0, st, 
         g.hdr, g.blk_start, E, D, g.DP, g.cstart, g.cid, g.rnk, g.pts, g.perm, g.cell);
     if (g.n_total > 0)
-        launch_pdl(k_pack, dim3((unsigned)ceil_div(g.n_total / 2, 256)), dim3(256), 0, st, g.hdr, E, g.n_total / 2, D,
-                                                                       g.DP, g.perm, g.pts);
-    // warp tasks in row order (numbered by a scan: the query takes them in
-    // this order, so concurrent warps work on neighbouring cells; tasks
-    // appended by atomics in arbitrary order made the query 2.9 % slower)
-    enqueue_tasks(g, kTaskQueries, 1, g.tasks, g.scalars + kScNTasks, st);
+        launch_pdl(k_pack, dim3((unsigned)ceil_div(g.n_total, 256)), dim3(256), 0, st, g.hdr, E,
+                   g.n_total, D, g.DP, g.perm, g.pts);
+    // no task list: the grid query takes chunks of kChunkQ slots in slot order
 }
 
 frnn_status enqueue_build(GridBufs& g, const float* const* refs, const BuildOpts& o,

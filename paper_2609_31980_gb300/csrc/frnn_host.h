@@ -21,6 +21,10 @@ struct GridBufs {
     int64_t task_cap = 0;   // warp-task capacity
     int64_t nblk = 0;       // blocks of the per-point build kernels
     int64_t nparts = 0;     // scan partial sums needed
+    int64_t nchunks = 0;    // query chunks (kChunkQ slots) over all events
+    // the last query left its overflow list for a compact fill pass that has
+    // not run: the next query clears the list first
+    mutable bool ovf_stale = false;
 
     // allocation (reused when large enough)
     void* base = nullptr;
@@ -41,8 +45,8 @@ struct GridBufs {
     int32_t* cid = nullptr;        // [n_total] input order -> local cell id
     int32_t* rnk = nullptr;        // [n_total] input order -> rank inside its cell
     int32_t* cstart = nullptr;     // [L] cell counts, then (scanned) global start slots
-    int32_t* rtask = nullptr;      // [L] per-row task counts, then task starts
-    Task* tasks = nullptr;         // [task_cap]
+    int32_t* rtask = nullptr;      // [L] per-row task counts, then task starts (tensor-core tiles)
+    Task* tasks = nullptr;         // [task_cap] (unused by the grid query, which takes chunks)
     Overflow* ovf = nullptr;       // [n_total]
     int32_t* scalars = nullptr;    // [kScalars] counters (below)
     int32_t* parts = nullptr;      // [nparts] scan partial sums
@@ -51,7 +55,8 @@ struct GridBufs {
     bool tc_ready = false;
     void* tc_base = nullptr;
     size_t tc_bytes = 0;
-    int64_t tc_cap_rows = 0, tc_cap_tasks = 0, tc_cap_E = 0;
+    int64_t tc_cap_rows = 0, tc_cap_tasks = 0, tc_cap_E = 0, tc_cap_L = 0;
+    int32_t* tc_rtask = nullptr;   // [L] the task builder's per-row scratch
     int tc_K = 0;                  // operand row length (bf16 elements, multiple of 16)
     uint16_t* tcA = nullptr;       // [rows] query-role rows, core-matrix layout
     uint16_t* tcB = nullptr;       // [rows] candidate-role rows, core-matrix layout
@@ -72,27 +77,31 @@ constexpr int kBuildPtsPerBlock = 256;
 // indices into GridBufs::scalars
 constexpr int kScNTasks = 0;        // number of warp tasks
 constexpr int kScCellTotal = 1;     // total of the cell-count scan (= n_total)
-constexpr int kScTaskCounter = 2;   // dynamic task counter of the query kernel
+constexpr int kScTaskCounter = 2;   // chunk counter of the grid query kernel
 constexpr int kScOvfCount = 3;      // overflowed queries
 constexpr int kScTcCounter = 4;     // task counter of the tensor-core kernel
 constexpr int kScTcTasks = 5;      // number of tensor-core tasks
+constexpr int kScOvfDone = 6;       // finished blocks of the selection kernel
 constexpr int kScalars = 16;
 constexpr int kTcRowPad = 512;      // rows readable past the last slot (chunk round-up)
 
-int64_t cell_cap_for(int64_t n);
+// Cells allowed for an n-point event gridded over naxes coordinates (the
+// parameter step enlarges the cells when the grid would need more).
+int64_t cell_cap_for(int64_t n, int naxes);
 
 // Compute the layout for E events of sizes n[e] and allocate (or reuse).
 // caps (optional): per-event cell capacities (a query set binned with a
-// reference grid's parameters must use that grid's capacities).
+// reference grid's parameters must use that grid's capacities); otherwise
+// cell_cap_for(n[e], naxes).
 frnn_status grid_alloc(GridBufs& g, int E, const int64_t* n, int D, std::string& err,
-                       const int64_t* caps = nullptr);
+                       const int64_t* caps = nullptr, int naxes = kMaxAxes);
 void grid_free(GridBufs& g);
 
 struct BuildOpts {
     float r = 0.f;          // grid radius
     int m = 1;              // cell multiple
     int axes_mode = 0;      // 0: last axes, 1: widest axes
-    int naxes = 3;          // gridded axes requested (at most D, at most 4)
+    int naxes = 3;          // gridded axes requested (at most D, at most kMaxAxes)
 };
 
 // Enqueue a full build (bounding boxes, parameters, binning, counting sort,
@@ -104,8 +113,10 @@ frnn_status enqueue_build(GridBufs& g, const float* const* refs, const BuildOpts
                           const GridBufs* params_from, int32_t* d_status, cudaStream_t st,
                           bool capturing, std::string& err);
 
-// Task list: windows of W slots aligned to A within each row of cells.
-void enqueue_tasks(GridBufs& g, int W, int A, Task* out, int32_t* count_out, cudaStream_t st);
+// Task list: windows of W slots aligned to A within each row of cells
+// (at most out_cap tasks; beyond it the status word records a capacity error).
+void enqueue_tasks(GridBufs& g, int W, int A, Task* out, int64_t out_cap, int32_t* count_out,
+                   int32_t* d_status, cudaStream_t st);
 
 // The build for per-event tables already resident on the device.
 frnn_status enqueue_build_resident(GridBufs& g, const BuildOpts& o, int32_t* d_status,
@@ -154,7 +165,7 @@ void enqueue_csr_gather(const int32_t* cnt, const int64_t* offsets, const int32_
 // Tensor-core path: prepare operands (and 128-query tasks) of a point set.
 // center_src: the grid whose per-event centres the operands use (the
 // reference grid; the set itself for self-queries).
-frnn_status tc_prepare(GridBufs& g, const GridBufs& center_src, cudaStream_t st,
+frnn_status tc_prepare(GridBufs& g, const GridBufs& center_src, int32_t* d_status, cudaStream_t st,
                        std::string& err);
 frnn_status enqueue_tc_query(const QueryLaunch& q, cudaStream_t st, std::string& err);
 frnn_status tc_reserve(GridBufs& g, std::string& err);

@@ -12,9 +12,14 @@ namespace frnn {
 
 constexpr int kMaxD = 16;
 constexpr int kMaxK = 1024;
-constexpr int kMaxAxes = 4;
+constexpr int kMaxAxes = 5;
 constexpr int kMaxDimsPerAxis = 1024;   // the grid roundoff proof assumes <= 2^10 cells per axis
-constexpr int kTaskQueries = 16;        // queries per warp task (two lanes each)
+constexpr int kTaskQueries = 16;        // task-list granularity of the build's task builder
+constexpr int kChunkQ = 16;             // query slots per chunk of the grid query kernel
+// neighbour rows of a row of cells, (2m+1)^(naxes-1), that the query kernels
+// enumerate (32 per round of a warp): 81 for five axes with m = 1, 125 for
+// four with m = 2, 49 for three with m = 3
+constexpr int kMaxNbrRows = 128;
 
 // Device status word bits (frnn_sync maps them to frnn_status).
 constexpr int kStatusNonFinite = 1;
@@ -35,13 +40,14 @@ constexpr uint32_t kSpinLimit = 1u << 30;
 // Padded point row: D floats rounded up to a multiple of 4 (16 bytes).
 __host__ __device__ constexpr int padded_dim(int D) { return (D + 3) & ~3; }
 
-// Cell-sorted points are stored pair-interleaved: slots 2p and 2p+1 share a
-// block of 2*DP floats laid out as [s0.d0, s1.d0, s0.d1, s1.d1, ...], so one
-// 16-byte load yields two dimensions of two candidates, the operand layout of
-// the packed f32x2 arithmetic.  Every event's slot range starts on a pair
-// boundary (odd events get one padding slot with NaN coordinates).
-__host__ __device__ constexpr int64_t pair_index(int64_t slot, int k, int DP) {
-    return (slot >> 1) * 2 * DP + 2 * k + (slot & 1);
+// Cell-sorted points are stored as rows of DP floats (coordinate k of slot s
+// at s * DP + k; the padding coordinates are zero), so the points of any
+// slot range form one contiguous, 16-byte aligned block: one bulk copy moves
+// a whole range of candidates into shared memory.  Every event's slot range
+// starts on an even slot (odd events get one padding slot with NaN
+// coordinates), the layout the build's scans and the tensor-core operands use.
+__host__ __device__ constexpr int64_t pt_index(int64_t slot, int k, int DP) {
+    return slot * DP + k;
 }
 
 // Per-event grid header (device-resident, one per event of a build).
@@ -52,7 +58,7 @@ struct EventHdr {
     int64_t cell_off;      // first entry of this event in the cell arrays (cap + 1 entries)
     int32_t cell_cap;      // cells allowed for this event
     int32_t ncells;        // product of dims (written by the parameter step)
-    int32_t naxes;         // gridded axes (1..4); preset by the host: requested count (0: default)
+    int32_t naxes;         // gridded axes (1..5); preset by the host: requested count (0: default)
     int32_t m;             // cell multiple: neighbours are within +-m cells per gridded axis
     int32_t valid;         // 0 if a coordinate was non-finite
     int32_t axes[kMaxAxes];   // gridded coordinate indices; axes[0] varies fastest
@@ -61,6 +67,7 @@ struct EventHdr {
     float hi[kMaxAxes];       // per-axis maximum coordinate
     float inv_h;           // 1 / cell edge (float; the value the cell ids use)
     int32_t path;          // batched queries: 0 = grid scan, 1 = tensor-core pre-filter
+    int32_t qchunk0;       // first query chunk (kChunkQ slots) of this event in its point set
     float ctr[16];         // per-dimension centre of the bounding box (tensor-core operands)
     // query outputs for batched self-queries (row = original point index)
     int32_t* counts;
@@ -74,11 +81,11 @@ struct Task {
     int32_t qslot;   // first query slot (global)
     int32_t nq;      // queries in the task (1..16 for warp tasks, 1..128 for tensor-core tiles)
     int32_t ev;      // event index
-    int32_t row;     // row index within the event: c1 + dims[1] * (c2 + dims[2] * c3)
+    int32_t row;     // row index within the event: c1 + dims[1] * (c2 + dims[2] * (c3 + ...))
 };
 
 // Neighbour rows of a row of cells.  A row fixes every gridded coordinate but
-// the fastest (c0); its neighbours are the rows whose coordinates c1..c3 each
+// the fastest (c0); its neighbours are the rows whose coordinates c1..c4 each
 // differ by at most m.  Neighbour l (0 <= l < neighbour_rows(h)) takes the
 // offsets given by the base-(2m+1) digits of l, minus m.  Returns false if
 // that row lies outside the grid, else its first cell index.
@@ -121,8 +128,9 @@ struct Overflow {
 // Everything the query kernels need, passed by value.
 struct QueryArgs {
     const EventHdr* ev;          // per-event headers (reference grids)
-    const Task* tasks;           // warp tasks over the query slots
-    const int32_t* ntasks;       // device scalar: number of tasks
+    const EventHdr* qev;         // per-event headers of the query set (== ev for self-queries)
+    int32_t nev;                 // events
+    int32_t nchunks;             // query chunks over all events
     const float* qpts;           // cell-sorted query coordinates [*, DP]
     const int32_t* qperm;        // query slot -> original query index (within its event)
     const int32_t* qcell;        // query slot -> local cell id
@@ -133,15 +141,16 @@ struct QueryArgs {
     int32_t* idx;
     float* dist2;
     float r2;                    // fl(r * r)
-    float r2_screen;             // r2 (1 + 2^-16) rounded up: conservative screen bound
     int32_t K;
     int32_t self;                // 1: query slot == reference slot is excluded
     int32_t D;
-    int32_t* task_counter;       // device scalar, zero at launch
+    int32_t* task_counter;       // device scalar: chunk counter, zero at launch
     int32_t* status;             // device status word
     Overflow* ovf;               // overflow list
     int32_t* ovf_count;          // device scalar
     int32_t ovf_cap;
+    int32_t* ovf_done;           // device scalar: finished blocks of the selection kernel
+    int32_t reset_ovf;           // selection kernel: 1 = clear the overflow list when done
     int32_t exit_dims;           // dims summed before the warp early-exit vote
     int32_t path_filter;         // -1: every event; else only events whose path matches
     // compact output.  csr = 1: rows go to idx/dist2 at row * kCsrStageW (no

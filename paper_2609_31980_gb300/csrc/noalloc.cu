@@ -44,13 +44,11 @@ constexpr size_t na_al(size_t x) { return (x + 255) / 256 * 256; }
 constexpr size_t na_bytes(int64_t n, int D) {
     const int64_t cn = ((n + 1) & ~(int64_t)1) > 0 ? ((n + 1) & ~(int64_t)1) : 1;
     const int64_t L = na_cap(n) + 1;
-    const int64_t tasks = n / kTaskQueries + na_cap(n) + 2;
     const int64_t parts = (L + kScanChunk - 1) / kScanChunk > 0 ? (L + kScanChunk - 1) / kScanChunk : 1;
     return na_al(sizeof(EventHdr)) + na_al(sizeof(int32_t) * 2) + na_al(sizeof(int64_t) * 2) +
            na_al(sizeof(int32_t) * kBBoxStride * kBBoxCopies) +
            na_al(sizeof(float) * padded_dim(D) * (cn + kTcRowPad)) + 4 * na_al(sizeof(int32_t) * cn) +
-           2 * na_al(sizeof(int32_t) * L) + na_al(sizeof(Task) * tasks) +
-           na_al(sizeof(Overflow) * cn) + na_al(sizeof(int32_t) * kScalars) +
+           na_al(sizeof(int32_t) * L) + na_al(sizeof(Overflow) * cn) + na_al(sizeof(int32_t) * kScalars) +
            na_al(sizeof(int32_t) * parts) + na_al(sizeof(int32_t) * 16);   // + status word
 }
 constexpr size_t kNoAllocBytes = na_bytes(kNoAllocMaxPoints, kMaxD);
@@ -87,9 +85,9 @@ static int32_t* carve(GridBufs& g, char* b, int64_t n, int D) {
     g.DP = padded_dim(D);
     g.n_total = (n + 1) & ~(int64_t)1;
     g.L = cap + 1;
-    g.task_cap = n / kTaskQueries + cap + 2;
     g.nblk = std::max<int64_t>(1, ceil_div(n, kBuildPtsPerBlock));
     g.nparts = scan_parts_needed(g.L);
+    g.nchunks = ceil_div(n, kChunkQ);   // the header's first chunk is 0
     size_t off = 0;
     auto take = [&](size_t bytes) {
         char* p = b + off;
@@ -106,8 +104,6 @@ static int32_t* carve(GridBufs& g, char* b, int64_t n, int D) {
     g.cid = reinterpret_cast<int32_t*>(take(sizeof(int32_t) * cn));
     g.rnk = reinterpret_cast<int32_t*>(take(sizeof(int32_t) * cn));
     g.cstart = reinterpret_cast<int32_t*>(take(sizeof(int32_t) * g.L));
-    g.rtask = reinterpret_cast<int32_t*>(take(sizeof(int32_t) * g.L));
-    g.tasks = reinterpret_cast<Task*>(take(sizeof(Task) * g.task_cap));
     g.ovf = reinterpret_cast<Overflow*>(take(sizeof(Overflow) * cn));
     g.scalars = reinterpret_cast<int32_t*>(take(sizeof(int32_t) * kScalars));
     g.parts = reinterpret_cast<int32_t*>(take(sizeof(int32_t) * g.nparts));

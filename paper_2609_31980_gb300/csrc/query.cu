@@ -1,6 +1,6 @@
 // query.cu — grid-path fixed-radius query: per-warp scan of the neighbouring
 // cells with candidate tiles staged in shared memory by bulk copies, the exact
-// float32 screen, and warp-level top-K.
+// float32 distance contract, and warp-level top-K.
 //
 // Method (Eq. 1, Sec. 1): for each query, every reference in the cells within
 // +-m cells along each gridded axis is a candidate (complete by the grid's
@@ -9,45 +9,37 @@
 //
 // Organisation on the GPU (differs from the paper's thread-per-query kernel,
 // whose profile showed dependent-load latency and divergence, Sec. 4.2):
-//   * a persistent grid; each warp takes warp tasks (16 cell-sorted queries in
-//     one row of cells) from an atomic counter; lanes q and q + 16 serve query
-//     q and split the candidates between them (even and odd pairs), so a warp
-//     screens the union of 16 neighbourhoods, not 32: fewer candidates per
-//     query (the union of a longer run of queries spans more cells);
-//   * the candidates of a task are the union of its lanes' neighbourhoods: per
-//     neighbour row one contiguous slot range; the ranges, widened to pair
-//     boundaries, form one stream of candidate pairs cut into tiles of TILEP
-//     pairs; the row lanes copy their parts of a tile into the warp's
-//     shared-memory ring with cp.async.bulk, completion tracked by one
-//     mbarrier per buffer (prefetch depth NBUF-1); once the last tile is
-//     consumed the ring is reused for the lists' distances;
-//   * every lane screens every candidate of the tile (broadcast shared loads):
-//     warp-uniform control flow.  Points are stored pair-interleaved, so each
-//     16-byte shared load gives two dimensions of two candidates and one
-//     packed f32x2 instruction serves two candidates.  The packed arithmetic
-//     is only a conservative screen (proof below);
-//   * early rejection: after the first `EXIT` dimensions the warp votes;
-//     partial sums never decrease (round-to-nearest of non-negative terms), so
-//     if every lane's partial sum already exceeds the screen bound the
-//     candidate is rejected for all of them without changing any verdict (the
-//     paper's "roundoff-safe early rejection", Sec. 6).  Gridded axes are the
-//     last ones by default, so the first dimensions are ungridded, the most
-//     selective ones;
-//   * a candidate that passes the whole screen is appended to the lane's list
-//     in shared memory as its stream position; at the end of the task the
-//     warp resolves every lane's entries together (row, slot, range filter)
-//     and recomputes each with the scalar contract, which alone decides
-//     membership and gives the distance (the paper's "conservative screening
-//     and canonical-order recomputation", Sec. 4.2); the original index is
-//     looked up only for the kept entries (the deferred lookup, Table 3);
-//   * for each query the warp loads its lanes' entries (at most 32, one per
-//     lane), sorts them by (d2, index) with a bitonic network across the lanes
-//     (shuffles), and writes the first K (count = min(degree, K)) coalesced,
-//     with the padding.  Lists longer than 32 (never in
-//     the tracking-like workloads) go to an exact selection kernel, keeping
-//     results exact for dense inputs (the paper's Sec. 5 caveat on heap-free
-//     top-K).
+//   * a persistent grid; each warp takes chunks of kChunkQ consecutive
+//     cell-sorted query slots from an atomic counter (no task list: the chunk
+//     number alone locates the slots).  Queries of a chunk that share a cell
+//     form a group; a group's candidates are the points of its neighbour
+//     rows (every gridded coordinate but the fastest within +-m), each
+//     restricted to the +-m cells around the group's cell along the fastest
+//     axis: one contiguous slot range per neighbour row;
+//   * the warp enumerates the neighbour rows of its groups 32 at a time
+//     (lanes), keeps the non-empty ranges in a compact list and concatenates
+//     them into one candidate stream, group after group;
+//   * the stream is cut into tiles of TILE candidates; every range part of a
+//     tile is copied from HBM/L2 into the warp's shared-memory ring with one
+//     cp.async.bulk (cell-sorted points are plain rows, so a slot range is one
+//     contiguous block), completion tracked by one mbarrier per buffer, the
+//     next tile in flight while the current one is evaluated;
+//   * evaluation puts candidates on lanes: each lane takes one candidate of
+//     the tile and computes the contract's squared distance to every query of
+//     that candidate's group (__fsub_rn / __fmul_rn / __fadd_rn in index
+//     order, never contracted), so lanes stay busy however few queries share
+//     a cell.  Accepted pairs (d2, slot) are appended to the query's list in
+//     shared memory (at most kListCap; a longer list sends the row to the
+//     exact selection kernel);
+//   * for each query the warp loads the list (entry e on lane e), resolves the
+//     original indices (the deferred lookup, Table 3), sorts the keys (d2 bits
+//     << 32 | original index) with a bitonic network across the lanes, only as
+//     wide as the row, and writes the first K (count = min(degree, K))
+//     coalesced, with the padding.  Lists longer than kListCap go to an exact
+//     selection kernel, keeping results exact for dense inputs (the paper's
+//     Sec. 5 caveat on heap-free top-K).
 #include <algorithm>
+#include <climits>
 #include <cmath>
 
 #include "frnn_host.h"
@@ -55,551 +47,511 @@
 namespace frnn {
 
 constexpr int kQueryWarps = 4;
-constexpr int kMaxNBuf = 4;
-// candidate streams per query: lanes q, q + G, q + 2G, ... (G = queries per
-// warp task) serve query q, each taking every kStreams-th candidate pair
-constexpr int kStreams = 32 / kTaskQueries;
-static_assert(kStreams * kTaskQueries == 32, "the lanes of a warp split evenly");
 constexpr uint32_t kFull = 0xffffffffu;
-// per-lane list in shared memory: a lane holds about half of its query's
-// entries, so 24 rarely overflows (an overflow only sends the row to the
-// selection kernel) and the smaller lists let seven CTAs share an SM
-constexpr int kListCap = 24;
-constexpr int kRowCap = 32;       // entries of one query sorted across the warp (one per lane)
-constexpr int kListStride = 33;   // entry e of lane l at e*33 + l: conflict-free both ways
-static_assert(kRowCap <= kCsrStageW, "a staged compact row holds a whole row");
+constexpr int kListCap = 32;      // accepted entries a query keeps in the kernel (one per lane)
+constexpr int kListStr = 33;      // list row stride (entries): conflict-free both ways
+constexpr int kRangeCap = 128;    // compact candidate ranges of one batch of groups
+constexpr int kNbrRounds = kMaxNbrRows / 32;
+static_assert(kListCap <= kCsrStageW, "a staged compact row holds a whole kernel row");
+static_assert(kRangeCap >= kMaxNbrRows, "one group's ranges always fit a batch");
+static_assert(kChunkQ <= 16, "group search over at most 16 groups");
 
 template <int D>
 struct QCfg {
     static constexpr int DP = padded_dim(D);
-    // candidate pairs per tile, ring buffers and CTAs per SM.  The ring (two
-    // tiles) doubles as the list distances once the tiles are consumed, so up
-    // to D = 8 a warp needs under 8 KB of shared memory and seven CTAs (28
-    // warps, at most 72 registers) share an SM, which the latency-bound scan
-    // prefers.  Measured at 300k x 8 (before the warp-wide row sort): 2 KB
-    // tiles with six CTAs 0.292 ms, 1 KB tiles 0.310 (0.321 with five CTAs),
-    // 3 KB tiles with five CTAs 0.298; after it, seven CTAs 0.266 against six
-    // 0.270.  At 500k x 12: 3 KB tiles 0.493 ms, 2.25 KB 0.512, 1.5 KB 0.548.
-    static constexpr int TILEP = DP == 4 ? 64 : (DP == 8 ? 32 : (DP == 12 ? 32 : 16));
-    static constexpr int MINB = DP <= 8 ? 7 : 4;
-    static constexpr int NBUF = 2;
-    // default vote point (measured: 2 and 3 tie at D = 8, 3 is best at D = 12)
-    static constexpr int EXIT = D <= 4 ? D : (D >= 10 ? 3 : 2);
-    // sort two short query rows at once, one per half-warp.  Measured: 500k x
-    // 12 (about 12 neighbours per clustered query) 0.437 -> 0.424 ms; at 300k
-    // x 8 (about 25, rows rarely pair) the paired loop cost 0.8 %, so lower
-    // dimensions keep the one-row loop
+    // candidates per tile and ring buffers; CTAs per SM from the per-warp
+    // shared memory (the scan is latency-bound and wants resident warps)
+    static constexpr int TILE = 64;
+    static constexpr int NB = 2;
+    static constexpr int MINB = DP <= 4 ? 6 : (DP <= 8 ? 5 : (DP <= 12 ? 4 : 3));
+    // sort two short query rows at once, one per half-warp (rows of at most
+    // 16 entries: the 500k x 12 event's clustered queries have about 12)
     static constexpr bool PAIR_ROWS = D >= 10;
 };
 
-__host__ __device__ constexpr size_t ring_floats(int DP, int TILEP, int NB) {
-    return (size_t)NB * TILEP * 2 * DP;
-}
-__host__ __device__ constexpr size_t warp_smem_bytes(int DP, int TILEP, int NB);
-__host__ __device__ constexpr size_t query_smem_bytes(int DP, int TILEP, int NB) {
-    return (size_t)kQueryWarps * warp_smem_bytes(DP, TILEP, NB);
+// Per-warp shared memory.  Every bulk-copy destination (the ring) starts on
+// a 128-byte boundary and holds whole rows of DP floats (16-byte multiples).
+struct WarpSmem {
+    float* ring;      // [NB][TILE][DP] candidate coordinates
+    int32_t* tslot;   // [NB][TILE] candidate slots
+    float* Q;         // [kChunkQ][DP] the chunk's query coordinates
+    float* Ld;        // [kChunkQ][kListStr] accepted squared distances
+    int32_t* Li;      // [kChunkQ][kListStr] accepted slots, then original indices
+    uint64_t* bars;   // [NB]
+    int32_t* rlo;     // [kRangeCap] first slot of each compact range
+    int32_t* rpre;    // [kRangeCap + 1] stream position of each range; sentinel = length
+    int32_t* cnt;     // [kChunkQ] accepted entries per query
+};
+
+template <int D>
+__host__ __device__ constexpr size_t warp_smem_bytes() {
+    using C = QCfg<D>;
+    return ((size_t)C::NB * C::TILE * C::DP * 4 + (size_t)C::NB * C::TILE * 4 +
+            (size_t)kChunkQ * C::DP * 4 + 2 * (size_t)kChunkQ * kListStr * 4 + C::NB * 8 +
+            (size_t)kRangeCap * 4 + (size_t)(kRangeCap + 1) * 4 + (size_t)kChunkQ * 4 + 127) /
+           128 * 128;
 }
 
-// ------------------------------------------------------------- packed f32x2
-// Two float32 lanes per instruction.  The assembler contracts packed
-// multiply/add pairs into fused multiply-adds whatever the flags (measured), so
-// packed arithmetic is used ONLY for a conservative screen: for any subset of
-// k <= 16 dimensions, fused or unfused rounding keeps the packed partial sum
-// s' within (1 +- 2^-24)^(2k) of the exact sum S of the same rounded squared
-// differences, and the contract's full sum s_D >= S (1 - 2^-24)^(2D).  Hence
-// s' > r2 (1 + 2^-16) implies s_D > r2: rejecting there never drops a pair.
-// Every candidate that survives is recomputed with the scalar contract
-// (__fsub_rn / __fmul_rn / __fadd_rn, never contracted), which decides
-// membership and gives the returned distance (the paper's "conservative
-// screening and canonical-order recomputation", Sec. 4.2).
-
-__device__ __forceinline__ uint64_t f2_sub(uint64_t a, uint64_t b) {
-    uint64_t d;
-    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-    return d;
-}
-__device__ __forceinline__ uint64_t f2_fma(uint64_t a, uint64_t b, uint64_t c) {
-    uint64_t d;
-    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
-    return d;
-}
-__device__ __forceinline__ uint64_t f2_pack(float lo, float hi) {
-    uint64_t d;
-    asm("mov.b64 %0, {%1, %2};" : "=l"(d) : "f"(lo), "f"(hi));
-    return d;
-}
-__device__ __forceinline__ void f2_unpack(uint64_t v, float& lo, float& hi) {
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
-}
-// screening step for two candidates: s' += (q - c)^2 (fused)
-__device__ __forceinline__ uint64_t f2_screen(uint64_t s, uint64_t q, uint64_t c) {
-    const uint64_t d = f2_sub(q, c);
-    return f2_fma(d, d, s);
+template <int D>
+__device__ __forceinline__ WarpSmem carve_warp(unsigned char* base) {
+    using C = QCfg<D>;
+    WarpSmem w;
+    w.ring = reinterpret_cast<float*>(base);
+    w.tslot = reinterpret_cast<int32_t*>(w.ring + C::NB * C::TILE * C::DP);
+    w.Q = reinterpret_cast<float*>(w.tslot + C::NB * C::TILE);
+    w.Ld = w.Q + kChunkQ * C::DP;
+    w.Li = reinterpret_cast<int32_t*>(w.Ld + kChunkQ * kListStr);
+    w.bars = reinterpret_cast<uint64_t*>(w.Li + kChunkQ * kListStr);
+    w.rlo = reinterpret_cast<int32_t*>(w.bars + C::NB);
+    w.rpre = w.rlo + kRangeCap;
+    w.cnt = w.rpre + kRangeCap + 1;
+    return w;
 }
 
 __device__ __forceinline__ uint64_t make_key(float d2, int32_t j) {
     return ((uint64_t)__float_as_uint(d2) << 32) | (uint32_t)j;
 }
 
-// ------------------------------------------------------------- grid query
-
-// Per-warp shared memory: the tile ring, the per-lane lists, the task's
-// neighbour-row table, per-lane accept counters and the ring's mbarriers.
-struct WarpSmem {
-    float* ring;
-    float* Ld;
-    int32_t* Li;
-    int32_t* Rpp;    // [32] first stream pair of neighbour row l
-    int32_t* Rprs;   // [32] its first pair in slot space
-    int32_t* Rrs;    // [32] its slot range [rs, re)
-    int32_t* Rre;
-    int32_t* acc;    // [32] exactly accepted entries per lane
-    uint64_t* bars;  // [NBUF]
-};
-
-// The ring and the lists' distances share one region (the distances are
-// written only after the last tile is consumed).  Rounded up to 128 bytes:
-// every warp's ring (a bulk-copy destination) must start on a 16-byte
-// boundary.
-__host__ __device__ constexpr size_t ring_region_floats(int DP, int TILEP, int NB) {
-    return ring_floats(DP, TILEP, NB) > (size_t)kListCap * kListStride
-               ? ring_floats(DP, TILEP, NB)
-               : (size_t)kListCap * kListStride;
-}
-__host__ __device__ constexpr size_t warp_smem_bytes(int DP, int TILEP, int NB) {
-    return (ring_region_floats(DP, TILEP, NB) * sizeof(float) + kListCap * kListStride * 4 +
-            5 * 32 * 4 + NB * sizeof(uint64_t) + 127) / 128 * 128;
-}
-
-__device__ __forceinline__ WarpSmem carve_warp(unsigned char* base, int DP, int TILEP, int NB) {
-    WarpSmem w;
-    w.ring = reinterpret_cast<float*>(base);
-    w.Ld = w.ring;   // after the tiles
-    w.Li = reinterpret_cast<int32_t*>(w.ring + ring_region_floats(DP, TILEP, NB));
-    w.Rpp = w.Li + kListCap * kListStride;
-    w.Rprs = w.Rpp + 32;
-    w.Rrs = w.Rprs + 32;
-    w.Rre = w.Rrs + 32;
-    w.acc = w.Rre + 32;
-    w.bars = reinterpret_cast<uint64_t*>(w.acc + 32);
-    return w;
-}
-
-// One warp task: 16 queries in one row of cells; their candidates are the
-// slot ranges of the neighbour rows (lane l < neighbour_rows owns row l),
-// each widened to pair boundaries and concatenated into one stream of
-// candidate pairs.  Tile t of the stream (TILEP pairs) may span several rows:
-// every row lane that overlaps it copies its own part with cp.async.bulk,
-// all completing on the buffer's one mbarrier.  A tentative entry is stored
-// as its stream code 2 * pair + half; the row it came from, its slot, the
-// row-range filter and the exact recheck are resolved at the end of the task.
-template <int TILEP, int PAIRF>
-__device__ __forceinline__ void issue_tile(const WarpSmem& w, int t, int b, int pp, int np,
-                                           int prs, int P, const float* rpts, int lane) {
-    const int T0 = t * TILEP;
-    const int T1 = min(T0 + TILEP, P);
-    if (lane == 0)
-        mbar_arrive_expect_tx(&w.bars[b], (uint32_t)(T1 - T0) * PAIRF * sizeof(float));
-    __syncwarp();
-    const int lo_s = max(pp, T0), hi_s = min(pp + np, T1);
-    if (hi_s > lo_s) {
-        fence_proxy_async_smem();   // the buffer's previous contents were read generically
-        bulk_g2s(w.ring + (size_t)b * TILEP * PAIRF + (size_t)(lo_s - T0) * PAIRF,
-                 rpts + (int64_t)(prs + lo_s - pp) * PAIRF,
-                 (uint32_t)(hi_s - lo_s) * PAIRF * sizeof(float), &w.bars[b]);
+// Event of a chunk: the last event whose first chunk is <= c.
+__device__ __forceinline__ int chunk_event(const EventHdr* qev, int E, int c) {
+    int lo = 0, hi = E - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (qev[mid].qchunk0 <= c) lo = mid; else hi = mid - 1;
     }
+    return lo;
 }
 
-template <int D, int EXIT>
+// Copy tile t of the batch's candidate stream into ring buffer b: every range
+// part inside [T0, T1) with one bulk copy (issued by the lane holding the
+// range), the slots of the copied candidates into tslot, completion on the
+// buffer's mbarrier.  cur: first range that may overlap the tile (advanced).
+template <int D>
+__device__ __forceinline__ void issue_tile(const WarpSmem& w, int t, int b, int U, int nr,
+                                           int& cur, const float* rpts, int lane) {
+    using C = QCfg<D>;
+    constexpr int DP = C::DP, T = C::TILE;
+    const int T0 = t * T;
+    const int T1 = min(T0 + T, U);
+    if (lane == 0) mbar_arrive_expect_tx(&w.bars[b], (uint32_t)(T1 - T0) * DP * sizeof(float));
+    __syncwarp();
+    fence_proxy_async_smem();   // the buffer's previous contents were read generically
+    for (int i = cur + lane; i < nr; i += 32) {
+        const int ps = w.rpre[i];
+        if (ps >= T1) break;
+        const int pe = w.rpre[i + 1];
+        const int s = max(ps, T0), e = min(pe, T1);
+        if (e > s) {
+            const int lo = w.rlo[i] + (s - ps);
+            bulk_g2s(w.ring + ((size_t)b * T + (s - T0)) * DP, rpts + (int64_t)lo * DP,
+                     (uint32_t)(e - s) * DP * sizeof(float), &w.bars[b]);
+            int32_t* ts = w.tslot + b * T + (s - T0);
+            for (int j = 0; j < e - s; ++j) ts[j] = lo + j;
+        }
+    }
+    // the first range still reaching past this tile
+    while (cur < nr && w.rpre[cur + 1] <= T1) ++cur;
+}
+
+template <int D>
 __global__ void __launch_bounds__(kQueryWarps * 32, QCfg<D>::MINB) k_grid_query(QueryArgs a) {
     pdl_trigger();
     pdl_wait();
     using C = QCfg<D>;
     constexpr int DP = C::DP;
-    constexpr int TILEP = C::TILEP;
-    constexpr int PAIRF = 2 * DP;   // floats per candidate pair
+    constexpr int T = C::TILE;
+    constexpr int NB = C::NB;
     extern __shared__ __align__(128) unsigned char smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    constexpr int NB = C::NBUF;
-    const WarpSmem w =
-        carve_warp(smem + (size_t)warp * warp_smem_bytes(DP, TILEP, NB), DP, TILEP, NB);
-    float* Ld = w.Ld;
-    int32_t* Li = w.Li;
-    // lanes q, q + G, ... serve the task's query q (G = kTaskQueries); lane
-    // q + s G screens the candidate pairs p with p mod kStreams == s
-    const int qi = lane % kTaskQueries;
-    const int sh = lane / kTaskQueries;
+    const WarpSmem w = carve_warp<D>(smem + (size_t)warp * warp_smem_bytes<D>());
     if (lane == 0)
         for (int b = 0; b < NB; ++b) mbar_init(&w.bars[b], 1);
     fence_mbar_init();
     __syncwarp();
     uint32_t phase = 0;   // bit b: parity to wait for on buffer b
+    const unsigned lt_mask = (1u << lane) - 1u;
 
-    const int ntasks = *a.ntasks;
     const float r2 = a.r2;
-    const float rs2 = a.r2_screen;
     const int K = a.K;
+    // neighbour-row digit table of the current (naxes, m): digit a-1 of row
+    // 32 rr + lane (offset + m, 3 bits per axis) in dig[rr]
+    int tab_key = -1;
+    uint32_t dig[kNbrRounds];
 
     for (;;) {
-        int t = 0;
-        if (lane == 0) t = atomicAdd(a.task_counter, 1);
-        t = __shfl_sync(kFull, t, 0);
-        if (t >= ntasks) break;
-        const Task task = a.tasks[t];
-        const EventHdr& h = a.ev[task.ev];
+        int c = 0;
+        if (lane == 0) c = atomicAdd(a.task_counter, 1);
+        c = __shfl_sync(kFull, c, 0);
+        if (c >= a.nchunks) break;
+        const int e = a.nev > 1 ? chunk_event(a.qev, a.nev, c) : 0;
+        const EventHdr& hq = a.qev[e];
+        const EventHdr& h = a.ev[e];
         if (a.path_filter >= 0 && h.path != a.path_filter) continue;   // another launch's event
         int32_t* counts = a.counts ? a.counts : h.counts;
         int32_t* oidx = a.counts ? a.idx : h.idx;
         float* od2 = a.counts ? a.dist2 : h.dist2;
 
-        const bool act = qi < task.nq;
-        const int qs = task.qslot + qi;
+        const int64_t q_off = hq.pt_off, q_n = hq.n;
+        const int s0 = (int)(q_off + (int64_t)(c - hq.qchunk0) * kChunkQ);
+        const int nqc = (int)min((int64_t)kChunkQ, q_off + q_n - (int64_t)s0);
+        const bool act = lane < nqc;
+        const int qs = s0 + lane;
         const int qorig = act ? a.qperm[qs] : 0;
         if (!h.valid) {
             // grid built from non-finite input: empty rows (frnn_sync reports it)
-            for (int ql = 0; ql < task.nq && !a.csr; ++ql) {
+            for (int ql = 0; ql < nqc && !a.csr; ++ql) {
                 const int qo = __shfl_sync(kFull, qorig, ql);
-                for (int e = lane; e < K; e += 32) {
-                    oidx[(int64_t)qo * K + e] = -1;
-                    od2[(int64_t)qo * K + e] = INFINITY;
+                for (int e2 = lane; e2 < K; e2 += 32) {
+                    oidx[(int64_t)qo * K + e2] = -1;
+                    od2[(int64_t)qo * K + e2] = INFINITY;
                 }
             }
-            if (act && sh == 0) counts[qorig] = 0;
-            if (act && sh == 0 && a.degree) a.degree[qorig] = 0;
+            if (act) counts[qorig] = 0;
+            if (act && a.degree) a.degree[qorig] = 0;
             continue;
         }
-        uint64_t qq[D];   // each query coordinate duplicated into both f32x2 lanes
-#pragma unroll
-        for (int k = 0; k < D; ++k) {
-            const float v = act ? a.qpts[pair_index(qs, k, DP)] : __int_as_float(0x7fc00000);
-            qq[k] = f2_pack(v, v);   // inactive lanes: NaN, never within r
+        // the chunk's query rows into shared memory; per-query counters
+        {
+            const float4* src = reinterpret_cast<const float4*>(a.qpts + (int64_t)s0 * DP);
+            float4* dst = reinterpret_cast<float4*>(w.Q);
+            for (int i = lane; i < nqc * (DP / 4); i += 32) dst[i] = src[i];
+            if (lane < kChunkQ) w.cnt[lane] = 0;
         }
-        const int qc = act ? a.qcell[qs] : 0;
-        const int dims0 = h.dims[0], m = h.m;
-        const int x = qc % dims0;
-        const int xa = __shfl_sync(kFull, x, 0);
-        const int xb = __shfl_sync(kFull, x, task.nq - 1);
-
-        // neighbour row of this lane (lane < neighbour_rows <= 32) and its
-        // place in the candidate stream
-        const int nrows = neighbour_rows(h);
-        int rs = 0, re = 0;
-        int64_t rowbase;
-        if (lane < nrows && neighbour_row(h, task.row, lane, rowbase)) {
-            const int x0 = max(xa - m, 0), x1 = min(xb + m, dims0 - 1);
-            rs = a.cstart[rowbase + x0];
-            re = a.cstart[rowbase + x1 + 1];
-        }
-        const int prs = rs >> 1;
-        const int np = re > rs ? ((re + 1) >> 1) - prs : 0;
-        int incl = np;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int v = __shfl_up_sync(kFull, incl, o);
-            if (lane >= o) incl += v;
-        }
-        const int pp = incl - np;
-        const int P = __shfl_sync(kFull, incl, 31);
-        w.Rpp[lane] = pp;   // nondecreasing over lanes (empty rows repeat the next start)
-        w.Rprs[lane] = prs;
-        w.Rrs[lane] = rs;
-        w.Rre[lane] = re;
-        w.acc[lane] = 0;
-        // the query's own slot lies in the centre row (every offset zero); in
-        // a self-query it is excluded by its stream code
-        const int lc = (nrows - 1) >> 1;
-        const int pp_c = __shfl_sync(kFull, pp, lc), prs_c = __shfl_sync(kFull, prs, lc);
-        const int self_code = (a.self && act) ? 2 * (pp_c + (qs >> 1) - prs_c) + (qs & 1) : -1;
-        const int ntiles = (P + TILEP - 1) / TILEP;
-
-        int cnt = 0;          // tentative entries (more than kListCap: the row goes to the selection kernel)
-
-        // prologue: fill the ring
-        const int pre = min(NB, ntiles);
-        for (int tt = 0; tt < pre; ++tt)
-            issue_tile<TILEP, PAIRF>(w, tt, tt, pp, np, prs, P, a.rpts, lane);
-        int timed_out_at = -1;
-        for (int tt = 0; tt < ntiles; ++tt) {
-            const int b = tt % NB;
-            if (!mbar_wait_bounded(&w.bars[b], (phase >> b) & 1u)) {
-                timed_out_at = tt;
-                break;
+        // groups: runs of queries with equal cells (slots are cell-sorted)
+        const int qc = act ? a.qcell[qs] : -1;
+        const int prev = __shfl_up_sync(kFull, qc, 1);
+        const bool head = act && (lane == 0 || prev != qc);
+        const unsigned gmask = __ballot_sync(kFull, head);
+        const int ng = __popc(gmask);
+        // lane g < ng: first query of group g; lanes >= ng: nqc
+        int gq = nqc;
+        {
+            unsigned mm = gmask;
+            for (int g = 0; g < ng; ++g) {
+                if (lane == g) gq = __ffs(mm) - 1;
+                mm &= mm - 1u;
             }
-            phase ^= 1u << b;
-            float* tile = w.ring + (size_t)b * TILEP * PAIRF;
-            const int T0 = tt * TILEP;
-            const int lenp = min(TILEP, P - T0);
-            {
-                // a row whose slot range starts (ends) inside a pair: put NaN
-                // into the first coordinate of the half outside the range, so
-                // it fails every screen (the neighbouring slot belongs to a
-                // cell outside the search range, or to another row's part)
-                const int lo_s = max(pp, T0), hi_s = min(pp + np, T0 + lenp);
-                if (hi_s > lo_s && (((lo_s == pp) && (rs & 1)) || ((hi_s == pp + np) && (re & 1)))) {
-                    if (lo_s == pp && (rs & 1)) tile[(lo_s - T0) * PAIRF] = __int_as_float(0x7fc00000);
-                    if (hi_s == pp + np && (re & 1))
-                        tile[(hi_s - 1 - T0) * PAIRF + 1] = __int_as_float(0x7fc00000);
-                    fence_proxy_async_smem();   // before the buffer is refilled by bulk copies
+        }
+        // the grid's parameters in registers (the loops below store to shared
+        // memory through generic pointers, which would otherwise force the
+        // header to be read again)
+        const int naxes = h.naxes, m = h.m;
+        int dims[kMaxAxes];
+#pragma unroll
+        for (int ax = 0; ax < kMaxAxes; ++ax) dims[ax] = h.dims[ax];
+        const int dims0 = dims[0];
+        const int64_t cell_off = h.cell_off;
+        // this lane's cell coordinates (c0 along the fastest axis, then the row's)
+        int cc[kMaxAxes];
+        {
+            int v = act ? qc : 0;
+            cc[0] = v % dims0;
+            v /= dims0;
+#pragma unroll
+            for (int ax = 1; ax < kMaxAxes; ++ax) {
+                cc[ax] = 0;
+                if (ax < naxes) {
+                    cc[ax] = v % dims[ax];
+                    v /= dims[ax];
                 }
-                // the last tile of the task: the pairs between its end and the
-                // end of the last screening step hold stale data; NaN makes
-                // them fail every screen (both halves)
-                const int pend = (lenp + 4 * kStreams - 1) / (4 * kStreams) * (4 * kStreams);
-                if (lane < pend - lenp) {
-                    float* f = tile + (size_t)(lenp + lane) * PAIRF;
-                    f[0] = __int_as_float(0x7fc00000);
-                    f[1] = __int_as_float(0x7fc00000);
-                    fence_proxy_async_smem();
+            }
+        }
+        int nrows = 1;
+        for (int ax = 1; ax < naxes; ++ax) nrows *= 2 * m + 1;
+        const int key = naxes * 16 + m;
+        if (key != tab_key) {
+            tab_key = key;
+            const int side = 2 * m + 1;
+#pragma unroll
+            for (int rr = 0; rr < kNbrRounds; ++rr) {
+                int l = rr * 32 + lane;
+                uint32_t d = 0;
+                for (int ax = 1; ax < naxes; ++ax) {
+                    d |= (uint32_t)(l % side) << (3 * (ax - 1));
+                    l /= side;
+                }
+                dig[rr] = d;
+            }
+        }
+        int rstride[kMaxAxes];
+        rstride[0] = 0;
+        rstride[1] = 1;
+#pragma unroll
+        for (int ax = 2; ax < kMaxAxes; ++ax) rstride[ax] = rstride[ax - 1] * dims[ax - 1];
+
+        // batches of groups whose compact ranges fit kRangeCap
+        bool timed_out = false;
+        int g0 = 0;
+        while (g0 < ng && !timed_out) {
+            int nr = 0, U = 0, g = g0;
+            int gsb = INT_MAX;   // lane j: stream start of batch group g0 + j
+            for (; g < ng; ++g) {
+                const int nr0 = nr, U0 = U;
+                const int hl = __shfl_sync(kFull, gq, g);
+                int gc[kMaxAxes];
+#pragma unroll
+                for (int ax = 0; ax < kMaxAxes; ++ax) gc[ax] = __shfl_sync(kFull, cc[ax], hl);
+                const int x0 = max(gc[0] - m, 0), x1 = min(gc[0] + m, dims0 - 1);
+#pragma unroll
+                for (int rr = 0; rr < kNbrRounds; ++rr) {
+                    if (rr * 32 >= nrows) break;
+                    const int l = rr * 32 + lane;
+                    int lo = 0, n = 0;
+                    if (l < nrows) {
+                        bool ok = true;
+                        int rowlin = 0;
+#pragma unroll
+                        for (int ax = 1; ax < kMaxAxes; ++ax) {
+                            if (ax < naxes) {
+                                const int v = gc[ax] + (int)((dig[rr] >> (3 * (ax - 1))) & 7u) - m;
+                                ok = ok && (unsigned)v < (unsigned)dims[ax];
+                                rowlin += v * rstride[ax];
+                            }
+                        }
+                        if (ok) {
+                            const int64_t base = cell_off + (int64_t)rowlin * dims0;
+                            lo = a.cstart[base + x0];
+                            n = a.cstart[base + x1 + 1] - lo;
+                        }
+                    }
+                    const unsigned bal = __ballot_sync(kFull, n > 0);
+                    int incl = n;
+#pragma unroll
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const int v = __shfl_up_sync(kFull, incl, o);
+                        if (lane >= o) incl += v;
+                    }
+                    const int pos = nr + __popc(bal & lt_mask);
+                    if (n > 0 && pos < kRangeCap) {
+                        w.rlo[pos] = lo;
+                        w.rpre[pos] = U + incl - n;
+                    }
+                    nr += __popc(bal);
+                    U += __shfl_sync(kFull, incl, 31);
+                }
+                if (nr > kRangeCap) {   // group g opens the next batch
+                    nr = nr0;
+                    U = U0;
+                    break;
+                }
+                if (lane == g - g0) gsb = U0;
+            }
+            const int gend = g;
+            // lane j <= gend - g0: first query of batch group j (the end for j = gend - g0)
+            const int gqb = __shfl_sync(kFull, gq, min(g0 + lane, 31));
+            if (lane == 0) w.rpre[nr] = U;
+            __syncwarp();
+
+            const int ntiles = (U + T - 1) / T;
+            int cur = 0;
+            const int pre = min(NB, ntiles);
+            for (int tt = 0; tt < pre; ++tt) issue_tile<D>(w, tt, tt, U, nr, cur, a.rpts, lane);
+            __syncwarp();   // slots written by the issuing lanes, before any lane reads them
+            int tt = 0;
+            for (; tt < ntiles; ++tt) {
+                const int b = tt % NB;
+                // warp-uniform verdict: every lane takes the timeout path if one does
+                if (!__all_sync(kFull, mbar_wait_bounded(&w.bars[b], (phase >> b) & 1u))) {
+                    timed_out = true;
+                    break;
+                }
+                phase ^= 1u << b;
+                const int T0 = tt * T;
+                const int len = min(T, U - T0);
+                const float* tile = w.ring + (size_t)b * T * DP;
+                const int32_t* tsl = w.tslot + b * T;
+#pragma unroll 1
+                for (int k0 = 0; k0 < len; k0 += 32) {
+                    const int ul = k0 + lane;
+                    const bool valid = ul < len;
+                    const int u = T0 + ul;
+                    // group of the candidate: last batch group starting at or before u
+                    int j = 0;
+#pragma unroll
+                    for (int st = 8; st > 0; st >>= 1) {
+                        const int v = __shfl_sync(kFull, gsb, j + st);
+                        if (v <= u) j += st;
+                    }
+                    const int qa = __shfl_sync(kFull, gqb, j);
+                    const int qe = __shfl_sync(kFull, gqb, j + 1);
+                    const int nq = valid ? qe - qa : 0;
+                    const int mx = __reduce_max_sync(kFull, (unsigned)nq);
+                    float cv[DP];
+                    const float4* cp = reinterpret_cast<const float4*>(tile + (size_t)(valid ? ul : 0) * DP);
+#pragma unroll
+                    for (int k4 = 0; k4 < DP / 4; ++k4) {
+                        const float4 v = cp[k4];
+                        cv[4 * k4] = v.x;
+                        cv[4 * k4 + 1] = v.y;
+                        cv[4 * k4 + 2] = v.z;
+                        cv[4 * k4 + 3] = v.w;
+                    }
+                    const int slot = valid ? tsl[ul] : -1;
+                    for (int jq = 0; jq < mx; ++jq) {
+                        const bool on = jq < nq;
+                        const int q = on ? qa + jq : 0;
+                        const float4* qp = reinterpret_cast<const float4*>(w.Q + q * DP);
+                        float s = 0.f;
+#pragma unroll
+                        for (int k4 = 0; k4 < DP / 4; ++k4) {
+                            const float4 v = qp[k4];
+                            const float qv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+                            for (int i = 0; i < 4; ++i) {
+                                if (4 * k4 + i < D) {
+                                    const float d = __fsub_rn(qv[i], cv[4 * k4 + i]);
+                                    s = __fadd_rn(s, __fmul_rn(d, d));
+                                }
+                            }
+                        }
+                        const bool acc = on && s <= r2 && !(a.self && slot == s0 + q);
+                        if (acc) {
+                            const int p = atomicAdd(&w.cnt[q], 1);
+                            if (p < kListCap) {
+                                w.Ld[q * kListStr + p] = s;
+                                w.Li[q * kListStr + p] = slot;
+                            }
+                        }
+                    }
                 }
                 __syncwarp();
+                if (tt + NB < ntiles) issue_tile<D>(w, tt + NB, b, U, nr, cur, a.rpts, lane);
             }
-            // four candidate pairs per stream and step: their first-stage
-            // screens are independent, which hides the packed pipeline's
-            // latency
-            for (int p0 = 0; p0 < lenp; p0 += 4 * kStreams) {
-                uint64_t sg[4];
-#pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    const int p = p0 + kStreams * j + sh;
-                    const ulonglong2* cp = reinterpret_cast<const ulonglong2*>(tile + p * PAIRF);
-                    uint64_t s2 = 0;
-#pragma unroll
-                    for (int k = 0; k < EXIT; ++k) {
-                        const ulonglong2 v = cp[k >> 1];
-                        s2 = f2_screen(s2, qq[k], (k & 1) ? v.y : v.x);
-                    }
-                    sg[j] = s2;
+            if (timed_out) {
+                // record, wait (bounded) for the copies still in flight, stop this warp
+                if (lane == 0) atomicOr(a.status, kStatusTimeout);
+                const int issued = min(ntiles, tt + NB);
+                for (int t2 = tt; t2 < issued; ++t2) {
+                    const int b2 = t2 % NB;
+                    mbar_wait_bounded(&w.bars[b2], (phase >> b2) & 1u);
+                    phase ^= 1u << b2;
                 }
-#pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    const int p = p0 + kStreams * j + sh;
-                    const ulonglong2* cp = reinterpret_cast<const ulonglong2*>(tile + p * PAIRF);
-                    uint64_t s2 = sg[j];
-                    float s0, s1;
-                    f2_unpack(s2, s0, s1);
-                    if (!__any_sync(kFull, fminf(s0, s1) <= rs2)) continue;
-                    if (EXIT < D) {
-#pragma unroll
-                        for (int k = EXIT; k < D; ++k) {
-                            const ulonglong2 v = cp[k >> 1];
-                            s2 = f2_screen(s2, qq[k], (k & 1) ? v.y : v.x);
-                        }
-                        f2_unpack(s2, s0, s1);
-                    }
-                    // tentative entries: the stream codes, resolved at the task's
-                    // end; appended without branches (predicated stores), so the
-                    // warp does not diverge here
-                    const int code0 = 2 * (T0 + p);
-                    const bool f0 = s0 <= rs2 && code0 != self_code;
-                    const bool f1 = s1 <= rs2 && code0 + 1 != self_code;
-                    const int c1 = cnt + (f0 ? 1 : 0);
-                    if (f0 && cnt < kListCap) Li[cnt * kListStride + lane] = code0;
-                    if (f1 && c1 < kListCap) Li[c1 * kListStride + lane] = code0 + 1;
-                    cnt = c1 + (f1 ? 1 : 0);
-                }
+                return;
             }
-            __syncwarp();
-            const int nt = tt + NB;
-            if (nt < ntiles) issue_tile<TILEP, PAIRF>(w, nt, b, pp, np, prs, P, a.rpts, lane);
+            g0 = gend;
         }
-        if (timed_out_at >= 0) {
-            // record, wait (bounded) for the copies still in flight, stop this warp
-            if (lane == 0) atomicOr(a.status, kStatusTimeout);
-            const int issued = min(ntiles, timed_out_at + NB);
-            for (int t2 = timed_out_at; t2 < issued; ++t2) {
-                const int b2 = t2 % NB;
-                mbar_wait_bounded(&w.bars[b2], (phase >> b2) & 1u);
-                phase ^= 1u << b2;
-            }
-            return;
-        }
+        __syncwarp();
 
-        const bool lost = cnt > kListCap;   // an entry did not fit the list
-        // exact recheck of every lane's tentative entries, spread over the
-        // whole warp: entry i of the task's concatenated lists goes to lane
-        // i % 32.  Each resolves its row (the last row whose stream part
-        // starts at or before the pair), its slot and the row-range filter
-        // (slots read only because parts start on pair boundaries are
-        // dropped), then applies the scalar contract in index order without
-        // contraction.  Accepted: (d2, slot); rejected: d2 = +inf, sorted last.
-        const int own = lost ? 0 : cnt;
-        int cin = own;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int v = __shfl_up_sync(kFull, cin, o);
-            if (lane >= o) cin += v;
-        }
-        const int cex = cin - own;
-        const int T = __shfl_sync(kFull, cin, 31);
-        __syncwarp();
-        for (int base = 0; base < T; base += 32) {
-            const int i = base + lane;
-            // owner lane: the last lane whose entries start at or before i
-            int O = 0;
-#pragma unroll
-            for (int st = 16; st > 0; st >>= 1) {
-                const int v = __shfl_sync(kFull, cex, O + st);
-                if (v <= i) O += st;
-            }
-            const int e = i - __shfl_sync(kFull, cex, O);
-            if (i < T) {
-                const int code = Li[e * kListStride + O];
-                const int sp = code >> 1;
-                int L = 0;
-#pragma unroll
-                for (int st = 16; st > 0; st >>= 1)
-                    if (w.Rpp[L + st] <= sp) L += st;
-                const int slot = 2 * (w.Rprs[L] + sp - w.Rpp[L]) + (code & 1);
-                float sv = INFINITY;
-                int32_t orig = 0;
-                if (slot >= w.Rrs[L] && slot < w.Rre[L]) {
-                    orig = a.rperm[slot];   // in flight with the coordinate loads
-                    const int qo_slot = task.qslot + (O % kTaskQueries);
-                    float acc = 0.f;
-#pragma unroll
-                    for (int k = 0; k < D; ++k) {
-                        const float d = __fsub_rn(a.qpts[pair_index(qo_slot, k, DP)],
-                                                  a.rpts[pair_index(slot, k, DP)]);
-                        acc = __fadd_rn(acc, __fmul_rn(d, d));
-                    }
-                    if (acc <= r2) {
-                        sv = acc;
-                        atomicAdd(&w.acc[O], 1);
-                    }
-                }
-                Ld[e * kListStride + O] = sv;
-                Li[e * kListStride + O] = sv <= r2 ? orig : 0;   // rejected: +inf sorts last
-            }
-        }
-        __syncwarp();
-        const int kept = w.acc[lane];
-        // per query: its lanes' entries together (rejected ones carry +inf)
-        int cnt_q = cnt, kept_q = kept;
-        bool lost_q = lost;
-#pragma unroll
-        for (int st = 1; st < kStreams; ++st) {
-            cnt_q += __shfl_sync(kFull, cnt, qi + st * kTaskQueries);
-            kept_q += __shfl_sync(kFull, kept, qi + st * kTaskQueries);
-            lost_q |= __shfl_sync(kFull, lost, qi + st * kTaskQueries);
-        }
-        // more than 32 entries: the exact selection kernel finishes the row
-        const bool spill = sh == 0 && act && (lost_q || cnt_q > kRowCap);
-        if (sh == 0 && act && !spill) counts[qorig] = min(kept_q, K);
+        // per query: counts, degree, rows for the selection kernel
+        const int kept = act ? w.cnt[lane] : 0;
+        const bool spill = act && kept > kListCap;
+        if (act && !spill) counts[qorig] = min(kept, K);
         if (spill && a.csr) counts[qorig] = kCsrSpill;   // counted by the selection kernel
-        if (sh == 0 && act && !spill && a.degree) a.degree[qorig] = kept_q;
+        if (act && !spill && a.degree) a.degree[qorig] = kept;
         if (spill) {
             const int pos = atomicAdd(a.ovf_count, 1);
             if (pos < a.ovf_cap) {
                 a.ovf[pos].qslot = qs;
-                a.ovf[pos].ev = task.ev;
+                a.ovf[pos].ev = e;
             } else {
                 atomicOr(a.status, kStatusCapacity);
             }
         }
-        // one query row at a time (for D >= 10 two short rows at a time, one
-        // per half-warp): lane l takes entry l of the query's lists, the warp
-        // sorts the 32 keys (d2 bits << 32 | original index; unused lanes hold
-        // the largest key) with a bitonic network across lanes, and lane l
-        // writes position l of the row (coalesced), then the padding
         const unsigned spill_mask = __ballot_sync(kFull, spill);
-        const int rstride = a.csr ? kCsrStageW : K;
-        if constexpr (!C::PAIR_ROWS) {
-            for (int ql = 0; ql < task.nq; ++ql) {
-                if (spill_mask & (1u << ql)) continue;
-                uint64_t key = ~0ull;
-                int base = 0;
+        // original indices of the kept entries (entry lane of each query),
+        // all loads issued before the first store
+        {
+            int orig[kChunkQ];
 #pragma unroll
-                for (int st = 0; st < kStreams; ++st) {
-                    const int col = ql + st * kTaskQueries;
-                    const int c = __shfl_sync(kFull, cnt, col);
-                    if (lane >= base && lane < base + c)
-                        key = make_key(Ld[(lane - base) * kListStride + col],
-                                       Li[(lane - base) * kListStride + col]);
-                    base += c;
-                }
-                // the network only as wide as the row needs (base entries sit in
-                // lanes 0 .. base-1; wider stages would compare largest keys only)
+            for (int q = 0; q < kChunkQ; ++q) {
+                const int cq = __shfl_sync(kFull, kept, q);
+                orig[q] = 0;
+                if (q < nqc && !((spill_mask >> q) & 1u) && lane < cq)
+                    orig[q] = a.rperm[w.Li[q * kListStr + lane]];
+            }
+#pragma unroll
+            for (int q = 0; q < kChunkQ; ++q) {
+                const int cq = __shfl_sync(kFull, kept, q);
+                if (q < nqc && !((spill_mask >> q) & 1u) && lane < cq) w.Li[q * kListStr + lane] = orig[q];
+            }
+        }
+        __syncwarp();
+        // one query row at a time (for D >= 10 two short rows at a time, one
+        // per half-warp): lane l takes entry l of the query's list, the warp
+        // sorts the keys (unused lanes hold the largest key) with a bitonic
+        // network across lanes, and lane l writes position l of the row
+        // (coalesced), then the padding
+        const int rstride_out = a.csr ? kCsrStageW : K;
+        if constexpr (!C::PAIR_ROWS) {
+            for (int ql = 0; ql < nqc; ++ql) {
+                if ((spill_mask >> ql) & 1u) continue;
+                const int n = __shfl_sync(kFull, kept, ql);
+                uint64_t key = ~0ull;
+                if (lane < n) key = make_key(w.Ld[ql * kListStr + lane], w.Li[ql * kListStr + lane]);
+                // the network only as wide as the row needs (entries sit in
+                // lanes 0 .. n-1; wider stages would compare largest keys only)
 #pragma unroll
                 for (int k2 = 2; k2 <= 32; k2 <<= 1) {
-                    if ((k2 >> 1) >= base) break;
+                    if ((k2 >> 1) >= n) break;
 #pragma unroll
-                    for (int j = k2 >> 1; j > 0; j >>= 1) {
-                        const uint64_t other = __shfl_xor_sync(kFull, key, j);
-                        const bool take_min = ((lane & j) == 0) == ((lane & k2) == 0);
-                        // one comparison: equal keys (rejected entries, empty lanes)
-                        // are interchangeable, all others are distinct
+                    for (int jj = k2 >> 1; jj > 0; jj >>= 1) {
+                        const uint64_t other = __shfl_xor_sync(kFull, key, jj);
+                        const bool take_min = ((lane & jj) == 0) == ((lane & k2) == 0);
+                        // one comparison: keys are distinct (indices differ) except
+                        // the unused lanes' largest keys, which are interchangeable
                         key = (take_min == (other < key)) ? other : key;
                     }
                 }
-                const int c = min(__shfl_sync(kFull, kept_q, ql), K);
+                const int cK = min(n, K);
                 const int qo = __shfl_sync(kFull, qorig, ql);
-                int32_t* irow = oidx + (int64_t)qo * rstride;
-                float* drow = od2 + (int64_t)qo * rstride;
-                if (lane < c) {
+                int32_t* irow = oidx + (int64_t)qo * rstride_out;
+                float* drow = od2 + (int64_t)qo * rstride_out;
+                if (lane < cK) {
                     irow[lane] = (int32_t)(uint32_t)key;
                     drow[lane] = __uint_as_float((uint32_t)(key >> 32));
                 } else if (!a.csr && lane < K) {
                     irow[lane] = -1;
                     drow[lane] = INFINITY;
                 }
-                for (int e = 32 + lane; e < K && !a.csr; e += 32) {
-                    irow[e] = -1;
-                    drow[e] = INFINITY;
+                for (int e2 = 32 + lane; e2 < K && !a.csr; e2 += 32) {
+                    irow[e2] = -1;
+                    drow[e2] = INFINITY;
                 }
             }
         } else {
             // two rows at a time, one per half-warp, when both hold at most
             // 16 entries (the network then stays within each half and both
             // halves end ascending); otherwise one row per warp as above
-            for (int ql = 0; ql < task.nq;) {
-                if (spill_mask & (1u << ql)) {
+            for (int ql = 0; ql < nqc;) {
+                if ((spill_mask >> ql) & 1u) {
                     ++ql;
                     continue;
                 }
-                const int ql1 = ql + 1;   // <= 16: a valid lane
-                const int n0 = __shfl_sync(kFull, cnt_q, ql);
-                const int n1 = __shfl_sync(kFull, cnt_q, ql1);
-                const bool two =
-                    n0 <= 16 && ql1 < task.nq && !(spill_mask & (1u << ql1)) && n1 <= 16;
+                const int ql1 = ql + 1;
+                const int n0 = __shfl_sync(kFull, kept, ql);
+                const int n1 = __shfl_sync(kFull, kept, ql1 & 31);
+                const bool two = n0 <= 16 && ql1 < nqc && !((spill_mask >> ql1) & 1u) && n1 <= 16;
                 const int hw = two ? 16 : 32;   // lanes per row
                 const int row = two ? ql + (lane >> 4) : ql;
                 const int hl = two ? (lane & 15) : lane;
+                const int n = two ? (lane >> 4 ? n1 : n0) : n0;
                 const int width = two ? max(n0, n1) : n0;
                 uint64_t key = ~0ull;
-                int base = 0;
-#pragma unroll
-                for (int st = 0; st < kStreams; ++st) {
-                    const int col = row + st * kTaskQueries;
-                    const int c = __shfl_sync(kFull, cnt, col);
-                    if (hl >= base && hl < base + c)
-                        key = make_key(Ld[(hl - base) * kListStride + col],
-                                       Li[(hl - base) * kListStride + col]);
-                    base += c;
-                }
+                if (hl < n) key = make_key(w.Ld[row * kListStr + hl], w.Li[row * kListStr + hl]);
 #pragma unroll
                 for (int k2 = 2; k2 <= 32; k2 <<= 1) {
                     if ((k2 >> 1) >= width) break;
 #pragma unroll
-                    for (int j = k2 >> 1; j > 0; j >>= 1) {
-                        const uint64_t other = __shfl_xor_sync(kFull, key, j);
-                        const bool take_min = ((hl & j) == 0) == ((hl & k2) == 0);
+                    for (int jj = k2 >> 1; jj > 0; jj >>= 1) {
+                        const uint64_t other = __shfl_xor_sync(kFull, key, jj);
+                        const bool take_min = ((hl & jj) == 0) == ((hl & k2) == 0);
                         key = (take_min == (other < key)) ? other : key;
                     }
                 }
-                const int c = min(__shfl_sync(kFull, kept_q, row), K);
+                const int cK = min(n, K);
                 const int qo = __shfl_sync(kFull, qorig, row);
-                int32_t* irow = oidx + (int64_t)qo * rstride;
-                float* drow = od2 + (int64_t)qo * rstride;
-                if (hl < c) {
+                int32_t* irow = oidx + (int64_t)qo * rstride_out;
+                float* drow = od2 + (int64_t)qo * rstride_out;
+                if (hl < cK) {
                     irow[hl] = (int32_t)(uint32_t)key;
                     drow[hl] = __uint_as_float((uint32_t)(key >> 32));
                 } else if (!a.csr && hl < K) {
                     irow[hl] = -1;
                     drow[hl] = INFINITY;
                 }
-                for (int e = hw + hl; e < K && !a.csr; e += hw) {
-                    irow[e] = -1;
-                    drow[e] = INFINITY;
+                for (int e2 = hw + hl; e2 < K && !a.csr; e2 += hw) {
+                    irow[e2] = -1;
+                    drow[e2] = INFINITY;
                 }
                 ql += two ? 2 : 1;
             }
@@ -610,11 +562,15 @@ __global__ void __launch_bounds__(kQueryWarps * 32, QCfg<D>::MINB) k_grid_query(
 
 // ------------------------------------------------------------- overflow path
 // Exact selection for queries with more than kListCap neighbours (whether or
-// not that exceeds K): one warp per query scans
-// the query's own +-m neighbourhood with lanes over candidates, appends keys
-// below the current threshold to a shared buffer, and whenever the buffer is
-// nearly full sorts it and keeps the K smallest (the threshold becomes the
-// K-th key).  Keys are unique (indices differ), so the K smallest are unique.
+// not that exceeds K): one warp per query scans the query's own +-m
+// neighbourhood with lanes over candidates, appends keys below the current
+// threshold to a shared buffer, and whenever the buffer is nearly full sorts
+// it and keeps the K smallest (the threshold becomes the K-th key).  Keys are
+// unique (indices differ), so the K smallest are unique.  The kernel always
+// follows the grid query on its stream; its last block to finish clears the
+// query's chunk counter (and, unless a compact fill pass still needs the
+// overflow list, the list) for the next query, so no host-side memset
+// interrupts the chain of programmatically dependent launches.
 
 constexpr int kOvfWarps = 4;
 
@@ -656,7 +612,7 @@ __global__ void __launch_bounds__(kOvfWarps * 32) k_overflow(QueryArgs a, int ca
         const int qo = a.qperm[qs];
         float qv[kMaxD];
 #pragma unroll
-        for (int k = 0; k < kMaxD; ++k) qv[k] = k < D ? a.qpts[pair_index(qs, k, DP)] : 0.f;
+        for (int k = 0; k < kMaxD; ++k) qv[k] = k < D ? a.qpts[pt_index(qs, k, DP)] : 0.f;
         const int qc = a.qcell[qs];
         const int dims0 = h.dims[0], m = h.m;
         const int x = qc % dims0, qrow = qc / dims0;
@@ -682,7 +638,7 @@ __global__ void __launch_bounds__(kOvfWarps * 32) k_overflow(QueryArgs a, int ca
 #pragma unroll
                         for (int k = 0; k < kMaxD; ++k) {
                             if (k < D) {
-                                const float d = __fsub_rn(qv[k], a.rpts[pair_index(cs, k, DP)]);
+                                const float d = __fsub_rn(qv[k], a.rpts[pt_index(cs, k, DP)]);
                                 s = __fadd_rn(s, __fmul_rn(d, d));
                             }
                         }
@@ -731,30 +687,31 @@ __global__ void __launch_bounds__(kOvfWarps * 32) k_overflow(QueryArgs a, int ca
         if (lane == 0 && !csr_rows) (a.counts ? a.counts : h.counts)[qo] = c;
         __syncwarp();
     }
+    // the last block to finish clears the query's counters for the next launch
+    __syncthreads();
+    if (threadIdx.x == 0 && a.ovf_done) {
+        __threadfence();
+        if (atomicAdd(a.ovf_done, 1) == (int)gridDim.x - 1) {
+            *a.task_counter = 0;
+            if (a.reset_ovf) *a.ovf_count = 0;
+            __threadfence();
+            *a.ovf_done = 0;
+        }
+    }
 }
 
 // ------------------------------------------------------------- host launch
 
 template <int D>
-static cudaError_t launch_grid_query_d(const QueryArgs& a, int exit_dims, int num_sms,
-                                       cudaStream_t st) {
+static cudaError_t launch_grid_query_d(const QueryArgs& a, int num_sms, cudaStream_t st) {
     using C = QCfg<D>;
-    static_assert(C::TILEP % (4 * kStreams) == 0, "whole screening steps per tile");
-    static_assert(C::NBUF <= kMaxNBuf, "phase bits and barriers per warp");
-    static_assert(warp_smem_bytes(C::DP, C::TILEP, C::NBUF) % 16 == 0 &&
-                      (ring_region_floats(C::DP, C::TILEP, C::NBUF) * sizeof(float)) % 16 == 0 &&
-                      (2 * C::DP * sizeof(float)) % 16 == 0,
+    static_assert(C::TILE % 32 == 0, "whole lane rounds per tile");
+    static_assert(C::NB <= 4, "phase bits and barriers per warp");
+    static_assert(warp_smem_bytes<D>() % 128 == 0 && (C::TILE * C::DP * sizeof(float)) % 16 == 0 &&
+                      (C::DP * sizeof(float)) % 16 == 0,
                   "bulk-copy destinations and sizes must be 16-byte multiples");
-    const size_t smem = query_smem_bytes(C::DP, C::TILEP, C::NBUF);
-    auto kern = &k_grid_query<D, C::EXIT>;
-    // other vote points are compiled for the tracking-like dimensions only
-    if constexpr (D == 8 || D == 12) {
-        if (exit_dims == 1) kern = &k_grid_query<D, 1>;
-        else if (exit_dims == 2) kern = &k_grid_query<D, 2>;
-        else if (exit_dims == 3) kern = &k_grid_query<D, 3>;
-        else if (exit_dims == 4) kern = &k_grid_query<D, 4>;
-        else if (exit_dims >= 5) kern = &k_grid_query<D, 6>;
-    }
+    const size_t smem = (size_t)kQueryWarps * warp_smem_bytes<D>();
+    auto kern = &k_grid_query<D>;
     cudaError_t ce = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                           (int)smem);
     if (ce != cudaSuccess) return ce;
@@ -762,17 +719,21 @@ static cudaError_t launch_grid_query_d(const QueryArgs& a, int exit_dims, int nu
     ce = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kQueryWarps * 32, smem);
     if (ce != cudaSuccess) return ce;
     per_sm = std::max(per_sm, 1);
-    launch_pdl(kern, dim3(num_sms * per_sm), dim3(kQueryWarps * 32), smem, st, a);
+    const int64_t warps = (int64_t)num_sms * per_sm * kQueryWarps;
+    const int64_t blocks = std::max<int64_t>(
+        1, std::min<int64_t>((int64_t)num_sms * per_sm, ceil_div(std::min<int64_t>(a.nchunks, warps), kQueryWarps)));
+    launch_pdl(kern, dim3((unsigned)blocks), dim3(kQueryWarps * 32), smem, st, a);
     return cudaGetLastError();
 }
 
-frnn_status enqueue_grid_query(const QueryLaunch& q, cudaStream_t st, std::string& err) {
+static QueryArgs query_args(const QueryLaunch& q) {
     const GridBufs& qs = *q.qset;
     const GridBufs& rs = *q.rset;
     QueryArgs a{};
     a.ev = rs.hdr;
-    a.tasks = qs.tasks;
-    a.ntasks = qs.scalars + kScNTasks;
+    a.qev = qs.hdr;
+    a.nev = qs.E;
+    a.nchunks = (int32_t)qs.nchunks;
     a.qpts = qs.pts;
     a.qperm = qs.perm;
     a.qcell = qs.cell;
@@ -783,7 +744,6 @@ frnn_status enqueue_grid_query(const QueryLaunch& q, cudaStream_t st, std::strin
     a.idx = q.idx;
     a.dist2 = q.dist2;
     a.r2 = q.r2;
-    a.r2_screen = std::nextafter((float)((double)q.r2 * (1.0 + 0x1p-16)), INFINITY);
     a.K = q.K;
     a.self = q.self;
     a.D = rs.D;
@@ -792,24 +752,40 @@ frnn_status enqueue_grid_query(const QueryLaunch& q, cudaStream_t st, std::strin
     a.ovf = qs.ovf;
     a.ovf_count = qs.scalars + kScOvfCount;
     a.ovf_cap = (int32_t)std::max<int64_t>(qs.n_total, 1);
+    a.ovf_done = qs.scalars + kScOvfDone;
+    a.reset_ovf = q.ovf_mode == 1 ? 0 : 1;
     a.exit_dims = q.exit_dims;
     a.path_filter = q.path_filter;
     a.csr = q.csr;
     a.ovf_mode = q.ovf_mode;
     a.degree = q.degree;
     a.row_off = q.row_off;
-    cudaMemsetAsync(qs.scalars + kScTaskCounter, 0, 2 * sizeof(int32_t), st);   // counter + ovf
+    return a;
+}
+
+frnn_status enqueue_grid_query(const QueryLaunch& q, cudaStream_t st, std::string& err) {
+    const GridBufs& qs = *q.qset;
+    const GridBufs& rs = *q.rset;
+    const QueryArgs a = query_args(q);
+    // the chunk counter is zero here: the build clears it, and every query's
+    // selection kernel clears it again when done.  The overflow list is
+    // cleared the same way, except after a compact count pass whose fill pass
+    // did not run.
+    if (qs.ovf_stale) cudaMemsetAsync(qs.scalars + kScOvfCount, 0, sizeof(int32_t), st);
+    qs.ovf_stale = q.ovf_mode == 1;
     if (q.kev[0]) cudaEventRecord(q.kev[0], st);
     cudaError_t ce = cudaSuccess;
-    switch (rs.D) {
-#define FRNN_CASE(d) case d: ce = launch_grid_query_d<d>(a, q.exit_dims, q.num_sms, st); break;
-        FRNN_CASE(1) FRNN_CASE(2) FRNN_CASE(3) FRNN_CASE(4) FRNN_CASE(5) FRNN_CASE(6)
-        FRNN_CASE(7) FRNN_CASE(8) FRNN_CASE(9) FRNN_CASE(10) FRNN_CASE(11) FRNN_CASE(12)
-        FRNN_CASE(13) FRNN_CASE(14) FRNN_CASE(15) FRNN_CASE(16)
+    if (qs.nchunks > 0) {
+        switch (rs.D) {
+#define FRNN_CASE(d) case d: ce = launch_grid_query_d<d>(a, q.num_sms, st); break;
+            FRNN_CASE(1) FRNN_CASE(2) FRNN_CASE(3) FRNN_CASE(4) FRNN_CASE(5) FRNN_CASE(6)
+            FRNN_CASE(7) FRNN_CASE(8) FRNN_CASE(9) FRNN_CASE(10) FRNN_CASE(11) FRNN_CASE(12)
+            FRNN_CASE(13) FRNN_CASE(14) FRNN_CASE(15) FRNN_CASE(16)
 #undef FRNN_CASE
-        default:
-            err = "unsupported D";
-            return FRNN_ERR_INVALID_ARG;
+            default:
+                err = "unsupported D";
+                return FRNN_ERR_INVALID_ARG;
+        }
     }
     if (ce != cudaSuccess) {
         err = std::string("grid query launch failed: ") + cudaGetErrorString(ce);
@@ -820,32 +796,10 @@ frnn_status enqueue_grid_query(const QueryLaunch& q, cudaStream_t st, std::strin
 }
 
 frnn_status enqueue_overflow_only(const QueryLaunch& q, cudaStream_t st, std::string& err) {
-    const GridBufs& qs = *q.qset;
-    const GridBufs& rs = *q.rset;
-    QueryArgs o{};
-    o.ev = rs.hdr;
-    o.qpts = qs.pts;
-    o.qperm = qs.perm;
-    o.qcell = qs.cell;
-    o.rpts = rs.pts;
-    o.rperm = rs.perm;
-    o.cstart = rs.cstart;
-    o.counts = q.counts;
-    o.idx = q.idx;
-    o.dist2 = q.dist2;
-    o.r2 = q.r2;
-    o.K = q.K;
-    o.self = q.self;
-    o.D = rs.D;
-    o.status = q.d_status;
-    o.ovf = qs.ovf;
-    o.ovf_count = qs.scalars + kScOvfCount;
-    o.ovf_cap = (int32_t)std::max<int64_t>(qs.n_total, 1);
+    QueryArgs o = query_args(q);
     o.path_filter = -1;
-    o.csr = q.csr;
-    o.ovf_mode = q.ovf_mode;
-    o.degree = q.degree;
-    o.row_off = q.row_off;
+    o.reset_ovf = 1;   // the fill pass consumes the list
+    q.qset->ovf_stale = false;
     return enqueue_overflow(o, q.num_sms, st, err);
 }
 

@@ -25,14 +25,13 @@ using namespace frnn;
 namespace {
 
 // Device bytes one request holds while in flight: its input and outputs, its
-// share of the batch grid (sorted rows, maps, cell arrays, tasks), the
-// tensor-core operands when D >= 8, and slack for alignment.
+// share of the batch grid (sorted rows, maps, cell array), the tensor-core
+// operands when D >= 8, and slack for alignment.
 size_t request_bytes(int64_t n, int D, int K) {
     const int DP = padded_dim(D);
-    const int64_t cap = cell_cap_for(n);
+    const int64_t cap = cell_cap_for(n, std::min(D, kMaxAxes));
     size_t b = (size_t)n * D * 4 + (size_t)n * (4 + 8 * (size_t)K);
-    b += (size_t)(n + 1 + kTcRowPad) * (4 * DP + 16 + 8) + (size_t)(cap + 1) * 8 +
-         (size_t)(n / 32 + cap + 2) * 16;
+    b += (size_t)(n + 1 + kTcRowPad) * (4 * DP + 16 + 8) + (size_t)(cap + 1) * 4;
     if (D >= 8) b += (size_t)(n + 8 + kTcRowPad) * (4 * (size_t)((3 * D + 2 + 15) / 16 * 16) + 4);
     return b + 64 * 1024;
 }

@@ -64,7 +64,7 @@ constexpr int kTcEpi = 256;      // epilogue threads: warp w < 8 owns TMEM lanes
 constexpr int kTcThreads = kTcEpi + 32;   // + one producer warp (bulk copies, MMA issue)
 constexpr int kTcLStr = kTcM + 1;         // list table: one column per query row
 constexpr int kTcMaxChunks = 128;         // chunk table entries kept in shared memory
-constexpr int kTcMaxRows = 32;   // neighbour rows per task (m <= 2)
+constexpr int kTcMaxRows = kMaxNbrRows;   // neighbour rows per task
 constexpr int kTcCols = 256;     // TMEM columns per CTA: two accumulators (2 CTAs / SM)
 // (the producer warp is warp 4; epilogue warps 0..3 own the TMEM lane quarters)
 constexpr int kTcList = 30;      // per-query survivor list capacity (2 CTAs / SM up to D = 12)
@@ -142,7 +142,7 @@ __global__ void k_tc_prep(const EventHdr* own, const EventHdr* ctr, int E, int64
         hi[k] = 0;
         lo[k] = 0;
         if (real) {
-            const float xc = __fsub_rn(pts[pair_index(s, k, DP)], ctr[e].ctr[k]);
+            const float xc = __fsub_rn(pts[pt_index(s, k, DP)], ctr[e].ctr[k]);
             const __nv_bfloat16 bh = __float2bfloat16_rn(xc);
             const __nv_bfloat16 bl = __float2bfloat16_rn(__fsub_rn(xc, __bfloat162float(bh)));
             const float xh = __fadd_rn(__bfloat162float(bh), __bfloat162float(bl));
@@ -451,45 +451,54 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_tc_query(TcArgs a) {
             const int dims0 = h.dims[0], m = h.m;
             const int xa = a.qcell[tk.qslot] % dims0;
             const int xb = a.qcell[tk.qslot + tk.nq - 1] % dims0;
-            const int nrows = neighbour_rows(h);   // <= 32 (the grid parameters ensure it)
-            int rs = 0, re = 0;
-            int64_t rowbase;
-            if (lane < nrows && neighbour_row(h, tk.row, lane, rowbase)) {
-                rs = a.cstart[rowbase + max(xa - m, 0)];
-                re = a.cstart[rowbase + min(xb + m, dims0 - 1) + 1];
-            }
-            const int b8 = rs & ~7;
-            const int e8 = (re + 7) & ~7;
-            const int nch = re > rs ? (e8 - b8 + kTcN - 1) / kTcN : 0;
-            int pre = nch;
+            // (2m+1)^(naxes-1) <= kTcMaxRows rows (the grid parameters ensure
+            // it), 32 per round with a running chunk count
+            const int nrows = neighbour_rows(h);
+            int carry = 0;
+            for (int rr = 0; rr * 32 < nrows; ++rr) {
+                const int l = rr * 32 + lane;
+                int rs = 0, re = 0;
+                int64_t rowbase;
+                if (l < nrows && neighbour_row(h, tk.row, l, rowbase)) {
+                    rs = a.cstart[rowbase + max(xa - m, 0)];
+                    re = a.cstart[rowbase + min(xb + m, dims0 - 1) + 1];
+                }
+                const int b8 = rs & ~7;
+                const int e8 = (re + 7) & ~7;
+                const int nch = re > rs ? (e8 - b8 + kTcN - 1) / kTcN : 0;
+                int pre = nch;
 #pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const int v = __shfl_up_sync(0xffffffffu, pre, o);
-                if (lane >= o) pre += v;
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int v = __shfl_up_sync(0xffffffffu, pre, o);
+                    if (lane >= o) pre += v;
+                }
+                if (l < kTcMaxRows) {
+                    s_ct.rs[l] = rs;
+                    s_ct.re[l] = re;
+                    s_ct.b8[l] = b8;
+                    s_ct.pref[l] = carry + pre - nch;
+                }
+                // this lane's row: its chunks' (start, n, lo, hi)
+                for (int j = 0; j < nch; ++j) {
+                    const int c = carry + pre - nch + j;
+                    if (c >= kTcMaxChunks) break;
+                    const int start = b8 + j * kTcN;
+                    int n = min(kTcN, e8 - start);
+                    n = (n + 31) & ~31;
+                    s_ct.chunk[c] = make_int4(start, n, rs, re);
+                }
+                carry += __shfl_sync(0xffffffffu, pre, 31);
             }
-            s_ct.rs[lane] = rs;
-            s_ct.re[lane] = re;
-            s_ct.b8[lane] = b8;
-            s_ct.pref[lane] = pre - nch;
-            if (lane == 31) {
-                s_ct.nch = pre;
+            if (lane == 0) {
+                s_ct.nch = carry;
                 s_ct.nrows = nrows;
-            }
-            // this lane's row: its chunks' (start, n, lo, hi)
-            for (int j = 0; j < nch; ++j) {
-                const int c = pre - nch + j;
-                if (c >= kTcMaxChunks) break;
-                const int start = b8 + j * kTcN;
-                int n = min(kTcN, e8 - start);
-                n = (n + 31) & ~31;
-                s_ct.chunk[c] = make_int4(start, n, rs, re);
             }
         } else if (half == 0) {
             // this thread's query: float32 coordinates (shared: the recheck
             // reads them from any lane)
 #pragma unroll
             for (int k = 0; k < D; ++k)
-                Qs[row * DP + k] = active ? a.qpts[pair_index(qs, k, DP)] : 0.f;
+                Qs[row * DP + k] = active ? a.qpts[pt_index(qs, k, DP)] : 0.f;
             s_cnt[row] = 0;
         }
         __syncthreads();
@@ -521,8 +530,8 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_tc_query(TcArgs a) {
                     mbar_arrive_expect_tx(&bar_b[slot], bB + bF);
                     bulk_g2s(Bs + (size_t)slot * kTcN * K, a.tcB + cm_off(start, 0, K), bB,
                              &bar_b[slot]);
-                    bulk_g2s(Fs + (size_t)slot * kTcN * DP, a.rpts + (int64_t)(start >> 1) * 2 * DP,
-                             bF, &bar_b[slot]);
+                    bulk_g2s(Fs + (size_t)slot * kTcN * DP, a.rpts + (int64_t)start * DP, bF,
+                             &bar_b[slot]);
                 };
                 const uint32_t bA = (uint32_t)kTcM * K * 2;
                 mbar_arrive_expect_tx(&bar_a, bA);
@@ -663,12 +672,12 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_tc_query(TcArgs a) {
                                 const int r = 32 * (warp & 3) + (pr >> 5);
                                 const int cs = c0 + (pr & 31);
                                 // exact contract from the staged float32 coordinates
-                                const float* f = F + ((cs - start) >> 1) * 2 * DP + (cs & 1);
+                                const float* f = F + (size_t)(cs - start) * DP;
                                 const float* qv = Qs + r * DP;
                                 float sd = 0.f;
 #pragma unroll
                                 for (int k = 0; k < D; ++k) {
-                                    const float d = __fsub_rn(qv[k], f[2 * k]);
+                                    const float d = __fsub_rn(qv[k], f[k]);
                                     sd = __fadd_rn(sd, __fmul_rn(d, d));
                                 }
                                 if (sd <= r2) {
@@ -755,7 +764,9 @@ void tc_free(GridBufs& g) {
     if (g.tc_base) cudaFree(g.tc_base);
     g.tc_base = nullptr;
     g.tc_bytes = 0;
-    g.tc_cap_rows = g.tc_cap_tasks = g.tc_cap_E = 0;
+    g.tc_cap_rows = g.tc_cap_tasks = g.tc_cap_E = g.tc_cap_L = 0;
+    g.tc_rtask = nullptr;
+    g.rtask = nullptr;
     g.tc_ready = false;
 }
 
@@ -767,19 +778,27 @@ static size_t al256(size_t x) { return (x + 255) / 256 * 256; }
 frnn_status tc_reserve(GridBufs& g, std::string& err) {
     const int K = tc_k_for(g.D);
     const int64_t rows = (g.n_total + 7) / 8 * 8 + kTcRowPad;
+    // a tile never spans two rows of cells and only rows holding a point open
+    // one: a row of c queries takes at most floor(c / 128) + 1 tiles, or + 2
+    // when its start alignment (up to 7 slots) carries it past a multiple of
+    // 128, which needs c >= 121; so per event at most n / 128 + rows + n / 121
     int64_t tcap = 0;
     for (int e = 0; e < g.E; ++e)
-        tcap += g.h_hdr[e].n / kTcM + g.h_hdr[e].cell_cap + 2;
+        tcap += g.h_hdr[e].n / kTcM + g.h_hdr[e].n / 64 +
+                std::min<int64_t>(g.h_hdr[e].cell_cap, g.h_hdr[e].n) + 2;
     if (g.tc_base && g.tc_K == K && g.tc_cap_rows >= rows && g.tc_cap_tasks >= tcap &&
-        g.tc_cap_E >= g.E)
+        g.tc_cap_E >= g.E && g.tc_cap_L >= g.L) {
+        g.rtask = g.tc_rtask;
         return FRNN_OK;
+    }
     tc_free(g);
     const size_t bA = al256(sizeof(uint16_t) * rows * K);
     const size_t bn = al256(sizeof(float) * rows);
     const size_t bnu = al256(sizeof(int32_t) * std::max(g.E, 1));
     const size_t bt = al256(sizeof(Task) * tcap);
+    const size_t brt = al256(sizeof(int32_t) * std::max<int64_t>(g.L, 1));
     void* base = nullptr;
-    cudaError_t ce = cudaMalloc(&base, 2 * bA + bn + bnu + bt + 256);
+    cudaError_t ce = cudaMalloc(&base, 2 * bA + bn + bnu + bt + brt + 256);
     if (ce != cudaSuccess) {
         cudaGetLastError();
         err = "cudaMalloc of tensor-core operands failed";
@@ -787,12 +806,15 @@ frnn_status tc_reserve(GridBufs& g, std::string& err) {
     }
     char* b = static_cast<char*>(base);
     g.tc_base = base;
-    g.tc_bytes = 2 * bA + bn + bnu + bt + 256;
+    g.tc_bytes = 2 * bA + bn + bnu + bt + brt + 256;
     g.tcA = reinterpret_cast<uint16_t*>(b);
     g.tcB = reinterpret_cast<uint16_t*>(b + bA);
     g.tcn = reinterpret_cast<float*>(b + 2 * bA);
     g.tcnu = reinterpret_cast<int32_t*>(b + 2 * bA + bn);
     g.tc_tasks = reinterpret_cast<Task*>(b + 2 * bA + bn + bnu);
+    g.tc_rtask = reinterpret_cast<int32_t*>(b + 2 * bA + bn + bnu + bt);
+    g.rtask = g.tc_rtask;   // scratch of the task builder (per row of cells)
+    g.tc_cap_L = g.L;
     g.tc_cap_rows = rows;
     g.tc_cap_tasks = tcap;
     g.tc_cap_E = g.E;
@@ -807,8 +829,8 @@ frnn_status tc_reserve(GridBufs& g, std::string& err) {
     return FRNN_OK;
 }
 
-frnn_status tc_prepare(GridBufs& g, const GridBufs& center_src, cudaStream_t st,
-                       std::string& err) {
+frnn_status tc_prepare(GridBufs& g, const GridBufs& center_src, int32_t* d_status,
+                       cudaStream_t st, std::string& err) {
     frnn_status s0 = tc_reserve(g, err);
     if (s0 != FRNN_OK) return s0;
     const int K = tc_k_for(g.D);
@@ -830,7 +852,7 @@ frnn_status tc_prepare(GridBufs& g, const GridBufs& center_src, cudaStream_t st,
         }
         (void)K;
     }
-    enqueue_tasks(g, kTcM, 8, g.tc_tasks, g.scalars + kScTcTasks, st);
+    enqueue_tasks(g, kTcM, 8, g.tc_tasks, g.tc_cap_tasks, g.scalars + kScTcTasks, d_status, st);
     cudaError_t ce = cudaGetLastError();
     if (ce != cudaSuccess) {
         err = std::string("tensor-core prep launch failed: ") + cudaGetErrorString(ce);

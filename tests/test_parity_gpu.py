@@ -222,8 +222,8 @@ def test_grid_options_do_not_change_results(ctx, m, axes):
         ctx.set_option(frnn.FRNN_OPT_GRID_AXES, 0)
 
 
-@pytest.mark.parametrize("naxes", [1, 2, 3, 4])
-@pytest.mark.parametrize("m", [1, 2])
+@pytest.mark.parametrize("naxes", [1, 2, 3, 4, 5])
+@pytest.mark.parametrize("m", [1, 2, 3])
 @pytest.mark.parametrize("axes", [0, 1])
 def test_gridded_axis_counts_do_not_change_results(ctx, naxes, m, axes):
     from paper_2609_31980_gb300 import frnn
@@ -238,6 +238,23 @@ def test_gridded_axis_counts_do_not_change_results(ctx, naxes, m, axes):
         ctx.set_option(frnn.FRNN_OPT_GRID_NAXES, 0)
         ctx.set_option(frnn.FRNN_OPT_CELL_MULT, 0)
         ctx.set_option(frnn.FRNN_OPT_GRID_AXES, 0)
+
+
+def test_five_axes_dense_cells_many_ranges(ctx):
+    # every cell of a 4^5 block holds several points: each group of a query
+    # chunk has 81 non-empty neighbour rows, so a chunk's groups are served in
+    # several batches of candidate ranges, and rows exceed the kernel's list
+    # (the selection kernel finishes them)
+    from paper_2609_31980_gb300 import frnn
+    g = np.random.default_rng(330)
+    pts = (g.integers(0, 4, size=(6000, 5)) + g.uniform(0.1, 0.9, size=(6000, 5))).astype(np.float32)
+    pts *= np.float32(0.1)
+    ctx.set_option(frnn.FRNN_OPT_GRID_NAXES, 5)
+    try:
+        for K in (16, 200):
+            _assert_rows_equal(_gpu_self(ctx, pts, 0.1, K), oracle.self_query(pts, 0.1, K))
+    finally:
+        ctx.set_option(frnn.FRNN_OPT_GRID_NAXES, 0)
 
 
 @pytest.mark.parametrize("e", [1, 3, 4, 6])
