@@ -261,11 +261,11 @@ const char* frnn_last_error(const frnn_ctx* ctx);
 
 /*
  * Autotuner.  Times the candidate configurations on the given point set (a
- * representative event, device memory, self-query): grids over three
- * coordinates with cell multiple m in {1, 2} (cell edge ~ r/m, the grid's
- * search reach +-m cells) and over four with m = 1; on each, the grid scan
- * with its default and a later warp vote (D >= 5), and the tensor-core
- * pre-filter (D >= 8).
+ * representative event, device memory, self-query): grids over five
+ * coordinates with cell multiple m = 1, over four with m in {1, 2}, over
+ * three with m in {2, 3} (cell edge ~ r/m, search reach +-m cells; fewer
+ * axes when D is smaller); on each, the grid scan with either candidate
+ * staging, and the tensor-core pre-filter (D >= 8).
  * Each candidate is built and queried (first run untimed, best of three
  * timed with CUDA events on the context's stream) and the fastest build +
  * query is cached for the event size class (power-of-two bucket of N, D,
@@ -279,9 +279,10 @@ const char* frnn_last_error(const frnn_ctx* ctx);
 typedef struct frnn_tune_result {
     int path;        /* FRNN_PATH_GRID or FRNN_PATH_TC */
     int cell_mult;   /* m */
-    int exit_dims;   /* warp vote point of the grid scan (0 = default) */
+    int exit_dims;   /* always 0 (the grid scan has no vote) */
     float ms;        /* build + query time of the winner, milliseconds */
-    int grid_axes;   /* gridded coordinates (3, or 4 with m = 1) */
+    int grid_axes;   /* gridded coordinates requested (3, 4 or 5, at most D) */
+    int staging;     /* grid scan candidate staging (FRNN_OPT_STAGING values 1, 2) */
 } frnn_tune_result;
 
 frnn_status frnn_autotune(frnn_ctx* ctx, const float* refs, int64_t N, int D, float r, int K,
@@ -289,13 +290,16 @@ frnn_status frnn_autotune(frnn_ctx* ctx, const float* refs, int64_t N, int D, fl
 
 /* Tunable options (none changes results, only speed). */
 typedef enum frnn_option {
-    FRNN_OPT_CELL_MULT = 1,   /* m in {1, 2}: cell edge ~ r/m, search +-m cells;
+    FRNN_OPT_CELL_MULT = 1,   /* m in {1, 2, 3}: cell edge ~ r/m, search +-m cells;
                                  0 (default): autotuned, else 2 on grids of at
-                                 most three axes and 1 on four-axis grids */
+                                 most three requested axes and 1 otherwise */
     FRNN_OPT_GRID_AXES = 2,   /* which coordinates are gridded: 0 the last ones,
                                  1 the widest ones (count: FRNN_OPT_GRID_NAXES) */
-    FRNN_OPT_EXIT_DIMS = 3,   /* dims summed before the warp-uniform early exit
-                                 (0 = library default) */
+    FRNN_OPT_EXIT_DIMS = 3,   /* accepted for compatibility (0..16) and ignored:
+                                 the grid scan evaluates every candidate of a
+                                 group with the whole contract, since a warp
+                                 vote after the first dimensions skipped no
+                                 measurable work */
     FRNN_OPT_USE_GRAPH = 4,   /* 1 (default): batched calls replay a CUDA graph */
     FRNN_OPT_AUTOTUNE = 5,    /* 1 (default): FRNN_PATH_AUTO consults the tuner;
                                  setting 0 also clears the tuned cache */
@@ -310,10 +314,18 @@ typedef enum frnn_option {
                                  selection pass or operand preparation), read
                                  with frnn_kernel_times; 0 (default): off.
                                  Setting it discards recorded pairs. */
-    FRNN_OPT_GRID_NAXES = 10  /* gridded coordinates: 1..4 (at most D); 0
-                                 (default): autotuned, else min(D, 4).  With 4
-                                 axes the cell multiple is 1 (the neighbour
-                                 rows, (2m+1)^3, must not exceed 32). */
+    FRNN_OPT_GRID_NAXES = 10, /* gridded coordinates: 1..5 (at most D); 0
+                                 (default): autotuned, else the build's choice
+                                 between min(D, 5) and one fewer (the smaller
+                                 expected neighbourhood under the cell
+                                 budget).  The cell multiple is lowered until
+                                 the neighbour rows, (2m+1)^(axes-1), are at
+                                 most 128. */
+    FRNN_OPT_STAGING = 11     /* candidate staging of the grid scan: 1 each lane
+                                 loads its candidate's row from global memory
+                                 (L2), the next round in flight; 2 bulk copies
+                                 (cp.async.bulk) of tiles into a shared-memory
+                                 ring; 0 (default): autotuned, else 1 */
 } frnn_option;
 
 frnn_status frnn_set_option(frnn_ctx* ctx, frnn_option opt, int64_t value);

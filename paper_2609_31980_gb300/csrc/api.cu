@@ -36,6 +36,7 @@ struct frnn_ctx {
     int grid_naxes = 0;       // gridded axes: 0 tuned / default, else 1..4
     int axes_mode = 0;
     int exit_dims = 0;
+    int staging = 0;          // FRNN_OPT_STAGING (0: tuned, else 1)
     int use_graph = 1;
     int autotune = 1;
     int auto_tc = 1;          // FRNN_PATH_AUTO uses the tensor-core path for D >= 8
@@ -54,6 +55,7 @@ struct frnn_ctx {
         int exit_dims;
         float ms;
         int naxes;
+        int staging;   // FRNN_OPT_STAGING value (1 or 2)
     };
     std::map<uint32_t, Tuned> tuned;
     // live grids built through this context (detached when it is destroyed)
@@ -68,7 +70,7 @@ struct frnn_ctx {
     int g_D = 0, g_K = 0;
     float g_r = 0.f;
     unsigned g_flags = 0;
-    int g_opts[4] = {0, 0, 0, 0};
+    int g_opts[5] = {0, 0, 0, 0, 0};
     // compact output: staging rows of the pending count pass, and what the
     // fill pass needs (valid until the next call on this context)
     void* csr_buf = nullptr;
@@ -97,6 +99,7 @@ void ctx_copy_tuning(frnn_ctx* dst, const frnn_ctx* src) {
     dst->grid_naxes = src->grid_naxes;
     dst->axes_mode = src->axes_mode;
     dst->exit_dims = src->exit_dims;
+    dst->staging = src->staging;
     dst->autotune = src->autotune;
     dst->auto_tc = src->auto_tc;
     dst->tuned = src->tuned;
@@ -466,9 +469,13 @@ static frnn_status query_impl(frnn_ctx* ctx, const frnn_grid* grid, const float*
     q.K = K;
     q.self = self ? 1 : 0;
     q.exit_dims = ctx->exit_dims;
-    if (q.exit_dims == 0 && !(flags & (FRNN_PATH_GRID | FRNN_PATH_TC))) {
-        const frnn_ctx::Tuned* t = find_tuned(ctx, grid->N, grid->D, K);
-        if (t) q.exit_dims = t->exit_dims;
+    {
+        int stg = ctx->staging;
+        if (stg == 0) {
+            const frnn_ctx::Tuned* t = find_tuned(ctx, grid->N, grid->D, K);
+            if (t) stg = t->staging;
+        }
+        q.stage = stg == 2 ? 1 : 0;
     }
     q.counts = counts;
     q.idx = idx;
@@ -671,6 +678,7 @@ static frnn_status enqueue_batched(frnn_ctx* ctx, const frnn_event* ev, int n_ev
     q.K = K;
     q.self = 1;
     q.exit_dims = ctx->exit_dims;
+    q.stage = ctx->staging == 2 ? 1 : 0;
     q.d_status = ctx->d_status;
     q.num_sms = ctx->num_sms;
     const bool mixed = any_grid && any_tc;
@@ -725,7 +733,8 @@ frnn_status frnn_query_batched(frnn_ctx* ctx, const frnn_event* ev, int n_events
             return fail(ctx, FRNN_ERR_INVALID_ARG, "event pointer is NULL");
         n[e] = x.n;
     }
-    const int opts[4] = {ctx->cell_mult, ctx->axes_mode, ctx->exit_dims, ctx->grid_naxes};
+    const int opts[5] = {ctx->cell_mult, ctx->axes_mode, ctx->exit_dims, ctx->grid_naxes,
+                         ctx->staging};
     const bool hit = ctx->use_graph && ctx->graph && same_events(ctx, ev, n_events) &&
                      ctx->g_D == D && ctx->g_K == K && ctx->g_r == r && ctx->g_flags == flags &&
                      std::memcmp(opts, ctx->g_opts, sizeof(opts)) == 0;
@@ -980,8 +989,9 @@ frnn_status frnn_autotune(frnn_ctx* ctx, const float* refs, int64_t N, int D, fl
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
-    const int saved_m = ctx->cell_mult, saved_x = ctx->exit_dims, saved_a = ctx->grid_naxes;
-    frnn_tune_result bestr{FRNN_PATH_GRID, 1, 0, INFINITY, std::min(D, kMaxAxes)};
+    const int saved_m = ctx->cell_mult, saved_x = ctx->exit_dims, saved_a = ctx->grid_naxes,
+              saved_s = ctx->staging;
+    frnn_tune_result bestr{FRNN_PATH_GRID, 1, 0, INFINITY, std::min(D, kMaxAxes), 1};
     frnn_status s = FRNN_OK;
     frnn_grid* g = nullptr;
     auto timed = [&](auto&& fn, float& ms) -> frnn_status {
@@ -1022,16 +1032,19 @@ frnn_status frnn_autotune(frnn_ctx* ctx, const float* refs, int64_t N, int D, fl
         float bms = 0.f;
         s = timed([&] { return frnn_build_grid(ctx, refs, N, D, r, &g); }, bms);
         if (s != FRNN_OK) break;
-        struct Cand { unsigned path; int exit_dims; };
+        struct Cand { unsigned path; int staging; };
         std::vector<Cand> cands;
-        if (!(flags & FRNN_PATH_TC)) cands.push_back({FRNN_PATH_GRID, 0});
-        if (D >= 8 && !(flags & FRNN_PATH_GRID)) cands.push_back({FRNN_PATH_TC, 0});
+        if (!(flags & FRNN_PATH_TC)) {
+            cands.push_back({FRNN_PATH_GRID, 1});
+            cands.push_back({FRNN_PATH_GRID, 2});
+        }
+        if (D >= 8 && !(flags & FRNN_PATH_GRID)) cands.push_back({FRNN_PATH_TC, 1});
         if (cands.empty()) {
             s = fail(ctx, FRNN_ERR_UNSUPPORTED, "the tensor-core path needs D >= 8");
             break;
         }
         for (const Cand& c : cands) {
-            ctx->exit_dims = c.exit_dims;
+            ctx->staging = c.staging;
             float qms = 0.f;
             s = timed([&] {
                 return frnn_query(ctx, g, refs, N, r, K, FRNN_SELF_QUERY | c.path, counts, idx,
@@ -1039,19 +1052,20 @@ frnn_status frnn_autotune(frnn_ctx* ctx, const float* refs, int64_t N, int D, fl
             }, qms);
             if (s != FRNN_OK) break;
             if (bms + qms < bestr.ms)
-                bestr = {(int)c.path, m, c.exit_dims, bms + qms, gcfg[gi].naxes};
+                bestr = {(int)c.path, m, 0, bms + qms, gcfg[gi].naxes, c.staging};
         }
     }
     ctx->cell_mult = saved_m;
     ctx->exit_dims = saved_x;
     ctx->grid_naxes = saved_a;
+    ctx->staging = saved_s;
     if (g) frnn_grid_destroy(g);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     cudaFree(out);
     if (s != FRNN_OK) return s;
     ctx->tuned[tune_key(N, D, K)] = {bestr.path == FRNN_PATH_TC ? 1 : 0, bestr.cell_mult,
-                                     bestr.exit_dims, bestr.ms, bestr.grid_axes};
+                                     bestr.exit_dims, bestr.ms, bestr.grid_axes, bestr.staging};
     if (ctx->graph) {   // captured batches may now take other paths
         cudaGraphExecDestroy(ctx->graph);
         ctx->graph = nullptr;
@@ -1081,6 +1095,11 @@ frnn_status frnn_set_option(frnn_ctx* ctx, frnn_option opt, int64_t value) {
         case FRNN_OPT_EXIT_DIMS:
             if (value < 0 || value > kMaxD) return fail(ctx, FRNN_ERR_INVALID_ARG, "exit dims");
             ctx->exit_dims = (int)value;
+            return FRNN_OK;
+        case FRNN_OPT_STAGING:
+            if (value < 0 || value > 2)
+                return fail(ctx, FRNN_ERR_INVALID_ARG, "staging must be 0 (tuned), 1 or 2");
+            ctx->staging = (int)value;
             return FRNN_OK;
         case FRNN_OPT_USE_GRAPH:
             ctx->use_graph = value ? 1 : 0;
@@ -1130,6 +1149,7 @@ frnn_status frnn_get_option(const frnn_ctx* ctx, frnn_option opt, int64_t* value
         case FRNN_OPT_GRID_AXES: *value = ctx->axes_mode; return FRNN_OK;
         case FRNN_OPT_GRID_NAXES: *value = ctx->grid_naxes; return FRNN_OK;
         case FRNN_OPT_EXIT_DIMS: *value = ctx->exit_dims; return FRNN_OK;
+        case FRNN_OPT_STAGING: *value = ctx->staging; return FRNN_OK;
         case FRNN_OPT_USE_GRAPH: *value = ctx->use_graph; return FRNN_OK;
         case FRNN_OPT_AUTOTUNE: *value = ctx->autotune; return FRNN_OK;
         case FRNN_OPT_AUTO_TC: *value = ctx->auto_tc; return FRNN_OK;

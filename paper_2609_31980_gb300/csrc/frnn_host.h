@@ -101,7 +101,7 @@ struct BuildOpts {
     float r = 0.f;          // grid radius
     int m = 1;              // cell multiple
     int axes_mode = 0;      // 0: last axes, 1: widest axes
-    int naxes = 3;          // gridded axes requested (at most D, at most kMaxAxes)
+    int naxes = 0;          // gridded axes requested (at most D, kMaxAxes); 0 = automatic
 };
 
 // Enqueue a full build (bounding boxes, parameters, binning, counting sort,
@@ -134,6 +134,7 @@ struct QueryLaunch {
     int K;
     int self;
     int exit_dims;          // 0 = default
+    int stage = 0;          // grid query candidate staging: 0 lanes load rows, 1 bulk copies
     int32_t* counts;        // single event outputs, or NULL to use the event headers'
     int32_t* idx;
     float* dist2;

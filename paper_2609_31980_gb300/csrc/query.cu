@@ -56,14 +56,25 @@ static_assert(kListCap <= kCsrStageW, "a staged compact row holds a whole kernel
 static_assert(kRangeCap >= kMaxNbrRows, "one group's ranges always fit a batch");
 static_assert(kChunkQ <= 16, "group search over at most 16 groups");
 
-template <int D>
+// Candidate staging.  kStageLoads: each lane loads its candidate's row from
+// global memory (the cell-sorted rows of an event stay L2-resident), the next
+// round's rows in flight while the current round is evaluated.  kStageBulk:
+// the stream is cut into tiles that cp.async.bulk copies into a two-buffer
+// shared-memory ring (one copy per range part, completion on an mbarrier).
+constexpr int kStageLoads = 0;
+constexpr int kStageBulk = 1;
+
+template <int D, int STAGE>
 struct QCfg {
     static constexpr int DP = padded_dim(D);
-    // candidates per tile and ring buffers; CTAs per SM from the per-warp
-    // shared memory (the scan is latency-bound and wants resident warps)
+    // candidates per tile and ring buffers of the bulk-copy staging
     static constexpr int TILE = 64;
     static constexpr int NB = 2;
-    static constexpr int MINB = DP <= 4 ? 6 : (DP <= 8 ? 5 : (DP <= 12 ? 4 : 3));
+    // CTAs per SM (the scan is latency-bound and wants resident warps): as
+    // many as the per-warp shared memory and the registers allow
+    static constexpr int MINB = STAGE == kStageBulk
+                                    ? (DP <= 4 ? 6 : (DP <= 8 ? 5 : (DP <= 12 ? 4 : 3)))
+                                    : (DP <= 8 ? 6 : (DP <= 12 ? 4 : 3));
     // sort two short query rows at once, one per half-warp (rows of at most
     // 16 entries: the 500k x 12 event's clustered queries have about 12)
     static constexpr bool PAIR_ROWS = D >= 10;
@@ -72,37 +83,38 @@ struct QCfg {
 // Per-warp shared memory.  Every bulk-copy destination (the ring) starts on
 // a 128-byte boundary and holds whole rows of DP floats (16-byte multiples).
 struct WarpSmem {
-    float* ring;      // [NB][TILE][DP] candidate coordinates
-    int32_t* tslot;   // [NB][TILE] candidate slots
+    float* ring;      // [NB][TILE][DP] candidate coordinates (bulk staging)
+    int32_t* tslot;   // [NB][TILE] candidate slots (bulk staging)
     float* Q;         // [kChunkQ][DP] the chunk's query coordinates
     float* Ld;        // [kChunkQ][kListStr] accepted squared distances
     int32_t* Li;      // [kChunkQ][kListStr] accepted slots, then original indices
-    uint64_t* bars;   // [NB]
+    uint64_t* bars;   // [NB] (bulk staging)
     int32_t* rlo;     // [kRangeCap] first slot of each compact range
     int32_t* rpre;    // [kRangeCap + 1] stream position of each range; sentinel = length
     int32_t* cnt;     // [kChunkQ] accepted entries per query
 };
 
-template <int D>
+template <int D, int STAGE>
 __host__ __device__ constexpr size_t warp_smem_bytes() {
-    using C = QCfg<D>;
-    return ((size_t)C::NB * C::TILE * C::DP * 4 + (size_t)C::NB * C::TILE * 4 +
-            (size_t)kChunkQ * C::DP * 4 + 2 * (size_t)kChunkQ * kListStr * 4 + C::NB * 8 +
+    using C = QCfg<D, STAGE>;
+    constexpr size_t ring = STAGE == kStageBulk ? (size_t)C::NB * C::TILE * (C::DP + 1) * 4 + C::NB * 8 : 0;
+    return (ring + (size_t)kChunkQ * C::DP * 4 + 2 * (size_t)kChunkQ * kListStr * 4 +
             (size_t)kRangeCap * 4 + (size_t)(kRangeCap + 1) * 4 + (size_t)kChunkQ * 4 + 127) /
            128 * 128;
 }
 
-template <int D>
+template <int D, int STAGE>
 __device__ __forceinline__ WarpSmem carve_warp(unsigned char* base) {
-    using C = QCfg<D>;
+    using C = QCfg<D, STAGE>;
+    constexpr int NBUF = STAGE == kStageBulk ? C::NB : 0;
     WarpSmem w;
     w.ring = reinterpret_cast<float*>(base);
-    w.tslot = reinterpret_cast<int32_t*>(w.ring + C::NB * C::TILE * C::DP);
-    w.Q = reinterpret_cast<float*>(w.tslot + C::NB * C::TILE);
+    w.tslot = reinterpret_cast<int32_t*>(w.ring + NBUF * C::TILE * C::DP);
+    w.Q = reinterpret_cast<float*>(w.tslot + NBUF * C::TILE);
     w.Ld = w.Q + kChunkQ * C::DP;
     w.Li = reinterpret_cast<int32_t*>(w.Ld + kChunkQ * kListStr);
     w.bars = reinterpret_cast<uint64_t*>(w.Li + kChunkQ * kListStr);
-    w.rlo = reinterpret_cast<int32_t*>(w.bars + C::NB);
+    w.rlo = reinterpret_cast<int32_t*>(w.bars + NBUF);
     w.rpre = w.rlo + kRangeCap;
     w.cnt = w.rpre + kRangeCap + 1;
     return w;
@@ -126,10 +138,10 @@ __device__ __forceinline__ int chunk_event(const EventHdr* qev, int E, int c) {
 // part inside [T0, T1) with one bulk copy (issued by the lane holding the
 // range), the slots of the copied candidates into tslot, completion on the
 // buffer's mbarrier.  cur: first range that may overlap the tile (advanced).
-template <int D>
+template <int D, int STAGE>
 __device__ __forceinline__ void issue_tile(const WarpSmem& w, int t, int b, int U, int nr,
                                            int& cur, const float* rpts, int lane) {
-    using C = QCfg<D>;
+    using C = QCfg<D, STAGE>;
     constexpr int DP = C::DP, T = C::TILE;
     const int T0 = t * T;
     const int T1 = min(T0 + T, U);
@@ -153,22 +165,24 @@ __device__ __forceinline__ void issue_tile(const WarpSmem& w, int t, int b, int 
     while (cur < nr && w.rpre[cur + 1] <= T1) ++cur;
 }
 
-template <int D>
-__global__ void __launch_bounds__(kQueryWarps * 32, QCfg<D>::MINB) k_grid_query(QueryArgs a) {
+template <int D, int STAGE>
+__global__ void __launch_bounds__(kQueryWarps * 32, QCfg<D, STAGE>::MINB) k_grid_query(QueryArgs a) {
     pdl_trigger();
     pdl_wait();
-    using C = QCfg<D>;
+    using C = QCfg<D, STAGE>;
     constexpr int DP = C::DP;
     constexpr int T = C::TILE;
     constexpr int NB = C::NB;
     extern __shared__ __align__(128) unsigned char smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const WarpSmem w = carve_warp<D>(smem + (size_t)warp * warp_smem_bytes<D>());
-    if (lane == 0)
-        for (int b = 0; b < NB; ++b) mbar_init(&w.bars[b], 1);
-    fence_mbar_init();
-    __syncwarp();
-    uint32_t phase = 0;   // bit b: parity to wait for on buffer b
+    const WarpSmem w = carve_warp<D, STAGE>(smem + (size_t)warp * warp_smem_bytes<D, STAGE>());
+    if constexpr (STAGE == kStageBulk) {
+        if (lane == 0)
+            for (int b = 0; b < NB; ++b) mbar_init(&w.bars[b], 1);
+        fence_mbar_init();
+        __syncwarp();
+    }
+    uint32_t phase = 0;   // bit b: parity to wait for on buffer b (bulk staging)
     const unsigned lt_mask = (1u << lane) - 1u;
 
     const float r2 = a.r2;
@@ -279,41 +293,68 @@ __global__ void __launch_bounds__(kQueryWarps * 32, QCfg<D>::MINB) k_grid_query(
 #pragma unroll
         for (int ax = 2; ax < kMaxAxes; ++ax) rstride[ax] = rstride[ax - 1] * dims[ax - 1];
 
+        // Row ranges of group g (lane l of round rr: neighbour row 32 rr + l):
+        // every round's two cell-start loads are issued together, and the next
+        // group's are issued before the current group is compacted.
+        int nlo[kNbrRounds], nhi[kNbrRounds];
+        auto fetch = [&](int g) {
+            const int hl = __shfl_sync(kFull, gq, g);
+            int gc[kMaxAxes];
+#pragma unroll
+            for (int ax = 0; ax < kMaxAxes; ++ax) gc[ax] = __shfl_sync(kFull, cc[ax], hl);
+            const int x0 = max(gc[0] - m, 0), x1 = min(gc[0] + m, dims0 - 1);
+#pragma unroll
+            for (int rr = 0; rr < kNbrRounds; ++rr) {
+                nlo[rr] = 0;
+                nhi[rr] = 0;
+                const int l = rr * 32 + lane;
+                if (l < nrows) {
+                    bool ok = true;
+                    int rowlin = 0;
+#pragma unroll
+                    for (int ax = 1; ax < kMaxAxes; ++ax) {
+                        if (ax < naxes) {
+                            const int v = gc[ax] + (int)((dig[rr] >> (3 * (ax - 1))) & 7u) - m;
+                            ok = ok && (unsigned)v < (unsigned)dims[ax];
+                            rowlin += v * rstride[ax];
+                        }
+                    }
+                    if (ok) {
+                        const int64_t base = cell_off + (int64_t)rowlin * dims0;
+                        nlo[rr] = __ldg(a.cstart + base + x0);
+                        nhi[rr] = __ldg(a.cstart + base + x1 + 1);
+                    }
+                }
+            }
+        };
+
         // batches of groups whose compact ranges fit kRangeCap
         bool timed_out = false;
-        int g0 = 0;
+        int g0 = 0, pf = -1;   // pf: group whose ranges nlo/nhi hold
         while (g0 < ng && !timed_out) {
             int nr = 0, U = 0, g = g0;
             int gsb = INT_MAX;   // lane j: stream start of batch group g0 + j
+            if (pf != g0) {
+                fetch(g0);
+                pf = g0;
+            }
             for (; g < ng; ++g) {
-                const int nr0 = nr, U0 = U;
-                const int hl = __shfl_sync(kFull, gq, g);
-                int gc[kMaxAxes];
+                int clo[kNbrRounds], chi[kNbrRounds];
 #pragma unroll
-                for (int ax = 0; ax < kMaxAxes; ++ax) gc[ax] = __shfl_sync(kFull, cc[ax], hl);
-                const int x0 = max(gc[0] - m, 0), x1 = min(gc[0] + m, dims0 - 1);
+                for (int rr = 0; rr < kNbrRounds; ++rr) {
+                    clo[rr] = nlo[rr];
+                    chi[rr] = nhi[rr];
+                }
+                if (g + 1 < ng) {
+                    fetch(g + 1);
+                    pf = g + 1;
+                }
+                const int nr0 = nr, U0 = U;
 #pragma unroll
                 for (int rr = 0; rr < kNbrRounds; ++rr) {
                     if (rr * 32 >= nrows) break;
-                    const int l = rr * 32 + lane;
-                    int lo = 0, n = 0;
-                    if (l < nrows) {
-                        bool ok = true;
-                        int rowlin = 0;
-#pragma unroll
-                        for (int ax = 1; ax < kMaxAxes; ++ax) {
-                            if (ax < naxes) {
-                                const int v = gc[ax] + (int)((dig[rr] >> (3 * (ax - 1))) & 7u) - m;
-                                ok = ok && (unsigned)v < (unsigned)dims[ax];
-                                rowlin += v * rstride[ax];
-                            }
-                        }
-                        if (ok) {
-                            const int64_t base = cell_off + (int64_t)rowlin * dims0;
-                            lo = a.cstart[base + x0];
-                            n = a.cstart[base + x1 + 1] - lo;
-                        }
-                    }
+                    const int lo = clo[rr];
+                    const int n = chi[rr] - lo;
                     const unsigned bal = __ballot_sync(kFull, n > 0);
                     int incl = n;
 #pragma unroll
@@ -342,92 +383,142 @@ __global__ void __launch_bounds__(kQueryWarps * 32, QCfg<D>::MINB) k_grid_query(
             if (lane == 0) w.rpre[nr] = U;
             __syncwarp();
 
-            const int ntiles = (U + T - 1) / T;
-            int cur = 0;
-            const int pre = min(NB, ntiles);
-            for (int tt = 0; tt < pre; ++tt) issue_tile<D>(w, tt, tt, U, nr, cur, a.rpts, lane);
-            __syncwarp();   // slots written by the issuing lanes, before any lane reads them
-            int tt = 0;
-            for (; tt < ntiles; ++tt) {
-                const int b = tt % NB;
-                // warp-uniform verdict: every lane takes the timeout path if one does
-                if (!__all_sync(kFull, mbar_wait_bounded(&w.bars[b], (phase >> b) & 1u))) {
-                    timed_out = true;
-                    break;
-                }
-                phase ^= 1u << b;
-                const int T0 = tt * T;
-                const int len = min(T, U - T0);
-                const float* tile = w.ring + (size_t)b * T * DP;
-                const int32_t* tsl = w.tslot + b * T;
-#pragma unroll 1
-                for (int k0 = 0; k0 < len; k0 += 32) {
-                    const int ul = k0 + lane;
-                    const bool valid = ul < len;
-                    const int u = T0 + ul;
-                    // group of the candidate: last batch group starting at or before u
-                    int j = 0;
+            // one round: candidate u = k0 + lane of the stream (coordinates cv,
+            // slot) against every query of its group, exact contract
+            auto eval_round = [&](int u, bool valid, const float (&cv)[DP], int slot) {
+                // group of the candidate: last batch group starting at or before u
+                int j = 0;
 #pragma unroll
-                    for (int st = 8; st > 0; st >>= 1) {
-                        const int v = __shfl_sync(kFull, gsb, j + st);
-                        if (v <= u) j += st;
-                    }
-                    const int qa = __shfl_sync(kFull, gqb, j);
-                    const int qe = __shfl_sync(kFull, gqb, j + 1);
-                    const int nq = valid ? qe - qa : 0;
-                    const int mx = __reduce_max_sync(kFull, (unsigned)nq);
-                    float cv[DP];
-                    const float4* cp = reinterpret_cast<const float4*>(tile + (size_t)(valid ? ul : 0) * DP);
+                for (int st = 8; st > 0; st >>= 1) {
+                    const int v = __shfl_sync(kFull, gsb, j + st);
+                    if (v <= u) j += st;
+                }
+                const int qa = __shfl_sync(kFull, gqb, j);
+                const int qe = __shfl_sync(kFull, gqb, j + 1);
+                const int nq = valid ? qe - qa : 0;
+                const int mx = __reduce_max_sync(kFull, (unsigned)nq);
+                for (int jq = 0; jq < mx; ++jq) {
+                    const bool on = jq < nq;
+                    const int q = on ? qa + jq : 0;
+                    const float4* qp4 = reinterpret_cast<const float4*>(w.Q + q * DP);
+                    float qv[DP];
 #pragma unroll
                     for (int k4 = 0; k4 < DP / 4; ++k4) {
-                        const float4 v = cp[k4];
-                        cv[4 * k4] = v.x;
-                        cv[4 * k4 + 1] = v.y;
-                        cv[4 * k4 + 2] = v.z;
-                        cv[4 * k4 + 3] = v.w;
+                        const float4 v = qp4[k4];
+                        qv[4 * k4] = v.x;
+                        qv[4 * k4 + 1] = v.y;
+                        qv[4 * k4 + 2] = v.z;
+                        qv[4 * k4 + 3] = v.w;
                     }
-                    const int slot = valid ? tsl[ul] : -1;
-                    for (int jq = 0; jq < mx; ++jq) {
-                        const bool on = jq < nq;
-                        const int q = on ? qa + jq : 0;
-                        const float4* qp = reinterpret_cast<const float4*>(w.Q + q * DP);
-                        float s = 0.f;
+                    // the whole contract for every candidate: a warp vote after
+                    // the first dimensions (exact early rejection) was measured
+                    // slower on grids of three, four and five axes alike, since a
+                    // round of 32 candidates usually holds a neighbour of the query
+                    float s = 0.f;
+#pragma unroll
+                    for (int k = 0; k < D; ++k) {
+                        const float d = __fsub_rn(qv[k], cv[k]);
+                        s = __fadd_rn(s, __fmul_rn(d, d));
+                    }
+                    const bool acc = on && s <= r2 && !(a.self && slot == s0 + q);
+                    if (acc) {
+                        const int p = atomicAdd(&w.cnt[q], 1);
+                        if (p < kListCap) {
+                            w.Ld[q * kListStr + p] = s;
+                            w.Li[q * kListStr + p] = slot;
+                        }
+                    }
+                }
+            };
+
+            if constexpr (STAGE == kStageLoads) {
+                // candidate u: its range by binary search over the stream
+                // positions, its row loaded from global memory
+                auto load_cand = [&](int u, int& slot, float (&cv)[DP]) {
+                    slot = -1;
+#pragma unroll
+                    for (int k = 0; k < DP; ++k) cv[k] = 0.f;
+                    if (u < U) {
+                        int i = 0;
+#pragma unroll
+                        for (int st = kRangeCap / 2; st > 0; st >>= 1)
+                            if (i + st < nr && w.rpre[i + st] <= u) i += st;
+                        slot = w.rlo[i] + (u - w.rpre[i]);
+                        const float4* p = reinterpret_cast<const float4*>(a.rpts + (int64_t)slot * DP);
 #pragma unroll
                         for (int k4 = 0; k4 < DP / 4; ++k4) {
-                            const float4 v = qp[k4];
-                            const float qv[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-                            for (int i = 0; i < 4; ++i) {
-                                if (4 * k4 + i < D) {
-                                    const float d = __fsub_rn(qv[i], cv[4 * k4 + i]);
-                                    s = __fadd_rn(s, __fmul_rn(d, d));
-                                }
-                            }
-                        }
-                        const bool acc = on && s <= r2 && !(a.self && slot == s0 + q);
-                        if (acc) {
-                            const int p = atomicAdd(&w.cnt[q], 1);
-                            if (p < kListCap) {
-                                w.Ld[q * kListStr + p] = s;
-                                w.Li[q * kListStr + p] = slot;
-                            }
+                            const float4 v = __ldg(p + k4);
+                            cv[4 * k4] = v.x;
+                            cv[4 * k4 + 1] = v.y;
+                            cv[4 * k4 + 2] = v.z;
+                            cv[4 * k4 + 3] = v.w;
                         }
                     }
+                };
+                int slot;
+                float cv[DP];
+                load_cand(lane, slot, cv);
+#pragma unroll 1
+                for (int k0 = 0; k0 < U; k0 += 32) {
+                    int slot_n;
+                    float cvn[DP];
+                    load_cand(k0 + 32 + lane, slot_n, cvn);   // next round in flight
+                    eval_round(k0 + lane, k0 + lane < U, cv, slot);
+                    slot = slot_n;
+#pragma unroll
+                    for (int k = 0; k < DP; ++k) cv[k] = cvn[k];
                 }
-                __syncwarp();
-                if (tt + NB < ntiles) issue_tile<D>(w, tt + NB, b, U, nr, cur, a.rpts, lane);
-            }
-            if (timed_out) {
-                // record, wait (bounded) for the copies still in flight, stop this warp
-                if (lane == 0) atomicOr(a.status, kStatusTimeout);
-                const int issued = min(ntiles, tt + NB);
-                for (int t2 = tt; t2 < issued; ++t2) {
-                    const int b2 = t2 % NB;
-                    mbar_wait_bounded(&w.bars[b2], (phase >> b2) & 1u);
-                    phase ^= 1u << b2;
+            } else {
+                const int ntiles = (U + T - 1) / T;
+                int cur = 0;
+                const int pre = min(NB, ntiles);
+                for (int tt = 0; tt < pre; ++tt) issue_tile<D, STAGE>(w, tt, tt, U, nr, cur, a.rpts, lane);
+                __syncwarp();   // slots written by the issuing lanes, before any lane reads them
+                int tt = 0;
+                for (; tt < ntiles; ++tt) {
+                    const int b = tt % NB;
+                    // warp-uniform verdict: every lane takes the timeout path if one does
+                    if (!__all_sync(kFull, mbar_wait_bounded(&w.bars[b], (phase >> b) & 1u))) {
+                        timed_out = true;
+                        break;
+                    }
+                    phase ^= 1u << b;
+                    const int T0 = tt * T;
+                    const int len = min(T, U - T0);
+                    const float* tile = w.ring + (size_t)b * T * DP;
+                    const int32_t* tsl = w.tslot + b * T;
+#pragma unroll 1
+                    for (int k0 = 0; k0 < len; k0 += 32) {
+                        const int ul = k0 + lane;
+                        const bool valid = ul < len;
+                        float cv[DP];
+                        const float4* cp = reinterpret_cast<const float4*>(tile + (size_t)(valid ? ul : 0) * DP);
+#pragma unroll
+                        for (int k4 = 0; k4 < DP / 4; ++k4) {
+                            const float4 v = cp[k4];
+                            cv[4 * k4] = v.x;
+                            cv[4 * k4 + 1] = v.y;
+                            cv[4 * k4 + 2] = v.z;
+                            cv[4 * k4 + 3] = v.w;
+                        }
+                        eval_round(T0 + ul, valid, cv, valid ? tsl[ul] : -1);
+                    }
+                    __syncwarp();
+                    if (tt + NB < ntiles) issue_tile<D, STAGE>(w, tt + NB, b, U, nr, cur, a.rpts, lane);
                 }
-                return;
+                if (timed_out) {
+                    // record, wait (bounded) for the copies still in flight, stop this warp
+                    if (lane == 0) atomicOr(a.status, kStatusTimeout);
+                    const int issued = min(ntiles, tt + NB);
+                    for (int t2 = tt; t2 < issued; ++t2) {
+                        const int b2 = t2 % NB;
+                        mbar_wait_bounded(&w.bars[b2], (phase >> b2) & 1u);
+                        phase ^= 1u << b2;
+                    }
+                    return;
+                }
             }
+            __syncwarp();   // the batch's ranges are rewritten by the next batch
             g0 = gend;
         }
         __syncwarp();
@@ -702,16 +793,16 @@ __global__ void __launch_bounds__(kOvfWarps * 32) k_overflow(QueryArgs a, int ca
 
 // ------------------------------------------------------------- host launch
 
-template <int D>
-static cudaError_t launch_grid_query_d(const QueryArgs& a, int num_sms, cudaStream_t st) {
-    using C = QCfg<D>;
+template <int D, int STAGE>
+static cudaError_t launch_grid_query_ds(const QueryArgs& a, int num_sms, cudaStream_t st) {
+    using C = QCfg<D, STAGE>;
     static_assert(C::TILE % 32 == 0, "whole lane rounds per tile");
     static_assert(C::NB <= 4, "phase bits and barriers per warp");
-    static_assert(warp_smem_bytes<D>() % 128 == 0 && (C::TILE * C::DP * sizeof(float)) % 16 == 0 &&
-                      (C::DP * sizeof(float)) % 16 == 0,
+    static_assert(warp_smem_bytes<D, STAGE>() % 128 == 0 &&
+                      (C::TILE * C::DP * sizeof(float)) % 16 == 0 && (C::DP * sizeof(float)) % 16 == 0,
                   "bulk-copy destinations and sizes must be 16-byte multiples");
-    const size_t smem = (size_t)kQueryWarps * warp_smem_bytes<D>();
-    auto kern = &k_grid_query<D>;
+    const size_t smem = (size_t)kQueryWarps * warp_smem_bytes<D, STAGE>();
+    auto kern = &k_grid_query<D, STAGE>;
     cudaError_t ce = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                           (int)smem);
     if (ce != cudaSuccess) return ce;
@@ -721,9 +812,16 @@ static cudaError_t launch_grid_query_d(const QueryArgs& a, int num_sms, cudaStre
     per_sm = std::max(per_sm, 1);
     const int64_t warps = (int64_t)num_sms * per_sm * kQueryWarps;
     const int64_t blocks = std::max<int64_t>(
-        1, std::min<int64_t>((int64_t)num_sms * per_sm, ceil_div(std::min<int64_t>(a.nchunks, warps), kQueryWarps)));
+        1, std::min<int64_t>((int64_t)num_sms * per_sm,
+                             ceil_div(std::min<int64_t>(a.nchunks, warps), kQueryWarps)));
     launch_pdl(kern, dim3((unsigned)blocks), dim3(kQueryWarps * 32), smem, st, a);
     return cudaGetLastError();
+}
+
+template <int D>
+static cudaError_t launch_grid_query_d(const QueryArgs& a, int stage, int num_sms, cudaStream_t st) {
+    return stage == kStageBulk ? launch_grid_query_ds<D, kStageBulk>(a, num_sms, st)
+                               : launch_grid_query_ds<D, kStageLoads>(a, num_sms, st);
 }
 
 static QueryArgs query_args(const QueryLaunch& q) {
@@ -777,7 +875,7 @@ frnn_status enqueue_grid_query(const QueryLaunch& q, cudaStream_t st, std::strin
     cudaError_t ce = cudaSuccess;
     if (qs.nchunks > 0) {
         switch (rs.D) {
-#define FRNN_CASE(d) case d: ce = launch_grid_query_d<d>(a, q.num_sms, st); break;
+#define FRNN_CASE(d) case d: ce = launch_grid_query_d<d>(a, q.stage, q.num_sms, st); break;
             FRNN_CASE(1) FRNN_CASE(2) FRNN_CASE(3) FRNN_CASE(4) FRNN_CASE(5) FRNN_CASE(6)
             FRNN_CASE(7) FRNN_CASE(8) FRNN_CASE(9) FRNN_CASE(10) FRNN_CASE(11) FRNN_CASE(12)
             FRNN_CASE(13) FRNN_CASE(14) FRNN_CASE(15) FRNN_CASE(16)

@@ -47,6 +47,7 @@ FRNN_ERR_CAPACITY = -8
 FRNN_ERR_TIMEOUT = -7
 FRNN_ERR_INVALID_ARG = -1
 FRNN_OPT_GRID_NAXES = 10
+FRNN_OPT_STAGING = 11
 
 EXPORTED = ["frnn_version", "frnn_create", "frnn_destroy", "frnn_build_grid",
             "frnn_grid_destroy", "frnn_query", "frnn_query_batched", "frnn_self_query_host",
@@ -58,7 +59,7 @@ EXPORTED = ["frnn_version", "frnn_create", "frnn_destroy", "frnn_build_grid",
 
 class frnn_tune_result(ctypes.Structure):
     _fields_ = [("path", ctypes.c_int), ("cell_mult", ctypes.c_int), ("exit_dims", ctypes.c_int),
-                ("ms", ctypes.c_float), ("grid_axes", ctypes.c_int)]
+                ("ms", ctypes.c_float), ("grid_axes", ctypes.c_int), ("staging", ctypes.c_int)]
 
 
 class frnn_request(ctypes.Structure):
@@ -345,7 +346,7 @@ class Context:
         _check(self.handle, rc)
         return {"path": {FRNN_PATH_GRID: "grid", FRNN_PATH_TC: "tc"}.get(res.path, res.path),
                 "cell_mult": res.cell_mult, "exit_dims": res.exit_dims, "ms": res.ms,
-                "grid_axes": res.grid_axes}
+                "grid_axes": res.grid_axes, "staging": res.staging}
 
     def serve(self, events, arrivals, r: float, K: int, budget_bytes: int = 0, slots: int = 4,
               max_batch: int = 16, outs=None):

@@ -240,6 +240,37 @@ def test_gridded_axis_counts_do_not_change_results(ctx, naxes, m, axes):
         ctx.set_option(frnn.FRNN_OPT_GRID_AXES, 0)
 
 
+@pytest.mark.parametrize("staging", [1, 2])
+@pytest.mark.parametrize("D,naxes", [(8, 3), (8, 4), (8, 5), (12, 5), (3, 3)])
+def test_staging_modes_match_oracle(ctx, staging, D, naxes):
+    # candidate rows loaded by the lanes (1) or bulk-copied into shared memory (2)
+    from paper_2609_31980_gb300 import frnn
+    pts = synth.clustered(500, 25, 4000, D, 0.025, seed=340 + D)
+    r = 0.1 * np.sqrt(D / 8.0)
+    ctx.set_option(frnn.FRNN_OPT_STAGING, staging)
+    ctx.set_option(frnn.FRNN_OPT_GRID_NAXES, naxes)
+    try:
+        _assert_rows_equal(_gpu_self(ctx, pts, r, 48), oracle.self_query(pts, r, 48))
+    finally:
+        ctx.set_option(frnn.FRNN_OPT_STAGING, 0)
+        ctx.set_option(frnn.FRNN_OPT_GRID_NAXES, 0)
+
+
+@pytest.mark.parametrize("which", ["config2", "config3"])
+def test_staging_modes_equal_at_full_size(ctx, which):
+    # the full 300k x 8 and 500k x 12 events: bulk-copy staging equals the
+    # default staging bit for bit on every row (the default is compared with
+    # the oracle on every row by the tests above)
+    from paper_2609_31980_gb300 import frnn
+    w = getattr(synth, which)()
+    ref = _gpu_self(ctx, w.points, w.r, w.K)
+    ctx.set_option(frnn.FRNN_OPT_STAGING, 2)
+    try:
+        _assert_rows_equal(_gpu_self(ctx, w.points, w.r, w.K), ref)
+    finally:
+        ctx.set_option(frnn.FRNN_OPT_STAGING, 0)
+
+
 def test_five_axes_dense_cells_many_ranges(ctx):
     # every cell of a 4^5 block holds several points: each group of a query
     # chunk has 81 non-empty neighbour rows, so a chunk's groups are served in
