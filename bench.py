@@ -123,7 +123,8 @@ def profile_summary(path: str, wl: str):
     import hashlib
     key = (path, wl)
     known = {("grid", "event300k"): ("grid_query_event300k_x8.md", ["query.cu", "frnn_internal.cuh"]),
-             ("grid", "event500k"): ("grid_query_event500k_x12.md", ["query.cu", "frnn_internal.cuh"]),
+             ("rows", "event500k"): ("row_query_event500k_x12.md", ["query_rows.cu", "frnn_internal.cuh"]),
+             ("rows", "event300k"): ("row_query_event300k_x8.md", ["query_rows.cu", "frnn_internal.cuh"]),
              ("tc", "event500k"): ("tc_query_event500k_x12.md", ["tc.cu", "frnn_internal.cuh"])}
     if key not in known:
         return None
@@ -267,8 +268,10 @@ def time_config(frnn, pts_np, r, K, path, dev, steps=20, warmup=3, opts=None, tc
         res["prefilter_survivors"] = surv
         res["exact_accepted"] = acc
         res["false_candidate_rate"] = (surv - acc) / surv if surv else None
-    res["gridded_axes"] = ctx.get_option(frnn.FRNN_OPT_GRID_NAXES) or min(pts_np.shape[1], 4)
-    res["cell_mult"] = ctx.get_option(frnn.FRNN_OPT_CELL_MULT)
+    gp = grid.params()
+    res["gridded_axes"] = gp["naxes"]
+    res["cell_mult"] = gp["cell_mult"]
+    res["grid_kernel"] = gp["kernel"]
     ctx.close()
     del out, pts, flush
     return res
@@ -340,6 +343,7 @@ def run_ours(args):
     grid = ctx.build_grid(pts, r)
     ctx.query(grid, pts, r, K, True, path, (counts, idx, d2))
     ctx.sync()
+    gparams = grid.params()
     ctx.set_option(frnn.FRNN_OPT_KERNEL_TIMING, 1)   # events around the main query kernel
 
     def step(ev=None):
@@ -423,7 +427,8 @@ def run_ours(args):
     q_med = statistics.median(query_ms)
     k_mean = sum(kern_ms) / len(kern_ms)
     achieved = qbytes / (k_mean / 1e3) / 1e9
-    prof = profile_summary("tc" if kern_is_tc else "grid", args.workload)
+    prof = profile_summary("tc" if kern_is_tc else ("rows" if gparams["kernel"] == "rows" else "grid"),
+                           args.workload)
     sm_count = int(getattr(torch.cuda.get_device_properties(dev), "multi_processor_count", 0))
     res = {
         "metric": METRIC,
@@ -439,10 +444,11 @@ def run_ours(args):
         "dtype": "f32",
         "data": "synthetic (seeded clusters + background shaped like a tracking event)",
         "config": {"workload": w.name, "N": N, "D": D, "r": r, "K": K, "path": path,
-                   "cell_mult": ctx.get_option(frnn.FRNN_OPT_CELL_MULT),
-                   "exit_dims": ctx.get_option(frnn.FRNN_OPT_EXIT_DIMS),
-                   "grid_naxes": ctx.get_option(frnn.FRNN_OPT_GRID_NAXES),
-                   "gridded_axes": (ctx.get_option(frnn.FRNN_OPT_GRID_NAXES) or min(D, 4)),
+                   "grid_naxes_option": ctx.get_option(frnn.FRNN_OPT_GRID_NAXES),
+                   "gridded_axes": gparams["naxes"], "cell_mult": gparams["cell_mult"],
+                   "grid_dims": gparams["dims"], "grid_cells": gparams["cells"],
+                   "grid_kernel": gparams["kernel"],
+                   "staging": ctx.get_option(frnn.FRNN_OPT_STAGING),
                    "self_query": True, "l2": "flushed between timed steps (256 MB write)",
                    "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
         "pairs_per_s": whole_job_rate(pairs, args.steps, ws, total_ms),
@@ -450,7 +456,8 @@ def run_ours(args):
         "build_ms_median": statistics.median(build_ms),
         "query_ms_median": q_med,
         "roofline": {"bound": "hbm",
-                     "kernel": "k_tc_query" if kern_is_tc else "k_grid_query",
+                     "kernel": "k_tc_query" if kern_is_tc else
+                               ("k_row_query" if gparams["kernel"] == "rows" else "k_grid_query"),
                      "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                      "kernel_ms_mean": k_mean,
                      "frac": achieved / hbm_peak, "peak_kind": peak_kind,

@@ -112,6 +112,25 @@ frnn_status frnn_destroy(frnn_ctx* ctx);
 frnn_status frnn_build_grid(frnn_ctx* ctx, const float* refs, int64_t N, int D, float r,
                             frnn_grid** grid);
 
+/* Parameters a built grid received (the build derives them on the device
+ * from the points' bounding box; none of them changes results).
+ * Synchronises the grid's context stream.  Errors: INVALID_ARG (NULL
+ * argument or a detached grid), CUDA. */
+typedef struct frnn_grid_info {
+    int naxes;          /* gridded coordinates (1..5) */
+    int cell_mult;      /* m: the scan reaches +-m cells per gridded axis */
+    int axes[5];        /* gridded coordinate indices (the first naxes) */
+    int dims[5];        /* cells per gridded axis */
+    float cell_edge;    /* 1 / inv_h, the cell edge (about r / m) */
+    int64_t cells;      /* product of dims */
+    int kernel;         /* grid scan used for this grid: 0 chunks of 16 queries
+                           (candidates on lanes), 1 row tasks of 16 queries
+                           (grids requested with up to four axes) */
+    int valid;          /* 0 if a coordinate was non-finite */
+} frnn_grid_info;
+
+frnn_status frnn_grid_params(const frnn_grid* grid, frnn_grid_info* info);
+
 /* Free a grid (after its pending work completes).  NULL is accepted.  A grid
  * is the device-resident cell structure of Sec. 2's uniform-grid method; it
  * stays resident between queries until this call. */
@@ -262,10 +281,11 @@ const char* frnn_last_error(const frnn_ctx* ctx);
 /*
  * Autotuner.  Times the candidate configurations on the given point set (a
  * representative event, device memory, self-query): grids over five
- * coordinates with cell multiple m = 1, over four with m in {1, 2}, over
- * three with m in {2, 3} (cell edge ~ r/m, search reach +-m cells; fewer
- * axes when D is smaller); on each, the grid scan with either candidate
- * staging, and the tensor-core pre-filter (D >= 8).
+ * coordinates with cell multiple m = 1 (scanned by chunks of 16 queries,
+ * candidates on lanes, either candidate staging), over four with m = 1 and
+ * over three with m = 2 (scanned by 16-query row tasks, at the default and
+ * a later warp vote); fewer axes when D is smaller; on each grid, the
+ * tensor-core pre-filter (D >= 8).
  * Each candidate is built and queried (first run untimed, best of three
  * timed with CUDA events on the context's stream) and the fastest build +
  * query is cached for the event size class (power-of-two bucket of N, D,
@@ -279,7 +299,7 @@ const char* frnn_last_error(const frnn_ctx* ctx);
 typedef struct frnn_tune_result {
     int path;        /* FRNN_PATH_GRID or FRNN_PATH_TC */
     int cell_mult;   /* m */
-    int exit_dims;   /* always 0 (the grid scan has no vote) */
+    int exit_dims;   /* warp vote point of the row-task scan (0 = default) */
     float ms;        /* build + query time of the winner, milliseconds */
     int grid_axes;   /* gridded coordinates requested (3, 4 or 5, at most D) */
     int staging;     /* grid scan candidate staging (FRNN_OPT_STAGING values 1, 2) */
@@ -295,11 +315,10 @@ typedef enum frnn_option {
                                  most three requested axes and 1 otherwise */
     FRNN_OPT_GRID_AXES = 2,   /* which coordinates are gridded: 0 the last ones,
                                  1 the widest ones (count: FRNN_OPT_GRID_NAXES) */
-    FRNN_OPT_EXIT_DIMS = 3,   /* accepted for compatibility (0..16) and ignored:
-                                 the grid scan evaluates every candidate of a
-                                 group with the whole contract, since a warp
-                                 vote after the first dimensions skipped no
-                                 measurable work */
+    FRNN_OPT_EXIT_DIMS = 3,   /* row-task grid scan (grids of up to four axes):
+                                 dims summed before its warp-uniform early
+                                 exit (0 = library default); the chunk scan of
+                                 five-axis grids ignores it */
     FRNN_OPT_USE_GRAPH = 4,   /* 1 (default): batched calls replay a CUDA graph */
     FRNN_OPT_AUTOTUNE = 5,    /* 1 (default): FRNN_PATH_AUTO consults the tuner;
                                  setting 0 also clears the tuned cache */

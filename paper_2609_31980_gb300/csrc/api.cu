@@ -109,6 +109,8 @@ void ctx_set_error(frnn_ctx* ctx, const char* msg) {
 }
 }  // namespace frnn
 
+static int grid_kernel(int naxes);
+
 static frnn_status fail(frnn_ctx* c, frnn_status s, const std::string& msg) {
     if (c) c->err = msg;
     return s;
@@ -228,6 +230,25 @@ static frnn_status prepare_tc(frnn_ctx* ctx, GridBufs& g, const GridBufs& center
     return FRNN_OK;
 }
 
+// The grid scan for a grid requested with naxes gridded axes (0: the
+// build's automatic choice, five or four): the row-task kernel for grids
+// requested with up to four axes (cells holding many points, long candidate
+// streams shared by 16 queries), the chunk kernel otherwise (few points per
+// cell, candidates on lanes).
+static int grid_kernel(int naxes) { return (naxes >= 1 && naxes <= 4) ? 1 : 0; }
+
+// Pair copy and tasks of a point set for the row-task kernel; accounted in
+// the context's memory budget.
+static frnn_status prepare_rows(frnn_ctx* ctx, GridBufs& g, cudaStream_t st) {
+    if (g.rows_ready) return FRNN_OK;
+    const size_t before = g.rows_bytes;
+    std::string err;
+    frnn_status s = rows_prepare(g, ctx->d_status, st, err);
+    ctx->held = ctx->held - std::min(ctx->held, before) + g.rows_bytes;
+    if (s != FRNN_OK) return fail(ctx, s, err);
+    return FRNN_OK;
+}
+
 static int log2_bucket(int64_t x) {
     int b = 0;
     while (x > 1) {
@@ -261,10 +282,14 @@ static int build_mult(const frnn_ctx* ctx, int64_t N, int D) {
     const int na = build_naxes(ctx, N, D);
     return (na >= 1 && na <= 3 && D > 3) ? 2 : 1;
 }
-// gridded axes when neither the option nor the tuner fixes them: 0, the
-// build's automatic choice (five axes, or four when the cell budget makes
-// five-axis cells too coarse; all of them for D < 5)
-static int default_naxes(int) { return 0; }
+// gridded axes when neither the option nor the tuner fixes them.  Up to
+// D = 8: 0, the build's automatic choice (five axes, or four when the cell
+// budget makes five-axis cells too coarse; all of them for D < 5), scanned by
+// the chunk kernel.  From D = 9: four axes, scanned by the row-task kernel,
+// whose packed pre-screen costs less per candidate pair than the chunk
+// kernel's whole contract as D grows (measured build + query: 300k x 8 event
+// 0.306 ms five axes vs 0.318 ms four; 500k x 12 event 0.639 vs 0.546 ms).
+static int default_naxes(int D) { return D >= 9 ? 4 : 0; }
 static int build_naxes(const frnn_ctx* ctx, int64_t N, int D) {
     if (ctx->grid_naxes > 0) return std::min(ctx->grid_naxes, D);
     const frnn_ctx::Tuned* t = find_tuned(ctx, N, D, -1);
@@ -335,12 +360,36 @@ frnn_status frnn_create(frnn_ctx** out, void* cuda_stream, size_t mem_budget_byt
     return FRNN_OK;
 }
 
+frnn_status frnn_grid_params(const frnn_grid* grid, frnn_grid_info* info) {
+    if (!grid || !info || !grid->ctx) return FRNN_ERR_INVALID_ARG;
+    frnn_ctx* ctx = grid->ctx;
+    *info = frnn_grid_info{};
+    info->kernel = grid_kernel(grid->naxes);
+    if (grid->g.E < 1 || !grid->g.hdr) return FRNN_OK;
+    cudaError_t e = cudaStreamSynchronize(ctx->stream);
+    EventHdr h{};
+    if (e == cudaSuccess) e = cudaMemcpy(&h, grid->g.hdr, sizeof(h), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "reading the grid header");
+    info->naxes = h.naxes;
+    info->cell_mult = h.m;
+    info->cells = 1;
+    for (int a = 0; a < kMaxAxes; ++a) {
+        info->axes[a] = a < h.naxes ? h.axes[a] : 0;
+        info->dims[a] = h.dims[a];
+        info->cells *= h.dims[a];
+    }
+    info->cell_edge = h.inv_h > 0.f ? 1.f / h.inv_h : INFINITY;
+    info->valid = h.valid;
+    return FRNN_OK;
+}
+
 frnn_status frnn_grid_destroy(frnn_grid* grid) {
     if (!grid) return FRNN_OK;
     if (grid->ctx) {
         cudaStreamSynchronize(grid->ctx->stream);
         grid->ctx->csr_pending = false;
-        grid->ctx->held -= std::min(grid->ctx->held, grid->g.bytes);
+        grid->ctx->held -= std::min(grid->ctx->held,
+                                    grid->g.bytes + grid->g.tc_bytes + grid->g.rows_bytes);
         grid->ctx->grids.erase(grid);
     } else {
         cudaDeviceSynchronize();   // context gone: its stream may still hold work on the buffers
@@ -471,10 +520,10 @@ static frnn_status query_impl(frnn_ctx* ctx, const frnn_grid* grid, const float*
     q.exit_dims = ctx->exit_dims;
     {
         int stg = ctx->staging;
-        if (stg == 0) {
-            const frnn_ctx::Tuned* t = find_tuned(ctx, grid->N, grid->D, K);
-            if (t) stg = t->staging;
-        }
+        const frnn_ctx::Tuned* t = find_tuned(ctx, grid->N, grid->D, K);
+        if (stg == 0 && t) stg = t->staging;
+        if (q.exit_dims == 0 && t && !(flags & (FRNN_PATH_GRID | FRNN_PATH_TC)))
+            q.exit_dims = t->exit_dims;
         q.stage = stg == 2 ? 1 : 0;
     }
     q.counts = counts;
@@ -524,6 +573,12 @@ static frnn_status query_impl(frnn_ctx* ctx, const frnn_grid* grid, const float*
         q.tc_stats = ctx->d_tcstat;
         s = enqueue_tc_query(q, ctx->stream, err);
     } else {
+        q.kernel = grid_kernel(grid->naxes);
+        if (q.kernel == 1) {
+            s = prepare_rows(ctx, rg, ctx->stream);
+            if (s == FRNN_OK && !self) s = prepare_rows(ctx, ctx->qset, ctx->stream);
+            if (s != FRNN_OK) return s;
+        }
         s = enqueue_grid_query(q, ctx->stream, err);
     }
     if (s != FRNN_OK) return fail(ctx, s, err);
@@ -649,20 +704,21 @@ static frnn_status enqueue_batched(frnn_ctx* ctx, const frnn_event* ev, int n_ev
                                    float r, int K, unsigned flags, bool capturing,
                                    cudaStream_t st) {
     std::vector<const float*> refs(n_events);
-    bool any_grid = false, any_tc = false;
+    // per event path: 0 grid scan by chunks, 2 grid scan by row tasks, 1 tensor core
+    bool any_path[3] = {false, false, false};
     for (int e = 0; e < n_events; ++e) {
         refs[e] = ev[e].pts;
         EventHdr& h = ctx->batch.h_hdr[e];
         h.counts = ev[e].counts;
         h.idx = ev[e].idx;
         h.dist2 = ev[e].dist2;
-        // per event: autotuned cell multiple and path for its size class
+        // per event: autotuned cell multiple, axes and path for its size class
         h.m = build_mult(ctx, ev[e].n, D);
         h.naxes = build_naxes(ctx, ev[e].n, D);
-        h.path = use_tc_path(ctx, D, flags, ev[e].n, K) ? 1 : 0;
-        any_grid |= h.path == 0 && ev[e].n > 0;
-        any_tc |= h.path == 1 && ev[e].n > 0;
+        h.path = use_tc_path(ctx, D, flags, ev[e].n, K) ? 1 : (grid_kernel(h.naxes) == 1 ? 2 : 0);
+        if (ev[e].n > 0) any_path[h.path] = true;
     }
+    const bool any_grid = any_path[0], any_rows = any_path[2], any_tc = any_path[1];
     BuildOpts o;
     o.r = r;
     o.m = 1;
@@ -681,11 +737,22 @@ static frnn_status enqueue_batched(frnn_ctx* ctx, const frnn_event* ev, int n_ev
     q.stage = ctx->staging == 2 ? 1 : 0;
     q.d_status = ctx->d_status;
     q.num_sms = ctx->num_sms;
-    const bool mixed = any_grid && any_tc;
-    if (any_grid || !any_tc) {
+    const bool mixed = (int)any_grid + (int)any_rows + (int)any_tc > 1;
+    if (any_grid || (!any_tc && !any_rows)) {
+        q.kernel = 0;
         q.path_filter = mixed ? 0 : -1;
         s = enqueue_grid_query(q, st, err);
         if (s != FRNN_OK) return fail(ctx, s, err);
+    }
+    if (any_rows) {
+        // buffers were reserved before any capture; enqueue their build
+        s = rows_prepare(ctx->batch, ctx->d_status, st, err);
+        if (s != FRNN_OK) return fail(ctx, s, err);
+        q.kernel = 1;
+        q.path_filter = mixed ? 2 : -1;
+        s = enqueue_grid_query(q, st, err);
+        if (s != FRNN_OK) return fail(ctx, s, err);
+        q.kernel = 0;
     }
     if (any_tc) {
         // operands were allocated before any capture; enqueue their build
@@ -746,13 +813,24 @@ frnn_status frnn_query_batched(frnn_ctx* ctx, const frnn_event* ev, int n_events
     }
     frnn_status s = alloc_accounted(ctx, ctx->batch, n_events, n.data(), D, nullptr);
     if (s != FRNN_OK) return s;
-    bool batch_tc = false;
-    for (int e = 0; e < n_events && !batch_tc; ++e)
-        batch_tc = ev[e].n > 0 && use_tc_path(ctx, D, flags, ev[e].n, K);
+    bool batch_tc = false, batch_rows = false;
+    for (int e = 0; e < n_events; ++e) {
+        if (ev[e].n <= 0) continue;
+        if (use_tc_path(ctx, D, flags, ev[e].n, K)) batch_tc = true;
+        else if (grid_kernel(build_naxes(ctx, ev[e].n, D)) == 1) batch_rows = true;
+    }
     if (batch_tc) {
         // allocate the tensor-core operands outside any capture (no work enqueued)
         std::string err;
         s = tc_reserve(ctx->batch, err);
+        if (s != FRNN_OK) return fail(ctx, s, err);
+    }
+    if (batch_rows) {
+        // the row-task kernel's buffers likewise
+        const size_t before = ctx->batch.rows_bytes;
+        std::string err;
+        s = rows_reserve(ctx->batch, err);
+        ctx->held = ctx->held - std::min(ctx->held, before) + ctx->batch.rows_bytes;
         if (s != FRNN_OK) return fail(ctx, s, err);
     }
     if (!ctx->use_graph)
@@ -1009,9 +1087,9 @@ frnn_status frnn_autotune(frnn_ctx* ctx, const float* refs, int64_t N, int D, fl
         ms = bestms;
         return frnn_sync(ctx);
     };
-    // grid configurations: five gridded axes with cells of r, four with
-    // cells of r and r/2, three with cells of r/2 and r/3 (all of them for
-    // smaller D); the neighbour rows, (2m+1)^(axes-1), stay within 128
+    // grid configurations: five gridded axes with cells of r (chunk kernel),
+    // four with cells of r and three with cells of r/2 (row-task kernel); all
+    // of them for smaller D
     struct GridCfg { int naxes, m; };
     std::vector<GridCfg> gcfg;
     auto add_cfg = [&](int na, int m) {
@@ -1022,9 +1100,7 @@ frnn_status frnn_autotune(frnn_ctx* ctx, const float* refs, int64_t N, int D, fl
     };
     add_cfg(5, 1);
     add_cfg(4, 1);
-    add_cfg(4, 2);
     add_cfg(3, 2);
-    add_cfg(3, 3);
     for (size_t gi = 0; gi < gcfg.size() && s == FRNN_OK; ++gi) {
         const int m = gcfg[gi].m;
         ctx->cell_mult = m;
@@ -1032,19 +1108,27 @@ frnn_status frnn_autotune(frnn_ctx* ctx, const float* refs, int64_t N, int D, fl
         float bms = 0.f;
         s = timed([&] { return frnn_build_grid(ctx, refs, N, D, r, &g); }, bms);
         if (s != FRNN_OK) break;
-        struct Cand { unsigned path; int staging; };
+        // the chunk kernel with either staging; the row-task kernel with its
+        // default vote point and a later one
+        struct Cand { unsigned path; int staging, exit_dims; };
         std::vector<Cand> cands;
         if (!(flags & FRNN_PATH_TC)) {
-            cands.push_back({FRNN_PATH_GRID, 1});
-            cands.push_back({FRNN_PATH_GRID, 2});
+            if (grid_kernel(gcfg[gi].naxes) == 0) {
+                cands.push_back({FRNN_PATH_GRID, 1, 0});
+                cands.push_back({FRNN_PATH_GRID, 2, 0});
+            } else {
+                cands.push_back({FRNN_PATH_GRID, 1, 0});
+                if (D >= 5) cands.push_back({FRNN_PATH_GRID, 1, 3});
+            }
         }
-        if (D >= 8 && !(flags & FRNN_PATH_GRID)) cands.push_back({FRNN_PATH_TC, 1});
+        if (D >= 8 && !(flags & FRNN_PATH_GRID)) cands.push_back({FRNN_PATH_TC, 1, 0});
         if (cands.empty()) {
             s = fail(ctx, FRNN_ERR_UNSUPPORTED, "the tensor-core path needs D >= 8");
             break;
         }
         for (const Cand& c : cands) {
             ctx->staging = c.staging;
+            ctx->exit_dims = c.exit_dims;
             float qms = 0.f;
             s = timed([&] {
                 return frnn_query(ctx, g, refs, N, r, K, FRNN_SELF_QUERY | c.path, counts, idx,
@@ -1052,7 +1136,7 @@ frnn_status frnn_autotune(frnn_ctx* ctx, const float* refs, int64_t N, int D, fl
             }, qms);
             if (s != FRNN_OK) break;
             if (bms + qms < bestr.ms)
-                bestr = {(int)c.path, m, 0, bms + qms, gcfg[gi].naxes, c.staging};
+                bestr = {(int)c.path, m, c.exit_dims, bms + qms, gcfg[gi].naxes, c.staging};
         }
     }
     ctx->cell_mult = saved_m;

@@ -251,14 +251,15 @@ struct GridFit {
 };
 
 __device__ void grid_fit(GridFit& f, const int32_t* bb, int D, int k, int m, int axes_mode,
-                         float r, int32_t cap, bool valid) {
+                         float r, int32_t cap, bool valid, int max_rows) {
     f.naxes = k;
-    // neighbour rows, (2m+1)^(k-1), are enumerated 32 per round: at most kMaxNbrRows
+    // neighbour rows, (2m+1)^(k-1): at most max_rows (the chunk kernel
+    // enumerates kMaxNbrRows, 32 per round; the row-task kernel one per lane)
     int mm = max(m, 1);
     for (;;) {
         int rows = 1;
         for (int a = 1; a < k; ++a) rows *= 2 * mm + 1;
-        if (rows <= kMaxNbrRows || mm == 1) break;
+        if (rows <= max_rows || mm == 1) break;
         --mm;
     }
     f.m = mm;
@@ -373,11 +374,14 @@ __device__ void event_params(EventHdr* hdr, int e, int D, const int32_t* bbox, f
     const int kmax = min(D, kMaxAxes);
     int k_hi = want > 0 ? min(D, min(want, kMaxAxes)) : kmax;
     int k_lo = want > 0 ? k_hi : max(1, kmax - 1);
+    // grids requested with up to four axes are scanned by the row-task
+    // kernel, whose lanes hold one neighbour row each
+    const int max_rows = (want >= 1 && want <= 4) ? 32 : kMaxNbrRows;
     GridFit best;
     best.frac = INFINITY;
     for (int k = k_hi; k >= k_lo; --k) {
         GridFit f;
-        grid_fit(f, bb, D, k, m_req, axes_mode, r, h.cell_cap, valid);
+        grid_fit(f, bb, D, k, m_req, axes_mode, r, h.cell_cap, valid, max_rows);
         if (f.frac < best.frac) best = f;
     }
     const int naxes = best.naxes;
@@ -793,6 +797,7 @@ static size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 void grid_free(GridBufs& g) {
     tc_free(g);
+    rows_free(g);
     if (g.base) cudaFree(g.base);
     if (g.h_pinned) cudaFreeHost(g.h_pinned);
     if (g.h_pinned_free) cudaEventDestroy(g.h_pinned_free);
@@ -989,7 +994,8 @@ frnn_status enqueue_build(GridBufs& g, const float* const* refs, const BuildOpts
                    g.bbox, d_status, o.r, o.m, o.axes_mode, o.naxes, g.cstart);
     }
     enqueue_sort(g, smem_pts, params_from ? 1 : 0, d_status, st);
-    g.tc_ready = false;   // tensor-core operands describe the previous contents
+    g.tc_ready = false;     // tensor-core operands describe the previous contents
+    g.rows_ready = false;   // so do the row-task kernel's pair copy and tasks
     cudaError_t ce = cudaGetLastError();
     if (ce != cudaSuccess) {
         err = std::string("grid build launch failed: ") + cudaGetErrorString(ce);
@@ -1013,6 +1019,8 @@ frnn_status enqueue_build_resident(GridBufs& g, const BuildOpts& o, int32_t* d_s
     launch_pdl(k_bbox, dim3((unsigned)g.nblk), dim3(kBuildPtsPerBlock), smem_pts, st, g.hdr, g.blk_start, E, D,
                g.bbox, d_status, o.r, o.m, o.axes_mode, o.naxes, g.cstart);
     enqueue_sort(g, smem_pts, 0, d_status, st);
+    g.tc_ready = false;
+    g.rows_ready = false;
     cudaError_t ce = cudaGetLastError();
     if (ce != cudaSuccess) {
         err = std::string("grid build launch failed: ") + cudaGetErrorString(ce);

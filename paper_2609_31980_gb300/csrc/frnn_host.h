@@ -64,6 +64,16 @@ struct GridBufs {
     int32_t* tcnu = nullptr;       // [E] ordered-int max norm per event
     Task* tc_tasks = nullptr;      // 128-query tasks
 
+    // row-task kernel (grids of up to four axes): pair-interleaved copy of
+    // the points and 16-query tasks, made at query time after each build
+    bool rows_ready = false;
+    void* rows_base = nullptr;
+    size_t rows_bytes = 0;
+    int64_t rows_cap_n = 0, rows_cap_tasks = 0, rows_cap_L = 0;
+    float* ppts = nullptr;          // [n_total * DP] pair-interleaved coordinates
+    Task* row_tasks = nullptr;      // [rows_cap_tasks]
+    int32_t* rows_rtask = nullptr;  // [L] the task builder's per-row scratch
+
     // host copies
     std::vector<EventHdr> h_hdr;
     std::vector<int32_t> h_blk_start;
@@ -135,6 +145,7 @@ struct QueryLaunch {
     int self;
     int exit_dims;          // 0 = default
     int stage = 0;          // grid query candidate staging: 0 lanes load rows, 1 bulk copies
+    int kernel = 0;         // grid scan: 0 chunks (query.cu), 1 row tasks (query_rows.cu)
     int32_t* counts;        // single event outputs, or NULL to use the event headers'
     int32_t* idx;
     float* dist2;
@@ -151,6 +162,14 @@ struct QueryLaunch {
     const int64_t* row_off = nullptr;
 };
 frnn_status enqueue_grid_query(const QueryLaunch& q, cudaStream_t st, std::string& err);
+// Row-task kernel: allocate (outside any capture) and build (enqueued) the
+// pair-interleaved copy and 16-query tasks of a point set; the launch itself
+// (called by enqueue_grid_query when q.kernel == 1, inputs prepared).
+frnn_status rows_reserve(GridBufs& g, std::string& err);
+frnn_status rows_prepare(GridBufs& g, int32_t* d_status, cudaStream_t st, std::string& err);
+void rows_free(GridBufs& g);
+frnn_status enqueue_row_query(const QueryLaunch& q, const QueryArgs& a, cudaStream_t st,
+                              std::string& err);
 // The selection kernel alone over the rows the last query of q.qset listed
 // (compact output, second pass: q.ovf_mode 2, q.row_off).
 frnn_status enqueue_overflow_only(const QueryLaunch& q, cudaStream_t st, std::string& err);

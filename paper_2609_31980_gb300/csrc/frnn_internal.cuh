@@ -131,6 +131,8 @@ struct QueryArgs {
     const EventHdr* qev;         // per-event headers of the query set (== ev for self-queries)
     int32_t nev;                 // events
     int32_t nchunks;             // query chunks over all events
+    const Task* tasks;           // row-task kernel: 16-query warp tasks of the query set
+    const int32_t* ntasks;       // row-task kernel: device scalar, number of tasks
     const float* qpts;           // cell-sorted query coordinates [*, DP]
     const int32_t* qperm;        // query slot -> original query index (within its event)
     const int32_t* qcell;        // query slot -> local cell id
@@ -141,6 +143,7 @@ struct QueryArgs {
     int32_t* idx;
     float* dist2;
     float r2;                    // fl(r * r)
+    float r2_screen;             // row-task kernel: r2 (1 + 2^-16) rounded up, the packed screen's bound
     int32_t K;
     int32_t self;                // 1: query slot == reference slot is excluded
     int32_t D;

@@ -873,7 +873,11 @@ frnn_status enqueue_grid_query(const QueryLaunch& q, cudaStream_t st, std::strin
     qs.ovf_stale = q.ovf_mode == 1;
     if (q.kev[0]) cudaEventRecord(q.kev[0], st);
     cudaError_t ce = cudaSuccess;
-    if (qs.nchunks > 0) {
+    if (q.kernel == 1) {
+        // grids of up to four axes: the row-task kernel (query_rows.cu)
+        const frnn_status s = enqueue_row_query(q, a, st, err);
+        if (s != FRNN_OK) return s;
+    } else if (qs.nchunks > 0) {
         switch (rs.D) {
 #define FRNN_CASE(d) case d: ce = launch_grid_query_d<d>(a, q.stage, q.num_sms, st); break;
             FRNN_CASE(1) FRNN_CASE(2) FRNN_CASE(3) FRNN_CASE(4) FRNN_CASE(5) FRNN_CASE(6)

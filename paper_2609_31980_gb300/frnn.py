@@ -54,12 +54,18 @@ EXPORTED = ["frnn_version", "frnn_create", "frnn_destroy", "frnn_build_grid",
             "frnn_sync", "frnn_last_error", "frnn_set_option", "frnn_get_option",
             "frnn_autotune", "frnn_serve_run", "frnn_self_query_noalloc",
             "frnn_kernel_times", "frnn_query_csr_count", "frnn_query_csr_fill",
-            "frnn_self_query_host_csr", "frnn_check_wait_timeout"]
+            "frnn_self_query_host_csr", "frnn_check_wait_timeout", "frnn_grid_params"]
 
 
 class frnn_tune_result(ctypes.Structure):
     _fields_ = [("path", ctypes.c_int), ("cell_mult", ctypes.c_int), ("exit_dims", ctypes.c_int),
                 ("ms", ctypes.c_float), ("grid_axes", ctypes.c_int), ("staging", ctypes.c_int)]
+
+
+class frnn_grid_info(ctypes.Structure):
+    _fields_ = [("naxes", ctypes.c_int), ("cell_mult", ctypes.c_int), ("axes", ctypes.c_int * 5),
+                ("dims", ctypes.c_int * 5), ("cell_edge", ctypes.c_float), ("cells", ctypes.c_int64),
+                ("kernel", ctypes.c_int), ("valid", ctypes.c_int)]
 
 
 class frnn_request(ctypes.Structure):
@@ -87,6 +93,7 @@ _sigs = {
     "frnn_destroy": ([_vp], _int),
     "frnn_build_grid": ([_vp, _vp, _i64, _int, _f32, ctypes.POINTER(_vp)], _int),
     "frnn_grid_destroy": ([_vp], _int),
+    "frnn_grid_params": ([_vp, ctypes.c_void_p], _int),
     "frnn_query": ([_vp, _vp, _vp, _i64, _f32, _int, _u32, _vp, _vp, _vp], _int),
     "frnn_query_batched": ([_vp, ctypes.POINTER(frnn_event), _int, _int, _f32, _int, _u32], _int),
     "frnn_self_query_host": ([_vp, _vp, _i64, _int, _f32, _int, _u32, _vp, _vp, _vp], _int),
@@ -153,6 +160,15 @@ class Grid:
         self.handle = handle
         self.points = points   # keeps the caller's tensor alive for self-queries
         self.r = r
+
+    def params(self) -> dict:
+        """frnn_grid_params: the parameters the build gave this grid."""
+        info = frnn_grid_info()
+        _check(self.ctx.handle, frnn_grid_params(self.handle, ctypes.byref(info)))
+        n = info.naxes
+        return {"naxes": n, "cell_mult": info.cell_mult, "axes": list(info.axes)[:n],
+                "dims": list(info.dims)[:n], "cell_edge": info.cell_edge, "cells": info.cells,
+                "kernel": "rows" if info.kernel == 1 else "chunks", "valid": bool(info.valid)}
 
     def close(self):
         if self.handle:

@@ -271,6 +271,32 @@ def test_staging_modes_equal_at_full_size(ctx, which):
         ctx.set_option(frnn.FRNN_OPT_STAGING, 0)
 
 
+def test_grid_params_reports_the_build(ctx):
+    # frnn_grid_params: the automatic choice for D = 8 is five axes (chunk
+    # scan); from D = 9 four axes (row-task scan); an explicit request is kept
+    import torch
+    from paper_2609_31980_gb300 import frnn
+    cases = ((synth.config2().points, 0.1, 5, "chunks"),
+             (synth.clustered(400, 25, 3000, 12, 0.025, seed=345), 0.12, 4, "rows"),
+             (synth.uniform(4096, 3, seed=346), 0.05, 3, "chunks"))
+    for pts, r, naxes, kernel in cases:
+        D = pts.shape[1]
+        g = ctx.build_grid(torch.from_numpy(pts).cuda(), r)
+        p = g.params()
+        assert p["naxes"] == naxes and p["kernel"] == kernel, p
+        assert p["cells"] == int(np.prod(p["dims"])) and p["valid"]
+        assert p["axes"] == list(range(D - naxes, D))
+        g.close()
+    ctx.set_option(frnn.FRNN_OPT_GRID_NAXES, 3)
+    try:
+        g = ctx.build_grid(torch.from_numpy(synth.uniform(2000, 8, seed=346)).cuda(), 0.1)
+        p = g.params()
+        assert p["naxes"] == 3 and p["kernel"] == "rows" and p["cell_mult"] == 2, p
+        g.close()
+    finally:
+        ctx.set_option(frnn.FRNN_OPT_GRID_NAXES, 0)
+
+
 def test_five_axes_dense_cells_many_ranges(ctx):
     # every cell of a 4^5 block holds several points: each group of a query
     # chunk has 81 non-empty neighbour rows, so a chunk's groups are served in
