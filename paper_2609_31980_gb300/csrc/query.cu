@@ -187,10 +187,13 @@ __global__ void __launch_bounds__(kQueryWarps * 32, QCfg<D, STAGE>::MINB) k_grid
 
     const float r2 = a.r2;
     const int K = a.K;
-    // neighbour-row digit table of the current (naxes, m): digit a-1 of row
-    // 32 rr + lane (offset + m, 3 bits per axis) in dig[rr]
-    int tab_key = -1;
-    uint32_t dig[kNbrRounds];
+    // neighbour-row table of the current event, for row l = 32 rr + lane:
+    // tdelta[rr] = its linear offset from the group's row; tedge[rr] = for
+    // m = 1 the axes whose offset is -1 (bits 0-3) and +1 (bits 8-11), for
+    // larger m the offsets + m (3 bits per axis); bit 31: l is beyond the rows
+    int tab_e = -1;
+    int tdelta[kNbrRounds];
+    uint32_t tedge[kNbrRounds];
 
     for (;;) {
         int c = 0;
@@ -272,26 +275,31 @@ __global__ void __launch_bounds__(kQueryWarps * 32, QCfg<D, STAGE>::MINB) k_grid
         }
         int nrows = 1;
         for (int ax = 1; ax < naxes; ++ax) nrows *= 2 * m + 1;
-        const int key = naxes * 16 + m;
-        if (key != tab_key) {
-            tab_key = key;
-            const int side = 2 * m + 1;
-#pragma unroll
-            for (int rr = 0; rr < kNbrRounds; ++rr) {
-                int l = rr * 32 + lane;
-                uint32_t d = 0;
-                for (int ax = 1; ax < naxes; ++ax) {
-                    d |= (uint32_t)(l % side) << (3 * (ax - 1));
-                    l /= side;
-                }
-                dig[rr] = d;
-            }
-        }
         int rstride[kMaxAxes];
         rstride[0] = 0;
         rstride[1] = 1;
 #pragma unroll
         for (int ax = 2; ax < kMaxAxes; ++ax) rstride[ax] = rstride[ax - 1] * dims[ax - 1];
+        if (e != tab_e) {
+            tab_e = e;
+            const int side = 2 * m + 1;
+#pragma unroll
+            for (int rr = 0; rr < kNbrRounds; ++rr) {
+                const int l = rr * 32 + lane;
+                int ll = l, dl = 0;
+                uint32_t dg = 0, lowm = 0, highm = 0;
+                for (int ax = 1; ax < naxes; ++ax) {
+                    const int d = ll % side;
+                    ll /= side;
+                    dg |= (uint32_t)d << (3 * (ax - 1));
+                    dl += (d - m) * rstride[ax];
+                    if (d < m) lowm |= 1u << (ax - 1);
+                    if (d > m) highm |= 1u << (ax - 1);
+                }
+                tdelta[rr] = dl;
+                tedge[rr] = (m == 1 ? (lowm | (highm << 8)) : dg) | (l >= nrows ? (1u << 31) : 0u);
+            }
+        }
 
         // Row ranges of group g (lane l of round rr: neighbour row 32 rr + l):
         // every round's two cell-start loads are issued together, and the next
@@ -303,24 +311,38 @@ __global__ void __launch_bounds__(kQueryWarps * 32, QCfg<D, STAGE>::MINB) k_grid
 #pragma unroll
             for (int ax = 0; ax < kMaxAxes; ++ax) gc[ax] = __shfl_sync(kFull, cc[ax], hl);
             const int x0 = max(gc[0] - m, 0), x1 = min(gc[0] + m, dims0 - 1);
+            // the group's row and, for m = 1, the axes on which it touches the
+            // grid's low (bits 0-3) or high (bits 8-11) edge
+            int grow = 0;
+            uint32_t gedge = 1u << 31;
+#pragma unroll
+            for (int ax = 1; ax < kMaxAxes; ++ax) {
+                if (ax < naxes) {
+                    grow += gc[ax] * rstride[ax];
+                    if (gc[ax] == 0) gedge |= 1u << (ax - 1);
+                    if (gc[ax] == dims[ax] - 1) gedge |= 1u << (ax + 7);
+                }
+            }
 #pragma unroll
             for (int rr = 0; rr < kNbrRounds; ++rr) {
                 nlo[rr] = 0;
                 nhi[rr] = 0;
-                const int l = rr * 32 + lane;
-                if (l < nrows) {
-                    bool ok = true;
-                    int rowlin = 0;
+                if (rr * 32 < nrows) {
+                    bool ok;
+                    if (m == 1) {
+                        ok = (tedge[rr] & gedge) == 0;   // in range on every axis, row exists
+                    } else {
+                        ok = !(tedge[rr] >> 31);
 #pragma unroll
-                    for (int ax = 1; ax < kMaxAxes; ++ax) {
-                        if (ax < naxes) {
-                            const int v = gc[ax] + (int)((dig[rr] >> (3 * (ax - 1))) & 7u) - m;
-                            ok = ok && (unsigned)v < (unsigned)dims[ax];
-                            rowlin += v * rstride[ax];
+                        for (int ax = 1; ax < kMaxAxes; ++ax) {
+                            if (ax < naxes) {
+                                const int v = gc[ax] + (int)((tedge[rr] >> (3 * (ax - 1))) & 7u) - m;
+                                ok = ok && (unsigned)v < (unsigned)dims[ax];
+                            }
                         }
                     }
                     if (ok) {
-                        const int64_t base = cell_off + (int64_t)rowlin * dims0;
+                        const int64_t base = cell_off + (int64_t)(grow + tdelta[rr]) * dims0;
                         nlo[rr] = __ldg(a.cstart + base + x0);
                         nhi[rr] = __ldg(a.cstart + base + x1 + 1);
                     }
@@ -332,8 +354,8 @@ __global__ void __launch_bounds__(kQueryWarps * 32, QCfg<D, STAGE>::MINB) k_grid
         bool timed_out = false;
         int g0 = 0, pf = -1;   // pf: group whose ranges nlo/nhi hold
         while (g0 < ng && !timed_out) {
-            int nr = 0, U = 0, g = g0;
-            int gsb = INT_MAX;   // lane j: stream start of batch group g0 + j
+            int nr = 0, g = g0;
+            int gr = 0;   // lane j: first compact range of batch group g0 + j
             if (pf != g0) {
                 fetch(g0);
                 pf = g0;
@@ -349,39 +371,48 @@ __global__ void __launch_bounds__(kQueryWarps * 32, QCfg<D, STAGE>::MINB) k_grid
                     fetch(g + 1);
                     pf = g + 1;
                 }
-                const int nr0 = nr, U0 = U;
+                const int nr0 = nr;
 #pragma unroll
                 for (int rr = 0; rr < kNbrRounds; ++rr) {
                     if (rr * 32 >= nrows) break;
                     const int lo = clo[rr];
                     const int n = chi[rr] - lo;
                     const unsigned bal = __ballot_sync(kFull, n > 0);
-                    int incl = n;
-#pragma unroll
-                    for (int o = 1; o < 32; o <<= 1) {
-                        const int v = __shfl_up_sync(kFull, incl, o);
-                        if (lane >= o) incl += v;
-                    }
                     const int pos = nr + __popc(bal & lt_mask);
                     if (n > 0 && pos < kRangeCap) {
                         w.rlo[pos] = lo;
-                        w.rpre[pos] = U + incl - n;
+                        w.rpre[pos] = n;   // a count until the batch's scan
                     }
                     nr += __popc(bal);
-                    U += __shfl_sync(kFull, incl, 31);
                 }
                 if (nr > kRangeCap) {   // group g opens the next batch
                     nr = nr0;
-                    U = U0;
                     break;
                 }
-                if (lane == g - g0) gsb = U0;
+                if (lane == g - g0) gr = nr0;
             }
             const int gend = g;
             // lane j <= gend - g0: first query of batch group j (the end for j = gend - g0)
             const int gqb = __shfl_sync(kFull, gq, min(g0 + lane, 31));
+            // one exclusive scan turns the ranges' counts into stream positions
+            __syncwarp();
+            int U = 0;
+            for (int b0 = 0; b0 < nr; b0 += 32) {
+                const int i = b0 + lane;
+                const int v = i < nr ? w.rpre[i] : 0;
+                int incl = v;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int t = __shfl_up_sync(kFull, incl, o);
+                    if (lane >= o) incl += t;
+                }
+                if (i < nr) w.rpre[i] = U + incl - v;
+                U += __shfl_sync(kFull, incl, 31);
+            }
             if (lane == 0) w.rpre[nr] = U;
             __syncwarp();
+            // lane j: stream start of batch group g0 + j (INT_MAX beyond the batch)
+            const int gsb = lane < gend - g0 ? w.rpre[gr] : INT_MAX;
 
             // one round: candidate u = k0 + lane of the stream (coordinates cv,
             // slot) against every query of its group, exact contract

@@ -3,16 +3,20 @@
 The kernel (query.cu, k_grid_query) takes chunks of 16 cell-sorted query
 slots; queries sharing a cell form a group.  For each group it enumerates the
 (2m+1)^(naxes-1) neighbour rows 32 at a time (lane l of round rr handles row
-32 rr + l, whose per-axis offsets are the base-(2m+1) digits of that number,
-kept 3 bits per axis), looks up each row's slot range over the cells x-m ..
-x+m along the fastest axis, and appends the non-empty ranges to a compact list
-(at most 128 entries; a group that does not fit is rolled back and opens the
-next batch).  The ranges of a batch form one candidate stream cut into tiles
-of 64 candidates: for each tile, the lanes holding overlapping ranges copy
-their parts (and write the candidates' slots) into one of two ring buffers,
-and a cursor moves to the first range reaching past the tile.  Lanes then take
-candidates and find the candidate's group by a four-step search over the
-groups' stream starts.
+32 rr + l, whose per-axis offsets are the base-(2m+1) digits of that number:
+a per-event table holds each row's linear offset and, for m = 1, bit masks of
+the axes whose offset is -1 or +1, tested against the group's grid-edge
+bits), looks up each row's slot range over the cells x-m .. x+m along the
+fastest axis, and appends the non-empty ranges with their counts to a
+compact list (at most 128 entries; a group that does not fit is rolled back
+and opens the next batch); one exclusive scan per batch turns the counts into
+stream positions.  The stream is presented either in tiles of 64 candidates
+(the lanes holding overlapping ranges copy their parts, and write the
+candidates' slots, into one of two ring buffers, a cursor moving to the first
+range reaching past the tile) or by rounds of 32 candidates whose slots the
+lanes find by binary search over the stream positions; both are re-enacted
+and must agree.  Lanes find a candidate's group by a four-step search over
+the groups' stream starts.
 
 This file re-enacts those steps lane by lane on random and adversarial grids
 and checks: every shared-memory index stays inside its array, every copy's
@@ -69,19 +73,33 @@ def run_kernel(dims, scell, cstart, naxes, m):
     nrows = (2 * m + 1) ** (naxes - 1)
     assert nrows <= MAX_NBR_ROWS
     side = 2 * m + 1
-    dig = []
-    for rr in range(MAX_NBR_ROWS // 32):
-        row = []
-        for lane in range(32):
-            l, d = rr * 32 + lane, 0
-            for ax in range(1, naxes):
-                d |= (l % side) << (3 * (ax - 1))
-                l //= side
-            row.append(d)
-        dig.append(row)
     rstride = [0, 1, 0, 0, 0]
     for ax in range(2, 5):
         rstride[ax] = rstride[ax - 1] * d5[ax - 1]
+    # per-event table of row l = 32 rr + lane: linear offset, and edge bits
+    # (m = 1: axes with offset -1 in bits 0-3, +1 in bits 8-11) or digits
+    tdelta, tedge = [], []
+    for rr in range(MAX_NBR_ROWS // 32):
+        dl_row, te_row = [], []
+        for lane in range(32):
+            l = rr * 32 + lane
+            ll, dl, dg, lowm, highm = l, 0, 0, 0, 0
+            for ax in range(1, naxes):
+                d = ll % side
+                ll //= side
+                dg |= d << (3 * (ax - 1))
+                dl += (d - m) * rstride[ax]
+                if d < m:
+                    lowm |= 1 << (ax - 1)
+                if d > m:
+                    highm |= 1 << (ax - 1)
+            te = (lowm | (highm << 8)) if m == 1 else dg
+            if l >= nrows:
+                te |= 1 << 31
+            dl_row.append(dl)
+            te_row.append(te)
+        tdelta.append(dl_row)
+        tedge.append(te_row)
     pairs = []
     nchunks = (n + KCHUNKQ - 1) // KCHUNKQ
     for c in range(nchunks):
@@ -93,58 +111,78 @@ def run_kernel(dims, scell, cstart, naxes, m):
         ng = len(heads)
         gq = [heads[l] if l < ng else nqc for l in range(32)]
         cc = [decode(qc[l] if l < nqc else 0, d5, naxes) for l in range(32)]
+
+        def fetch(g):
+            gc = cc[gq[g]]
+            x0, x1 = max(gc[0] - m, 0), min(gc[0] + m, d5[0] - 1)
+            grow, gedge = 0, 1 << 31
+            for ax in range(1, naxes):
+                grow += gc[ax] * rstride[ax]
+                if gc[ax] == 0:
+                    gedge |= 1 << (ax - 1)
+                if gc[ax] == d5[ax] - 1:
+                    gedge |= 1 << (ax + 7)
+            lo = [[0] * 32 for _ in range(MAX_NBR_ROWS // 32)]
+            hi = [[0] * 32 for _ in range(MAX_NBR_ROWS // 32)]
+            for rr in range(MAX_NBR_ROWS // 32):
+                if rr * 32 >= nrows:
+                    continue
+                for lane in range(32):
+                    if m == 1:
+                        ok = (tedge[rr][lane] & gedge) == 0
+                    else:
+                        ok = not (tedge[rr][lane] >> 31)
+                        for ax in range(1, naxes):
+                            v = gc[ax] + ((tedge[rr][lane] >> (3 * (ax - 1))) & 7) - m
+                            ok = ok and 0 <= v < d5[ax]
+                    if ok:
+                        base = (grow + tdelta[rr][lane]) * d5[0]
+                        assert 0 <= base + x0 and base + x1 + 1 < len(cstart)
+                        lo[rr][lane] = int(cstart[base + x0])
+                        hi[rr][lane] = int(cstart[base + x1 + 1])
+            return lo, hi
+
         g0 = 0
         while g0 < ng:
-            nr, U, g = 0, 0, g0
-            gsb = [INT_MAX] * 32
+            nr, g = 0, g0
+            gr = [0] * 32
             rlo = [None] * RANGE_CAP
             rpre = [None] * (RANGE_CAP + 1)
             while g < ng:
-                nr0, U0 = nr, U
-                gc = cc[gq[g]]
-                x0, x1 = max(gc[0] - m, 0), min(gc[0] + m, d5[0] - 1)
+                nr0 = nr
+                clo, chi = fetch(g)
                 for rr in range(MAX_NBR_ROWS // 32):
                     if rr * 32 >= nrows:
                         break
-                    lo, cnt = [0] * 32, [0] * 32
-                    for lane in range(32):
-                        l = rr * 32 + lane
-                        if l >= nrows:
-                            continue
-                        ok, rowlin = True, 0
-                        for ax in range(1, 5):
-                            if ax < naxes:
-                                v = gc[ax] + ((dig[rr][lane] >> (3 * (ax - 1))) & 7) - m
-                                ok = ok and 0 <= v < d5[ax]
-                                rowlin += v * rstride[ax]
-                        if ok:
-                            base = rowlin * d5[0]
-                            assert 0 <= base + x0 and base + x1 + 1 < len(cstart)
-                            lo[lane] = int(cstart[base + x0])
-                            cnt[lane] = int(cstart[base + x1 + 1]) - lo[lane]
-                    incl = np.cumsum(cnt)
                     k = 0
                     for lane in range(32):
-                        if cnt[lane] > 0:
+                        cnt = chi[rr][lane] - clo[rr][lane]
+                        if cnt > 0:
                             pos = nr + k
                             k += 1
                             if pos < RANGE_CAP:
-                                rlo[pos] = lo[lane]
-                                rpre[pos] = U + int(incl[lane]) - cnt[lane]
+                                rlo[pos] = clo[rr][lane]
+                                rpre[pos] = cnt
                     nr += k
-                    U += int(incl[31])
                 if nr > RANGE_CAP:
-                    nr, U = nr0, U0
+                    nr = nr0
                     break
                 assert g - g0 < 32
-                gsb[g - g0] = U0
+                gr[g - g0] = nr0
                 g += 1
             gend = g
             assert gend > g0, "a single group must fit one batch"
             gqb = [gq[min(g0 + lane, 31)] for lane in range(32)]
             assert nr <= RANGE_CAP
+            U = 0
+            for i in range(nr):
+                v = rpre[i]
+                rpre[i] = U
+                U += v
             rpre[nr] = U
-            # tiles
+            gsb = [rpre[gr[lane]] if lane < gend - g0 else INT_MAX for lane in range(32)]
+            # tiles (bulk staging) / rounds (direct loads) present the same
+            # candidates in stream order; the tile logic is re-enacted here
             ring_slot = [[None] * TILE for _ in range(NB)]
             ntiles = (U + TILE - 1) // TILE
             cur = [0]
@@ -173,6 +211,16 @@ def run_kernel(dims, scell, cstart, naxes, m):
                 while cur[0] < nr and rpre[cur[0] + 1] <= T1:
                     cur[0] += 1
 
+            def direct_slot(u):
+                # the direct-load staging: binary search over the stream positions
+                i = 0
+                st = RANGE_CAP // 2
+                while st > 0:
+                    if i + st < nr and rpre[i + st] <= u:
+                        i += st
+                    st >>= 1
+                return rlo[i] + (u - rpre[i])
+
             for t in range(min(NB, ntiles)):
                 issue(t, t)
             for t in range(ntiles):
@@ -191,6 +239,8 @@ def run_kernel(dims, scell, cstart, naxes, m):
                                 j += st
                         qa, qe = gqb[j], gqb[j + 1]
                         nq = qe - qa if valid else 0
+                        if valid:
+                            assert direct_slot(u) == ring_slot[b][ul]
                         for jq in range(nq):
                             q = qa + jq
                             assert 0 <= q < nqc
