@@ -179,12 +179,11 @@ def algorithmic_query_bytes(N: int, D: int, K: int) -> int:
     return N * DP * 4 * 2 + N * 4 + N * 4 + N * K * 8
 
 
-def _cell_cap(N: int, D: int) -> int:
-    """Cells the library allows an N-point grid with its default axes
-    (mirrors cell_cap_for in build.cu: 24 N for five axes, 2 N for four)."""
-    na = min(D, 5)
-    c = 24 * N if na >= 5 else (2 * N if na == 4 else N // 2 + 1)
-    return min(max(16384, c), (1 << 27) if na >= 5 else (1 << 24))
+def _cell_cap(N: int, naxes: int) -> int:
+    """Cells the library allows an N-point grid requested with naxes axes
+    (mirrors cell_cap_for in build.cu: 18 N for five, 2 N for four)."""
+    c = 18 * N if naxes >= 5 else (2 * N if naxes == 4 else N // 2 + 1)
+    return min(max(16384, c), (1 << 27) if naxes >= 5 else (1 << 24))
 
 
 def _scan_launches(L: int) -> int:
@@ -192,14 +191,23 @@ def _scan_launches(L: int) -> int:
     return 1 if nb == 1 else (2 if nb <= 512 else 3)
 
 
-def launches_per_step(N: int, D: int, path: str = "grid") -> int:
-    """Kernels one build + query launches (mirrors the library's host code)."""
-    L = _cell_cap(N, D) + 1
+def launches_per_step(N: int, D: int, path: str = "grid", naxes_requested: int = 0) -> int:
+    """Kernels one build + query launches (mirrors the library's host code):
+    requested axes 0 (automatic, up to D = 8) or 5 take the chunk scan,
+    1..4 the row-task scan, whose query call first makes the pair copy and
+    the task list."""
+    if naxes_requested == 0 and path != "tc":
+        naxes_requested = 0 if D <= 8 else 4
+    cap_axes = naxes_requested or min(D, 5)
+    L = _cell_cap(N, cap_axes) + 1
     build = 5 + _scan_launches(L)          # init bbox cellid scan(s) scatter pack
     if path == "tc":
         # operand preparation + 128-query tasks (rowtasks scan emit), tc query, selection pass
         return build + 1 + (1 + _scan_launches(L) + 1) + 2
-    return build + 2                       # grid query + selection pass
+    if 1 <= naxes_requested <= 4:
+        # pair copy + 16-query tasks (rowtasks scan emit), row-task query, selection pass
+        return build + 1 + (1 + _scan_launches(L) + 1) + 2
+    return build + 2                       # chunk query + selection pass
 
 
 def max_over_ranks(x: float, device) -> float:
@@ -476,7 +484,8 @@ def run_ours(args):
                       "d2h_bytes_per_step": N * 4 + 2 * N * K * 4,
                       "ms_per_step": e2e_s * 1e3, "output": "dense rows (frnn_self_query_host)",
                       "matches_device_path": bool(ok_e2e)},
-        "gpu_launches": launches_per_step(N, D, "tc" if kern_is_tc else "grid") * args.steps,
+        "gpu_launches": launches_per_step(N, D, "tc" if kern_is_tc else "grid",
+                                          ctx.get_option(frnn.FRNN_OPT_GRID_NAXES)) * args.steps,
         "wall_s": wall,
     }
     if clocks:

@@ -287,14 +287,16 @@ const char* frnn_last_error(const frnn_ctx* ctx);
  * a later warp vote); fewer axes when D is smaller; on each grid, the
  * tensor-core pre-filter (D >= 8).
  * Each candidate is built and queried (first run untimed, best of three
- * timed with CUDA events on the context's stream) and the fastest build +
- * query is cached for the event size class (power-of-two bucket of N, D,
+ * timed with CUDA events on the context's stream, the L2 cache flushed
+ * before each run) and the fastest build + query is cached for the event
+ * size class (power-of-two bucket of N, D,
  * power-of-two bucket of K).  Afterwards FRNN_PATH_AUTO queries, grid builds
  * with the cell-multiple option at 0 (the default) and every event of
  * frnn_query_batched use the cached choice of their size class.  Results
  * never depend on the choice.  flags: FRNN_PATH_GRID or FRNN_PATH_TC limits
  * the candidates to that path (0: all).  Synchronises; allocates temporary
- * outputs (N + 2 N K words).  best (may be NULL) receives the winner.
+ * outputs (N + 2 N K words) and a flush buffer of twice the L2 size.  best
+ * (may be NULL) receives the winner.
  */
 typedef struct frnn_tune_result {
     int path;        /* FRNN_PATH_GRID or FRNN_PATH_TC */

@@ -1064,6 +1064,16 @@ frnn_status frnn_autotune(frnn_ctx* ctx, const float* refs, int64_t N, int D, fl
     int32_t* counts = static_cast<int32_t*>(out);
     int32_t* idx = counts + N;
     float* dist2 = reinterpret_cast<float*>(idx + (size_t)N * K);
+    // each timed run starts with the L2 cache flushed (a write larger than it,
+    // not timed), as a run over many events or after other work would
+    int l2 = 0;
+    cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, ctx->device);
+    const size_t flush_bytes = std::max<size_t>(2 * (size_t)std::max(l2, 0), 1 << 20);
+    void* flush = nullptr;
+    if (cudaMalloc(&flush, flush_bytes) != cudaSuccess) {
+        cudaGetLastError();
+        flush = nullptr;   // timed without the flush
+    }
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
@@ -1075,6 +1085,7 @@ frnn_status frnn_autotune(frnn_ctx* ctx, const float* refs, int64_t N, int D, fl
     auto timed = [&](auto&& fn, float& ms) -> frnn_status {
         float bestms = INFINITY;
         for (int rep = 0; rep < 4; ++rep) {   // first run warms up
+            if (flush) cudaMemsetAsync(flush, rep, flush_bytes, ctx->stream);
             cudaEventRecord(e0, ctx->stream);
             frnn_status st = fn();
             if (st != FRNN_OK) return st;
@@ -1147,6 +1158,7 @@ frnn_status frnn_autotune(frnn_ctx* ctx, const float* refs, int64_t N, int D, fl
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     cudaFree(out);
+    if (flush) cudaFree(flush);
     if (s != FRNN_OK) return s;
     ctx->tuned[tune_key(N, D, K)] = {bestr.path == FRNN_PATH_TC ? 1 : 0, bestr.cell_mult,
                                      bestr.exit_dims, bestr.ms, bestr.grid_axes, bestr.staging};

@@ -248,6 +248,7 @@ struct GridFit {
     float inv_h = 0.f;
     int32_t ncells = 1;
     float frac = INFINITY;
+    bool at_start = false;   // the starting cell edge fitted (no enlargement)
 };
 
 __device__ void grid_fit(GridFit& f, const int32_t* bb, int D, int k, int m, int axes_mode,
@@ -303,7 +304,10 @@ __device__ void grid_fit(GridFit& f, const int32_t* bb, int D, int k, int m, int
             cells *= dims[a];
             if ((double)ih * (rho + 0x1p-21 * ext[a]) + 0x1p-148 >= (double)mm - 0x1p-20) ok = false;
         }
-        if (ok && cells <= cap) break;
+        if (ok && cells <= cap) {
+            f.at_start = it == 0;
+            break;
+        }
         ih = __double2float_rd((double)ih * 0.9);
         if (!(ih > 0.f)) {
             ih = 0.f;
@@ -383,6 +387,9 @@ __device__ void event_params(EventHdr* hdr, int e, int D, const int32_t* bbox, f
         GridFit f;
         grid_fit(f, bb, D, k, m_req, axes_mode, r, h.cell_cap, valid, max_rows);
         if (f.frac < best.frac) best = f;
+        // at the starting cell edge a grid over more axes covers at most the
+        // fraction of one over fewer (one factor <= 1 more): no need to try fewer
+        if (f.at_start) break;
     }
     const int naxes = best.naxes;
     h.naxes = naxes;
@@ -781,13 +788,14 @@ void enqueue_scan(int32_t* data, int64_t n, int32_t* parts, int32_t* total, cuda
 // ------------------------------------------------------------------ host
 
 // Five gridded axes at a cell edge of about r need about (extent / r)^5
-// cells (5.2 M for the 300k x 8 tracking-like event, whose coordinates span
-// [-1.06, 1.06] at r = 0.1), four about (extent / r)^4; the budget grows with
-// n so that the cells stay near r on such events, and the parameter step
-// falls back to one axis fewer when the budget would make the five-axis
-// cells too coarse.
+// cells (5.15 M = 17.2 n for the 300k x 8 tracking-like event, whose
+// coordinates span [-1.06, 1.06] at r = 0.1), four about (extent / r)^4; the
+// budget grows with n so that the cells stay near r on such events (every
+// build zeroes and scans the whole budget), and the parameter step falls
+// back to one axis fewer when the budget would make five-axis cells too
+// coarse.
 int64_t cell_cap_for(int64_t n, int naxes) {
-    const int64_t per = naxes >= 5 ? 24 : (naxes == 4 ? 2 : 0);
+    const int64_t per = naxes >= 5 ? 18 : (naxes == 4 ? 2 : 0);
     int64_t c = per ? per * n : n / 2 + 1;
     c = std::max<int64_t>(16384, c);
     return std::min<int64_t>(c, naxes >= 5 ? ((int64_t)1 << 27) : ((int64_t)1 << 24));
