@@ -187,6 +187,9 @@ def _cell_cap(N: int, naxes: int) -> int:
 
 
 def _scan_launches(L: int) -> int:
+    """Launches of one exclusive scan of L entries (blocks of 2048): one for
+    a single block, else the reduce pass, a scan of the block sums beyond 512
+    blocks, the down pass."""
     nb = (L + 2047) // 2048
     return 1 if nb == 1 else (2 if nb <= 512 else 3)
 
@@ -200,7 +203,7 @@ def launches_per_step(N: int, D: int, path: str = "grid", naxes_requested: int =
         naxes_requested = 0 if D <= 8 else 4
     cap_axes = naxes_requested or min(D, 5)
     L = _cell_cap(N, cap_axes) + 1
-    build = 5 + _scan_launches(L)          # init bbox cellid scan(s) scatter pack
+    build = 4 + _scan_launches(L)          # init bbox cellid scan(s) scatter
     if path == "tc":
         # operand preparation + 128-query tasks (rowtasks scan emit), tc query, selection pass
         return build + 1 + (1 + _scan_launches(L) + 1) + 2

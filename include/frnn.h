@@ -280,15 +280,16 @@ const char* frnn_last_error(const frnn_ctx* ctx);
 
 /*
  * Autotuner.  Times the candidate configurations on the given point set (a
- * representative event, device memory, self-query): grids over five
- * coordinates with cell multiple m = 1 (scanned by chunks of 16 queries,
- * candidates on lanes, either candidate staging), over four with m = 1 and
- * over three with m = 2 (scanned by 16-query row tasks, at the default and
- * a later warp vote); fewer axes when D is smaller; on each grid, the
+ * representative event, device memory, self-query): the automatic axis
+ * choice with cell multiple m = 1 (five coordinates, or four when the cell
+ * budget makes five-axis cells too coarse; scanned by chunks of 16 queries,
+ * candidates on lanes, either candidate staging), four coordinates with
+ * m = 1 and three with m = 2 (scanned by 16-query row tasks, at the default
+ * and a later warp vote); fewer axes when D is smaller; on each grid, the
  * tensor-core pre-filter (D >= 8).
- * Each candidate is built and queried (first run untimed, best of three
- * timed with CUDA events on the context's stream, the L2 cache flushed
- * before each run) and the fastest build + query is cached for the event
+ * Each candidate runs whole steps, build then query (first run untimed,
+ * best of three timed with CUDA events on the context's stream, the L2
+ * cache flushed before each run), and the fastest is cached for the event
  * size class (power-of-two bucket of N, D,
  * power-of-two bucket of K).  Afterwards FRNN_PATH_AUTO queries, grid builds
  * with the cell-multiple option at 0 (the default) and every event of
@@ -303,7 +304,7 @@ typedef struct frnn_tune_result {
     int cell_mult;   /* m */
     int exit_dims;   /* warp vote point of the row-task scan (0 = default) */
     float ms;        /* build + query time of the winner, milliseconds */
-    int grid_axes;   /* gridded coordinates requested (3, 4 or 5, at most D) */
+    int grid_axes;   /* gridded coordinates requested (0: the automatic choice; 3 or 4) */
     int staging;     /* grid scan candidate staging (FRNN_OPT_STAGING values 1, 2) */
 } frnn_tune_result;
 

@@ -746,7 +746,7 @@ static frnn_status enqueue_batched(frnn_ctx* ctx, const frnn_event* ev, int n_ev
     }
     if (any_rows) {
         // buffers were reserved before any capture; enqueue their build
-        s = rows_prepare(ctx->batch, ctx->d_status, st, err);
+        s = rows_prepare(ctx->batch, ctx->d_status, st, err, mixed ? 2 : -1);
         if (s != FRNN_OK) return fail(ctx, s, err);
         q.kernel = 1;
         q.path_filter = mixed ? 2 : -1;
@@ -756,7 +756,7 @@ static frnn_status enqueue_batched(frnn_ctx* ctx, const frnn_event* ev, int n_ev
     }
     if (any_tc) {
         // operands were allocated before any capture; enqueue their build
-        s = tc_prepare(ctx->batch, ctx->batch, ctx->d_status, st, err);
+        s = tc_prepare(ctx->batch, ctx->batch, ctx->d_status, st, err, mixed ? 1 : -1);
         if (s != FRNN_OK) return fail(ctx, s, err);
         q.tc_stats = ctx->d_tcstat;
         q.path_filter = mixed ? 1 : -1;
@@ -1079,7 +1079,7 @@ frnn_status frnn_autotune(frnn_ctx* ctx, const float* refs, int64_t N, int D, fl
     cudaEventCreate(&e1);
     const int saved_m = ctx->cell_mult, saved_x = ctx->exit_dims, saved_a = ctx->grid_naxes,
               saved_s = ctx->staging;
-    frnn_tune_result bestr{FRNN_PATH_GRID, 1, 0, INFINITY, std::min(D, kMaxAxes), 1};
+    frnn_tune_result bestr{FRNN_PATH_GRID, 1, 0, INFINITY, 0, 1};
     frnn_status s = FRNN_OK;
     frnn_grid* g = nullptr;
     auto timed = [&](auto&& fn, float& ms) -> frnn_status {
@@ -1098,27 +1098,25 @@ frnn_status frnn_autotune(frnn_ctx* ctx, const float* refs, int64_t N, int D, fl
         ms = bestms;
         return frnn_sync(ctx);
     };
-    // grid configurations: five gridded axes with cells of r (chunk kernel),
-    // four with cells of r and three with cells of r/2 (row-task kernel); all
-    // of them for smaller D
+    // grid configurations: the automatic axis choice (five axes, or four
+    // when the cell budget makes five-axis cells too coarse; chunk kernel),
+    // four axes with cells of r and three with cells of r/2 (row-task
+    // kernel); fewer for smaller D
     struct GridCfg { int naxes, m; };
     std::vector<GridCfg> gcfg;
     auto add_cfg = [&](int na, int m) {
-        na = std::min(na, D);
+        if (na > 0) na = std::min(na, D);
         for (const GridCfg& c : gcfg)
             if (c.naxes == na && c.m == m) return;
         gcfg.push_back({na, m});
     };
-    add_cfg(5, 1);
+    add_cfg(0, 1);
     add_cfg(4, 1);
     add_cfg(3, 2);
     for (size_t gi = 0; gi < gcfg.size() && s == FRNN_OK; ++gi) {
         const int m = gcfg[gi].m;
         ctx->cell_mult = m;
         ctx->grid_naxes = gcfg[gi].naxes;
-        float bms = 0.f;
-        s = timed([&] { return frnn_build_grid(ctx, refs, N, D, r, &g); }, bms);
-        if (s != FRNN_OK) break;
         // the chunk kernel with either staging; the row-task kernel with its
         // default vote point and a later one
         struct Cand { unsigned path; int staging, exit_dims; };
@@ -1137,17 +1135,21 @@ frnn_status frnn_autotune(frnn_ctx* ctx, const float* refs, int64_t N, int D, fl
             s = fail(ctx, FRNN_ERR_UNSUPPORTED, "the tensor-core path needs D >= 8");
             break;
         }
+        // each run is a whole step, build then query: a query's per-build
+        // preparation (the row-task scan's pair copy and task list, the
+        // tensor-core operands) is timed with it
         for (const Cand& c : cands) {
             ctx->staging = c.staging;
             ctx->exit_dims = c.exit_dims;
-            float qms = 0.f;
+            float ms = 0.f;
             s = timed([&] {
+                frnn_status st = frnn_build_grid(ctx, refs, N, D, r, &g);
+                if (st != FRNN_OK) return st;
                 return frnn_query(ctx, g, refs, N, r, K, FRNN_SELF_QUERY | c.path, counts, idx,
                                   dist2);
-            }, qms);
+            }, ms);
             if (s != FRNN_OK) break;
-            if (bms + qms < bestr.ms)
-                bestr = {(int)c.path, m, c.exit_dims, bms + qms, gcfg[gi].naxes, c.staging};
+            if (ms < bestr.ms) bestr = {(int)c.path, m, c.exit_dims, ms, gcfg[gi].naxes, c.staging};
         }
     }
     ctx->cell_mult = saved_m;

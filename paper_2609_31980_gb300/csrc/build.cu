@@ -3,7 +3,7 @@
 //
 // The uniform grid / cell list is the method of the original FRNN the paper
 // starts from (Sec. 2: uniform-grid kernel, spacing chosen so that r is an
-// integer multiple of it).  Here at most 4 coordinates are gridded; the cell
+// integer multiple of it).  Here at most 5 coordinates are gridded; the cell
 // assignment is "roundoff-safe" (Table 1): it provably never separates two
 // points the float32 contract accepts by more than m cells per axis (proof at
 // event_params below).
@@ -16,8 +16,8 @@
 //               gridded axes, cell edge, cells per axis
 //   k_cellid    cell id of every point and its rank inside the cell (atomics)
 //   scan        exclusive warp-shuffle prefix scan of the counts -> cell starts
-//   k_scatter   slot -> original index, slot -> cell
-//   k_pack      cell-sorted coordinates, one row of DP floats per slot
+//   k_scatter   slot -> original index, slot -> cell, and the point's row of
+//               DP floats at its slot (cell-sorted coordinates)
 // (the tensor-core path adds its 128-query tiles: k_rowtasks, a scan, k_emit)
 #include <algorithm>
 #include <cmath>
@@ -116,7 +116,11 @@ __global__ void k_init(int32_t* counts, int64_t L, int32_t* bbox, int E, int32_t
         cell_off[1] = t1.cell_end;
     }
     int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t j = i; j < L; j += stride) counts[j] = 0;
+    // counts: 16-byte stores (the array starts 256-byte aligned)
+    int4* c4 = reinterpret_cast<int4*>(counts);
+    const int64_t L4 = L / 4;
+    for (int64_t j = i; j < L4; j += stride) c4[j] = make_int4(0, 0, 0, 0);
+    for (int64_t j = 4 * L4 + i; j < L; j += stride) counts[j] = 0;
     for (int64_t j = i; j < (int64_t)E * kBBoxCopies * kBBoxStride; j += stride) {
         int k = (int)(j % kBBoxStride);
         bbox[j] = k < 16 ? bb_min_init : (k < 32 ? bb_max_init : 0);   // flag, block counter: 0
@@ -214,7 +218,7 @@ __global__ void __launch_bounds__(kBuildPtsPerBlock, 6) k_bbox(EventHdr* hdr,
 }
 
 // Grid parameters of one event (one CTA: its warps combine the box copies,
-// then one thread derives the parameters).
+// then warp 0 derives the parameters, lane a handling gridded axis a).
 //
 // Roundoff-safe cell assignment (proof).  Let u = 2^-24.  If the contract
 // accepts (x, y), every rounded square t_a = fl(fl(x_a - y_a)^2) is <= the
@@ -226,33 +230,41 @@ __global__ void __launch_bounds__(kBuildPtsPerBlock, 6) k_bbox(EventHdr* hdr,
 // that bound is < m, floor(g(y)) - floor(g(x)) <= m, and clamping to
 // [0, dim-1] keeps it so; queries are clamped to [lo, hi] first, which only
 // shrinks their distance to any reference.  So searching +-m cells per gridded
-// axis finds every accepted pair.  inv_h starts at fl_down(m / (r (1+2^-10)))
-// and is lowered until the bound holds with 2^-20 to spare, every axis has at
-// most 1024 cells, and the event's cell count fits its capacity.
+// axis finds every accepted pair.  The bound is evaluated in float32 with
+// every operation rounded upward (rho, E and each step), which can only
+// overestimate it: inv_h starts at fl_down(m / fl_up(r (1+2^-10))) and is
+// lowered until the overestimate is below m - 2^-20, every axis has at most
+// 1024 cells and the event's cell count fits its capacity.
 static_assert(kBBoxCopies == 32, "one copy per lane when the copies are combined");
 
 static_assert(kBuildPtsPerBlock == 256, "eight warps combine the box copies");
+static_assert(kMaxD <= 32 && kMaxAxes <= 32, "one lane per coordinate");
 
-// One candidate grid: k gridded axes (the last k coordinates, or the k
-// widest), cell multiple m, the cell edge fitted to the proof's condition,
-// 1024 cells per axis and the event's cell budget (inv_h starts at
-// fl_down(m / (r (1+2^-10))) and is lowered until all three hold), and the
+// One candidate grid, held by warp 0: k gridded axes (the last k coordinates,
+// or the k widest), cell multiple m, the cell edge fitted to the proof's
+// condition, 1024 cells per axis and the event's cell budget, and the
 // expected fraction of the event a query's neighbourhood covers if the
 // points were spread evenly: the product over the gridded axes of
 // min(1, (2m+1) cells / extent).  The parameter step keeps the candidate
-// with the smallest fraction; the choice never changes results.
+// with the smallest fraction; the choice never changes results.  Lane a < k
+// holds gridded axis a (coordinate, cells, extremes); the other fields are
+// the same on every lane.
 struct GridFit {
     int naxes = 1, m = 1;
-    int axes[kMaxAxes] = {0, 0, 0, 0, 0};
-    int dims[kMaxAxes] = {1, 1, 1, 1, 1};
+    int axis = 0, dim = 1;
+    float lo = 0.f, hi = 0.f;
     float inv_h = 0.f;
     int32_t ncells = 1;
     float frac = INFINITY;
     bool at_start = false;   // the starting cell edge fitted (no enlargement)
 };
 
-__device__ void grid_fit(GridFit& f, const int32_t* bb, int D, int k, int m, int axes_mode,
-                         float r, int32_t cap, bool valid, int max_rows) {
+// lo_j, hi_j: the extremes of coordinate j on lane j < D.  Called by all
+// lanes of warp 0.
+__device__ void grid_fit(GridFit& f, float lo_j, float hi_j, int D, int k, int m, int axes_mode,
+                         float r, int64_t cap, bool valid, int max_rows) {
+    constexpr unsigned kAll = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
     f.naxes = k;
     // neighbour rows, (2m+1)^(k-1): at most max_rows (the chunk kernel
     // enumerates kMaxNbrRows, 32 per round; the row-task kernel one per lane)
@@ -264,75 +276,80 @@ __device__ void grid_fit(GridFit& f, const int32_t* bb, int D, int k, int m, int
         --mm;
     }
     f.m = mm;
-    if (axes_mode == 1 && D > k) {
+    int ax = lane < k ? D - k + lane : 0;
+    if (valid && axes_mode == 1 && D > k) {
         // the k widest coordinates (ties by lower index), in index order
-        bool used[kMaxD];
-        for (int j = 0; j < kMaxD; ++j) used[j] = false;
-        for (int a = 0; a < k; ++a) {
-            int best = -1;
-            float bw = -1.f;
-            for (int j = 0; j < D; ++j) {
-                if (used[j]) continue;
-                float w = ordered_to_float(bb[16 + j]) - ordered_to_float(bb[j]);
-                if (!(w <= bw)) { best = j; bw = w; }   // NaN-safe: first wins on NaN
-            }
-            used[best] = true;
+        const float wj = __fsub_rn(hi_j, lo_j);
+        int rank = 0;
+        for (int i = 0; i < D; ++i) {
+            const float wi = __shfl_sync(kAll, wj, i);
+            if (wi > wj || (wi == wj && i < lane)) ++rank;
         }
-        int a = 0;
-        for (int j = 0; j < D; ++j) if (used[j]) f.axes[a++] = j;
-    } else {
-        for (int a = 0; a < k; ++a) f.axes[a] = D - k + a;
+        const unsigned sel = __ballot_sync(kAll, lane < D && rank < k);
+        int cnt = 0;
+        ax = 0;
+        for (int j = 0; j < D; ++j) {
+            if ((sel >> j) & 1u) {
+                if (cnt == lane) ax = j;
+                ++cnt;
+            }
+        }
     }
+    const float lo = __shfl_sync(kAll, lo_j, ax);
+    const float hi = __shfl_sync(kAll, hi_j, ax);
+    f.axis = lane < k ? ax : 0;
+    f.lo = lo;
+    f.hi = hi;
     if (!valid) {
         f.frac = 1.f;
         return;
     }
-    double ext[kMaxAxes] = {0.0, 0.0, 0.0, 0.0, 0.0};
-    for (int a = 0; a < k; ++a)
-        ext[a] = (double)ordered_to_float(bb[16 + f.axes[a]]) - (double)ordered_to_float(bb[f.axes[a]]);
-    const double rd = (double)r;
-    const double rho = rd * (1.0 + 0x1p-20);
-    float ih = __double2float_rd((double)mm / (rd * (1.0 + 0x1p-10)));
-    int dims[kMaxAxes] = {1, 1, 1, 1, 1};
+    // the cell coordinate of hi is floor(fl(ext * inv_h)): dim = that + 1
+    const float ext = __fsub_rn(hi, lo);
+    const float ext_up = __fsub_ru(hi, lo);
+    const float rho_up = __fmul_ru(r, 1.0f + 0x1p-20f);
+    const float need = (float)mm - 0x1p-20f;
+    float ih = __fdiv_rd((float)mm, __fmul_ru(r, 1.0f + 0x1p-10f));
+    int dim = 1;
+    int64_t cells = 1;
+    bool fit = false;
     for (int it = 0; it < 4096; ++it) {
         bool ok = true;
-        int64_t cells = 1;
-        for (int a = 0; a < k; ++a) {
-            double c = floor(ext[a] * (double)ih) + 1.0;
-            if (c > kMaxDimsPerAxis) { ok = false; break; }
-            dims[a] = (int)c;
-            cells *= dims[a];
-            if ((double)ih * (rho + 0x1p-21 * ext[a]) + 0x1p-148 >= (double)mm - 0x1p-20) ok = false;
+        dim = 1;
+        if (lane < k) {
+            const float c = floorf(__fmul_rn(ext, ih)) + 1.0f;
+            if (!(c <= (float)kMaxDimsPerAxis)) ok = false;
+            else dim = (int)c;
+            const float bound =
+                __fadd_ru(__fmul_ru(ih, __fadd_ru(rho_up, __fmul_ru(0x1p-21f, ext_up))), 0x1p-148f);
+            if (!(bound < need)) ok = false;
         }
-        if (ok && cells <= cap) {
+        cells = 1;
+        for (int a = 0; a < k; ++a) cells *= __shfl_sync(kAll, dim, a);
+        if (__all_sync(kAll, ok) && cells <= cap) {
+            fit = true;
             f.at_start = it == 0;
             break;
         }
-        ih = __double2float_rd((double)ih * 0.9);
-        if (!(ih > 0.f)) {
-            ih = 0.f;
-            for (int a = 0; a < kMaxAxes; ++a) dims[a] = 1;
-            break;
-        }
+        ih = __fmul_rd(ih, 0.9f);
+        if (!(ih > 0.f)) break;
     }
-    int64_t cells = 1;
-    for (int a = 0; a < kMaxAxes; ++a) {
-        f.dims[a] = a < k ? dims[a] : 1;
-        cells *= f.dims[a];
-    }
-    if (cells > cap) {   // unreachable in practice; one cell is always safe
+    if (!fit) {   // one cell is always safe
         ih = 0.f;
+        dim = 1;
         cells = 1;
-        for (int a = 0; a < kMaxAxes; ++a) f.dims[a] = 1;
     }
+    f.dim = lane < k ? dim : 1;
     f.inv_h = ih;
     f.ncells = (int32_t)cells;
-    double frac = 1.0;
-    for (int a = 0; a < k; ++a) {
-        const double span = ih > 0.f ? (2.0 * mm + 1.0) / (double)ih : INFINITY;
-        if (ext[a] > 0.0) frac *= fmin(1.0, span / ext[a]);
+    float fr = 1.f;
+    if (lane < k && ext_up > 0.f) {
+        const float span = ih > 0.f ? (2.f * (float)mm + 1.f) / ih : INFINITY;
+        fr = fminf(1.f, span / ext_up);
     }
-    f.frac = (float)frac;
+    float frac = 1.f;
+    for (int a = 0; a < k; ++a) frac *= __shfl_sync(kAll, fr, a);
+    f.frac = frac;
 }
 
 __device__ void event_params(EventHdr* hdr, int e, int D, const int32_t* bbox, float r, int m,
@@ -359,25 +376,27 @@ __device__ void event_params(EventHdr* hdr, int e, int D, const int32_t* bbox, f
         if (lane == 0 && k < kBBoxStride) bb[k] = v[i];
     }
     __syncthreads();
-    if (threadIdx.x != 0) return;
-    // work on a private copy (global read-after-write chains are slow) and
-    // store it once at the end
-    EventHdr h = hdr[e];
-    // the last cell-array entry of the event counts its pair padding slot, so
-    // the next event's slots start on a pair boundary
-    counts[h.cell_off + h.cell_cap] = (int32_t)(h.n & 1);
+    if (warp != 0) return;
+    EventHdr& H = hdr[e];
+    const int64_t n = H.n;
+    const int64_t cell_off = H.cell_off;
+    const int32_t cell_cap = H.cell_cap;
     // per-event presets (batched autotuning) win over the call's options;
     // 0 = automatic: the widest count up to kMaxAxes, or one fewer axis when
     // the cell budget makes that grid's neighbourhoods smaller
-    const int want = h.naxes > 0 ? h.naxes : naxes_req;
-    const int m_req = h.m > 0 ? h.m : m;
-    bool valid = bb[32] == 0 && h.n > 0;
-    for (int k = 0; k < D && valid; ++k) {
-        if (!isfinite(ordered_to_float(bb[k])) || !isfinite(ordered_to_float(bb[16 + k]))) valid = false;
-    }
+    const int want = H.naxes > 0 ? H.naxes : naxes_req;
+    const int m_req = H.m > 0 ? H.m : m;
+    __syncwarp();   // every lane has read the header before it is written
+    // the last cell-array entry of the event counts its pair padding slot, so
+    // the next event's slots start on a pair boundary
+    if (lane == 0) counts[cell_off + cell_cap] = (int32_t)(n & 1);
+    const float lo_j = lane < D ? ordered_to_float(bb[lane]) : 0.f;
+    const float hi_j = lane < D ? ordered_to_float(bb[16 + lane]) : 0.f;
+    const bool fin = lane >= D || (isfinite(lo_j) && isfinite(hi_j));
+    const bool valid = __all_sync(0xffffffffu, fin) && bb[32] == 0 && n > 0;
     const int kmax = min(D, kMaxAxes);
-    int k_hi = want > 0 ? min(D, min(want, kMaxAxes)) : kmax;
-    int k_lo = want > 0 ? k_hi : max(1, kmax - 1);
+    const int k_hi = want > 0 ? min(D, min(want, kMaxAxes)) : kmax;
+    const int k_lo = want > 0 ? k_hi : max(1, kmax - 1);
     // grids requested with up to four axes are scanned by the row-task
     // kernel, whose lanes hold one neighbour row each
     const int max_rows = (want >= 1 && want <= 4) ? 32 : kMaxNbrRows;
@@ -385,36 +404,35 @@ __device__ void event_params(EventHdr* hdr, int e, int D, const int32_t* bbox, f
     best.frac = INFINITY;
     for (int k = k_hi; k >= k_lo; --k) {
         GridFit f;
-        grid_fit(f, bb, D, k, m_req, axes_mode, r, h.cell_cap, valid, max_rows);
+        grid_fit(f, lo_j, hi_j, D, k, m_req, axes_mode, r, cell_cap, valid, max_rows);
         if (f.frac < best.frac) best = f;
         // at the starting cell edge a grid over more axes covers at most the
         // fraction of one over fewer (one factor <= 1 more): no need to try fewer
         if (f.at_start) break;
     }
-    const int naxes = best.naxes;
-    h.naxes = naxes;
-    h.m = best.m;
-    h.valid = valid ? 1 : 0;
-    for (int a = 0; a < kMaxAxes; ++a) {
-        h.axes[a] = a < naxes ? best.axes[a] : 0;
-        h.dims[a] = a < naxes ? best.dims[a] : 1;
-        h.lo[a] = a < naxes && valid ? ordered_to_float(bb[best.axes[a]]) : 0.f;
-        h.hi[a] = a < naxes && valid ? ordered_to_float(bb[16 + best.axes[a]]) : 0.f;
+    const int na = best.naxes;
+    if (lane < kMaxAxes) {
+        const bool gridded = lane < na;
+        H.axes[lane] = gridded ? best.axis : 0;
+        H.dims[lane] = gridded && valid ? best.dim : 1;
+        H.lo[lane] = gridded && valid ? best.lo : 0.f;
+        H.hi[lane] = gridded && valid ? best.hi : 0.f;
     }
-    for (int k = 0; k < kMaxD; ++k) {
+    if (lane < kMaxD) {
         float c = 0.f;
-        if (valid && k < D) {
-            const float lo = ordered_to_float(bb[k]), hi = ordered_to_float(bb[16 + k]);
-            c = __fadd_rn(lo, __fmul_rn(0.5f, __fsub_rn(hi, lo)));
+        if (valid && lane < D) {
+            c = __fadd_rn(lo_j, __fmul_rn(0.5f, __fsub_rn(hi_j, lo_j)));
             if (!isfinite(c)) c = 0.f;
         }
-        h.ctr[k] = c;
+        H.ctr[lane] = c;
     }
-    h.inv_h = valid ? best.inv_h : 0.f;
-    h.ncells = valid ? best.ncells : 1;
-    if (!valid)
-        for (int a = 0; a < kMaxAxes; ++a) h.dims[a] = 1;
-    hdr[e] = h;
+    if (lane == 0) {
+        H.naxes = na;
+        H.m = best.m;
+        H.valid = valid ? 1 : 0;
+        H.inv_h = valid ? best.inv_h : 0.f;
+        H.ncells = valid ? best.ncells : 1;
+    }
 }
 
 // Cross-set binning: take the reference grid's parameters for each event.
@@ -471,6 +489,11 @@ __global__ void __launch_bounds__(kBuildPtsPerBlock) k_cellid(const EventHdr* hd
     rnk[gi] = atomicAdd(counts + h.cell_off + c, 1);
 }
 
+// Slot maps and cell-sorted coordinates: each point's slot (its cell's start
+// plus its rank), the slot's original index and cell, and the point's row of
+// DP floats (zero padding) written with 16-byte stores (one 32-byte sector
+// for D <= 8); the input rows are staged in shared memory with 16-byte loads.
+// An odd event's padding slot gets NaN coordinates: never within any radius.
 __global__ void __launch_bounds__(kBuildPtsPerBlock) k_scatter(const EventHdr* hdr,
                                                                const int32_t* blk_start, int E,
                                                                int D, int DP,
@@ -480,16 +503,21 @@ __global__ void __launch_bounds__(kBuildPtsPerBlock) k_scatter(const EventHdr* h
                                                                int32_t* perm, int32_t* cell) {
     pdl_trigger();
     pdl_wait();
+    extern __shared__ float sm[];
     const int e = find_event(blk_start, E, blockIdx.x);
     const EventHdr& h = hdr[e];
     const int64_t p0 = (int64_t)(blockIdx.x - blk_start[e]) * kBuildPtsPerBlock;
     const int np = (int)min((int64_t)kBuildPtsPerBlock, h.n - p0);
     if (p0 == 0 && threadIdx.x == 0 && (h.n & 1)) {
-        // pair padding slot (its coordinates are NaN, written by k_pack)
         const int64_t slot = h.pt_off + h.n;
         perm[slot] = -1;
         cell[slot] = 0;
+        const float nan = __int_as_float(0x7fc00000);
+        float4* dst = reinterpret_cast<float4*>(pts + slot * DP);
+        for (int j = 0; j < DP / 4; ++j) dst[j] = make_float4(nan, nan, nan, nan);
     }
+    if (np > 0) stage_floats(sm, h.refs + p0 * D, np * D);
+    __syncthreads();
     const int i = threadIdx.x;
     if (i >= np) return;
     const int64_t gi = h.pt_off + p0 + i;
@@ -497,41 +525,14 @@ __global__ void __launch_bounds__(kBuildPtsPerBlock) k_scatter(const EventHdr* h
     const int64_t slot = (int64_t)cstart[h.cell_off + c] + rnk[gi];
     perm[slot] = (int32_t)(p0 + i);
     cell[slot] = c;
-}
-
-// Cell-sorted coordinates, one thread per slot: the point's input row is
-// gathered and written as one row of DP floats (zero padding) with 16-byte
-// stores, consecutive slots by consecutive threads.  A slot without a point
-// (an odd event's padding) gets NaN: never within any radius.
-__global__ void __launch_bounds__(256) k_pack(const EventHdr* hdr, int E, int64_t nslots, int D,
-                                              int DP, const int32_t* perm, float* pts) {
-    pdl_trigger();
-    pdl_wait();
-    const int64_t s0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (s0 >= nslots) return;
-    // event of this slot: events occupy pair-aligned slot ranges
-    int lo = 0, hi = E - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (hdr[mid].pt_off <= s0) lo = mid; else hi = mid - 1;
-    }
-    const float* refs = hdr[lo].refs;
-    const int32_t i0 = perm[s0];
-    const float* a = i0 >= 0 ? refs + (int64_t)i0 * D : nullptr;
-    const float nan = __int_as_float(0x7fc00000);
-    float4* dst = reinterpret_cast<float4*>(pts + s0 * DP);
-    if ((D & 3) == 0 && (reinterpret_cast<uintptr_t>(refs) & 15) == 0) {
-        const float4 nan4 = make_float4(nan, nan, nan, nan);
-        for (int j = 0; j < D / 4; ++j)
-            dst[j] = a ? __ldg(reinterpret_cast<const float4*>(a) + j) : nan4;
-        return;
-    }
+    const float* src = sm + i * D;
+    float4* dst = reinterpret_cast<float4*>(pts + slot * DP);
     for (int j = 0; j < DP / 4; ++j) {
         float4 v;
-        v.x = a ? (4 * j + 0 < D ? __ldg(a + 4 * j + 0) : 0.f) : nan;
-        v.y = a ? (4 * j + 1 < D ? __ldg(a + 4 * j + 1) : 0.f) : nan;
-        v.z = a ? (4 * j + 2 < D ? __ldg(a + 4 * j + 2) : 0.f) : nan;
-        v.w = a ? (4 * j + 3 < D ? __ldg(a + 4 * j + 3) : 0.f) : nan;
+        v.x = 4 * j + 0 < D ? src[4 * j + 0] : 0.f;
+        v.y = 4 * j + 1 < D ? src[4 * j + 1] : 0.f;
+        v.z = 4 * j + 2 < D ? src[4 * j + 2] : 0.f;
+        v.w = 4 * j + 3 < D ? src[4 * j + 3] : 0.f;
         dst[j] = v;
     }
 }
@@ -556,7 +557,8 @@ __device__ __forceinline__ void row_slots(const EventHdr& h, const int32_t* csta
 }
 
 __global__ void k_rowtasks(const EventHdr* hdr, const int64_t* cell_off, int E, int64_t L,
-                           const int32_t* cstart, int32_t* rtask, int W, int A) {
+                           const int32_t* cstart, int32_t* rtask, int W, int A,
+                           int path_filter) {
     pdl_trigger();
     pdl_wait();
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -567,7 +569,8 @@ __global__ void k_rowtasks(const EventHdr* hdr, const int64_t* cell_off, int E, 
     int64_t nrows = 1;   // rows: every gridded coordinate but the fastest
     for (int a = 1; a < kMaxAxes && h.valid; ++a) nrows *= h.dims[a];
     int32_t nt = 0;
-    if (row < nrows) {
+    // events another launch of a mixed batch queries get no tasks
+    if (row < nrows && (path_filter < 0 || h.path == path_filter)) {
         int32_t base, cnt;
         row_slots(h, cstart, row, base, cnt);
         if (cnt > 0) {
@@ -613,9 +616,10 @@ __global__ void k_emit(const EventHdr* hdr, const int64_t* cell_off, int E, int6
 }
 
 void enqueue_tasks(GridBufs& g, int W, int A, Task* out, int64_t out_cap, int32_t* count_out,
-                   int32_t* d_status, cudaStream_t st) {
+                   int32_t* d_status, cudaStream_t st, int path_filter) {
     const unsigned nb = (unsigned)std::max<int64_t>(1, ceil_div(g.L, 256));
-    launch_pdl(k_rowtasks, dim3(nb), dim3(256), 0, st, g.hdr, g.cell_off, g.E, g.L, g.cstart, g.rtask, W, A);
+    launch_pdl(k_rowtasks, dim3(nb), dim3(256), 0, st, g.hdr, g.cell_off, g.E, g.L, g.cstart, g.rtask, W, A,
+               path_filter);
     enqueue_scan(g.rtask, g.L, g.parts, count_out, st);
     launch_pdl(k_emit, dim3(nb), dim3(256), 0, st, g.hdr, g.cell_off, g.E, g.L, g.cstart, g.rtask,
                count_out, out, out_cap, W, A, d_status);
@@ -942,14 +946,11 @@ static inline unsigned blocks_for(int64_t n, int t) {
 static void enqueue_sort(GridBufs& g, size_t smem_pts, int check_finite, int32_t* d_status,
                          cudaStream_t st) {
     const int E = g.E, D = g.D;
-    launch_pdl(k_cellid, dim3((unsigned)g.nblk), dim3(kBuildPtsPerBlock), smem_pts, st, 
-        g.hdr, g.blk_start, E, D, g.cstart, g.cid, g.rnk, check_finite, d_status);
+    launch_pdl(k_cellid, dim3((unsigned)g.nblk), dim3(kBuildPtsPerBlock), smem_pts, st,
+               g.hdr, g.blk_start, E, D, g.cstart, g.cid, g.rnk, check_finite, d_status);
     enqueue_scan(g.cstart, g.L, g.parts, g.scalars + kScCellTotal, st);
-    launch_pdl(k_scatter, dim3((unsigned)g.nblk), dim3(kBuildPtsPerBlock), 0, st, 
-        g.hdr, g.blk_start, E, D, g.DP, g.cstart, g.cid, g.rnk, g.pts, g.perm, g.cell);
-    if (g.n_total > 0)
-        launch_pdl(k_pack, dim3((unsigned)ceil_div(g.n_total, 256)), dim3(256), 0, st, g.hdr, E,
-                   g.n_total, D, g.DP, g.perm, g.pts);
+    launch_pdl(k_scatter, dim3((unsigned)g.nblk), dim3(kBuildPtsPerBlock), smem_pts, st,
+               g.hdr, g.blk_start, E, D, g.DP, g.cstart, g.cid, g.rnk, g.pts, g.perm, g.cell);
     // no task list: the grid query takes chunks of kChunkQ slots in slot order
 }
 
@@ -996,7 +997,8 @@ frnn_status enqueue_build(GridBufs& g, const float* const* refs, const BuildOpts
         g.cstart, g.L, g.bbox, E, g.scalars, bbmin, bbmax, t1, g.hdr, g.blk_start, g.cell_off);
     const size_t smem_pts = sizeof(float) * kBuildPtsPerBlock * D;
     if (params_from) {
-        launch_pdl(k_copy_params, dim3(blocks_for(E, 128)), dim3(128), 0, st, g.hdr, params_from->hdr, E, g.cstart);
+        launch_pdl(k_copy_params, dim3(blocks_for(E, 128)), dim3(128), 0, st, g.hdr, params_from->hdr, E,
+                   g.cstart);
     } else {
         launch_pdl(k_bbox, dim3((unsigned)g.nblk), dim3(kBuildPtsPerBlock), smem_pts, st, g.hdr, g.blk_start, E, D,
                    g.bbox, d_status, o.r, o.m, o.axes_mode, o.naxes, g.cstart);
@@ -1022,7 +1024,8 @@ frnn_status enqueue_build_resident(GridBufs& g, const BuildOpts& o, int32_t* d_s
     const int32_t bbmax = host_float_to_ordered(-INFINITY);
     const int64_t init_n = std::max<int64_t>(g.L, (int64_t)E * kBBoxCopies * kBBoxStride);
     launch_pdl(k_init, dim3(std::min<unsigned>(blocks_for(init_n, 256), 4096)), dim3(256), 0, st, 
-        g.cstart, g.L, g.bbox, E, g.scalars, bbmin, bbmax, OneEventTables{}, g.hdr, g.blk_start, g.cell_off);
+        g.cstart, g.L, g.bbox, E, g.scalars, bbmin, bbmax, OneEventTables{}, g.hdr, g.blk_start,
+        g.cell_off);
     const size_t smem_pts = sizeof(float) * kBuildPtsPerBlock * D;
     launch_pdl(k_bbox, dim3((unsigned)g.nblk), dim3(kBuildPtsPerBlock), smem_pts, st, g.hdr, g.blk_start, E, D,
                g.bbox, d_status, o.r, o.m, o.axes_mode, o.naxes, g.cstart);

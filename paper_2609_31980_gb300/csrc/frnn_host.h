@@ -125,8 +125,10 @@ frnn_status enqueue_build(GridBufs& g, const float* const* refs, const BuildOpts
 
 // Task list: windows of W slots aligned to A within each row of cells
 // (at most out_cap tasks; beyond it the status word records a capacity error).
+// path_filter >= 0: only rows of events whose path is path_filter get tasks
+// (a mixed batch queries its other events in other launches).
 void enqueue_tasks(GridBufs& g, int W, int A, Task* out, int64_t out_cap, int32_t* count_out,
-                   int32_t* d_status, cudaStream_t st);
+                   int32_t* d_status, cudaStream_t st, int path_filter = -1);
 
 // The build for per-event tables already resident on the device.
 frnn_status enqueue_build_resident(GridBufs& g, const BuildOpts& o, int32_t* d_status,
@@ -166,7 +168,8 @@ frnn_status enqueue_grid_query(const QueryLaunch& q, cudaStream_t st, std::strin
 // pair-interleaved copy and 16-query tasks of a point set; the launch itself
 // (called by enqueue_grid_query when q.kernel == 1, inputs prepared).
 frnn_status rows_reserve(GridBufs& g, std::string& err);
-frnn_status rows_prepare(GridBufs& g, int32_t* d_status, cudaStream_t st, std::string& err);
+frnn_status rows_prepare(GridBufs& g, int32_t* d_status, cudaStream_t st, std::string& err,
+                         int path_filter = -1);
 void rows_free(GridBufs& g);
 frnn_status enqueue_row_query(const QueryLaunch& q, const QueryArgs& a, cudaStream_t st,
                               std::string& err);
@@ -186,7 +189,7 @@ void enqueue_csr_gather(const int32_t* cnt, const int64_t* offsets, const int32_
 // center_src: the grid whose per-event centres the operands use (the
 // reference grid; the set itself for self-queries).
 frnn_status tc_prepare(GridBufs& g, const GridBufs& center_src, int32_t* d_status, cudaStream_t st,
-                       std::string& err);
+                       std::string& err, int path_filter = -1);
 frnn_status enqueue_tc_query(const QueryLaunch& q, cudaStream_t st, std::string& err);
 frnn_status tc_reserve(GridBufs& g, std::string& err);
 void tc_free(GridBufs& g);

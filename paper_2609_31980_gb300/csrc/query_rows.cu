@@ -687,7 +687,8 @@ frnn_status rows_reserve(GridBufs& g, std::string& err) {
     return FRNN_OK;
 }
 
-frnn_status rows_prepare(GridBufs& g, int32_t* d_status, cudaStream_t st, std::string& err) {
+frnn_status rows_prepare(GridBufs& g, int32_t* d_status, cudaStream_t st, std::string& err,
+                         int path_filter) {
     if (g.rows_ready) return FRNN_OK;
     frnn_status s = rows_reserve(g, err);
     if (s != FRNN_OK) return s;
@@ -696,7 +697,7 @@ frnn_status rows_prepare(GridBufs& g, int32_t* d_status, cudaStream_t st, std::s
                    (const float*)g.pts, g.n_total / 2, g.DP, g.ppts);
     g.rtask = g.rows_rtask;   // the task builder's scratch
     enqueue_tasks(g, kTaskQueries, 1, g.row_tasks, g.rows_cap_tasks, g.scalars + kScNTasks,
-                  d_status, st);
+                  d_status, st, path_filter);
     cudaError_t ce = cudaGetLastError();
     if (ce != cudaSuccess) {
         err = std::string("row-task preparation failed: ") + cudaGetErrorString(ce);

@@ -830,7 +830,7 @@ frnn_status tc_reserve(GridBufs& g, std::string& err) {
 }
 
 frnn_status tc_prepare(GridBufs& g, const GridBufs& center_src, int32_t* d_status,
-                       cudaStream_t st, std::string& err) {
+                       cudaStream_t st, std::string& err, int path_filter) {
     frnn_status s0 = tc_reserve(g, err);
     if (s0 != FRNN_OK) return s0;
     const int K = tc_k_for(g.D);
@@ -852,7 +852,8 @@ frnn_status tc_prepare(GridBufs& g, const GridBufs& center_src, int32_t* d_statu
         }
         (void)K;
     }
-    enqueue_tasks(g, kTcM, 8, g.tc_tasks, g.tc_cap_tasks, g.scalars + kScTcTasks, d_status, st);
+    enqueue_tasks(g, kTcM, 8, g.tc_tasks, g.tc_cap_tasks, g.scalars + kScTcTasks, d_status, st,
+                  path_filter);
     cudaError_t ce = cudaGetLastError();
     if (ce != cudaSuccess) {
         err = std::string("tensor-core prep launch failed: ") + cudaGetErrorString(ce);

@@ -1,42 +1,73 @@
 """The roundoff-safe grid, checked on the CPU.
 
 The build picks, per gridded axis, lo and hi (the coordinates' extremes) and
-one inverse cell edge inv_h: it starts at m / (r (1 + 2^-10)) rounded down to
-float32 and shrinks by 0.9 until inv_h (rho + 2^-21 E) + 2^-148 < m - 2^-20
-(rho = r (1 + 2^-20), E = hi - lo), every axis has at most 1024 cells and the
-cell count fits the capacity.  A point's cell coordinate is
-floor(fl(fl(x' - lo) * inv_h)) clamped to [0, dim - 1], x' = x clamped to
-[lo, hi].  The claim: two points the float32 contract accepts are at most m
+one inverse cell edge inv_h: it starts at fl_down(m / fl_up(r (1 + 2^-10)))
+and shrinks (times 0.9, rounded down) until an overestimate of
+inv_h (rho + 2^-21 E) + 2^-148, every operation in float32 rounded upward
+(rho = r (1 + 2^-20), E = hi - lo), is below m - 2^-20, every axis has at
+most 1024 cells and the cell count fits the capacity.  A point's cell
+coordinate is floor(fl(fl(x' - lo) * inv_h)) clamped to [0, dim - 1],
+x' = x clamped to [lo, hi], and an axis has floor(fl(fl(hi - lo) * inv_h)) + 1
+cells.  The claim: two points the float32 contract accepts are at most m
 cells apart on every gridded axis, so searching +-m cells finds them.
-Emulated here in float32 with the same steps, on pairs placed at the radius
-and around cell boundaries, for small and large extents and offsets.
+Emulated here with the same steps (the directed roundings exactly, through
+rational arithmetic), on pairs placed at the radius and around cell
+boundaries, for small and large extents and offsets.
 """
+from fractions import Fraction
+
 import numpy as np
 import pytest
 
 
-def f32_rd(x):
-    """float64 -> float32 rounded down."""
-    y = np.float32(x)
-    return np.nextafter(y, np.float32(-np.inf)) if np.float64(y) > x else y
+def f32_dir(x, up):
+    """The rational x rounded to float32 upward (up) or downward."""
+    x = Fraction(x)
+    y = np.float32(float(x))
+    inf = np.float32(np.inf)
+    if up:
+        while Fraction(float(y)) < x:
+            y = np.nextafter(y, inf)
+        while Fraction(float(np.nextafter(y, -inf))) >= x:
+            y = np.nextafter(y, -inf)
+    else:
+        while Fraction(float(y)) > x:
+            y = np.nextafter(y, -inf)
+        while Fraction(float(np.nextafter(y, inf))) <= x:
+            y = np.nextafter(y, inf)
+    return y
 
 
-def choose_inv_h(ext, r, m, cap):
-    rho = float(r) * (1.0 + 2.0 ** -20)
-    ih = f32_rd(m / (float(r) * (1.0 + 2.0 ** -10)))
+def F(v):
+    return Fraction(float(v))
+
+
+def choose_inv_h(lo, hi, r, m, cap):
+    """The build's inverse cell edge for float32 extremes lo, hi (per axis)."""
+    r = np.float32(r)
+    ext = (hi - lo).astype(np.float32)                                 # round to nearest
+    ext_up = [f32_dir(F(h) - F(l), True) for l, h in zip(lo, hi)]
+    rho_up = f32_dir(F(r) * (1 + Fraction(1, 2 ** 20)), True)
+    need = np.float32(m) - np.float32(2.0 ** -20)
+    ih = f32_dir(Fraction(m) / F(f32_dir(F(r) * (1 + Fraction(1, 2 ** 10)), True)), False)
     for _ in range(4096):
         ok, cells = True, 1
-        for e in ext:
-            c = np.floor(e * float(ih)) + 1.0
+        for e, eu in zip(ext, ext_up):
+            c = np.floor(np.float32(e * ih)) + 1.0
             if c > 1024:
                 ok = False
                 break
             cells *= int(c)
-            if float(ih) * (rho + 2.0 ** -21 * e) + 2.0 ** -148 >= m - 2.0 ** -20:
+            t1 = f32_dir(Fraction(1, 2 ** 21) * F(eu), True)
+            t2 = f32_dir(F(rho_up) + F(t1), True)
+            t3 = f32_dir(F(ih) * F(t2), True)
+            bound = f32_dir(F(t3) + Fraction(1, 2 ** 148), True)
+            if not bound < need:
                 ok = False
         if ok and cells <= cap:
             return ih
-        ih = f32_rd(float(ih) * 0.9)
+        ih = f32_dir(F(ih) * F(np.float32(0.9)), False)
+        assert ih > 0
     raise AssertionError("no inv_h")
 
 
@@ -58,9 +89,8 @@ def check_event(pts, pairs_a, pairs_b, r, m, cap=1 << 24):
     r = np.float32(r)
     r2 = np.float32(r * r)
     lo, hi = pts.min(axis=0), pts.max(axis=0)
-    ext = hi.astype(np.float64) - lo.astype(np.float64)
-    ih = choose_inv_h(ext, r, m, cap)
-    dims = np.floor(ext * float(ih)).astype(np.int64) + 1
+    ih = choose_inv_h(lo, hi, r, m, cap)
+    dims = np.floor((hi - lo).astype(np.float32) * ih).astype(np.int64) + 1
     ok = contract(pairs_a, pairs_b) <= r2
     for a in range(pts.shape[1]):
         ca = cell(pairs_a[:, a], lo[a], hi[a], ih, dims[a])
@@ -114,7 +144,7 @@ def test_pairs_straddling_cell_boundaries(m, r):
     r2 = np.float32(r * r)
     pts = g.uniform(0, 1, size=(n, D)).astype(np.float32)
     lo, hi = pts.min(axis=0), pts.max(axis=0)
-    ih = choose_inv_h(hi.astype(np.float64) - lo.astype(np.float64), r, m, 1 << 24)
+    ih = choose_inv_h(lo, hi, r, m, 1 << 24)
     k = g.integers(1, int(np.floor((hi[0] - lo[0]) * ih)), size=n)
     base = (lo[0] + (k / float(ih))).astype(np.float32)       # near a boundary
     for step in range(-3, 4):
