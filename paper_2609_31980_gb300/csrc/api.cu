@@ -700,12 +700,21 @@ static bool same_events(const frnn_ctx* c, const frnn_event* ev, int n) {
     return true;
 }
 
+// Path of one event of a batch: 0 grid scan by chunks, 2 grid scan by row
+// tasks, 1 tensor core (autotuned per size class, else the defaults).
+static int batch_path(const frnn_ctx* ctx, int64_t n, int D, int K, unsigned flags) {
+    if (use_tc_path(ctx, D, flags, n, K)) return 1;
+    return grid_kernel(build_naxes(ctx, n, D)) == 1 ? 2 : 0;
+}
+
+// ev: ordered by path (chunks, row tasks, tensor core), so that each path's
+// events occupy one range of chunks, cell-array entries and slots.
 static frnn_status enqueue_batched(frnn_ctx* ctx, const frnn_event* ev, int n_events, int D,
                                    float r, int K, unsigned flags, bool capturing,
                                    cudaStream_t st) {
     std::vector<const float*> refs(n_events);
-    // per event path: 0 grid scan by chunks, 2 grid scan by row tasks, 1 tensor core
     bool any_path[3] = {false, false, false};
+    int first_rows = n_events, first_tc = n_events;   // first event of each later path
     for (int e = 0; e < n_events; ++e) {
         refs[e] = ev[e].pts;
         EventHdr& h = ctx->batch.h_hdr[e];
@@ -715,9 +724,13 @@ static frnn_status enqueue_batched(frnn_ctx* ctx, const frnn_event* ev, int n_ev
         // per event: autotuned cell multiple, axes and path for its size class
         h.m = build_mult(ctx, ev[e].n, D);
         h.naxes = build_naxes(ctx, ev[e].n, D);
-        h.path = use_tc_path(ctx, D, flags, ev[e].n, K) ? 1 : (grid_kernel(h.naxes) == 1 ? 2 : 0);
+        h.path = batch_path(ctx, ev[e].n, D, K, flags);
         if (ev[e].n > 0) any_path[h.path] = true;
+        if (h.path != 0 && first_rows == n_events) first_rows = e;
+        if (h.path == 1 && first_tc == n_events) first_tc = e;
     }
+    const GridBufs& gb = ctx->batch;
+    const auto slot_of = [&](int e) { return e < n_events ? gb.h_hdr[e].pt_off : gb.n_total; };
     const bool any_grid = any_path[0], any_rows = any_path[2], any_tc = any_path[1];
     BuildOpts o;
     o.r = r;
@@ -741,14 +754,19 @@ static frnn_status enqueue_batched(frnn_ctx* ctx, const frnn_event* ev, int n_ev
     if (any_grid || (!any_tc && !any_rows)) {
         q.kernel = 0;
         q.path_filter = mixed ? 0 : -1;
+        // the chunks of the chunk-scan events only
+        if (mixed && first_rows < n_events) q.chunk_end = gb.h_hdr[first_rows].qchunk0;
         s = enqueue_grid_query(q, st, err);
         if (s != FRNN_OK) return fail(ctx, s, err);
     }
     if (any_rows) {
         // buffers were reserved before any capture; enqueue their build
-        s = rows_prepare(ctx->batch, ctx->d_status, st, err, mixed ? 2 : -1);
+        s = mixed ? rows_prepare(ctx->batch, ctx->d_status, st, err, 2, gb.h_cell_off[first_rows],
+                                 gb.h_cell_off[first_tc], slot_of(first_rows), slot_of(first_tc))
+                  : rows_prepare(ctx->batch, ctx->d_status, st, err);
         if (s != FRNN_OK) return fail(ctx, s, err);
         q.kernel = 1;
+        q.chunk_end = -1;
         q.path_filter = mixed ? 2 : -1;
         s = enqueue_grid_query(q, st, err);
         if (s != FRNN_OK) return fail(ctx, s, err);
@@ -756,7 +774,9 @@ static frnn_status enqueue_batched(frnn_ctx* ctx, const frnn_event* ev, int n_ev
     }
     if (any_tc) {
         // operands were allocated before any capture; enqueue their build
-        s = tc_prepare(ctx->batch, ctx->batch, ctx->d_status, st, err, mixed ? 1 : -1);
+        s = mixed ? tc_prepare(ctx->batch, ctx->batch, ctx->d_status, st, err, 1,
+                               gb.h_cell_off[first_tc], gb.h_cell_off[n_events])
+                  : tc_prepare(ctx->batch, ctx->batch, ctx->d_status, st, err);
         if (s != FRNN_OK) return fail(ctx, s, err);
         q.tc_stats = ctx->d_tcstat;
         q.path_filter = mixed ? 1 : -1;
@@ -792,14 +812,13 @@ frnn_status frnn_query_batched(frnn_ctx* ctx, const frnn_event* ev, int n_events
     if ((flags & FRNN_PATH_TC) && D < 8)
         return fail(ctx, FRNN_ERR_UNSUPPORTED, "the tensor-core path needs D >= 8");
     if (n_events == 0) return FRNN_OK;
-    std::vector<int64_t> n(n_events);
     for (int e = 0; e < n_events; ++e) {
         const frnn_event& x = ev[e];
         if (x.n < 0 || x.n >= INT32_MAX) return fail(ctx, FRNN_ERR_INVALID_ARG, "event n");
         if (x.n > 0 && (!x.pts || !x.counts || !x.idx || !x.dist2))
             return fail(ctx, FRNN_ERR_INVALID_ARG, "event pointer is NULL");
-        n[e] = x.n;
     }
+    const frnn_event* caller_ev = ev;
     const int opts[5] = {ctx->cell_mult, ctx->axes_mode, ctx->exit_dims, ctx->grid_naxes,
                          ctx->staging};
     const bool hit = ctx->use_graph && ctx->graph && same_events(ctx, ev, n_events) &&
@@ -811,6 +830,17 @@ frnn_status frnn_query_batched(frnn_ctx* ctx, const frnn_event* ev, int n_events
         ctx->graph = nullptr;
         ctx->g_ev.clear();
     }
+    // the batch in path order (chunk scan, row-task scan, tensor core; stable
+    // within a path): each path's preparation and launch then covers only
+    // its own events' chunks, cells and slots
+    std::vector<frnn_event> ordered;
+    ordered.reserve(n_events);
+    for (int want : {0, 2, 1})
+        for (int e = 0; e < n_events; ++e)
+            if (batch_path(ctx, ev[e].n, D, K, flags) == want) ordered.push_back(ev[e]);
+    ev = ordered.data();
+    std::vector<int64_t> n(n_events);
+    for (int e = 0; e < n_events; ++e) n[e] = ev[e].n;
     frnn_status s = alloc_accounted(ctx, ctx->batch, n_events, n.data(), D, nullptr);
     if (s != FRNN_OK) return s;
     bool batch_tc = false, batch_rows = false;
@@ -860,7 +890,7 @@ frnn_status frnn_query_batched(frnn_ctx* ctx, const frnn_event* ev, int n_events
     cudaGraphDestroy(graph);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaGraphInstantiate");
     ctx->graph = exec;
-    ctx->g_ev.assign(ev, ev + n_events);
+    ctx->g_ev.assign(caller_ev, caller_ev + n_events);
     ctx->g_D = D;
     ctx->g_K = K;
     ctx->g_r = r;

@@ -556,13 +556,13 @@ __device__ __forceinline__ void row_slots(const EventHdr& h, const int32_t* csta
     }
 }
 
-__global__ void k_rowtasks(const EventHdr* hdr, const int64_t* cell_off, int E, int64_t L,
-                           const int32_t* cstart, int32_t* rtask, int W, int A,
+__global__ void k_rowtasks(const EventHdr* hdr, const int64_t* cell_off, int E, int64_t i0,
+                           int64_t i1, const int32_t* cstart, int32_t* rtask, int W, int A,
                            int path_filter) {
     pdl_trigger();
     pdl_wait();
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= L) return;
+    const int64_t i = i0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= i1) return;
     const int e = find_event64(cell_off, E, i);
     const EventHdr& h = hdr[e];
     const int64_t row = i - cell_off[e];
@@ -581,19 +581,19 @@ __global__ void k_rowtasks(const EventHdr* hdr, const int64_t* cell_off, int E, 
     rtask[i] = nt;
 }
 
-__global__ void k_emit(const EventHdr* hdr, const int64_t* cell_off, int E, int64_t L,
-                       const int32_t* cstart, const int32_t* rtask_start,
+__global__ void k_emit(const EventHdr* hdr, const int64_t* cell_off, int E, int64_t i0,
+                       int64_t i1, const int32_t* cstart, const int32_t* rtask_start,
                        const int32_t* rtask_count_src, Task* tasks, int64_t task_cap, int W,
                        int A, int32_t* status) {
     pdl_trigger();
     pdl_wait();
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= L) return;
+    const int64_t i = i0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= i1) return;
     const int e = find_event64(cell_off, E, i);
     const EventHdr& h = hdr[e];
     const int64_t row = i - cell_off[e];
     const int32_t t0 = rtask_start[i];
-    const int32_t t1 = (i + 1 < L) ? rtask_start[i + 1] : rtask_count_src[0];
+    const int32_t t1 = (i + 1 < i1) ? rtask_start[i + 1] : rtask_count_src[0];
     if (t1 <= t0) return;
     int32_t base, cnt;
     row_slots(h, cstart, row, base, cnt);
@@ -616,12 +616,16 @@ __global__ void k_emit(const EventHdr* hdr, const int64_t* cell_off, int E, int6
 }
 
 void enqueue_tasks(GridBufs& g, int W, int A, Task* out, int64_t out_cap, int32_t* count_out,
-                   int32_t* d_status, cudaStream_t st, int path_filter) {
-    const unsigned nb = (unsigned)std::max<int64_t>(1, ceil_div(g.L, 256));
-    launch_pdl(k_rowtasks, dim3(nb), dim3(256), 0, st, g.hdr, g.cell_off, g.E, g.L, g.cstart, g.rtask, W, A,
-               path_filter);
-    enqueue_scan(g.rtask, g.L, g.parts, count_out, st);
-    launch_pdl(k_emit, dim3(nb), dim3(256), 0, st, g.hdr, g.cell_off, g.E, g.L, g.cstart, g.rtask,
+                   int32_t* d_status, cudaStream_t st, int path_filter, int64_t i0, int64_t i1) {
+    if (i1 < 0) i1 = g.L;
+    i0 = std::min(std::max<int64_t>(i0, 0), i1);
+    const int64_t n = i1 - i0;
+    const unsigned nb = (unsigned)std::max<int64_t>(1, ceil_div(n, 256));
+    launch_pdl(k_rowtasks, dim3(nb), dim3(256), 0, st, g.hdr, g.cell_off, g.E, i0, i1, g.cstart,
+               g.rtask, W, A, path_filter);
+    // the scan of the range's task counts gives each row its first task
+    enqueue_scan(g.rtask + i0, n, g.parts, count_out, st);
+    launch_pdl(k_emit, dim3(nb), dim3(256), 0, st, g.hdr, g.cell_off, g.E, i0, i1, g.cstart, g.rtask,
                count_out, out, out_cap, W, A, d_status);
 }
 

@@ -126,9 +126,12 @@ frnn_status enqueue_build(GridBufs& g, const float* const* refs, const BuildOpts
 // Task list: windows of W slots aligned to A within each row of cells
 // (at most out_cap tasks; beyond it the status word records a capacity error).
 // path_filter >= 0: only rows of events whose path is path_filter get tasks
-// (a mixed batch queries its other events in other launches).
+// (a mixed batch queries its other events in other launches).  [i0, i1):
+// the cell-array entries (rows) considered (i1 < 0: to the end); a batch
+// ordered by path passes the range of its events of this path.
 void enqueue_tasks(GridBufs& g, int W, int A, Task* out, int64_t out_cap, int32_t* count_out,
-                   int32_t* d_status, cudaStream_t st, int path_filter = -1);
+                   int32_t* d_status, cudaStream_t st, int path_filter = -1, int64_t i0 = 0,
+                   int64_t i1 = -1);
 
 // The build for per-event tables already resident on the device.
 frnn_status enqueue_build_resident(GridBufs& g, const BuildOpts& o, int32_t* d_status,
@@ -155,6 +158,7 @@ struct QueryLaunch {
     int num_sms;
     unsigned long long* tc_stats = nullptr;   // [2]: pre-filter survivors, exact accepts
     int path_filter = -1;                     // batched: only events of this path
+    int64_t chunk_end = -1;                   // chunk scan: chunks [0, chunk_end) (-1: all)
     cudaEvent_t kev[2] = {nullptr, nullptr};  // optional: recorded around the main kernel
     // compact output (csr.cu): staging mode of the main kernels and the
     // selection kernel's mode (0 dense, 1 count, 2 rows at row_off)
@@ -168,8 +172,11 @@ frnn_status enqueue_grid_query(const QueryLaunch& q, cudaStream_t st, std::strin
 // pair-interleaved copy and 16-query tasks of a point set; the launch itself
 // (called by enqueue_grid_query when q.kernel == 1, inputs prepared).
 frnn_status rows_reserve(GridBufs& g, std::string& err);
+// [i0, i1): cell-array range of the events to prepare, [s0, s1): their slots
+// (negative ends: to the end of the set)
 frnn_status rows_prepare(GridBufs& g, int32_t* d_status, cudaStream_t st, std::string& err,
-                         int path_filter = -1);
+                         int path_filter = -1, int64_t i0 = 0, int64_t i1 = -1, int64_t s0 = 0,
+                         int64_t s1 = -1);
 void rows_free(GridBufs& g);
 frnn_status enqueue_row_query(const QueryLaunch& q, const QueryArgs& a, cudaStream_t st,
                               std::string& err);
@@ -189,7 +196,7 @@ void enqueue_csr_gather(const int32_t* cnt, const int64_t* offsets, const int32_
 // center_src: the grid whose per-event centres the operands use (the
 // reference grid; the set itself for self-queries).
 frnn_status tc_prepare(GridBufs& g, const GridBufs& center_src, int32_t* d_status, cudaStream_t st,
-                       std::string& err, int path_filter = -1);
+                       std::string& err, int path_filter = -1, int64_t i0 = 0, int64_t i1 = -1);
 frnn_status enqueue_tc_query(const QueryLaunch& q, cudaStream_t st, std::string& err);
 frnn_status tc_reserve(GridBufs& g, std::string& err);
 void tc_free(GridBufs& g);

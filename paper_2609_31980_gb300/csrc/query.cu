@@ -862,7 +862,7 @@ static QueryArgs query_args(const QueryLaunch& q) {
     a.ev = rs.hdr;
     a.qev = qs.hdr;
     a.nev = qs.E;
-    a.nchunks = (int32_t)qs.nchunks;
+    a.nchunks = (int32_t)(q.chunk_end >= 0 ? std::min<int64_t>(q.chunk_end, qs.nchunks) : qs.nchunks);
     a.qpts = qs.pts;
     a.qperm = qs.perm;
     a.qcell = qs.cell;
@@ -908,7 +908,7 @@ frnn_status enqueue_grid_query(const QueryLaunch& q, cudaStream_t st, std::strin
         // grids of up to four axes: the row-task kernel (query_rows.cu)
         const frnn_status s = enqueue_row_query(q, a, st, err);
         if (s != FRNN_OK) return s;
-    } else if (qs.nchunks > 0) {
+    } else if (a.nchunks > 0) {
         switch (rs.D) {
 #define FRNN_CASE(d) case d: ce = launch_grid_query_d<d>(a, q.stage, q.num_sms, st); break;
             FRNN_CASE(1) FRNN_CASE(2) FRNN_CASE(3) FRNN_CASE(4) FRNN_CASE(5) FRNN_CASE(6)

@@ -688,16 +688,20 @@ frnn_status rows_reserve(GridBufs& g, std::string& err) {
 }
 
 frnn_status rows_prepare(GridBufs& g, int32_t* d_status, cudaStream_t st, std::string& err,
-                         int path_filter) {
+                         int path_filter, int64_t i0, int64_t i1, int64_t s0, int64_t s1) {
     if (g.rows_ready) return FRNN_OK;
     frnn_status s = rows_reserve(g, err);
     if (s != FRNN_OK) return s;
-    if (g.n_total > 0)
-        launch_pdl(k_pack_pairs, dim3((unsigned)ceil_div(g.n_total / 2, 256)), dim3(256), 0, st,
-                   (const float*)g.pts, g.n_total / 2, g.DP, g.ppts);
+    // slots of the events to prepare (event regions start on even slots)
+    if (s1 < 0) s1 = g.n_total;
+    s0 = std::min(std::max<int64_t>(s0, 0), s1) & ~(int64_t)1;
+    const int64_t np = (s1 - s0) / 2;
+    if (np > 0)
+        launch_pdl(k_pack_pairs, dim3((unsigned)ceil_div(np, 256)), dim3(256), 0, st,
+                   (const float*)g.pts + s0 * g.DP, np, g.DP, g.ppts + s0 * g.DP);
     g.rtask = g.rows_rtask;   // the task builder's scratch
     enqueue_tasks(g, kTaskQueries, 1, g.row_tasks, g.rows_cap_tasks, g.scalars + kScNTasks,
-                  d_status, st, path_filter);
+                  d_status, st, path_filter, i0, i1);
     cudaError_t ce = cudaGetLastError();
     if (ce != cudaSuccess) {
         err = std::string("row-task preparation failed: ") + cudaGetErrorString(ce);

@@ -830,7 +830,8 @@ frnn_status tc_reserve(GridBufs& g, std::string& err) {
 }
 
 frnn_status tc_prepare(GridBufs& g, const GridBufs& center_src, int32_t* d_status,
-                       cudaStream_t st, std::string& err, int path_filter) {
+                       cudaStream_t st, std::string& err, int path_filter, int64_t i0,
+                       int64_t i1) {
     frnn_status s0 = tc_reserve(g, err);
     if (s0 != FRNN_OK) return s0;
     const int K = tc_k_for(g.D);
@@ -853,7 +854,7 @@ frnn_status tc_prepare(GridBufs& g, const GridBufs& center_src, int32_t* d_statu
         (void)K;
     }
     enqueue_tasks(g, kTcM, 8, g.tc_tasks, g.tc_cap_tasks, g.scalars + kScTcTasks, d_status, st,
-                  path_filter);
+                  path_filter, i0, i1);
     cudaError_t ce = cudaGetLastError();
     if (ce != cudaSuccess) {
         err = std::string("tensor-core prep launch failed: ") + cudaGetErrorString(ce);
