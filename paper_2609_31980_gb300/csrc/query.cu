@@ -595,25 +595,11 @@ __global__ void __launch_bounds__(kQueryWarps * 32, QCfg<D, STAGE>::MINB) k_grid
         // (coalesced), then the padding
         const int rstride_out = a.csr ? kCsrStageW : K;
         if constexpr (!C::PAIR_ROWS) {
-            for (int ql = 0; ql < nqc; ++ql) {
-                if ((spill_mask >> ql) & 1u) continue;
-                const int n = __shfl_sync(kFull, kept, ql);
-                uint64_t key = ~0ull;
-                if (lane < n) key = make_key(w.Ld[ql * kListStr + lane], w.Li[ql * kListStr + lane]);
-                // the network only as wide as the row needs (entries sit in
-                // lanes 0 .. n-1; wider stages would compare largest keys only)
-#pragma unroll
-                for (int k2 = 2; k2 <= 32; k2 <<= 1) {
-                    if ((k2 >> 1) >= n) break;
-#pragma unroll
-                    for (int jj = k2 >> 1; jj > 0; jj >>= 1) {
-                        const uint64_t other = __shfl_xor_sync(kFull, key, jj);
-                        const bool take_min = ((lane & jj) == 0) == ((lane & k2) == 0);
-                        // one comparison: keys are distinct (indices differ) except
-                        // the unused lanes' largest keys, which are interchangeable
-                        key = (take_min == (other < key)) ? other : key;
-                    }
-                }
+            // two rows at a time, each in its own key: the two networks'
+            // shuffle-compare chains are independent, so their latencies
+            // overlap (a full-width network sorts any row, so the pair takes
+            // the wider row's width)
+            auto write_row = [&](int ql, int n, uint64_t key) {
                 const int cK = min(n, K);
                 const int qo = __shfl_sync(kFull, qorig, ql);
                 int32_t* irow = oidx + (int64_t)qo * rstride_out;
@@ -629,6 +615,34 @@ __global__ void __launch_bounds__(kQueryWarps * 32, QCfg<D, STAGE>::MINB) k_grid
                     irow[e2] = -1;
                     drow[e2] = INFINITY;
                 }
+            };
+            const unsigned rows_left = ((nqc >= 32 ? 0xffffffffu : ((1u << nqc) - 1u))) & ~spill_mask;
+            unsigned todo = rows_left;
+            while (todo) {
+                const int qa = __ffs(todo) - 1;
+                todo &= todo - 1u;
+                const int qb = todo ? __ffs(todo) - 1 : -1;
+                if (todo) todo &= todo - 1u;
+                const int na = __shfl_sync(kFull, kept, qa);
+                const int nb = __shfl_sync(kFull, kept, qb < 0 ? qa : qb);
+                uint64_t ka = ~0ull, kb = ~0ull;
+                if (lane < na) ka = make_key(w.Ld[qa * kListStr + lane], w.Li[qa * kListStr + lane]);
+                if (qb >= 0 && lane < nb) kb = make_key(w.Ld[qb * kListStr + lane], w.Li[qb * kListStr + lane]);
+                const int width = qb >= 0 ? max(na, nb) : na;
+#pragma unroll
+                for (int k2 = 2; k2 <= 32; k2 <<= 1) {
+                    if ((k2 >> 1) >= width) break;
+#pragma unroll
+                    for (int jj = k2 >> 1; jj > 0; jj >>= 1) {
+                        const uint64_t oa = __shfl_xor_sync(kFull, ka, jj);
+                        const uint64_t ob = __shfl_xor_sync(kFull, kb, jj);
+                        const bool take_min = ((lane & jj) == 0) == ((lane & k2) == 0);
+                        ka = (take_min == (oa < ka)) ? oa : ka;
+                        kb = (take_min == (ob < kb)) ? ob : kb;
+                    }
+                }
+                write_row(qa, na, ka);
+                if (qb >= 0) write_row(qb, nb, kb);
             }
         } else {
             // two rows at a time, one per half-warp, when both hold at most
