@@ -1,4 +1,4 @@
-"""The grid kernel's per-row sort, checked on the CPU lane by lane.
+"""The grid kernels' per-row sort, checked on the CPU lane by lane.
 
 A query row's entries sit in lanes 0 .. n-1 of a warp as 64-bit keys
 (d2 bits << 32 | index; a rejected entry is +inf with index 0, so all
@@ -7,8 +7,11 @@ kernel sorts them with a bitonic network across the lanes, only as wide as
 the row (stages whose half-size reaches n are skipped), one comparison per
 step (equal keys are interchangeable).  For D >= 10 two rows of at most 16
 entries are sorted at once, one per half-warp, every step taking its
-direction from the lane index within the half.  Checked here by simulating
-the 32 lanes for every row length and random keys with ties."""
+direction from the lane index within the half.  The chunk kernel sorts two
+rows at once, their networks' steps interleaved, at the wider row's width
+(checked below: a wider network leaves a row's result unchanged).  Checked
+here by simulating the 32 lanes for every row length and random keys with
+ties."""
 import numpy as np
 import pytest
 
@@ -78,3 +81,21 @@ def test_accepted_keys_precede_rejected_ones():
     out = network(keys, 20, False)
     acc = int((keys[:20] < REJECT).sum())
     assert (out[:acc] < REJECT).all() and (out[acc:20] == REJECT).all()
+
+
+def test_two_rows_sorted_at_the_wider_width():
+    # the chunk kernel sorts two rows together with the wider row's width:
+    # each row ends sorted exactly as alone
+    g = np.random.default_rng(4100)
+    for _ in range(500):
+        rows = []
+        for _u in range(2):
+            keys = np.full(32, EMPTY)
+            n = int(g.integers(0, 33))
+            keys[:n] = row_keys(g, n)
+            rows.append((keys, n))
+        width = max(rows[0][1], rows[1][1])
+        for keys, n in rows:
+            out = network(keys, width, False)
+            assert np.array_equal(out, network(keys, n, False))
+            assert np.array_equal(out[:n], np.sort(keys[:n]))
