@@ -60,22 +60,43 @@ __device__ __forceinline__ int find_event64(const int64_t* starts, int E, int64_
     return lo;
 }
 
-// Stage nf consecutive floats of a row-major point array into shared memory,
-// using 16-byte vector loads for the aligned body.
-__device__ __forceinline__ void stage_floats(float* sm, const float* src, int nf) {
+// Staged point rows in shared memory: float j of the block's rows sits at
+// j + j / 32 when D is a multiple of 4 (one padding word per 32), else at j,
+// so that a warp reading coordinate k of 32 consecutive rows (stride D) hits
+// distinct banks for D = 4, 8, 16 and at most two per bank otherwise.
+__device__ __forceinline__ int stage_slot(int j, bool pad) { return pad ? j + (j >> 5) : j; }
+__host__ __device__ constexpr size_t staged_floats(int D) {
+    return (size_t)kBuildPtsPerBlock * D + (size_t)kBuildPtsPerBlock * D / 32 + 1;
+}
+
+// Row i of the staged rows, indexed by coordinate.
+struct StagedRow {
+    const float* sm;
+    int j0;
+    bool pad;
+    __device__ __forceinline__ float operator[](int k) const { return sm[stage_slot(j0 + k, pad)]; }
+};
+
+// Stage nf consecutive floats of a row-major point array into shared memory
+// (at stage_slot), using 16-byte vector loads for the aligned body.
+__device__ __forceinline__ void stage_floats(float* sm, const float* src, int nf, bool pad) {
     const uintptr_t a = reinterpret_cast<uintptr_t>(src);
     int head = (int)(((16u - (uint32_t)(a & 15u)) & 15u) >> 2);
     if (a & 3u) head = nf;   // not even 4-byte aligned: scalar path (cannot happen for float*)
     head = min(head, nf);
-    for (int i = threadIdx.x; i < head; i += blockDim.x) sm[i] = __ldg(src + i);
+    for (int i = threadIdx.x; i < head; i += blockDim.x) sm[stage_slot(i, pad)] = __ldg(src + i);
     const int n4 = (nf - head) >> 2;
     const float4* s4 = reinterpret_cast<const float4*>(src + head);
     for (int i = threadIdx.x; i < n4; i += blockDim.x) {
         float4 v = __ldg(s4 + i);
-        float* d = sm + head + 4 * i;
-        d[0] = v.x; d[1] = v.y; d[2] = v.z; d[3] = v.w;
+        const int j = head + 4 * i;
+        sm[stage_slot(j, pad)] = v.x;
+        sm[stage_slot(j + 1, pad)] = v.y;
+        sm[stage_slot(j + 2, pad)] = v.z;
+        sm[stage_slot(j + 3, pad)] = v.w;
     }
-    for (int i = head + 4 * n4 + threadIdx.x; i < nf; i += blockDim.x) sm[i] = __ldg(src + i);
+    for (int i = head + 4 * n4 + threadIdx.x; i < nf; i += blockDim.x)
+        sm[stage_slot(i, pad)] = __ldg(src + i);
 }
 
 // Cell coordinate along one gridded axis: floor(fl(fl(x' - lo) * inv_h))
@@ -88,7 +109,8 @@ __device__ __forceinline__ int cell_coord(float x, float lo, float hi, float inv
     return min(max(c, 0), dim - 1);
 }
 
-__device__ __forceinline__ int point_cell(const float* p, const EventHdr& h) {
+template <class Row>
+__device__ __forceinline__ int point_cell(const Row& p, const EventHdr& h) {
     int c = 0, stride = 1;
 #pragma unroll
     for (int a = 0; a < kMaxAxes; ++a) {
@@ -156,14 +178,15 @@ __global__ void __launch_bounds__(kBuildPtsPerBlock, 6) k_bbox(EventHdr* hdr,
     const int64_t p0 = (int64_t)(blockIdx.x - blk_start[e]) * kBuildPtsPerBlock;
     const int np = (int)min((int64_t)kBuildPtsPerBlock, h.n - p0);
     if (threadIdx.x == 0) red_bad = 0;
-    if (np > 0) stage_floats(sm, h.refs + p0 * D, np * D);
+    const bool pad = (D & 3) == 0;
+    if (np > 0) stage_floats(sm, h.refs + p0 * D, np * D, pad);
     __syncthreads();
     float mn[kMaxD], mx[kMaxD];
     bool bad = false;
 #pragma unroll
     for (int k = 0; k < kMaxD; ++k) { mn[k] = INFINITY; mx[k] = -INFINITY; }
     if ((int)threadIdx.x < np) {
-        const float* p = sm + threadIdx.x * D;
+        const StagedRow p{sm, (int)threadIdx.x * D, pad};
 #pragma unroll
         for (int k = 0; k < kMaxD; ++k) {
             if (k < D) {
@@ -472,11 +495,12 @@ __global__ void __launch_bounds__(kBuildPtsPerBlock) k_cellid(const EventHdr* hd
     const EventHdr& h = hdr[e];
     const int64_t p0 = (int64_t)(blockIdx.x - blk_start[e]) * kBuildPtsPerBlock;
     const int np = (int)min((int64_t)kBuildPtsPerBlock, h.n - p0);
-    if (np > 0) stage_floats(sm, h.refs + p0 * D, np * D);
+    const bool pad = (D & 3) == 0;
+    if (np > 0) stage_floats(sm, h.refs + p0 * D, np * D, pad);
     __syncthreads();
     const int i = threadIdx.x;
     if (i >= np) return;
-    const float* p = sm + i * D;
+    const StagedRow p{sm, i * D, pad};
     int c = 0;
     if (check_finite) {
         bool bad = false;
@@ -516,7 +540,8 @@ __global__ void __launch_bounds__(kBuildPtsPerBlock) k_scatter(const EventHdr* h
         float4* dst = reinterpret_cast<float4*>(pts + slot * DP);
         for (int j = 0; j < DP / 4; ++j) dst[j] = make_float4(nan, nan, nan, nan);
     }
-    if (np > 0) stage_floats(sm, h.refs + p0 * D, np * D);
+    const bool pad = (D & 3) == 0;
+    if (np > 0) stage_floats(sm, h.refs + p0 * D, np * D, pad);
     __syncthreads();
     const int i = threadIdx.x;
     if (i >= np) return;
@@ -525,7 +550,7 @@ __global__ void __launch_bounds__(kBuildPtsPerBlock) k_scatter(const EventHdr* h
     const int64_t slot = (int64_t)cstart[h.cell_off + c] + rnk[gi];
     perm[slot] = (int32_t)(p0 + i);
     cell[slot] = c;
-    const float* src = sm + i * D;
+    const StagedRow src{sm, i * D, pad};
     float4* dst = reinterpret_cast<float4*>(pts + slot * DP);
     for (int j = 0; j < DP / 4; ++j) {
         float4 v;
@@ -685,34 +710,41 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const int32_t* dat
     }
 }
 
+// Shared-memory slot of chunk entry i: one padding word per 32 entries, so
+// that both the coalesced pass (entry k * 256 + t on thread t) and the
+// per-thread pass (entries 8t .. 8t + 7 on thread t) touch 32 distinct banks
+// per warp access.
+__device__ __forceinline__ int scan_slot(int i) { return i + (i >> 5); }
+constexpr int kScanSlots = kScanChunk + kScanChunk / 32;
+
 // Scan one chunk of kScanChunk values in place with an added offset.
 __device__ void scan_chunk(int32_t* data, int64_t n, int64_t base, int32_t offset,
                            int32_t* total_out) {
-    __shared__ int32_t buf[kScanChunk];
+    __shared__ int32_t buf[kScanSlots];
     __shared__ int32_t warp_tot[kScanThreads / 32];
     __shared__ int32_t btot;
     for (int k = 0; k < kScanItems; ++k) {
         int64_t i = base + (int64_t)k * kScanThreads + threadIdx.x;
-        buf[k * kScanThreads + threadIdx.x] = i < n ? data[i] : 0;
+        buf[scan_slot(k * kScanThreads + threadIdx.x)] = i < n ? data[i] : 0;
     }
     __syncthreads();
     int32_t v[kScanItems];
     int32_t t = 0;
 #pragma unroll
     for (int k = 0; k < kScanItems; ++k) {
-        v[k] = buf[threadIdx.x * kScanItems + k];
+        v[k] = buf[scan_slot(threadIdx.x * kScanItems + k)];
         t += v[k];
     }
     int32_t ex = block_exclusive_scan(t, warp_tot, &btot) + offset;
 #pragma unroll
     for (int k = 0; k < kScanItems; ++k) {
-        buf[threadIdx.x * kScanItems + k] = ex;
+        buf[scan_slot(threadIdx.x * kScanItems + k)] = ex;
         ex += v[k];
     }
     __syncthreads();
     for (int k = 0; k < kScanItems; ++k) {
         int64_t i = base + (int64_t)k * kScanThreads + threadIdx.x;
-        if (i < n) data[i] = buf[k * kScanThreads + threadIdx.x];
+        if (i < n) data[i] = buf[scan_slot(k * kScanThreads + threadIdx.x)];
     }
     if (total_out && threadIdx.x == 0) *total_out = btot + offset;
 }
@@ -999,7 +1031,7 @@ frnn_status enqueue_build(GridBufs& g, const float* const* refs, const BuildOpts
     const int64_t init_n = std::max<int64_t>(g.L, (int64_t)E * kBBoxCopies * kBBoxStride);
     launch_pdl(k_init, dim3(std::min<unsigned>(blocks_for(init_n, 256), 4096)), dim3(256), 0, st, 
         g.cstart, g.L, g.bbox, E, g.scalars, bbmin, bbmax, t1, g.hdr, g.blk_start, g.cell_off);
-    const size_t smem_pts = sizeof(float) * kBuildPtsPerBlock * D;
+    const size_t smem_pts = sizeof(float) * staged_floats(D);
     if (params_from) {
         launch_pdl(k_copy_params, dim3(blocks_for(E, 128)), dim3(128), 0, st, g.hdr, params_from->hdr, E,
                    g.cstart);
@@ -1030,7 +1062,7 @@ frnn_status enqueue_build_resident(GridBufs& g, const BuildOpts& o, int32_t* d_s
     launch_pdl(k_init, dim3(std::min<unsigned>(blocks_for(init_n, 256), 4096)), dim3(256), 0, st, 
         g.cstart, g.L, g.bbox, E, g.scalars, bbmin, bbmax, OneEventTables{}, g.hdr, g.blk_start,
         g.cell_off);
-    const size_t smem_pts = sizeof(float) * kBuildPtsPerBlock * D;
+    const size_t smem_pts = sizeof(float) * staged_floats(D);
     launch_pdl(k_bbox, dim3((unsigned)g.nblk), dim3(kBuildPtsPerBlock), smem_pts, st, g.hdr, g.blk_start, E, D,
                g.bbox, d_status, o.r, o.m, o.axes_mode, o.naxes, g.cstart);
     enqueue_sort(g, smem_pts, 0, d_status, st);
