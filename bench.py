@@ -188,10 +188,10 @@ def _cell_cap(N: int, naxes: int) -> int:
 
 def _scan_launches(L: int) -> int:
     """Launches of one exclusive scan of L entries (blocks of 2048): one for
-    a single block, else the reduce pass, a scan of the block sums beyond 512
-    blocks, the down pass."""
+    a single block, else the reduce pass, a scan of the block sums beyond
+    4096 blocks, the down pass."""
     nb = (L + 2047) // 2048
-    return 1 if nb == 1 else (2 if nb <= 512 else 3)
+    return 1 if nb == 1 else (2 if nb <= 4096 else 3)
 
 
 def launches_per_step(N: int, D: int, path: str = "grid", naxes_requested: int = 0) -> int:

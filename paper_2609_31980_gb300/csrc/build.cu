@@ -757,10 +757,11 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_single(int32_t* data, int
 }
 
 // Down pass.  summed == 0: block b first sums the partials of the blocks
-// before it (used while there are at most kScanSumParts of them), then scans
-// its chunk with that offset; the last block also writes the total.
-// summed == 1: the partials were already scanned (k_scan_parts).
-constexpr int kScanSumParts = 512;
+// before it (used while there are at most kScanSumParts of them: at most 16
+// L2 reads per thread, cheaper than a launch of the one-block partials scan),
+// then scans its chunk with that offset; the last block also writes the
+// total.  summed == 1: the partials were already scanned (k_scan_parts).
+constexpr int kScanSumParts = 4096;
 
 __global__ void __launch_bounds__(kScanThreads) k_scan_down(int32_t* data, int64_t n,
                                                             const int32_t* parts, int32_t* total,
