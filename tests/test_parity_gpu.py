@@ -733,3 +733,79 @@ def test_four_axes_event_500k_x12_equal_to_three_axes(ctx, path):
     _assert_rows_equal(got, ref)
     rows = _sample_rows(len(w.points), 300, 814)
     _assert_rows_equal(got, oracle.self_query(w.points, w.r, w.K, rows=rows), rows)
+
+
+# ------------------------------------------------------------ randomized sweep
+
+def _random_case(g):
+    """One seeded configuration: size, dimension, shape of the data, scale and
+    offset of the coordinates, radius relative to the spacing, K."""
+    N = int(g.choice([1, 2, 3, 17, 100, 777, 2048, 5000]))
+    D = int(g.integers(1, 17))
+    kind = g.choice(["uniform", "clusters", "lattice", "duplicates", "line"])
+    if kind == "uniform":
+        x = g.uniform(-1, 1, size=(N, D))
+    elif kind == "clusters":
+        c = g.uniform(-1, 1, size=(max(1, N // 20), D))
+        x = c[g.integers(0, len(c), size=N)] + g.normal(0, 0.03, size=(N, D))
+    elif kind == "lattice":
+        x = g.integers(0, 6, size=(N, D)) * 0.125
+    elif kind == "duplicates":
+        base = g.uniform(-1, 1, size=(max(1, N // 4), D))
+        x = base[g.integers(0, len(base), size=N)]
+    else:   # points on a line: one long axis, the others constant
+        x = np.zeros((N, D))
+        x[:, int(g.integers(0, D))] = g.uniform(-3, 3, size=N)
+    scale = float(g.choice([1e-3, 1.0, 37.0]))
+    offset = float(g.choice([0.0, 1.0, -250.0, 1e4]))
+    pts = (x * scale + offset).astype(np.float32)
+    spacing = scale * (2.0 / max(N, 1) ** (1.0 / D))
+    r = float(np.float32(spacing * g.choice([0.3, 1.0, 2.5, 6.0])))
+    if kind == "lattice":
+        r = float(np.float32(0.125 * scale * g.choice([1, 2])))   # exactly on lattice distances
+    K = int(g.choice([1, 5, 32, 33, 100, 200]))
+    return pts, max(r, 1e-6), K, kind
+
+
+@pytest.mark.parametrize("seed", range(24))
+def test_random_configurations_match_oracle(ctx, seed):
+    # every row of a seeded random configuration, through the default path
+    # and the grid path, against the oracle; plus cross-set queries drawn
+    # from the same recipe
+    import torch
+    g = np.random.default_rng(7000 + seed)
+    pts, r, K, kind = _random_case(g)
+    want = oracle.self_query(pts, r, K)
+    for path in ("auto", "grid"):
+        _assert_rows_equal(_gpu_self(ctx, pts, r, K, path=path), want)
+    if len(pts) >= 2:
+        qs = pts[g.permutation(len(pts))[: max(1, len(pts) // 3)]].copy()
+        qs += np.float32(r * 0.5) * g.standard_normal(qs.shape).astype(np.float32)
+        gr = ctx.build_grid(torch.from_numpy(pts).cuda(), r)
+        c, i, d = ctx.query(gr, torch.from_numpy(qs).cuda(), r, K, self_query=False, path="grid")
+        ctx.sync()
+        _assert_rows_equal((c.cpu().numpy(), i.cpu().numpy(), d.cpu().numpy()),
+                           oracle.frnn(qs, pts, r, K))
+        gr.close()
+
+
+def test_random_batches_match_oracle(ctx):
+    # batches of random events of mixed sizes and shapes (one D per batch)
+    import torch
+    g = np.random.default_rng(7100)
+    for rep in range(4):
+        D = int(g.integers(1, 17))
+        evs, rs = [], []
+        while len(evs) < 6:
+            pts, r, K, kind = _random_case(g)
+            if pts.shape[1] != D:
+                pts = np.ascontiguousarray(
+                    np.resize(pts, (pts.shape[0], D)).astype(np.float32))
+            evs.append(pts)
+        r = float(np.float32(0.1 * float(np.std(np.concatenate(evs))) + 1e-3))
+        K = int(g.choice([8, 64]))
+        outs = ctx.query_batched([torch.from_numpy(p).cuda() for p in evs], r, K, path="auto")
+        ctx.sync()
+        for p, (c, i, d) in zip(evs, outs):
+            _assert_rows_equal((c.cpu().numpy(), i.cpu().numpy(), d.cpu().numpy()),
+                               oracle.self_query(p, r, K))
