@@ -102,11 +102,13 @@ frnn_status frnn_destroy(frnn_ctx* ctx);
  *   grid  in/out.  If *grid is NULL a new grid is allocated.  If *grid is a
  *         grid from this context with D equal and capacity >= N, it is rebuilt
  *         in place without allocating (the previous contents are replaced).
- * The grid bins at most 4 coordinates (the last min(D, 4) by default; see
- * FRNN_OPT_GRID_NAXES and FRNN_OPT_GRID_AXES) with cells of edge
- * (r/m)(1+2^-10), m = the cell-multiple option, enlarged when needed so that
- * the cell count stays bounded; the choice never changes results (the cell
- * assignment is proven conservative).  A non-finite coordinate makes frnn_sync return
+ * The grid bins at most 5 coordinates (by default up to D = 8 the last
+ * min(D, 5), or the last 4 when the cell budget would make five-axis cells
+ * too coarse; from D = 9 the last 4; see FRNN_OPT_GRID_NAXES and
+ * FRNN_OPT_GRID_AXES) with cells of edge (r/m)(1+2^-10), m = the
+ * cell-multiple option, enlarged when needed so that the cell count stays
+ * bounded; the choice never changes results (the cell assignment is proven
+ * conservative).  A non-finite coordinate makes frnn_sync return
  * FRNN_ERR_NONFINITE and later queries on the grid return no neighbours.
  */
 frnn_status frnn_build_grid(frnn_ctx* ctx, const float* refs, int64_t N, int D, float r,
@@ -337,12 +339,16 @@ typedef enum frnn_option {
                                  with frnn_kernel_times; 0 (default): off.
                                  Setting it discards recorded pairs. */
     FRNN_OPT_GRID_NAXES = 10, /* gridded coordinates: 1..5 (at most D); 0
-                                 (default): autotuned, else the build's choice
-                                 between min(D, 5) and one fewer (the smaller
-                                 expected neighbourhood under the cell
-                                 budget).  The cell multiple is lowered until
-                                 the neighbour rows, (2m+1)^(axes-1), are at
-                                 most 128. */
+                                 (default): autotuned, else up to D = 8 the
+                                 build's choice between min(D, 5) and one
+                                 fewer (the smaller expected neighbourhood
+                                 under the cell budget), from D = 9 four.
+                                 Grids requested with 1..4 axes are scanned by
+                                 16-query row tasks, five-axis and automatic
+                                 ones by 16-query chunks.  The cell multiple
+                                 is lowered until the neighbour rows,
+                                 (2m+1)^(axes-1), are at most 32 (row tasks)
+                                 or 128 (chunks). */
     FRNN_OPT_STAGING = 11     /* candidate staging of the grid scan: 1 each lane
                                  loads its candidate's row from global memory
                                  (L2), the next round in flight; 2 bulk copies

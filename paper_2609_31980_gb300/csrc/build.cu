@@ -856,7 +856,7 @@ void grid_free(GridBufs& g) {
 frnn_status grid_alloc(GridBufs& g, int E, const int64_t* n, int D, std::string& err,
                        const int64_t* caps, int naxes) {
     const int DP = padded_dim(D);
-    int64_t n_total = 0, L = 0, task_cap = 0, nblk = 0, nchunks = 0;
+    int64_t n_total = 0, L = 0, nblk = 0, nchunks = 0;
     g.h_hdr.assign(E, EventHdr{});
     g.h_blk_start.assign(E + 1, 0);
     g.h_cell_off.assign(E + 1, 0);
@@ -873,12 +873,11 @@ frnn_status grid_alloc(GridBufs& g, int E, const int64_t* n, int D, std::string&
         g.h_cell_off[e] = L;
         n_total += (n[e] + 1) & ~(int64_t)1;   // pair-aligned event regions
         L += cap + 1;
-        task_cap += n[e] / kTaskQueries + cap + 2;
         nblk += std::max<int64_t>(1, ceil_div(n[e], kBuildPtsPerBlock));
     }
     g.h_blk_start[E] = (int32_t)nblk;
     g.h_cell_off[E] = L;
-    if (n_total >= INT32_MAX || L >= ((int64_t)1 << 30) || task_cap >= INT32_MAX ||
+    if (n_total >= INT32_MAX || L >= ((int64_t)1 << 30) ||
         nblk >= INT32_MAX || nchunks >= INT32_MAX) {
         err = "problem too large for one call (points, cells or tasks exceed the limits)";
         return FRNN_ERR_INVALID_ARG;
@@ -888,7 +887,6 @@ frnn_status grid_alloc(GridBufs& g, int E, const int64_t* n, int D, std::string&
     g.DP = DP;
     g.n_total = n_total;
     g.L = L;
-    g.task_cap = task_cap;
     g.nblk = nblk;
     g.nparts = scan_parts_needed(L);
     g.nchunks = nchunks;
@@ -924,7 +922,7 @@ frnn_status grid_alloc(GridBufs& g, int E, const int64_t* n, int D, std::string&
         if (ce != cudaSuccess) {
             cudaGetLastError();
             err = std::string("cudaMalloc of grid buffers failed: ") + cudaGetErrorString(ce);
-            g.cap_n = g.cap_L = g.cap_tasks = g.cap_E = g.cap_blk = 0;
+            g.cap_n = g.cap_L = g.cap_E = g.cap_blk = 0;
             return FRNN_ERR_OUT_OF_MEMORY;
         }
         char* b = static_cast<char*>(base);
@@ -941,13 +939,11 @@ frnn_status grid_alloc(GridBufs& g, int E, const int64_t* n, int D, std::string&
         g.rnk = reinterpret_cast<int32_t*>(b + o_rnk);
         g.cstart = reinterpret_cast<int32_t*>(b + o_cst);
         g.rtask = nullptr;   // the tensor-core operands carry the task builder's scratch
-        g.tasks = nullptr;
         g.ovf = reinterpret_cast<Overflow*>(b + o_ovf);
         g.scalars = reinterpret_cast<int32_t*>(b + o_sc);
         g.parts = reinterpret_cast<int32_t*>(b + o_parts);
         g.cap_n = n_total;
         g.cap_L = L;
-        g.cap_tasks = task_cap;
         g.cap_E = E;
         g.cap_blk = nblk;
     }

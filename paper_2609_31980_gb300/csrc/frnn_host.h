@@ -18,7 +18,6 @@ struct GridBufs {
     int D = 0, DP = 0;      // dimensions, padded row length (floats)
     int64_t n_total = 0;    // points over all events
     int64_t L = 0;          // cell-array entries: sum over events of (cell_cap + 1)
-    int64_t task_cap = 0;   // warp-task capacity
     int64_t nblk = 0;       // blocks of the per-point build kernels
     int64_t nparts = 0;     // scan partial sums needed
     int64_t nchunks = 0;    // query chunks (kChunkQ slots) over all events
@@ -29,7 +28,7 @@ struct GridBufs {
     // allocation (reused when large enough)
     void* base = nullptr;
     size_t bytes = 0;
-    int64_t cap_n = 0, cap_L = 0, cap_tasks = 0, cap_E = 0, cap_blk = 0;
+    int64_t cap_n = 0, cap_L = 0, cap_E = 0, cap_blk = 0;
     void* h_pinned = nullptr;      // page-locked host mirror of the small tables
     size_t h_pinned_bytes = 0;
     cudaEvent_t h_pinned_free = nullptr;   // last upload from the mirror has run
@@ -46,7 +45,6 @@ struct GridBufs {
     int32_t* rnk = nullptr;        // [n_total] input order -> rank inside its cell
     int32_t* cstart = nullptr;     // [L] cell counts, then (scanned) global start slots
     int32_t* rtask = nullptr;      // [L] per-row task counts, then task starts (tensor-core tiles)
-    Task* tasks = nullptr;         // [task_cap] (unused by the grid query, which takes chunks)
     Overflow* ovf = nullptr;       // [n_total]
     int32_t* scalars = nullptr;    // [kScalars] counters (below)
     int32_t* parts = nullptr;      // [nparts] scan partial sums

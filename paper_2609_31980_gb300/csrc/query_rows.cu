@@ -662,6 +662,10 @@ frnn_status rows_reserve(GridBufs& g, std::string& err) {
     int64_t tcap = 0;
     for (int e = 0; e < g.E; ++e)
         tcap += g.h_hdr[e].n / kTaskQueries + std::min<int64_t>(g.h_hdr[e].cell_cap, g.h_hdr[e].n) + 2;
+    if (tcap >= INT32_MAX) {
+        err = "too many row tasks for one call";
+        return FRNN_ERR_INVALID_ARG;
+    }
     const int64_t n = std::max<int64_t>(g.n_total, 2);
     if (g.rows_base && g.rows_cap_n >= n && g.rows_cap_tasks >= tcap && g.rows_cap_L >= g.L)
         return FRNN_OK;

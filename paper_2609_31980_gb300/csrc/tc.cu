@@ -786,6 +786,10 @@ frnn_status tc_reserve(GridBufs& g, std::string& err) {
     for (int e = 0; e < g.E; ++e)
         tcap += g.h_hdr[e].n / kTcM + g.h_hdr[e].n / 64 +
                 std::min<int64_t>(g.h_hdr[e].cell_cap, g.h_hdr[e].n) + 2;
+    if (tcap >= INT32_MAX) {
+        err = "too many tensor-core tiles for one call";
+        return FRNN_ERR_INVALID_ARG;
+    }
     if (g.tc_base && g.tc_K == K && g.tc_cap_rows >= rows && g.tc_cap_tasks >= tcap &&
         g.tc_cap_E >= g.E && g.tc_cap_L >= g.L) {
         g.rtask = g.tc_rtask;
