@@ -399,9 +399,11 @@ frnn_status frnn_query_csr_fill(frnn_ctx* ctx, int32_t* idx, float* dist2);
  * The whole path with HOST buffers and compact output, in one call: copies
  * refs to the device, builds the grid, runs the count pass of
  * frnn_query_csr_count (self-query) and, if the rows fit, the fill pass, then
- * copies the rows back; synchronises before it returns.  This is the shape of
- * the paper's NumPy binding (Sec. 4.2: host transfers and compact host
- * output).
+ * copies the rows back; synchronises before it returns.  The fill's gather
+ * starts before the edge count reaches the host, into device rows sized for
+ * min(edge_cap, N K) entries (when those take at most 1 GiB; else it waits
+ * for the count and is sized by it).  This is the shape of the paper's NumPy
+ * binding (Sec. 4.2: host transfers and compact host output).
  *   refs_host     [N, D] float32 in
  *   offsets_host  [N + 1] int64 out: row i at [offsets[i], offsets[i+1])
  *   idx_host, dist2_host  [edge_cap] out (may be NULL when edge_cap is 0)

@@ -65,6 +65,7 @@ struct frnn_ctx {
     // be captured)
     cudaStream_t gstream = nullptr;
     cudaEvent_t g_in = nullptr, g_out = nullptr;
+    cudaEvent_t ev_edges = nullptr;   // host-buffer compact path: edge count copied back
     cudaGraphExec_t graph = nullptr;
     std::vector<frnn_event> g_ev;
     int g_D = 0, g_K = 0;
@@ -399,6 +400,16 @@ frnn_status frnn_grid_destroy(frnn_grid* grid) {
     return FRNN_OK;
 }
 
+// The host-buffer paths keep one grid in the context; a call of another
+// dimension cannot rebuild it in place (frnn_build_grid would make a new grid
+// and drop this one), so it is released first.
+static void release_host_grid_if_other_dim(frnn_ctx* ctx, int D) {
+    if (ctx->host_grid && ctx->host_grid->D != D) {
+        frnn_grid_destroy(ctx->host_grid);
+        ctx->host_grid = nullptr;
+    }
+}
+
 frnn_status frnn_destroy(frnn_ctx* ctx) {
     if (!ctx) return FRNN_OK;
     cudaStreamSynchronize(ctx->stream);
@@ -407,6 +418,7 @@ frnn_status frnn_destroy(frnn_ctx* ctx) {
     if (ctx->gstream) cudaStreamDestroy(ctx->gstream);
     if (ctx->g_in) cudaEventDestroy(ctx->g_in);
     if (ctx->g_out) cudaEventDestroy(ctx->g_out);
+    if (ctx->ev_edges) cudaEventDestroy(ctx->ev_edges);
     for (cudaEvent_t e : ctx->kev) cudaEventDestroy(e);
     if (ctx->host_grid) {
         frnn_grid* g = ctx->host_grid;
@@ -627,31 +639,44 @@ static frnn_status csr_reserve(frnn_ctx* ctx, int64_t M) {
     return FRNN_OK;
 }
 
+// The count pass of the compact output, enqueued: the search with staged
+// rows, the offset scan, and the copy of the edge count into page-locked
+// *h_edges (valid once the stream reaches it).  q: the search's launch.
+static frnn_status csr_count_enqueue(frnn_ctx* ctx, const frnn_grid* grid, const float* queries,
+                                     int64_t M, float r, int K, unsigned flags, int64_t* offsets,
+                                     int32_t* degree, int64_t** h_edges, QueryLaunch* q) {
+    if (!grid || grid->ctx != ctx) return fail(ctx, FRNN_ERR_INVALID_ARG, "grid is not of ctx");
+    int32_t dummy = 0;   // check_query_args wants row outputs: the staging is ours
+    frnn_status s = check_query_args(ctx, M, r, K, flags, &dummy, &dummy, reinterpret_cast<float*>(&dummy));
+    if (s != FRNN_OK) return s;
+    s = csr_reserve(ctx, M);
+    if (s != FRNN_OK) return s;
+    *q = QueryLaunch{};
+    if (M > 0) {
+        const CsrPass cp{degree};
+        s = query_impl(ctx, grid, queries, M, r, K, flags, ctx->csr_cnt, ctx->csr_idx,
+                       ctx->csr_d2, &cp, q);
+        if (s != FRNN_OK) return s;
+    }
+    enqueue_csr_offsets(ctx->csr_cnt, M, ctx->csr_parts, offsets, ctx->stream);
+    *h_edges = reinterpret_cast<int64_t*>(ctx->h_status + 2);
+    cudaError_t e = cudaMemcpyAsync(*h_edges, offsets + M, sizeof(int64_t), cudaMemcpyDeviceToHost,
+                                    ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "reading the edge count");
+    return FRNN_OK;
+}
+
 frnn_status frnn_query_csr_count(frnn_ctx* ctx, const frnn_grid* grid, const float* queries,
                                  int64_t M, float r, int K, unsigned flags, int64_t* offsets,
                                  int32_t* degree, int64_t* n_edges) {
     if (!ctx) return FRNN_ERR_INVALID_ARG;
     ctx->csr_pending = false;
-    if (!grid || grid->ctx != ctx) return fail(ctx, FRNN_ERR_INVALID_ARG, "grid is not of ctx");
     if (!offsets || !n_edges) return fail(ctx, FRNN_ERR_INVALID_ARG, "offsets or n_edges is NULL");
-    int32_t dummy = 0;   // check_query_args wants row outputs: the staging is ours
-    frnn_status s = check_query_args(ctx, M, r, K, flags, &dummy, &dummy, reinterpret_cast<float*>(&dummy));
-    if (s != FRNN_OK) return s;
     *n_edges = 0;
-    s = csr_reserve(ctx, M);
-    if (s != FRNN_OK) return s;
+    int64_t* h_edges = nullptr;
     QueryLaunch q{};
-    if (M > 0) {
-        const CsrPass cp{degree};
-        s = query_impl(ctx, grid, queries, M, r, K, flags, ctx->csr_cnt, ctx->csr_idx,
-                       ctx->csr_d2, &cp, &q);
-        if (s != FRNN_OK) return s;
-    }
-    enqueue_csr_offsets(ctx->csr_cnt, M, ctx->csr_parts, offsets, ctx->stream);
-    int64_t* h_edges = reinterpret_cast<int64_t*>(ctx->h_status + 2);
-    cudaError_t e = cudaMemcpyAsync(h_edges, offsets + M, sizeof(int64_t), cudaMemcpyDeviceToHost,
-                                    ctx->stream);
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "reading the edge count");
+    frnn_status s = csr_count_enqueue(ctx, grid, queries, M, r, K, flags, offsets, degree, &h_edges, &q);
+    if (s != FRNN_OK) return s;
     s = frnn_sync(ctx);
     if (s != FRNN_OK) return s;
     *n_edges = *h_edges;
@@ -943,6 +968,7 @@ frnn_status frnn_self_query_host(frnn_ctx* ctx, const float* refs_host, int64_t 
                          : reinterpret_cast<float*>(b + al(b_in) + al(b_cnt) + al(b_row));
     cudaError_t e = cudaMemcpyAsync(d_in, refs_host, b_in, cudaMemcpyHostToDevice, ctx->stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "H2D copy");
+    release_host_grid_if_other_dim(ctx, D);
     s = frnn_build_grid(ctx, d_in, N, D, r, &ctx->host_grid);
     if (s != FRNN_OK) return s;
     s = frnn_query(ctx, ctx->host_grid, d_in, N, r, K, flags | FRNN_SELF_QUERY, d_cnt, d_idx,
@@ -1005,32 +1031,75 @@ frnn_status frnn_self_query_host_csr(frnn_ctx* ctx, const float* refs_host, int6
     int64_t* d_off = reinterpret_cast<int64_t*>(static_cast<char*>(ctx->hp_buf) + al(b_in));
     cudaError_t e = cudaMemcpyAsync(d_in, refs_host, b_in, cudaMemcpyHostToDevice, ctx->stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "H2D copy");
+    release_host_grid_if_other_dim(ctx, D);
     s = frnn_build_grid(ctx, d_in, N, D, r, &ctx->host_grid);
     if (s != FRNN_OK) return s;
-    int64_t E = 0;
-    s = frnn_query_csr_count(ctx, ctx->host_grid, d_in, N, r, K, flags | FRNN_SELF_QUERY, d_off,
-                             nullptr, &E);
+    // the count pass, then the gather of the staged rows before the host has
+    // read the edge count back: the host's wait overlaps the gather.  The
+    // device rows are sized for the caller's capacity (at most N K entries);
+    // the gather writes nothing past it, and the call fails when the count
+    // exceeds it.  Beyond kEarlyGatherBytes of rows the gather waits for the
+    // count and is sized by it.
+    ctx->csr_pending = false;
+    int64_t* h_edges = nullptr;
+    QueryLaunch q{};
+    s = csr_count_enqueue(ctx, ctx->host_grid, d_in, N, r, K, flags | FRNN_SELF_QUERY, d_off,
+                          nullptr, &h_edges, &q);
     if (s != FRNN_OK) return s;
+    if (!ctx->ev_edges) {
+        e = cudaEventCreateWithFlags(&ctx->ev_edges, cudaEventDisableTiming);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "event for the edge count");
+    }
+    e = cudaEventRecord(ctx->ev_edges, ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "event for the edge count");
+    constexpr size_t kEarlyGatherBytes = size_t(1) << 30;
+    const int64_t cap = std::min<int64_t>(edge_cap, N * (int64_t)K);
+    const bool early = 2 * al(sizeof(int32_t) * (size_t)std::max<int64_t>(cap, 1)) <= kEarlyGatherBytes;
+    int32_t* d_idx = nullptr;
+    float* d_d2 = nullptr;
+    auto rows_buffers = [&](int64_t entries) -> frnn_status {
+        const size_t b_rows = al(sizeof(int32_t) * (size_t)std::max<int64_t>(entries, 1));
+        // the rows are gathered in HBM and copied back by the copy engine
+        // (measured faster here than gathering straight into page-locked
+        // host memory: 0.82 vs 0.95 ms for the 300k x 8 event)
+        frnn_status st = grow(ctx, ctx->hr_buf, ctx->hr_bytes, 2 * b_rows, "compact host-path rows");
+        if (st != FRNN_OK) return st;
+        d_idx = static_cast<int32_t*>(ctx->hr_buf);
+        d_d2 = reinterpret_cast<float*>(static_cast<char*>(ctx->hr_buf) + b_rows);
+        return FRNN_OK;
+    };
+    if (early) {
+        s = rows_buffers(cap);
+        if (s != FRNN_OK) return s;
+        enqueue_csr_gather(ctx->csr_cnt, d_off, ctx->csr_idx, ctx->csr_d2, N, d_idx, d_d2,
+                           ctx->num_sms, ctx->stream, cap);
+    }
+    e = cudaEventSynchronize(ctx->ev_edges);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "waiting for the edge count");
+    const int64_t E = *h_edges;
     *n_edges = E;
     if (E > edge_cap) {
-        ctx->csr_pending = false;
         e = cudaMemcpyAsync(offsets_host, d_off, b_off, cudaMemcpyDeviceToHost, ctx->stream);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "D2H copy");
+        s = frnn_sync(ctx);   // a device-side error takes precedence
+        if (s != FRNN_OK) return s;
         return fail(ctx, FRNN_ERR_CAPACITY, "more edges than edge_cap (n_edges has the count)");
     }
-    const size_t b_rows = sizeof(int32_t) * (size_t)std::max<int64_t>(E, 1);
-    // the rows are gathered in HBM and copied back by the copy engine (measured
-    // faster here than gathering straight into page-locked host memory:
-    // 0.82 vs 0.95 ms for the 300k x 8 event)
-    s = grow(ctx, ctx->hr_buf, ctx->hr_bytes, 2 * al(b_rows), "compact host-path rows");
-    if (s != FRNN_OK) return s;
-    int32_t* d_idx = static_cast<int32_t*>(ctx->hr_buf);
-    float* d_d2 = reinterpret_cast<float*>(static_cast<char*>(ctx->hr_buf) + al(b_rows));
-    // grow() drained the stream only when it reallocated; the pending rows
-    // survive it (no other call on the context came between)
-    s = frnn_query_csr_fill(ctx, d_idx, d_d2);
-    if (s != FRNN_OK) return s;
+    if (!early) {
+        s = rows_buffers(E);
+        if (s != FRNN_OK) return s;
+        enqueue_csr_gather(ctx->csr_cnt, d_off, ctx->csr_idx, ctx->csr_d2, N, d_idx, d_d2,
+                           ctx->num_sms, ctx->stream, E);
+    }
+    // rows longer than the in-kernel list: the selection kernel writes them
+    q.ovf_mode = 2;
+    q.row_off = d_off;
+    q.idx = d_idx;
+    q.dist2 = d_d2;
+    q.degree = nullptr;
+    std::string err;
+    s = enqueue_overflow_only(q, ctx->stream, err);
+    if (s != FRNN_OK) return fail(ctx, s, err);
     e = cudaMemcpyAsync(offsets_host, d_off, b_off, cudaMemcpyDeviceToHost, ctx->stream);
     if (e == cudaSuccess && E > 0)
         e = cudaMemcpyAsync(idx_host, d_idx, sizeof(int32_t) * (size_t)E, cudaMemcpyDeviceToHost,

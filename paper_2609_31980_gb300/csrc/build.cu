@@ -890,7 +890,9 @@ frnn_status grid_alloc(GridBufs& g, int E, const int64_t* n, int D, std::string&
     g.nblk = nblk;
     g.nparts = scan_parts_needed(L);
     g.nchunks = nchunks;
-    const bool fits = g.base && g.cap_n >= n_total && g.cap_L >= L && g.cap_E >= E &&
+    // the buffers are reused only if every region is large enough, the
+    // point rows included (a set of a higher dimension needs wider rows)
+    const bool fits = g.base && g.cap_n >= n_total && g.cap_DP >= DP && g.cap_L >= L && g.cap_E >= E &&
                       g.cap_blk >= nblk;
     const int64_t cn = std::max<int64_t>(n_total, 1);
     if (!fits) {
@@ -923,6 +925,7 @@ frnn_status grid_alloc(GridBufs& g, int E, const int64_t* n, int D, std::string&
             cudaGetLastError();
             err = std::string("cudaMalloc of grid buffers failed: ") + cudaGetErrorString(ce);
             g.cap_n = g.cap_L = g.cap_E = g.cap_blk = 0;
+            g.cap_DP = 0;
             return FRNN_ERR_OUT_OF_MEMORY;
         }
         char* b = static_cast<char*>(base);
@@ -943,6 +946,7 @@ frnn_status grid_alloc(GridBufs& g, int E, const int64_t* n, int D, std::string&
         g.scalars = reinterpret_cast<int32_t*>(b + o_sc);
         g.parts = reinterpret_cast<int32_t*>(b + o_parts);
         g.cap_n = n_total;
+        g.cap_DP = DP;
         g.cap_L = L;
         g.cap_E = E;
         g.cap_blk = nblk;

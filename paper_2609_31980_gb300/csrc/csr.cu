@@ -130,7 +130,8 @@ __global__ void __launch_bounds__(kCsrThreads) k_csr_down(const int32_t* cnt, in
 // lane copies one entry per step and the stores of a step are contiguous.
 __global__ void __launch_bounds__(256) k_csr_gather(const int32_t* cnt, const int64_t* offsets,
                                                     const int32_t* sidx, const float* sd2,
-                                                    int64_t M, int32_t* idx, float* dist2) {
+                                                    int64_t M, int32_t* idx, float* dist2,
+                                                    int64_t cap) {
     pdl_trigger();
     pdl_wait();
     const int lane = threadIdx.x & 31;
@@ -159,7 +160,10 @@ __global__ void __launch_bounds__(256) k_csr_gather(const int32_t* cnt, const in
             }
             const int e = t - __shfl_sync(0xffffffffu, excl, R);
             const int64_t dst = __shfl_sync(0xffffffffu, o_lane, R) + e;
-            if (t < T) {
+            // cap: entries the output holds (a caller that gathers before
+            // it knows the edge count passes its capacity; the call then
+            // fails when the count exceeds it, and nothing past it is written)
+            if (t < T && dst < cap) {
                 const int64_t src = (r0 + R) * kCsrStageW + e;
                 idx[dst] = sidx[src];
                 dist2[dst] = sd2[src];
@@ -184,12 +188,12 @@ int64_t csr_parts_needed(int64_t M) { return std::max<int64_t>(1, ceil_div(M, kC
 
 void enqueue_csr_gather(const int32_t* cnt, const int64_t* offsets, const int32_t* sidx,
                         const float* sd2, int64_t M, int32_t* idx, float* dist2, int num_sms,
-                        cudaStream_t st) {
+                        cudaStream_t st, int64_t cap) {
     if (M <= 0) return;
     const int64_t warps = ceil_div(M, 32);
     const int64_t blocks = std::min<int64_t>(ceil_div(warps, 8), (int64_t)num_sms * 8);
-    launch_pdl(k_csr_gather, dim3((unsigned)std::max<int64_t>(blocks, 1)), dim3(256), 0, st, cnt, offsets, sidx, sd2, M,
-                                                                         idx, dist2);
+    launch_pdl(k_csr_gather, dim3((unsigned)std::max<int64_t>(blocks, 1)), dim3(256), 0, st, cnt,
+               offsets, sidx, sd2, M, idx, dist2, cap);
 }
 
 }  // namespace frnn

@@ -29,6 +29,7 @@ struct GridBufs {
     void* base = nullptr;
     size_t bytes = 0;
     int64_t cap_n = 0, cap_L = 0, cap_E = 0, cap_blk = 0;
+    int cap_DP = 0;         // row width the point rows were carved for
     void* h_pinned = nullptr;      // page-locked host mirror of the small tables
     size_t h_pinned_bytes = 0;
     cudaEvent_t h_pinned_free = nullptr;   // last upload from the mirror has run
@@ -68,6 +69,7 @@ struct GridBufs {
     void* rows_base = nullptr;
     size_t rows_bytes = 0;
     int64_t rows_cap_n = 0, rows_cap_tasks = 0, rows_cap_L = 0;
+    int rows_cap_DP = 0;            // row width the pair copy was sized for
     float* ppts = nullptr;          // [n_total * DP] pair-interleaved coordinates
     Task* row_tasks = nullptr;      // [rows_cap_tasks]
     int32_t* rows_rtask = nullptr;  // [L] the task builder's per-row scratch
@@ -186,9 +188,10 @@ frnn_status enqueue_overflow_only(const QueryLaunch& q, cudaStream_t st, std::st
 int64_t csr_parts_needed(int64_t M);
 void enqueue_csr_offsets(const int32_t* cnt, int64_t M, int64_t* parts, int64_t* offsets,
                          cudaStream_t st);
+// cap: entries idx / dist2 hold; entries at or past it are not written
 void enqueue_csr_gather(const int32_t* cnt, const int64_t* offsets, const int32_t* sidx,
                         const float* sd2, int64_t M, int32_t* idx, float* dist2, int num_sms,
-                        cudaStream_t st);
+                        cudaStream_t st, int64_t cap = INT64_MAX);
 
 // Tensor-core path: prepare operands (and 128-query tasks) of a point set.
 // center_src: the grid whose per-event centres the operands use (the

@@ -651,6 +651,7 @@ void rows_free(GridBufs& g) {
     g.rows_base = nullptr;
     g.rows_bytes = 0;
     g.rows_cap_n = g.rows_cap_tasks = g.rows_cap_L = 0;
+    g.rows_cap_DP = 0;
     g.ppts = nullptr;
     g.row_tasks = nullptr;
     g.rows_rtask = nullptr;
@@ -667,7 +668,8 @@ frnn_status rows_reserve(GridBufs& g, std::string& err) {
         return FRNN_ERR_INVALID_ARG;
     }
     const int64_t n = std::max<int64_t>(g.n_total, 2);
-    if (g.rows_base && g.rows_cap_n >= n && g.rows_cap_tasks >= tcap && g.rows_cap_L >= g.L)
+    if (g.rows_base && g.rows_cap_n >= n && g.rows_cap_DP >= g.DP && g.rows_cap_tasks >= tcap &&
+        g.rows_cap_L >= g.L)
         return FRNN_OK;
     rows_free(g);
     const size_t bp = al256r(sizeof(float) * (size_t)g.DP * (n + kTcRowPad));
@@ -686,6 +688,7 @@ frnn_status rows_reserve(GridBufs& g, std::string& err) {
     g.row_tasks = reinterpret_cast<Task*>(b + bp);
     g.rows_rtask = reinterpret_cast<int32_t*>(b + bp + bt);
     g.rows_cap_n = n;
+    g.rows_cap_DP = g.DP;
     g.rows_cap_tasks = tcap;
     g.rows_cap_L = g.L;
     return FRNN_OK;

@@ -809,3 +809,48 @@ def test_random_batches_match_oracle(ctx):
         for p, (c, i, d) in zip(evs, outs):
             _assert_rows_equal((c.cpu().numpy(), i.cpu().numpy(), d.cpu().numpy()),
                                oracle.self_query(p, r, K))
+
+
+# ------------------------------------------------------------ workspaces reused across dimensions
+
+def test_context_workspaces_reused_across_dimensions():
+    # the context keeps workspaces between calls (the cross-set query grid,
+    # the batch grid, the host-buffer grid and the row-task pair copy); a call
+    # of a higher dimension with fewer points must not reuse rows carved for a
+    # lower one
+    import torch
+    from paper_2609_31980_gb300 import frnn
+    g = np.random.default_rng(7200)
+    with frnn.Context() as c:
+        for D, n, path in ((3, 20000, "grid"), (16, 3000, "grid"), (4, 12000, "grid"),
+                           (12, 2500, "grid"), (2, 9000, "grid"), (15, 1666, "grid")):
+            refs = synth.clustered(max(1, n // 30), 25, n - (n // 30) * 25, D, 0.03,
+                                   seed=int(g.integers(1 << 30)))
+            qs = (refs[g.permutation(len(refs))[: len(refs) // 3]] +
+                  np.float32(0.02) * g.standard_normal((len(refs) // 3, D)).astype(np.float32))
+            qs = np.ascontiguousarray(qs, np.float32)
+            r, K = 0.15, 33
+            gr = c.build_grid(torch.from_numpy(refs).cuda(), r)
+            cc, ii, dd = c.query(gr, torch.from_numpy(qs).cuda(), r, K, self_query=False, path=path)
+            c.sync()
+            _assert_rows_equal((cc.cpu().numpy(), ii.cpu().numpy(), dd.cpu().numpy()),
+                               oracle.frnn(qs, refs, r, K))
+            gr.close()
+            # batched: the context's batch grid
+            evs = [refs[: len(refs) // 2], refs[len(refs) // 2:]]
+            outs = c.query_batched([torch.from_numpy(np.ascontiguousarray(e)).cuda() for e in evs],
+                                   r, K, path="auto")
+            c.sync()
+            for e, (bc, bi, bd) in zip(evs, outs):
+                _assert_rows_equal((bc.cpu().numpy(), bi.cpu().numpy(), bd.cpu().numpy()),
+                                   oracle.self_query(np.ascontiguousarray(e), r, K))
+            # host buffers: the context's host-path grid, dense and compact
+            want = oracle.self_query(refs, r, K)
+            _assert_rows_equal(c.self_query_host(refs, r, K), want)
+            off, idx, d2 = c.self_query_host_csr(refs, r, K)
+            assert np.array_equal(np.diff(off), want[0])
+            for row in range(0, len(refs), 97):
+                n_row = want[0][row]
+                assert np.array_equal(idx[off[row]: off[row] + n_row], want[1][row][:n_row])
+                assert np.array_equal(d2[off[row]: off[row] + n_row].view(np.uint32),
+                                      want[2][row][:n_row].view(np.uint32))
