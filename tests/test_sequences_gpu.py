@@ -3,7 +3,8 @@ oracle.
 
 The context keeps state between calls: grids rebuilt in place, the cross-set
 query grid, the batch grid and its captured graph, the host-buffer grid and
-buffers, the compact-output staging, the row-task pair copies, options.  A
+buffers, the compact-output staging, the row-task pair copies, options and
+the autotuner's choices per size class (so that batches mix scans).  A
 sequence mixes builds (new and in place), self and cross-set queries on
 every path, batches, host-buffer calls (dense and compact), device compact
 output and option changes (gridded axes, cell multiple, staging), with sizes,
@@ -58,13 +59,21 @@ def test_random_call_sequences(seed):
     with frnn.Context() as ctx:
         grid, grid_pts, grid_r = None, None, None
         for step in range(40):
-            op = g.choice(["build", "rebuild", "self", "cross", "batch", "host", "host_csr",
-                           "csr", "option"])
+            op = g.choice(["build", "rebuild", "self", "cross", "batch", "batch", "host",
+                           "host_csr", "csr", "option", "tune"])
             D = int(g.choice([2, 3, 5, 8, 9, 12, 16]))
             n = int(g.choice([1, 40, 700, 3000]))
             K = int(g.choice([1, 16, 33, 64]))
             r = float(np.float32(g.choice([0.05, 0.1, 0.2])))
             what = f"seed {seed} step {step} {op} D={D} n={n} K={K} r={r}"
+            if op == "tune":
+                # tune one size class (the scan, axes, cell multiple, staging
+                # or the tensor-core path it picks then serve that class in
+                # later calls and batches, next to untuned classes)
+                pts = _points(g, n, D)
+                path = "grid" if D < 8 else str(g.choice(["grid", "tc", "auto"]))
+                ctx.autotune(torch.from_numpy(pts).to(dev), r, K, path=path)
+                continue
             if op == "option":
                 ctx.set_option(frnn.FRNN_OPT_GRID_NAXES, int(g.choice([0, 0, 3, 4, 5])))
                 ctx.set_option(frnn.FRNN_OPT_CELL_MULT, int(g.choice([0, 0, 1, 2, 3])))
