@@ -427,7 +427,7 @@ def run_ours(args):
     e2e_s = max_over_ranks(e2e_s, dev)
     e2e_c_s = max_over_ranks(e2e_c_s, dev)
     if ws > 1:
-        # the remaining legs run on rank 0 alone and need no collective
+        # what follows needs no collective (the single-GPU legs run at N = 1 only)
         torch.distributed.destroy_process_group()
     keep = np.arange(K)[None, :] < h_c.numpy()[:, None]
     ok_c = bool(np.array_equal(np.diff(off_np), h_c.numpy()) and
@@ -493,15 +493,18 @@ def run_ours(args):
     }
     if clocks:
         res["clocks"] = clocks
-    if rank == 0 and not args.no_compact:
+    # the single-GPU legs: reported by the N = 1 run only, so that a run on
+    # N GPUs holds them for the replicated headline step alone
+    extras = rank == 0 and ws == 1
+    if extras and not args.no_compact:
         res["compact_rows"] = run_compact(ctx, grid, pts, r, K, path, stream)
-    if rank == 0 and not args.no_batched:
+    if extras and not args.no_batched:
         res["batched_vs_plain"] = run_batched(ctx, args, dev, args.batch_path)
         if not args.no_tuned_batch:
             res["batched_vs_plain_tuned"] = run_batched_tuned(args, dev)
-    if rank == 0 and not args.no_design_points:
+    if extras and not args.no_design_points:
         res["design_points"] = run_design_points(args, dev)
-    if rank == 0 and not args.no_serving:
+    if extras and not args.no_serving:
         res["serving"] = run_serving(ctx, args)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         res["cpu_baseline"] = cpu_baseline(pts_np, r, K, args.cpu_rows,
