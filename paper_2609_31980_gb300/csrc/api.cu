@@ -1038,8 +1038,8 @@ frnn_status frnn_self_query_host_csr(frnn_ctx* ctx, const float* refs_host, int6
     // read the edge count back: the host's wait overlaps the gather.  The
     // device rows are sized for the caller's capacity (at most N K entries);
     // the gather writes nothing past it, and the call fails when the count
-    // exceeds it.  Beyond kEarlyGatherBytes of rows the gather waits for the
-    // count and is sized by it.
+    // exceeds it.  Beyond kEarlyGatherBytes of rows, or beyond the context's
+    // memory budget, the gather waits for the count and is sized by it.
     ctx->csr_pending = false;
     int64_t* h_edges = nullptr;
     QueryLaunch q{};
@@ -1054,7 +1054,11 @@ frnn_status frnn_self_query_host_csr(frnn_ctx* ctx, const float* refs_host, int6
     if (e != cudaSuccess) return cuda_fail(ctx, e, "event for the edge count");
     constexpr size_t kEarlyGatherBytes = size_t(1) << 30;
     const int64_t cap = std::min<int64_t>(edge_cap, N * (int64_t)K);
-    const bool early = 2 * al(sizeof(int32_t) * (size_t)std::max<int64_t>(cap, 1)) <= kEarlyGatherBytes;
+    const size_t early_bytes = 2 * al(sizeof(int32_t) * (size_t)std::max<int64_t>(cap, 1));
+    // (within the context's memory budget too: else the rows wait for the
+    // count, which may need fewer bytes)
+    const bool early = early_bytes <= kEarlyGatherBytes &&
+                       (early_bytes <= ctx->hr_bytes || budget_allows(ctx, ctx->hr_bytes, early_bytes));
     int32_t* d_idx = nullptr;
     float* d_d2 = nullptr;
     auto rows_buffers = [&](int64_t entries) -> frnn_status {
