@@ -189,3 +189,32 @@ def test_host_compact_call_matches_oracle_and_reports_capacity(ctx):
     np.testing.assert_array_equal(idx3, want[1])
     empty = ctx.self_query_host_csr(np.zeros((0, 8), np.float32), 0.1, 48, "grid")
     assert empty[0].tolist() == [0] and len(empty[1]) == 0
+
+
+def test_host_compact_call_large_capacity_small_budget():
+    # the caller's buffers hold N K entries, more than the context's budget
+    # allows as device rows: the gather waits for the edge count and sizes
+    # the device rows by it (the result is the same); with room, it runs
+    # before the count is back, and a capacity just below the count fails
+    from paper_2609_31980_gb300 import frnn
+    pts = synth.clustered(300, 30, 8000, 8, 0.02, seed=721)
+    N, K = len(pts), 1000
+    want = oracle.csr(pts, pts, 0.1, K, query_ids=np.arange(N))
+    E = int(want[0][-1])
+    for budget in (60 * 10 ** 6, 0):
+        with frnn.Context(budget_bytes=budget) as c:
+            out = (np.empty(N + 1, np.int64), np.empty(N * K, np.int32), np.empty(N * K, np.float32))
+            off, idx, d2 = c.self_query_host_csr(pts, 0.1, K, "grid", out)
+            np.testing.assert_array_equal(off, want[0])
+            np.testing.assert_array_equal(idx, want[1])
+            np.testing.assert_array_equal(d2.view(np.uint32), want[2].view(np.uint32))
+            import ctypes
+            small = (np.empty(N + 1, np.int64), np.empty(E - 1, np.int32), np.empty(E - 1, np.float32))
+            ne = ctypes.c_int64(0)
+            rc = frnn.frnn_self_query_host_csr(c.handle, ctypes.c_void_p(pts.ctypes.data), N, 8, 0.1,
+                                               K, 0, ctypes.c_void_p(small[0].ctypes.data),
+                                               ctypes.c_void_p(small[1].ctypes.data),
+                                               ctypes.c_void_p(small[2].ctypes.data), E - 1,
+                                               ctypes.byref(ne))
+            assert rc == frnn.FRNN_ERR_CAPACITY and ne.value == E
+            np.testing.assert_array_equal(small[0], want[0])
