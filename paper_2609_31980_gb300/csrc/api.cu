@@ -66,6 +66,11 @@ struct frnn_ctx {
     cudaStream_t gstream = nullptr;
     cudaEvent_t g_in = nullptr, g_out = nullptr;
     cudaEvent_t ev_edges = nullptr;   // host-buffer compact path: edge count copied back
+    // host-buffer compact path: a copy stream for the rows, and one event per
+    // part of the gather plus one for the finished copies
+    cudaStream_t cstream = nullptr;
+    cudaEvent_t ev_part[4] = {nullptr, nullptr, nullptr, nullptr};
+    cudaEvent_t ev_copied = nullptr;
     cudaGraphExec_t graph = nullptr;
     std::vector<frnn_event> g_ev;
     int g_D = 0, g_K = 0;
@@ -419,6 +424,13 @@ frnn_status frnn_destroy(frnn_ctx* ctx) {
     if (ctx->g_in) cudaEventDestroy(ctx->g_in);
     if (ctx->g_out) cudaEventDestroy(ctx->g_out);
     if (ctx->ev_edges) cudaEventDestroy(ctx->ev_edges);
+    if (ctx->cstream) {
+        cudaStreamSynchronize(ctx->cstream);
+        cudaStreamDestroy(ctx->cstream);
+    }
+    for (cudaEvent_t ev : ctx->ev_part)
+        if (ev) cudaEventDestroy(ev);
+    if (ctx->ev_copied) cudaEventDestroy(ctx->ev_copied);
     for (cudaEvent_t e : ctx->kev) cudaEventDestroy(e);
     if (ctx->host_grid) {
         frnn_grid* g = ctx->host_grid;
@@ -1034,18 +1046,32 @@ frnn_status frnn_self_query_host_csr(frnn_ctx* ctx, const float* refs_host, int6
     release_host_grid_if_other_dim(ctx, D);
     s = frnn_build_grid(ctx, d_in, N, D, r, &ctx->host_grid);
     if (s != FRNN_OK) return s;
-    // the count pass, then the gather of the staged rows before the host has
-    // read the edge count back: the host's wait overlaps the gather.  The
-    // device rows are sized for the caller's capacity (at most N K entries);
-    // the gather writes nothing past it, and the call fails when the count
-    // exceeds it.  Beyond kEarlyGatherBytes of rows, or beyond the context's
-    // memory budget, the gather waits for the count and is sized by it.
+    // The count pass, then the fill before the host has read the edge count
+    // back: the device rows are sized for the caller's capacity (at most N K
+    // entries), and nothing is written past it (the call fails when the count
+    // exceeds it).  The fill runs in kParts ranges of rows, each copied back
+    // on a copy stream while the next range is gathered; the offsets go back
+    // as soon as the scan has made them.  Beyond kEarlyGatherBytes of rows,
+    // or beyond the context's memory budget, the fill waits for the count,
+    // is sized by it and is copied back after it.
+    constexpr int kParts = 4;
     ctx->csr_pending = false;
     int64_t* h_edges = nullptr;
     QueryLaunch q{};
     s = csr_count_enqueue(ctx, ctx->host_grid, d_in, N, r, K, flags | FRNN_SELF_QUERY, d_off,
                           nullptr, &h_edges, &q);
     if (s != FRNN_OK) return s;
+    // the offsets at the parts' first rows (multiples of 32), to the pinned
+    // block's next slots
+    int64_t cut[kParts + 1];
+    cut[0] = 0;
+    cut[kParts] = N;
+    for (int p = 1; p < kParts; ++p) cut[p] = std::min<int64_t>(N, (N * p / kParts + 31) / 32 * 32);
+    int64_t* h_cut = h_edges + 1;
+    for (int p = 1; p < kParts && e == cudaSuccess; ++p)
+        e = cudaMemcpyAsync(h_cut + (p - 1), d_off + cut[p], sizeof(int64_t), cudaMemcpyDeviceToHost,
+                            ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "reading the part offsets");
     if (!ctx->ev_edges) {
         e = cudaEventCreateWithFlags(&ctx->ev_edges, cudaEventDisableTiming);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "event for the edge count");
@@ -1072,38 +1098,82 @@ frnn_status frnn_self_query_host_csr(frnn_ctx* ctx, const float* refs_host, int6
         d_d2 = reinterpret_cast<float*>(static_cast<char*>(ctx->hr_buf) + b_rows);
         return FRNN_OK;
     };
+    // the selection kernel's rows (longer than the in-kernel list), then the
+    // gather of the others
+    auto fill = [&](int64_t rows_cap, bool in_parts) -> frnn_status {
+        QueryLaunch qf = q;
+        qf.ovf_mode = 2;
+        qf.row_off = d_off;
+        qf.idx = d_idx;
+        qf.dist2 = d_d2;
+        qf.degree = nullptr;
+        qf.row_cap = rows_cap;
+        std::string err;
+        frnn_status st = enqueue_overflow_only(qf, ctx->stream, err);
+        if (st != FRNN_OK) return fail(ctx, st, err);
+        for (int p = 0; p < (in_parts ? kParts : 1); ++p) {
+            const int64_t r0 = in_parts ? cut[p] : 0, r1 = in_parts ? cut[p + 1] : N;
+            enqueue_csr_gather(ctx->csr_cnt, d_off, ctx->csr_idx, ctx->csr_d2, N, d_idx, d_d2,
+                               ctx->num_sms, ctx->stream, rows_cap, r0, r1);
+            if (in_parts) cudaEventRecord(ctx->ev_part[p], ctx->stream);
+        }
+        const cudaError_t ce = cudaGetLastError();
+        if (ce != cudaSuccess) return cuda_fail(ctx, ce, "compact-output fill launch");
+        return FRNN_OK;
+    };
     if (early) {
+        if (!ctx->cstream) {
+            e = cudaStreamCreateWithFlags(&ctx->cstream, cudaStreamNonBlocking);
+            for (cudaEvent_t& ev : ctx->ev_part)
+                if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_copied, cudaEventDisableTiming);
+            if (e != cudaSuccess) return cuda_fail(ctx, e, "copy stream of the compact host path");
+        }
         s = rows_buffers(cap);
         if (s != FRNN_OK) return s;
-        enqueue_csr_gather(ctx->csr_cnt, d_off, ctx->csr_idx, ctx->csr_d2, N, d_idx, d_d2,
-                           ctx->num_sms, ctx->stream, cap);
+        // the offsets go back while the rows are filled
+        e = cudaStreamWaitEvent(ctx->cstream, ctx->ev_edges, 0);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(offsets_host, d_off, b_off, cudaMemcpyDeviceToHost, ctx->cstream);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "D2H copy");
+        s = fill(cap, true);
+        if (s != FRNN_OK) return s;
     }
     e = cudaEventSynchronize(ctx->ev_edges);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "waiting for the edge count");
     const int64_t E = *h_edges;
     *n_edges = E;
     if (E > edge_cap) {
-        e = cudaMemcpyAsync(offsets_host, d_off, b_off, cudaMemcpyDeviceToHost, ctx->stream);
+        if (early) e = cudaStreamSynchronize(ctx->cstream);   // the offsets are on their way
+        else e = cudaMemcpyAsync(offsets_host, d_off, b_off, cudaMemcpyDeviceToHost, ctx->stream);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "D2H copy");
         s = frnn_sync(ctx);   // a device-side error takes precedence
         if (s != FRNN_OK) return s;
         return fail(ctx, FRNN_ERR_CAPACITY, "more edges than edge_cap (n_edges has the count)");
     }
-    if (!early) {
-        s = rows_buffers(E);
-        if (s != FRNN_OK) return s;
-        enqueue_csr_gather(ctx->csr_cnt, d_off, ctx->csr_idx, ctx->csr_d2, N, d_idx, d_d2,
-                           ctx->num_sms, ctx->stream, E);
+    if (early) {
+        // each part's entries, [offset of its first row, offset of the next
+        // part's first row), once its gather is done
+        for (int p = 0; p < kParts && e == cudaSuccess; ++p) {
+            const int64_t a0 = p == 0 ? 0 : h_cut[p - 1];
+            const int64_t a1 = p + 1 < kParts ? h_cut[p] : E;
+            e = cudaStreamWaitEvent(ctx->cstream, ctx->ev_part[p], 0);
+            if (e == cudaSuccess && a1 > a0)
+                e = cudaMemcpyAsync(idx_host + a0, d_idx + a0, sizeof(int32_t) * (size_t)(a1 - a0),
+                                    cudaMemcpyDeviceToHost, ctx->cstream);
+            if (e == cudaSuccess && a1 > a0)
+                e = cudaMemcpyAsync(dist2_host + a0, d_d2 + a0, sizeof(float) * (size_t)(a1 - a0),
+                                    cudaMemcpyDeviceToHost, ctx->cstream);
+        }
+        if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_copied, ctx->cstream);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->stream, ctx->ev_copied, 0);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "D2H copy");
+        return frnn_sync(ctx);
     }
-    // rows longer than the in-kernel list: the selection kernel writes them
-    q.ovf_mode = 2;
-    q.row_off = d_off;
-    q.idx = d_idx;
-    q.dist2 = d_d2;
-    q.degree = nullptr;
-    std::string err;
-    s = enqueue_overflow_only(q, ctx->stream, err);
-    if (s != FRNN_OK) return fail(ctx, s, err);
+    s = rows_buffers(E);
+    if (s != FRNN_OK) return s;
+    s = fill(E, false);
+    if (s != FRNN_OK) return s;
     e = cudaMemcpyAsync(offsets_host, d_off, b_off, cudaMemcpyDeviceToHost, ctx->stream);
     if (e == cudaSuccess && E > 0)
         e = cudaMemcpyAsync(idx_host, d_idx, sizeof(int32_t) * (size_t)E, cudaMemcpyDeviceToHost,

@@ -131,15 +131,17 @@ __global__ void __launch_bounds__(kCsrThreads) k_csr_down(const int32_t* cnt, in
 __global__ void __launch_bounds__(256) k_csr_gather(const int32_t* cnt, const int64_t* offsets,
                                                     const int32_t* sidx, const float* sd2,
                                                     int64_t M, int32_t* idx, float* dist2,
-                                                    int64_t cap) {
+                                                    int64_t cap, int64_t row0, int64_t row1) {
     pdl_trigger();
     pdl_wait();
     const int lane = threadIdx.x & 31;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w * 32 < M; w += nw) {
+    // rows [row0, row1) (row0 a multiple of 32)
+    for (int64_t w = (row0 >> 5) + (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+         w * 32 < row1; w += nw) {
         const int64_t r0 = w * 32;
         const int64_t i = r0 + lane;
-        const int32_t c = i < M ? cnt[i] : 0;
+        const int32_t c = i < row1 ? cnt[i] : 0;
         const int own = (c & kCsrSpill) ? 0 : c;   // spilled rows: written by the selection kernel
         int incl = own;
 #pragma unroll
@@ -149,7 +151,7 @@ __global__ void __launch_bounds__(256) k_csr_gather(const int32_t* cnt, const in
         }
         const int excl = incl - own;
         const int T = __shfl_sync(0xffffffffu, incl, 31);
-        const int64_t o_lane = i < M ? offsets[i] : 0;
+        const int64_t o_lane = i < row1 ? offsets[i] : 0;
         for (int base = 0; base < T; base += 32) {
             const int t = base + lane;
             int R = 0;
@@ -188,12 +190,13 @@ int64_t csr_parts_needed(int64_t M) { return std::max<int64_t>(1, ceil_div(M, kC
 
 void enqueue_csr_gather(const int32_t* cnt, const int64_t* offsets, const int32_t* sidx,
                         const float* sd2, int64_t M, int32_t* idx, float* dist2, int num_sms,
-                        cudaStream_t st, int64_t cap) {
-    if (M <= 0) return;
-    const int64_t warps = ceil_div(M, 32);
+                        cudaStream_t st, int64_t cap, int64_t row0, int64_t row1) {
+    if (row1 < 0) row1 = M;
+    if (row1 <= row0) return;
+    const int64_t warps = ceil_div(row1 - row0, 32);
     const int64_t blocks = std::min<int64_t>(ceil_div(warps, 8), (int64_t)num_sms * 8);
     launch_pdl(k_csr_gather, dim3((unsigned)std::max<int64_t>(blocks, 1)), dim3(256), 0, st, cnt,
-               offsets, sidx, sd2, M, idx, dist2, cap);
+               offsets, sidx, sd2, M, idx, dist2, cap, row0, row1);
 }
 
 }  // namespace frnn

@@ -166,6 +166,7 @@ struct QueryLaunch {
     int ovf_mode = 0;
     int32_t* degree = nullptr;
     const int64_t* row_off = nullptr;
+    int64_t row_cap = INT64_MAX;   // compact rows: entries the output holds
 };
 frnn_status enqueue_grid_query(const QueryLaunch& q, cudaStream_t st, std::string& err);
 // Row-task kernel: allocate (outside any capture) and build (enqueued) the
@@ -188,10 +189,12 @@ frnn_status enqueue_overflow_only(const QueryLaunch& q, cudaStream_t st, std::st
 int64_t csr_parts_needed(int64_t M);
 void enqueue_csr_offsets(const int32_t* cnt, int64_t M, int64_t* parts, int64_t* offsets,
                          cudaStream_t st);
-// cap: entries idx / dist2 hold; entries at or past it are not written
+// cap: entries idx / dist2 hold; entries at or past it are not written.
+// [row0, row1): the rows gathered (row0 a multiple of 32; row1 < 0: to M).
 void enqueue_csr_gather(const int32_t* cnt, const int64_t* offsets, const int32_t* sidx,
                         const float* sd2, int64_t M, int32_t* idx, float* dist2, int num_sms,
-                        cudaStream_t st, int64_t cap = INT64_MAX);
+                        cudaStream_t st, int64_t cap = INT64_MAX, int64_t row0 = 0,
+                        int64_t row1 = -1);
 
 // Tensor-core path: prepare operands (and 128-query tasks) of a point set.
 // center_src: the grid whose per-event centres the operands use (the

@@ -164,6 +164,7 @@ struct QueryArgs {
     int32_t ovf_mode;
     int32_t* degree;             // optional full degree per query (csr)
     const int64_t* row_off;      // CSR row offsets (ovf_mode 2)
+    int64_t row_cap;             // entries idx / dist2 hold (ovf_mode 2): rows past it are skipped
 };
 
 // ---------------------------------------------------------------- PTX helpers

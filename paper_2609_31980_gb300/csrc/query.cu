@@ -810,8 +810,11 @@ __global__ void __launch_bounds__(kOvfWarps * 32) k_overflow(QueryArgs a, int ca
             }
             continue;
         }
-        smem_bitonic(buf, cap);
         const bool csr_rows = a.ovf_mode == 2;
+        // a compact output too small for the rows (its caller fails the
+        // call) is not written past its end
+        if (csr_rows && a.row_off[qo] + c > a.row_cap) continue;
+        smem_bitonic(buf, cap);
         int32_t* irow = oidx + (csr_rows ? a.row_off[qo] : (int64_t)qo * K);
         float* drow = od2 + (csr_rows ? a.row_off[qo] : (int64_t)qo * K);
         for (int e = lane; e < (csr_rows ? c : K); e += 32) {
@@ -903,6 +906,7 @@ static QueryArgs query_args(const QueryLaunch& q) {
     a.ovf_mode = q.ovf_mode;
     a.degree = q.degree;
     a.row_off = q.row_off;
+    a.row_cap = q.row_cap;
     return a;
 }
 
