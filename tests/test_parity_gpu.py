@@ -854,3 +854,25 @@ def test_context_workspaces_reused_across_dimensions():
                 assert np.array_equal(idx[off[row]: off[row] + n_row], want[1][row][:n_row])
                 assert np.array_equal(d2[off[row]: off[row] + n_row].view(np.uint32),
                                       want[2][row][:n_row].view(np.uint32))
+
+
+def test_extreme_coordinates(ctx):
+    # extents that overflow float32 (the parameter step falls back to fewer
+    # or one cell), huge offsets, tiny scales near the subnormal range, and
+    # radii at the edges of the accepted range: every row against the oracle
+    g = np.random.default_rng(7400)
+    cases = []
+    x = g.uniform(-3e38, 3e38, size=(600, 4)).astype(np.float32)          # hi - lo overflows
+    x[300:] = x[:300]                                                      # duplicates: pairs at 0
+    cases.append((x, float(np.float32(2.0 ** 60)), 16))                   # the largest radius
+    x = (g.uniform(-1, 1, size=(800, 6)) * 1e3 + 1e30).astype(np.float32)  # offset swamps the spread
+    cases.append((x, float(np.float32(1e18)), 16))
+    x = (g.uniform(-1, 1, size=(800, 5)) * 1e-17).astype(np.float32)      # squares near the subnormals
+    cases.append((x, float(np.float32(3e-18)), 16))
+    x = g.uniform(-1, 1, size=(500, 3)).astype(np.float32)
+    cases.append((x, float(np.float32(2.0 ** 59)), 8))                     # every pair within r
+    cases.append((x, float(np.float32(2.0 ** -59)), 8))                    # no pair within r
+    for pts, r, K in cases:
+        want = oracle.self_query(pts, r, K)
+        for path in ("grid", "auto"):
+            _assert_rows_equal(_gpu_self(ctx, pts, r, K, path=path), want)
