@@ -92,16 +92,55 @@ struct WarpSmem {
     int32_t* rlo;     // [kRangeCap] first slot of each compact range
     int32_t* rpre;    // [kRangeCap + 1] stream position of each range; sentinel = length
     int32_t* cnt;     // [kChunkQ] accepted entries per query
+    int32_t* tdelta;  // [kNbrRounds][32] neighbour-row table: offsets (table_in_smem only)
+    uint32_t* tedge;  // [kNbrRounds][32] neighbour-row table: edge codes (table_in_smem only)
 };
+
+constexpr size_t kSmemPerSm = 228 * 1024;      // shared memory of one SM
+constexpr size_t kSmemPerCtaReserved = 1024;   // taken by the system from each resident CTA
+constexpr size_t kNbrTableBytes = 2 * (size_t)kNbrRounds * 32 * 4;
+
+template <int D, int STAGE>
+__host__ __device__ constexpr size_t warp_smem_core_bytes() {
+    using C = QCfg<D, STAGE>;
+    constexpr size_t ring = STAGE == kStageBulk ? (size_t)C::NB * C::TILE * (C::DP + 1) * 4 + C::NB * 8 : 0;
+    return ring + (size_t)kChunkQ * C::DP * 4 + 2 * (size_t)kChunkQ * kListStr * 4 + (size_t)kRangeCap * 4 +
+           (size_t)(kRangeCap + 1) * 4 + (size_t)kChunkQ * 4;
+}
+
+// The neighbour-row table lives in shared memory (which frees eight
+// registers a lane for the scan) wherever that still lets MINB CTAs reside
+// on an SM; otherwise in registers.
+template <int D, int STAGE>
+__host__ __device__ constexpr bool table_in_smem() {
+    return (kQueryWarps * ((warp_smem_core_bytes<D, STAGE>() + kNbrTableBytes + 127) / 128 * 128) +
+            kSmemPerCtaReserved) * QCfg<D, STAGE>::MINB <= kSmemPerSm;
+}
 
 template <int D, int STAGE>
 __host__ __device__ constexpr size_t warp_smem_bytes() {
-    using C = QCfg<D, STAGE>;
-    constexpr size_t ring = STAGE == kStageBulk ? (size_t)C::NB * C::TILE * (C::DP + 1) * 4 + C::NB * 8 : 0;
-    return (ring + (size_t)kChunkQ * C::DP * 4 + 2 * (size_t)kChunkQ * kListStr * 4 +
-            (size_t)kRangeCap * 4 + (size_t)(kRangeCap + 1) * 4 + (size_t)kChunkQ * 4 + 127) /
+    return (warp_smem_core_bytes<D, STAGE>() + (table_in_smem<D, STAGE>() ? kNbrTableBytes : 0) + 127) /
            128 * 128;
 }
+
+// The table's two words for row l = 32 rr + lane, in registers or in the
+// warp's shared memory (row-major by rr, one word per lane: conflict-free).
+template <bool SMEM>
+struct NbrTable {
+    int32_t d[kNbrRounds];
+    uint32_t e[kNbrRounds];
+    __device__ __forceinline__ NbrTable(const WarpSmem&, int) {}
+    __device__ __forceinline__ int32_t& delta(int rr) { return d[rr]; }
+    __device__ __forceinline__ uint32_t& edge(int rr) { return e[rr]; }
+};
+template <>
+struct NbrTable<true> {
+    int32_t* d;
+    uint32_t* e;
+    __device__ __forceinline__ NbrTable(const WarpSmem& w, int lane) : d(w.tdelta + lane), e(w.tedge + lane) {}
+    __device__ __forceinline__ int32_t& delta(int rr) { return d[rr * 32]; }
+    __device__ __forceinline__ uint32_t& edge(int rr) { return e[rr * 32]; }
+};
 
 template <int D, int STAGE>
 __device__ __forceinline__ WarpSmem carve_warp(unsigned char* base) {
@@ -117,6 +156,8 @@ __device__ __forceinline__ WarpSmem carve_warp(unsigned char* base) {
     w.rlo = reinterpret_cast<int32_t*>(w.bars + NBUF);
     w.rpre = w.rlo + kRangeCap;
     w.cnt = w.rpre + kRangeCap + 1;
+    w.tdelta = w.cnt + kChunkQ;   // past the end of the warp's area unless table_in_smem
+    w.tedge = reinterpret_cast<uint32_t*>(w.tdelta + kNbrRounds * 32);
     return w;
 }
 
@@ -188,12 +229,11 @@ __global__ void __launch_bounds__(kQueryWarps * 32, QCfg<D, STAGE>::MINB) k_grid
     const float r2 = a.r2;
     const int K = a.K;
     // neighbour-row table of the current event, for row l = 32 rr + lane:
-    // tdelta[rr] = its linear offset from the group's row; tedge[rr] = for
-    // m = 1 the axes whose offset is -1 (bits 0-3) and +1 (bits 8-11), for
+    // tab.delta(rr) = its linear offset from the group's row; tab.edge(rr) =
+    // for m = 1 the axes whose offset is -1 (bits 0-3) and +1 (bits 8-11), for
     // larger m the offsets + m (3 bits per axis); bit 31: l is beyond the rows
     int tab_e = -1;
-    int tdelta[kNbrRounds];
-    uint32_t tedge[kNbrRounds];
+    NbrTable<table_in_smem<D, STAGE>()> tab(w, lane);
 
     for (;;) {
         int c = 0;
@@ -296,8 +336,8 @@ __global__ void __launch_bounds__(kQueryWarps * 32, QCfg<D, STAGE>::MINB) k_grid
                     if (d < m) lowm |= 1u << (ax - 1);
                     if (d > m) highm |= 1u << (ax - 1);
                 }
-                tdelta[rr] = dl;
-                tedge[rr] = (m == 1 ? (lowm | (highm << 8)) : dg) | (l >= nrows ? (1u << 31) : 0u);
+                tab.delta(rr) = dl;
+                tab.edge(rr) = (m == 1 ? (lowm | (highm << 8)) : dg) | (l >= nrows ? (1u << 31) : 0u);
             }
         }
 
@@ -330,19 +370,19 @@ __global__ void __launch_bounds__(kQueryWarps * 32, QCfg<D, STAGE>::MINB) k_grid
                 if (rr * 32 < nrows) {
                     bool ok;
                     if (m == 1) {
-                        ok = (tedge[rr] & gedge) == 0;   // in range on every axis, row exists
+                        ok = (tab.edge(rr) & gedge) == 0;   // in range on every axis, row exists
                     } else {
-                        ok = !(tedge[rr] >> 31);
+                        ok = !(tab.edge(rr) >> 31);
 #pragma unroll
                         for (int ax = 1; ax < kMaxAxes; ++ax) {
                             if (ax < naxes) {
-                                const int v = gc[ax] + (int)((tedge[rr] >> (3 * (ax - 1))) & 7u) - m;
+                                const int v = gc[ax] + (int)((tab.edge(rr) >> (3 * (ax - 1))) & 7u) - m;
                                 ok = ok && (unsigned)v < (unsigned)dims[ax];
                             }
                         }
                     }
                     if (ok) {
-                        const int64_t base = cell_off + (int64_t)(grow + tdelta[rr]) * dims0;
+                        const int64_t base = cell_off + (int64_t)(grow + tab.delta(rr)) * dims0;
                         nlo[rr] = __ldg(a.cstart + base + x0);
                         nhi[rr] = __ldg(a.cstart + base + x1 + 1);
                     }
