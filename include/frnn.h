@@ -287,8 +287,10 @@ const char* frnn_last_error(const frnn_ctx* ctx);
  * budget makes five-axis cells too coarse; scanned by chunks of 16 queries,
  * candidates on lanes, either candidate staging), four coordinates with
  * m = 1 and three with m = 2 (scanned by 16-query row tasks, at the default
- * and a later warp vote); fewer axes when D is smaller; on each grid, the
- * tensor-core pre-filter (D >= 8).
+ * and a later warp vote); fewer axes when D is smaller; for D <= 4 the
+ * automatic choice with m = 2 as well, and for D <= 3 with m = 3 (where
+ * the chunk scan's 128-row neighbour table holds the (2m + 1)^(axes - 1)
+ * rows); on each grid, the tensor-core pre-filter (D >= 8).
  * Each candidate runs whole steps, build then query (first run untimed,
  * best of three timed with CUDA events on the context's stream, the L2
  * cache flushed before each run), and the fastest is cached for the event

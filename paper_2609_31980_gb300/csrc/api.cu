@@ -1274,7 +1274,10 @@ frnn_status frnn_autotune(frnn_ctx* ctx, const float* refs, int64_t N, int D, fl
     // grid configurations: the automatic axis choice (five axes, or four
     // when the cell budget makes five-axis cells too coarse; chunk kernel),
     // four axes with cells of r and three with cells of r/2 (row-task
-    // kernel); fewer for smaller D
+    // kernel); fewer for smaller D.  Cells of r/2 and r/3 on the automatic
+    // choice too, where its (2m + 1)^(axes - 1) neighbour rows stay within
+    // the chunk kernel's table (m = 2 up to D = 4, m = 3 up to D = 3):
+    // beyond that the grid lowers m and the configuration repeats another
     struct GridCfg { int naxes, m; };
     std::vector<GridCfg> gcfg;
     auto add_cfg = [&](int na, int m) {
@@ -1286,6 +1289,11 @@ frnn_status frnn_autotune(frnn_ctx* ctx, const float* refs, int64_t N, int D, fl
     add_cfg(0, 1);
     add_cfg(4, 1);
     add_cfg(3, 2);
+    for (int m = 2; m <= 3; ++m) {
+        int rows = 1;
+        for (int a = 1; a < std::min(D, kMaxAxes); ++a) rows *= 2 * m + 1;
+        if (rows <= kMaxNbrRows) add_cfg(0, m);
+    }
     for (size_t gi = 0; gi < gcfg.size() && s == FRNN_OK; ++gi) {
         const int m = gcfg[gi].m;
         ctx->cell_mult = m;

@@ -617,6 +617,45 @@ def test_autotune_and_mixed_path_batches(ctx):
         ctx.set_option(frnn.FRNN_OPT_AUTOTUNE, 1)
 
 
+@pytest.mark.parametrize("D,m,r", [(2, 3, 0.03), (3, 2, 0.08), (3, 3, 0.08), (4, 2, 0.15)])
+def test_fine_cells_on_automatic_axes(ctx, D, m, r):
+    """Cells of r/2 and r/3 on the automatic axis choice at low D: the chunk
+    scan's table holds the (2m + 1)^(axes - 1) neighbour rows (up to 125),
+    so the grid keeps m, and the rows equal the oracle's."""
+    import torch
+    from paper_2609_31980_gb300 import frnn
+    pts = synth.uniform(6000, D, seed=990 + 10 * D + m)
+    ctx.set_option(frnn.FRNN_OPT_CELL_MULT, m)
+    try:
+        g = ctx.build_grid(torch.from_numpy(pts).cuda(), r)
+        p = g.params()
+        assert p["kernel"] == "chunks" and p["cell_mult"] == m, p
+        g.close()
+        _assert_rows_equal(_gpu_self(ctx, pts, r, 32), oracle.self_query(pts, r, 32))
+    finally:
+        ctx.set_option(frnn.FRNN_OPT_CELL_MULT, 0)
+
+
+def test_autotune_low_dimension_tries_finer_cells(ctx):
+    """At D = 3 the tuner also times cells of r/2 and r/3 on the automatic
+    axes; whatever it picks, tuned single and batched queries stay exact."""
+    import torch
+    from paper_2609_31980_gb300 import frnn
+    pts = synth.uniform(20000, 3, seed=995)
+    try:
+        a = ctx.autotune(torch.from_numpy(pts).cuda(), 0.05, 48, path="grid")
+        assert a["path"] == "grid" and a["cell_mult"] in (1, 2, 3) and a["ms"] > 0, a
+        want = oracle.self_query(pts, 0.05, 48)
+        _assert_rows_equal(_gpu_self(ctx, pts, 0.05, 48, path="auto"), want)
+        outs = ctx.query_batched([torch.from_numpy(pts).cuda()], 0.05, 48, path="auto")
+        ctx.sync()
+        c, i, d = outs[0]
+        _assert_rows_equal((c.cpu().numpy(), i.cpu().numpy(), d.cpu().numpy()), want)
+    finally:
+        ctx.set_option(frnn.FRNN_OPT_AUTOTUNE, 0)
+        ctx.set_option(frnn.FRNN_OPT_AUTOTUNE, 1)
+
+
 # ------------------------------------------------------------ serving loop
 
 def test_serving_results_equal_alone_and_overlap(ctx):
