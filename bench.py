@@ -171,6 +171,38 @@ def issue_roofline(warp_instructions, kernel_ms: float, sms: int, sm_mhz: float)
             "time of this run"}
 
 
+def link_bandwidth(dev, stream, nbytes: int = 64 << 20, reps: int = 5) -> dict:
+    """Page-locked host <-> device copy bandwidth of this GPU's host link
+    (GB/s each way; best of reps after one untimed copy, CUDA events on the
+    copy's stream).  Copies from the SMs (loads and stores to page-locked
+    memory) reach the same rates as the copy engines on this link."""
+    import torch
+    h = torch.empty(nbytes, dtype=torch.uint8).pin_memory()
+    d = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+    out = {"bytes": nbytes}
+    for name, dst, src in (("h2d_gbs", d, h), ("d2h_gbs", h, d)):
+        best = float("inf")
+        for k in range(reps + 1):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            with torch.cuda.stream(stream):
+                e0.record(stream)
+                dst.copy_(src, non_blocking=True)
+                e1.record(stream)
+            e1.synchronize()
+            if k:
+                best = min(best, e0.elapsed_time(e1))
+        out[name] = nbytes / (best / 1e3) / 1e9
+    return out
+
+
+def link_roofline(link: dict, h2d_bytes: int, d2h_bytes: int, step_ms: float) -> dict:
+    """The part of an end-to-end step the host transfers alone take at the
+    measured link rates (a lower bound on the step were nothing else in it)."""
+    t = (h2d_bytes / (link["h2d_gbs"] * 1e9) + d2h_bytes / (link["d2h_gbs"] * 1e9)) * 1e3
+    return {"h2d_gbs": link["h2d_gbs"], "d2h_gbs": link["d2h_gbs"], "transfer_ms": t,
+            "frac": t / step_ms if step_ms > 0 else None}
+
+
 def algorithmic_query_bytes(N: int, D: int, K: int) -> int:
     """Bytes the query step must move at least once: the cell-sorted padded
     rows read as queries and once as candidates, the slot->index map, and the
@@ -424,6 +456,7 @@ def run_ours(args):
         off_np, ci_np, _ = ctx.self_query_host_csr(h_pts.numpy(), r, K, path, c_out)
     e2e_c_s = (time.perf_counter() - t0) / args.steps
     n_edges = int(off_np[-1])
+    link = link_bandwidth(dev, stream)
     e2e_s = max_over_ranks(e2e_s, dev)
     e2e_c_s = max_over_ranks(e2e_c_s, dev)
     if ws > 1:
@@ -481,12 +514,14 @@ def run_ours(args):
                 "h2d_bytes_per_step": N * D * 4,
                 "d2h_bytes_per_step": (N + 1) * 8 + 2 * n_edges * 4,
                 "ms_per_step": e2e_c_s * 1e3, "output": "compact rows (frnn_self_query_host_csr)",
-                "matches_device_path": ok_c},
+                "matches_device_path": ok_c,
+                "link": link_roofline(link, N * D * 4, (N + 1) * 8 + 2 * n_edges * 4, e2e_c_s * 1e3)},
         "e2e_dense": {"value": N * ws / e2e_s, "unit": "queries/s",
                       "h2d_bytes_per_step": N * D * 4,
                       "d2h_bytes_per_step": N * 4 + 2 * N * K * 4,
                       "ms_per_step": e2e_s * 1e3, "output": "dense rows (frnn_self_query_host)",
-                      "matches_device_path": bool(ok_e2e)},
+                      "matches_device_path": bool(ok_e2e),
+                      "link": link_roofline(link, N * D * 4, N * 4 + 2 * N * K * 4, e2e_s * 1e3)},
         "gpu_launches": launches_per_step(N, D, "tc" if kern_is_tc else "grid",
                                           ctx.get_option(frnn.FRNN_OPT_GRID_NAXES)) * args.steps,
         "wall_s": wall,

@@ -38,6 +38,13 @@ def test_issue_roofline_arithmetic():
     assert bench.issue_roofline(1e6, 0.0, 152, 2070.0) is None
 
 
+def test_link_roofline_arithmetic():
+    # 200 MB in at 200 GB/s (1 ms) and 100 MB out at 100 GB/s (1 ms) in a 4 ms step
+    r = bench.link_roofline({"h2d_gbs": 200.0, "d2h_gbs": 100.0}, 200_000_000, 100_000_000, 4.0)
+    assert r["transfer_ms"] == pytest.approx(2.0) and r["frac"] == pytest.approx(0.5)
+    assert bench.link_roofline({"h2d_gbs": 1.0, "d2h_gbs": 1.0}, 0, 0, 0.0)["frac"] is None
+
+
 def test_profile_summaries_parse():
     # a summary is used only while it matches the kernel's sources; when it
     # does, both counters are present and plausible
