@@ -11,11 +11,13 @@
 // whose profile showed dependent-load latency and divergence, Sec. 4.2):
 //   * a persistent grid; each warp takes chunks of kChunkQ consecutive
 //     cell-sorted query slots from an atomic counter (no task list: the chunk
-//     number alone locates the slots).  Queries of a chunk that share a cell
+//     number alone locates the slots).  Runs of queries of a chunk whose
+//     cells are equal or follow each other along the fastest axis of one row
 //     form a group; a group's candidates are the points of its neighbour
 //     rows (every gridded coordinate but the fastest within +-m), each
-//     restricted to the +-m cells around the group's cell along the fastest
-//     axis: one contiguous slot range per neighbour row;
+//     restricted to the cells from m before the group's first cell to m
+//     after its last along the fastest axis: one contiguous slot range per
+//     neighbour row, a superset of each query's own +-m neighbourhood;
 //   * the warp enumerates the neighbour rows of its groups 32 at a time
 //     (lanes), keeps the non-empty ranges in a compact list and concatenates
 //     them into one candidate stream, group after group;
@@ -274,21 +276,8 @@ __global__ void __launch_bounds__(kQueryWarps * 32, QCfg<D, STAGE>::MINB) k_grid
             for (int i = lane; i < nqc * (DP / 4); i += 32) dst[i] = src[i];
             if (lane < kChunkQ) w.cnt[lane] = 0;
         }
-        // groups: runs of queries with equal cells (slots are cell-sorted)
         const int qc = act ? a.qcell[qs] : -1;
         const int prev = __shfl_up_sync(kFull, qc, 1);
-        const bool head = act && (lane == 0 || prev != qc);
-        const unsigned gmask = __ballot_sync(kFull, head);
-        const int ng = __popc(gmask);
-        // lane g < ng: first query of group g; lanes >= ng: nqc
-        int gq = nqc;
-        {
-            unsigned mm = gmask;
-            for (int g = 0; g < ng; ++g) {
-                if (lane == g) gq = __ffs(mm) - 1;
-                mm &= mm - 1u;
-            }
-        }
         // the grid's parameters in registers (the loops below store to shared
         // memory through generic pointers, which would otherwise force the
         // header to be read again)
@@ -315,6 +304,21 @@ __global__ void __launch_bounds__(kQueryWarps * 32, QCfg<D, STAGE>::MINB) k_grid
         }
         int nrows = 1;
         for (int ax = 1; ax < naxes; ++ax) nrows *= 2 * m + 1;
+        // groups: runs of queries (slots are cell-sorted) whose cells are equal
+        // or follow each other along the fastest axis of one row; a group scans
+        // the union of its cells' neighbourhoods, one range per neighbour row
+        const bool head = act && (lane == 0 || !(qc == prev || (qc == prev + 1 && cc[0] != 0)));
+        const unsigned gmask = __ballot_sync(kFull, head);
+        const int ng = __popc(gmask);
+        // lane g < ng: first query of group g; lanes >= ng: nqc
+        int gq = nqc;
+        {
+            unsigned mm = gmask;
+            for (int g = 0; g < ng; ++g) {
+                if (lane == g) gq = __ffs(mm) - 1;
+                mm &= mm - 1u;
+            }
+        }
         int rstride[kMaxAxes];
         rstride[0] = 0;
         rstride[1] = 1;
@@ -347,10 +351,12 @@ __global__ void __launch_bounds__(kQueryWarps * 32, QCfg<D, STAGE>::MINB) k_grid
         int nlo[kNbrRounds], nhi[kNbrRounds];
         auto fetch = [&](int g) {
             const int hl = __shfl_sync(kFull, gq, g);
+            const int hn = __shfl_sync(kFull, gq, g + 1);   // first query of the next group, or nqc
             int gc[kMaxAxes];
 #pragma unroll
             for (int ax = 0; ax < kMaxAxes; ++ax) gc[ax] = __shfl_sync(kFull, cc[ax], hl);
-            const int x0 = max(gc[0] - m, 0), x1 = min(gc[0] + m, dims0 - 1);
+            const int xl = __shfl_sync(kFull, cc[0], hn - 1);   // the group's last cell on the row
+            const int x0 = max(gc[0] - m, 0), x1 = min(xl + m, dims0 - 1);
             // the group's row and, for m = 1, the axes on which it touches the
             // grid's low (bits 0-3) or high (bits 8-11) edge
             int grow = 0;

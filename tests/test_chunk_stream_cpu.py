@@ -1,13 +1,15 @@
 """The grid query kernel's candidate stream, checked on the CPU.
 
 The kernel (query.cu, k_grid_query) takes chunks of 16 cell-sorted query
-slots; queries sharing a cell form a group.  For each group it enumerates the
+slots; runs of queries whose cells are equal or follow each other along the
+fastest axis of one row form a group.  For each group it enumerates the
 (2m+1)^(naxes-1) neighbour rows 32 at a time (lane l of round rr handles row
 32 rr + l, whose per-axis offsets are the base-(2m+1) digits of that number:
 a per-event table holds each row's linear offset and, for m = 1, bit masks of
 the axes whose offset is -1 or +1, tested against the group's grid-edge
-bits), looks up each row's slot range over the cells x-m .. x+m along the
-fastest axis, and appends the non-empty ranges with their counts to a
+bits), looks up each row's slot range over the cells x_first-m .. x_last+m
+along the fastest axis (x_first, x_last: the group's first and last cell on
+the row), and appends the non-empty ranges with their counts to a
 compact list (at most 128 entries; a group that does not fit is rolled back
 and opens the next batch); one exclusive scan per batch turns the counts into
 stream positions.  The stream is presented either in tiles of 64 candidates
@@ -21,8 +23,10 @@ the groups' stream starts.
 This file re-enacts those steps lane by lane on random and adversarial grids
 and checks: every shared-memory index stays inside its array, every copy's
 destination lies inside its ring buffer and its source inside the point set,
-and each query is paired with exactly the points of the cells within +-m of
-its own cell on every gridded axis (each once).
+and each query is paired with exactly the points of its group's box (each
+once): the cells within +-m of its own cell on every gridded axis but the
+fastest, and within x_first-m .. x_last+m on that one, a box that holds the
+query's own +-m neighbourhood.
 """
 import numpy as np
 import pytest
@@ -106,15 +110,18 @@ def run_kernel(dims, scell, cstart, naxes, m):
         s0 = c * KCHUNKQ
         nqc = min(KCHUNKQ, n - s0)
         qc = [int(scell[s0 + l]) if l < nqc else -1 for l in range(32)]
-        head = [l < nqc and (l == 0 or qc[l - 1] != qc[l]) for l in range(32)]
+        cc = [decode(qc[l] if l < nqc else 0, d5, naxes) for l in range(32)]
+        head = [l < nqc and (l == 0 or not (qc[l - 1] == qc[l] or (qc[l] == qc[l - 1] + 1 and cc[l][0] != 0)))
+                for l in range(32)]
         heads = [l for l in range(32) if head[l]]
         ng = len(heads)
         gq = [heads[l] if l < ng else nqc for l in range(32)]
-        cc = [decode(qc[l] if l < nqc else 0, d5, naxes) for l in range(32)]
 
         def fetch(g):
             gc = cc[gq[g]]
-            x0, x1 = max(gc[0] - m, 0), min(gc[0] + m, d5[0] - 1)
+            xl = cc[gq[g + 1] - 1][0]
+            assert all(cc[q][1:] == gc[1:] for q in range(gq[g], gq[g + 1])), "a group lies on one row"
+            x0, x1 = max(gc[0] - m, 0), min(xl + m, d5[0] - 1)
             grow, gedge = 0, 1 << 31
             for ax in range(1, naxes):
                 grow += gc[ax] * rstride[ax]
@@ -252,27 +259,46 @@ def run_kernel(dims, scell, cstart, naxes, m):
 
 
 def neighbourhoods(dims, scell, naxes, m):
-    """Brute force: for each slot, the slots whose cells are within +-m."""
+    """Brute force: for each slot, the slots whose cells are within +-m (its
+    own neighbourhood) and the slots of its group's box: chunks of 16 slots,
+    a group a maximal run of slots whose cells are equal or next to each
+    other along the fastest axis of one row, its box the cells within +-m on
+    the other axes and from its first cell's x - m to its last cell's x + m."""
     n = len(scell)
     coords = np.array([decode(int(c), [int(x) for x in dims] + [1] * (5 - naxes), naxes)[:naxes]
                        for c in scell]).reshape(n, naxes)
-    out = []
+    own, box = [], [None] * n
     for i in range(n):
         near = np.all(np.abs(coords - coords[i]) <= m, axis=1)
-        out.append(set(np.flatnonzero(near).tolist()))
-    return out
+        own.append(set(np.flatnonzero(near).tolist()))
+    for s0 in range(0, n, KCHUNKQ):
+        runs = []
+        for i in range(s0, min(s0 + KCHUNKQ, n)):
+            if runs and np.array_equal(coords[i, 1:], coords[runs[-1][-1], 1:]) and \
+                    0 <= coords[i, 0] - coords[runs[-1][-1], 0] <= 1:
+                runs[-1].append(i)
+            else:
+                runs.append([i])
+        for run in runs:
+            xa, xb = coords[run[0], 0], coords[run[-1], 0]
+            inb = np.all(np.abs(coords[:, 1:] - coords[run[0], 1:]) <= m, axis=1) & \
+                (coords[:, 0] >= xa - m) & (coords[:, 0] <= xb + m)
+            for i in run:
+                box[i] = set(np.flatnonzero(inb).tolist())
+    return own, box
 
 
 def check(pts, naxes, m, h):
     dims, scell, cstart = make_grid(pts, naxes, h)
     pairs = run_kernel(dims, scell, cstart, naxes, m)
-    want = neighbourhoods(dims, scell, naxes, m)
+    own, box = neighbourhoods(dims, scell, naxes, m)
     got = [[] for _ in range(len(pts))]
     for q, s in pairs:
         got[q].append(s)
     for i in range(len(pts)):
         assert len(got[i]) == len(set(got[i])), f"slot {i}: a candidate presented twice"
-        assert set(got[i]) == want[i], f"slot {i}: stream differs from the neighbourhood"
+        assert set(got[i]) == box[i], f"slot {i}: stream differs from the group's box"
+        assert own[i] <= set(got[i]), f"slot {i}: a neighbour cell missing"
 
 
 @pytest.mark.parametrize("naxes,m", [(1, 1), (2, 1), (3, 1), (3, 2), (3, 3), (4, 1), (4, 2), (5, 1)])
