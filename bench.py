@@ -335,7 +335,7 @@ def time_config(frnn, pts_np, r, K, path, dev, steps=20, warmup=3, opts=None, tc
 def run_design_points(args, dev):
     """Other configurations of the same path, each timed on its own:
     the 300k x 8 event on grids over three coordinates (cell multiple 1 and 2;
-    the library's default grids four), the uniform 4096 x 3 set, and the
+    the library's default grids five up to D = 8), the uniform 4096 x 3 set, and the
     500k x 12 event on the grid scan against the tensor-core pre-filter
     (false-candidate rate of the pre-filter; tensor-pipe activity from the
     committed ncu summary of that kernel)."""
@@ -387,7 +387,7 @@ def run_ours(args):
         ctx.set_option(frnn.FRNN_OPT_GRID_NAXES, args.grid_naxes)
     elif path == "tc":
         # the tensor-core path's 128-query tasks want the longer rows of a
-        # three-axis grid (the library's four-axis default suits the scan)
+        # three-axis grid (the library's five- and four-axis defaults suit the scans)
         ctx.set_option(frnn.FRNN_OPT_GRID_NAXES, 3)
     with torch.cuda.stream(stream):
         pts = torch.from_numpy(pts_np).to(dev)
@@ -432,7 +432,7 @@ def run_ours(args):
     torch.cuda.synchronize()
     wall = time.perf_counter() - wall0
     clocks = sampler.stop()
-    kern_is_tc = path == "tc"   # auto: the grid scan (four gridded axes by default)
+    kern_is_tc = path == "tc"   # auto: a grid scan (five gridded axes up to D = 8, four above)
     step_ms = [e[0].elapsed_time(e[2]) for e in evs]
     # attribution pass: the same K steps with events at the build/query
     # boundary and around the main query kernel (CUDA events on the launching
