@@ -124,7 +124,6 @@ def profile_summary(path: str, wl: str):
     key = (path, wl)
     known = {("grid", "event300k"): ("grid_query_event300k_x8.md", ["query.cu", "frnn_internal.cuh"]),
              ("rows", "event500k"): ("row_query_event500k_x12.md", ["query_rows.cu", "frnn_internal.cuh"]),
-             ("rows", "event300k"): ("row_query_event300k_x8.md", ["query_rows.cu", "frnn_internal.cuh"]),
              ("tc", "event500k"): ("tc_query_event500k_x12.md", ["tc.cu", "frnn_internal.cuh"])}
     if key not in known:
         return None
